@@ -1,0 +1,216 @@
+"""Oracle solvers: mirror-image convolution, leakage/conductivity fixed point,
+transient superposition.
+
+Test infrastructure only (see the package docstring). FP64 throughout.
+
+Model of the self-consistent temperature (this project's reading of
+Eqs. 4-8 and 12-14, generalised from a unit impulse to a power map):
+
+* power P = P_dyn + P_leak0 (1 + beta theta)       (Eq. 12, Eq. 5)
+* u = L[P], L = convolution with the imaged kernel (Eq. 2, Sec. III-G)
+* the Green's function is scaled at the field point by s (1 + alpha theta)
+  (Eqs. 7-8; s carries the conductivity variation), so theta = s u (1 + alpha
+  theta), i.e. theta = phi(u) = s u / (1 - alpha s u)
+* the fixed point u = L[P_dyn + P_leak0 (1 + beta phi(u))] is what the
+  paper's validation loop reaches by iterating power -> temperature ->
+  leakage/conductivity until convergence (Sec. V-B).
+"""
+from __future__ import annotations
+
+import numpy as np
+
+from . import physics
+
+
+# --------------------------------------------------------------------------- #
+# Mirror-image convolution                                                      #
+# --------------------------------------------------------------------------- #
+
+def mirror_operator(kper: np.ndarray) -> np.ndarray:
+    """Dense matrix of the mirror-image convolution on an n x n grid (n <= 64).
+
+    The power map is extended to twice its size with even mirror images at the
+    die edges (Sec. III-G) and convolved circularly with the 2n-periodic kernel
+    K_per; restricted to the die this is, for target i and source j,
+      L_ij = sum over (ex, ey) in {i-j, i+j+1} of K_per(ey mod 2n, ex mod 2n)
+    (four terms per pair). Row/column index = y*n + x.
+    """
+    n2 = kper.shape[0]
+    n = n2 // 2
+    iy, ix = np.meshgrid(np.arange(n), np.arange(n), indexing="ij")
+    iy = iy.ravel()
+    ix = ix.ravel()
+    dy_m = (iy[:, None] - iy[None, :]) % n2
+    dy_p = (iy[:, None] + iy[None, :] + 1) % n2
+    dx_m = (ix[:, None] - ix[None, :]) % n2
+    dx_p = (ix[:, None] + ix[None, :] + 1) % n2
+    return (kper[dy_m, dx_m] + kper[dy_m, dx_p] + kper[dy_p, dx_m] + kper[dy_p, dx_p])
+
+
+def direct_convolve(L: np.ndarray, q: np.ndarray) -> np.ndarray:
+    """Apply the dense mirror operator to maps q[..., n, n]."""
+    n = q.shape[-1]
+    flat = q.reshape(-1, n * n)
+    return (flat @ L.T).reshape(q.shape)
+
+
+def dct_matrix(n: int) -> np.ndarray:
+    """C[p, j] = cos(pi p (2j + 1) / (2n)) (unnormalised DCT-II)."""
+    p = np.arange(n)[:, None]
+    j = np.arange(n)[None, :]
+    return np.cos(np.pi * p * (2 * j + 1) / (2 * n))
+
+
+def idct_matrix(n: int) -> np.ndarray:
+    """Exact inverse of dct_matrix: x_j = (1/n)[X_0 + 2 sum_{p>0} X_p C[p, j]]."""
+    w = np.full(n, 2.0)
+    w[0] = 1.0
+    return (dct_matrix(n) * w[:, None]).T / n
+
+
+def spectral_convolve(Kt: np.ndarray, q: np.ndarray) -> np.ndarray:
+    """Same operator in the cosine basis: L[q] = IDCT2(DCT2(q) * K~). The even
+    extension of the map is what a DCT-II encodes, so the circular convolution
+    of the mirrored map with K_per is diagonal in it (symmetric convolution
+    theorem); dense cosine matrices, no fast transform."""
+    n = q.shape[-1]
+    C = dct_matrix(n)
+    Ci = idct_matrix(n)
+    X = C @ q @ C.T
+    return Ci @ (X * Kt) @ Ci.T
+
+
+# --------------------------------------------------------------------------- #
+# Fixed point                                                                   #
+# --------------------------------------------------------------------------- #
+
+class SolveError(RuntimeError):
+    pass
+
+
+def phi(u, s, alpha):
+    """theta = s u / (1 - alpha s u) (field-point factor, Eq. 8)."""
+    return s * u / (1.0 - alpha * s * u)
+
+
+def picard(apply_L, p_dyn, p_leak0, s, beta, alpha, tol=1e-8, max_iter=400,
+           guard=0.05):
+    """Plain Picard iteration on the unsplit fixed point from u = 0:
+    u_{n+1} = L[P_dyn + P_leak0 (1 + beta phi(u_n))], stop when
+    max |phi(u_{n+1}) - phi(u_n)| <= tol (the update-norm reading of the
+    paper's 'iterate until the temperature values converge', Sec. V-B).
+    Raises if 1 - alpha s u <= guard (conductivity runaway) or max_iter is hit.
+    Returns (theta, u, iterations)."""
+    u = np.zeros_like(p_dyn)
+    theta = np.zeros_like(p_dyn)
+    for it in range(1, max_iter + 1):
+        u = apply_L(p_dyn + p_leak0 * (1.0 + beta * theta))
+        den = 1.0 - alpha * s * u
+        if np.min(den) <= guard:
+            raise SolveError("conductivity runaway: 1 - alpha s u <= %g" % guard)
+        new = s * u / den
+        if not np.all(np.isfinite(new)):
+            raise SolveError("non-finite temperature")
+        d = np.max(np.abs(new - theta))
+        theta = new
+        if d <= tol:
+            return theta, u, it
+    raise SolveError("no convergence in %d iterations" % max_iter)
+
+
+def picard_split(Kt, p_dyn, p_leak0, s, beta, alpha, tol=1e-8, max_iter=400):
+    """The mean/variation split of Sec. III-C used as a preconditioner.
+
+    mu = mean(P_leak0), P_leak0 = mu + P_var. The shift-invariant part has the
+    modified kernel K_det = K~ / (1 - beta mu K~) (Eq. 20 with alpha = 0); the
+    remaining shift-variant source is iterated:
+      u_det = L_det[P_dyn + mu],
+      c_{n+1} = L_det[P_var + beta (P_leak0 phi(u_det + c_n) - mu (u_det + c_n))].
+    Since L_det = (I - beta mu L)^-1 L this has the same fixed point as
+    `picard`. Spectral (dense cosine) operators. Returns (theta, u, iters)."""
+    mu = float(np.mean(p_leak0))
+    Kd = Kt / (1.0 - beta * mu * Kt)
+    udet = spectral_convolve(Kd, p_dyn + mu)
+    c = np.zeros_like(udet)
+    theta = np.zeros_like(udet)
+    for it in range(1, max_iter + 1):
+        u = udet + c
+        new = phi(u, s, alpha)
+        d = np.max(np.abs(new - theta))
+        theta = new
+        if d <= tol and it > 1:
+            return theta, u, it
+        c = spectral_convolve(Kd, (p_leak0 - mu) + beta * (p_leak0 * theta - mu * u))
+    raise SolveError("no convergence")
+
+
+def shift_invariant(Kt, p_dyn, p_leak0, beta):
+    """Closed form for a uniform leakage map (no variation, alpha = 0):
+    u = IDCT(DCT(P_dyn + mu) K~ / (1 - beta mu K~)) (Eq. 20 with alpha = 0)."""
+    mu = float(np.mean(p_leak0))
+    return spectral_convolve(Kt / (1.0 - beta * mu * Kt), p_dyn + mu)
+
+
+# --------------------------------------------------------------------------- #
+# Transient (Eqs. 23-31)                                                        #
+# --------------------------------------------------------------------------- #
+
+def step_spectrum(n, die_m, t, kappa, h, heat_cap, t_s, rel=1e-18):
+    """Spectrum of the step-response Green's function at time t_s:
+    single pole per spatial frequency with tau(k) = C g^(k) (Eq. 23 with the
+    alpha term of tau dropped; C = areal heat capacity), so the response to a
+    unit power step is g^(k) (1 - exp(-t / (C g^(k)))) (Eq. 29).
+
+    Same real/spectral split as physics.spectrum: the top-layer part is static
+    (the exp factor of the aliases with large k vanishes), the spectral part
+    is R(k) - g^(k) exp(-t/(C g^(k))), which decays exponentially in k for t > 0.
+    """
+    import math
+    t = tuple(float(x) for x in t)
+    kappa = tuple(float(x) for x in kappa)
+    cell = die_m / n
+    a = physics.disc_radius(cell)
+    R = int(math.ceil(physics.real_space_cutoff(t[0], rel) / cell))
+    m = np.arange(-R, R + 1)
+    rad2 = m[:, None] ** 2 + m[None, :] ** 2
+    uniq, inv = np.unique(rad2, return_inverse=True)
+    g1 = physics.g_top_radial(cell * np.sqrt(uniq.astype(np.float64)), t[0], kappa[0], a)
+    G = g1[inv].reshape(rad2.shape)
+    p = np.arange(n)
+    C = np.cos(np.pi * np.outer(p, m) / n)
+    K1 = C @ G @ C.T
+    rate = t_s * kappa[0] / heat_cap                    # large-k decay length of exp term
+    dec = min(2 * t[0], rate)
+    S = int(math.ceil((cell * math.log(1.0 / rel) / (math.pi * dec) + 1) / 2)) + 1
+    KR = np.zeros((n, n))
+    for s_ in range(-S, S + 1):
+        ky = np.pi * (p + 2 * n * s_) / die_m
+        for t_ in range(-S, S + 1):
+            kx = np.pi * (p + 2 * n * t_) / die_m
+            kk = np.sqrt(ky[:, None] ** 2 + kx[None, :] ** 2)
+            g = physics.ghat(kk, t, kappa, h)
+            KR += (physics.ghat_rest(kk, t, kappa, h)
+                   - g * np.exp(-t_s / (heat_cap * g))) * physics._disc_factor(kk * a)
+    return K1 + KR / cell ** 2
+
+
+def duhamel(step_spectra, p_dyn_trace, p_leak0, s, beta, alpha):
+    """Untruncated superposition of power differences (Eq. 30):
+      u_n = sum_{j=1..n} S_j * (P_{n-j+1} - P_{n-j}),  P_0 = 0,
+    with leakage lagged one step, P_m = P_dyn,m + P_leak0 (1 + beta theta_{m-1}),
+    theta_0 = 0, and theta_n = phi(u_n). step_spectra[j-1] is S_j in the
+    cosine basis. Returns theta[n_steps, n, n]."""
+    n_steps = p_dyn_trace.shape[0]
+    theta = np.zeros_like(p_dyn_trace)
+    P = []
+    th_prev = np.zeros_like(p_leak0)
+    for k in range(n_steps):
+        P.append(p_dyn_trace[k] + p_leak0 * (1.0 + beta * th_prev))
+        u = np.zeros_like(p_leak0)
+        for j in range(1, k + 2):
+            m = k + 1 - j                        # P index (0-based) of P_{n-j+1}
+            dP = P[m] - (P[m - 1] if m >= 1 else 0.0)
+            u = u + spectral_convolve(step_spectra[j - 1], dP)
+        th_prev = phi(u, s, alpha)
+        theta[k] = th_prev
+    return theta
