@@ -1,0 +1,356 @@
+"""Benchmark: batched steady-state thermal maps per second at 256 x 256.
+
+One step = one run of the whole steady hot path (mean leakage reduction,
+shift-invariant modified kernel, mirror-image cosine-basis convolution,
+fused leakage/conductivity update, fixed point iterated to 1e-4 K per map)
+over a batch of maps already resident in device memory. Inputs (3 GiB for
+4096 maps) are larger than the 129 MB L2, so no flush is needed between steps.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Under torchrun every rank solves its own shard of maps (weak scaling, no data
+exchange); rank 0 prints one JSON line.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = ("thermal maps/s at 256² (max ΔT ≤0.05 K vs FP64), "
+          "chosen vs plain; % roofline")
+UNIT = "maps/s"
+ALG_BYTES_PER_PIXEL = 16      # read P_dyn, P_leak0, s; write theta (FP32)
+
+
+def _args():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--batch", type=int, default=4096)
+    ap.add_argument("--n", type=int, default=256)
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    return ap.parse_args()
+
+
+def _dist():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def _peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        d = json.load(open(p))
+        return float(d["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+def _kernel_source_hash() -> str:
+    h = hashlib.sha256()
+    csrc = os.path.join(ROOT, "paper_2307_12119_gb300", "csrc")
+    for f in sorted(os.listdir(csrc)):
+        h.update(open(os.path.join(csrc, f), "rb").read())
+    return h.hexdigest()[:16]
+
+
+def _traffic_record(kernel: str):
+    """DRAM bytes per launch of `kernel` from a committed ncu summary, or None
+    if the kernel sources changed since it was taken."""
+    p = os.path.join(ROOT, "profiles", "traffic.json")
+    if not os.path.exists(p):
+        return None
+    d = json.load(open(p)).get(kernel)
+    if not d or d.get("source_hash") != _kernel_source_hash():
+        return None
+    return d
+
+
+class Clocks:
+    """Samples SM clocks and throttle reasons with nvidia-smi during a region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.idx = gpu_index
+        self.proc = None
+        self.path = None
+
+    def __enter__(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.idx), "--query-gpu=" + self.FIELDS,
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+        time.sleep(0.3)
+        return self
+
+    def __exit__(self, *a):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        if self.proc is None or not self.path or not os.path.exists(self.path):
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        rows = []
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                rows.append((float(parts[1]), float(parts[2]), parts[5:9]))
+            except ValueError:
+                continue
+        os.unlink(self.path)
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for _, _, r in rows for i, v in enumerate(r)
+                          if v.lower() == "active"})
+        return {"sm_mhz": statistics.median(r[0] for r in rows),
+                "sm_max_mhz": max(r[1] for r in rows), "reasons": reasons,
+                "samples": len(rows)}
+
+
+def cpu_oracle_leg(w, pd, pl, s, gpu_theta, seconds: float):
+    """Times the FP64 oracle (as it stands) on the host cores over the first
+    maps of the same batch, and compares the GPU results of those maps with it.
+    The oracle's Green's-function build is done once, outside the timed
+    region (the GPU side likewise builds its kernel once per geometry)."""
+    import numpy as np
+    from oracle import physics as ph
+    from oracle import solve as so
+    st, phy = w.stack, w.physics
+    Kt = ph.spectrum(w.n, w.die_m, st.thickness_m, st.kappa_W_mK, st.h_conv_W_m2K)
+    f64 = lambda t: t.double().cpu().numpy()
+    done, worst, rel_worst = 0, 0.0, 0.0
+    t0 = time.perf_counter()
+    elapsed = 0.0
+    while done < pd.shape[0] and (done < 2 or elapsed < seconds):
+        a, b, c = f64(pd[done]), f64(pl[done]), f64(s[done])
+        t1 = time.perf_counter()
+        ref, _, _ = so.picard(lambda x: so.spectral_convolve(Kt, x), a, b, c, phy.beta_per_K,
+                              phy.alpha_per_K, tol=1e-8)
+        elapsed += time.perf_counter() - t1
+        if gpu_theta is not None:
+            d = f64(gpu_theta[done]) - ref
+            worst = max(worst, float(np.max(np.abs(d))))
+            rel_worst = max(rel_worst, float(np.linalg.norm(d) / np.linalg.norm(ref)))
+        done += 1
+    cores = len(os.sched_getaffinity(0))
+    return {"value": done / elapsed, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": "%d of the batch's 256x256 maps, FP64 dense-cosine spectral Picard to "
+                      "1e-8 K, %.1f s" % (done, elapsed)}, {
+        "max_abs_K": worst, "rel_l2": rel_worst, "maps_checked": done}
+
+
+def run_reference(a):
+    """The oracle as the reference arm (rank 0 only)."""
+    ws, rank, _ = _dist()
+    if rank != 0:
+        return
+    import torch
+    import synth
+    from oracle import physics as ph
+    from oracle import solve as so
+    n_maps = max(a.steps + a.warmup, 1) * 2
+    w, pd, pl, s = synth.batch_inputs(a.n, a.batch, device="cpu")
+    st, phy = w.stack, w.physics
+    Kt = ph.spectrum(w.n, w.die_m, st.thickness_m, st.kappa_W_mK, st.h_conv_W_m2K)
+    f64 = lambda t: t.double().numpy()
+    per_step = 2
+    idx = 0
+
+    def step():
+        nonlocal idx
+        for _ in range(per_step):
+            i = idx % pd.shape[0]
+            so.picard(lambda x: so.spectral_convolve(Kt, x), f64(pd[i]), f64(pl[i]), f64(s[i]),
+                      phy.beta_per_K, phy.alpha_per_K, tol=1e-8)
+            idx += 1
+
+    for _ in range(a.warmup):
+        step()
+    t0 = time.perf_counter()
+    for _ in range(a.steps):
+        step()
+    dt = time.perf_counter() - t0
+    v = a.steps * per_step / dt
+    cores = len(os.sched_getaffinity(0))
+    print(json.dumps({
+        "impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": ws,
+        "steps": a.steps, "warmup": a.warmup, "ms_per_step": 1e3 * dt / a.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic",
+        "config": {"workload": w.name, "n": w.n, "global_batch": a.batch,
+                   "note": "FP64 CPU oracle; each step solves %d maps of the batch" % per_step},
+        "cpu_baseline": {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle",
+                         "sample": "%d maps per step x %d steps" % (per_step, a.steps)},
+        "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }))
+
+
+def run_ours(a):
+    import torch
+    import torch.distributed as dist
+    ws, rank, local = _dist()
+    if ws > 1:
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    dev = torch.device("cuda", torch.cuda.current_device())
+    import paper_2307_12119_gb300 as vs
+    import synth
+
+    # every rank solves its own shard of the sample space (weak scaling)
+    w, pd, pl, s = synth.batch_inputs(a.n, a.batch, device=dev, seed=synth.SEED + 7919 * rank)
+    st, phy = w.stack, w.physics
+    stack = vs.Stack(st.thickness_m, st.kappa_W_mK, st.h_conv_W_m2K, st.heat_cap_J_m2K)
+    k = vs.Kernel(stack, vs.Grid(w.n, w.die_m))
+    params = vs.SolveParams(phy.beta_per_K, phy.alpha_per_K, 1e-4, 50)
+    theta = torch.empty_like(pd)
+    B = pd.shape[0]
+    plan = vs.Plan([(k, pd[i], pl[i], s[i], theta[i]) for i in range(B)], params)
+    stream = torch.cuda.current_stream()
+    for _ in range(a.warmup):
+        plan.run()
+    torch.cuda.synchronize()
+    infos = plan.info()
+    iters = [i["iterations"] for i in infos]
+    bad = sum(1 for i in infos if i["status"] != vs.VS_OK)
+
+    def barrier():
+        if ws > 1:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with Clocks(local) as clk:
+        barrier()
+        ev0.record(stream)
+        for _ in range(a.steps):
+            plan.run()
+        ev1.record(stream)
+        barrier()
+    clocks = clk.summary()
+    ms = ev0.elapsed_time(ev1) / a.steps
+    t = torch.tensor([ms], device=dev, dtype=torch.float64)
+    if ws > 1:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    ms_max = float(t.item())
+    value = ws * B / (ms_max * 1e-3)
+
+    # plain: the same solver, one map per vs_solve_steady call, no plan reuse
+    plain_maps = 32
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    plain_out = torch.empty_like(pd[0])
+    vs.solve_steady(k, pd[0], pl[0], s[0], params, plain_out)
+    e0.record(stream)
+    for i in range(plain_maps):
+        vs.solve_steady(k, pd[i], pl[i], s[i], params, plain_out)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    plain_value = plain_maps / (e0.elapsed_time(e1) * 1e-3)
+
+    # e2e: pinned host inputs -> device -> solve -> host theta, every step
+    e2e = None
+    if not a.no_e2e:
+        hpd = pd.cpu().pin_memory()
+        hpl = pl.cpu().pin_memory()
+        hs = s.cpu().pin_memory()
+        hth = torch.empty(theta.shape, dtype=theta.dtype, pin_memory=True)
+        e2e_steps = max(1, min(a.steps, 3))
+
+        def e2e_step():
+            pd.copy_(hpd, non_blocking=True)
+            pl.copy_(hpl, non_blocking=True)
+            s.copy_(hs, non_blocking=True)
+            plan.run()
+            hth.copy_(theta, non_blocking=True)
+
+        e2e_step()
+        barrier()
+        t0 = time.perf_counter()
+        for _ in range(e2e_steps):
+            e2e_step()
+        barrier()
+        dt = (time.perf_counter() - t0) / e2e_steps
+        tt = torch.tensor([dt], device=dev, dtype=torch.float64)
+        if ws > 1:
+            dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        e2e = {"value": ws * B / float(tt.item()), "unit": UNIT,
+               "h2d_bytes_per_step": 3 * pd.numel() * 4, "d2h_bytes_per_step": theta.numel() * 4,
+               "how": "vs_plan_run through the Python binding; pinned host inputs copied in and "
+                      "theta copied out every step"}
+
+    if rank == 0:
+        peak, peak_kind = _peaks()
+        alg_bytes = B * w.n * w.n * ALG_BYTES_PER_PIXEL
+        achieved = alg_bytes / (ms * 1e-3) / 1e9
+        tr = _traffic_record("k_solve_steady")
+        cpu, acc = cpu_oracle_leg(w, pd.cpu(), pl.cpu(), s.cpu(), theta.cpu(), a.cpu_seconds)
+        out = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": a.steps,
+            "warmup": a.warmup, "ms_per_step": ms_max, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": "steady %dx%d, 20x20 mm die, batch of %d maps per GPU "
+                                   "(64 floorplans x per-map variation fields)" % (w.n, w.n, B),
+                       "n": w.n, "global_batch": ws * B, "tol_K": 1e-4,
+                       "path": "chosen = persistent batched plan (one cooperative launch, FP32 "
+                               "fast cosine transforms)",
+                       "l2": "inputs %.1f GiB per GPU > L2, no flush" % (3 * pd.numel() * 4 / 2**30),
+                       "parallelism": "replicas x%d" % ws},
+            "plain": {"value": plain_value, "unit": UNIT,
+                      "how": "one map per vs_solve_steady call (plan built per call), %d maps"
+                             % plain_maps},
+            "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                         "frac": achieved / peak,
+                         "traffic": (tr["dram_bytes_per_map"] * B) if tr else None,
+                         "kernel": "k_solve_steady",
+                         "note": "achieved = 16 B/pixel algorithmic bytes x maps / launch time; "
+                                 "peak %s" % peak_kind},
+            "cpu_baseline": cpu,
+            "accuracy_vs_fp64_oracle": acc,
+            "e2e": e2e,
+            "gpu_launches": a.steps * plan.launches,
+            "iterations": {"mean": sum(iters) / len(iters), "max": max(iters),
+                           "not_ok": bad},
+            "clocks": clocks,
+        }
+        print(json.dumps(out))
+    if ws > 1:
+        dist.barrier()
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    args = _args()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)

@@ -1,0 +1,250 @@
+/*
+ * varsim.h -- C ABI of the GB300 (sm_103a) Green's-function thermal solver.
+ *
+ * The library computes the steady and transient temperature rise of a die
+ * whose leakage power and silicon conductivity vary across the die and depend
+ * on temperature, following the Green's-function method of Sultan & Sarangi
+ * ("VarSim", arXiv 2307.12119):
+ *   - T = f_sp * P: temperature is the Green's function convolved with the
+ *     power map (Sec. II-B, Eq. 2);
+ *   - the radially symmetric Green's function is obtained from its Hankel
+ *     transform (Sec. II-F, Eq. 10; Appendix, Theorem I);
+ *   - die edges are handled by mirror images (Sec. III-G);
+ *   - leakage P = P_dyn + P_leak0 (1 + beta dT) (Eqs. 5, 12) and the
+ *     conductivity factor f_sp(T) = f_sp0 (1 + alpha dT) (Eq. 8) are resolved
+ *     by iterating power -> temperature -> leakage/conductivity to a stated
+ *     tolerance (the convergence loop of Sec. V-B), preconditioned by the
+ *     mean/variation split into a shift-invariant and a shift-variant part
+ *     (Sec. III-C, Eqs. 17-22);
+ *   - the transient uses a single-pole response per spatial frequency and
+ *     superposition of power differences (Sec. III-D/E, Eqs. 23-31).
+ *
+ * Conventions for every call:
+ *   - Maps are row-major float32 [n][n] (x fastest), one value per grid cell.
+ *     Power inputs are watts PER CELL; temperatures are kelvin ABOVE AMBIENT.
+ *     Geometry is SI (metres, W/(m K), W/(m^2 K), J/(m^2 K)).
+ *   - Map pointers are caller-owned CUDA device memory, contiguous, 16-byte
+ *     aligned. The library never frees or retains them past the call (a batch
+ *     plan retains them until vs_plan_free, see below).
+ *   - `stream` is a cudaStream_t passed as void* (NULL = legacy default
+ *     stream). Work is asynchronous on it unless a call says otherwise.
+ *   - Errors are returned as vs_status codes; no call aborts, exits or traps.
+ *     vs_last_error() gives a human-readable message for the calling thread.
+ *   - Handles (vs_kernel, vs_plan) are library-owned until their free call.
+ *     A vs_kernel is read-only after creation and may be shared by calls on
+ *     different streams.
+ */
+#ifndef VARSIM_H
+#define VARSIM_H
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  VS_OK = 0,
+  VS_ERR_INVALID_ARG = 1,    /* bad pointer, size or parameter */
+  VS_ERR_CUDA = 2,           /* a CUDA runtime call failed */
+  VS_ERR_OOM = 3,            /* device allocation failed */
+  VS_ERR_NO_CONVERGENCE = 4, /* residual above tol after max_iter, or growing */
+  VS_ERR_RUNAWAY = 5,        /* beta*mu*max(K) >= 1 (thermal runaway) or
+                                1 - alpha*s*u <= 0.05 (conductivity model breaks) */
+  VS_ERR_NONFINITE = 6,      /* NaN/Inf met in a map */
+  VS_ERR_TIMEOUT = 7         /* an internal grid barrier gave up waiting */
+} vs_status;
+
+#define VS_MAX_LAYERS 8
+#define VS_MIN_N 8
+#define VS_MAX_N 2048
+
+/* Layer stack below the die surface (chip parameter table, Sec. V-A).
+ * Layer 0 is the power-dissipating silicon; the temperature is read in its
+ * top plane. Layers are in perfect contact; the bottom of the last layer sees
+ * a convective coefficient h; the top surface and the side walls are
+ * adiabatic. heat_cap_J_m2K is the areal thermal capacitance C of the
+ * transient model (Eq. 23); it is only used when a time step is given. */
+typedef struct {
+  int n_layers;                          /* 1 .. VS_MAX_LAYERS */
+  double thickness_m[VS_MAX_LAYERS];     /* > 0 */
+  double kappa_W_mK[VS_MAX_LAYERS];      /* > 0 */
+  double h_conv_W_m2K;                   /* > 0 */
+  double heat_cap_J_m2K;                 /* > 0 if dt_s > 0 */
+} vs_stack;
+
+/* Square die of side die_m split into n x n square cells (the paper's grid,
+ * Sec. V-A uses 64 x 64). n must be a power of two in [VS_MIN_N, VS_MAX_N]. */
+typedef struct {
+  int n;
+  double die_m;
+} vs_grid;
+
+/* Options of the Green's-function build.
+ *   quad_nodes: Gauss-Legendre nodes of the Hankel quadrature (0 => 256,
+ *               allowed 64..1024);
+ *   rel_tol:    truncation tolerance of the real-space radius and of the
+ *               spectral alias sum (0 => 1e-13, allowed 1e-16..1e-6);
+ *   dt_s:       time step of the transient (0 => no transient tables). */
+typedef struct {
+  int quad_nodes;
+  double rel_tol;
+  double dt_s;
+} vs_kernel_opts;
+
+#define VS_PREC_FP32 0        /* plain FP32 fast cosine transforms */
+
+/* Parameters of a solve.
+ *   beta_per_K : temperature coefficient of leakage (Eq. 5), >= 0
+ *   alpha_per_K: temperature coefficient of the Green's function (Eq. 8), >= 0
+ *   tol_K      : stop when max |theta_n - theta_{n-1}| <= tol_K (> 0)
+ *   max_iter   : 1 .. 1000
+ *   precision  : VS_PREC_FP32 */
+typedef struct {
+  double beta_per_K;
+  double alpha_per_K;
+  double tol_K;
+  int max_iter;
+  int precision;
+} vs_solve_params;
+
+/* Per-map outcome. status is a vs_status; iterations counts applications of
+ * the convolution after the initial one; residual_K is the last
+ * max |theta_n - theta_{n-1}|; mu_W is the mean of P_leak0 (W per cell). */
+typedef struct {
+  int status;
+  int iterations;
+  double residual_K;
+  double mu_W;
+} vs_solve_info;
+
+typedef struct vs_kernel_t* vs_kernel;
+typedef struct vs_plan_t* vs_plan;
+
+/* ------------------------------------------------------------------------ */
+/* Green's function build (Sec. II-B, Eq. 2; Sec. II-F Eq. 10; Theorem I;    */
+/* images Sec. III-G).                                                       */
+/* ------------------------------------------------------------------------ */
+
+/* Builds the imaged, cell-averaged Green's function of (stack, grid) in the
+ * cosine basis of the die, K[p][q], p,q in [0,n), on the GPU:
+ *   1. stack spectrum g(k) (impedance recursion of the heat equation, Eq. 1);
+ *   2. Hankel quadrature (Eq. 10, Theorem I normalisation) of the top-layer
+ *      ("rapidly decaying", Sec. II-B) Green's function at every lattice
+ *      radius, FP64: G1(r) = halfspace_disc(r) - sum_i w_i J0(k_i r);
+ *   3. fold of the lattice into the 2n-periodic mirror-imaged kernel and its
+ *      cosine transform;
+ *   4. spectral (Poisson) sum of the remaining smooth spreader part.
+ * If opts->dt_s > 0 the per-mode decay factors of the transient are built too.
+ * Synchronises `stream` before returning. *out is NULL on failure.
+ * Errors: VS_ERR_INVALID_ARG (sizes, non-positive physics), VS_ERR_OOM,
+ * VS_ERR_CUDA. */
+int vs_make_kernel(const vs_stack* stack, const vs_grid* grid,
+                   const vs_kernel_opts* opts, vs_kernel* out, void* stream);
+
+void vs_free_kernel(vs_kernel k);
+
+/* Grid side n of a kernel, or -1 for NULL. */
+int vs_kernel_n(vs_kernel k);
+
+/* Copies the FP64 cosine-basis kernel K[p][q] (n*n doubles, row p) to host
+ * memory `out_host`. Blocking. Errors: VS_ERR_INVALID_ARG, VS_ERR_CUDA. */
+int vs_kernel_spectrum(vs_kernel k, double* out_host);
+
+/* Copies the top-layer radial Green's function table G1(cell*sqrt(m)) for
+ * m = 0..m_max to `out_host` (entries for m that are not a sum of two squares
+ * are 0). m_max is written to *m_max_out; pass out_host = NULL to query it.
+ * Blocking. */
+int vs_kernel_radial(vs_kernel k, double* out_host, int* m_max_out);
+
+/* Evaluates the Hankel quadrature of step 2 above for arbitrary radii:
+ * out_dev[i] = G1(r_dev[i]) in K/W for the top layer of `stack` with the
+ * source disc of one cell of `grid`. r_dev, out_dev: device float64 arrays of
+ * length count. quad_nodes as in vs_kernel_opts. Asynchronous on `stream`. */
+int vs_hankel_radial(const vs_stack* stack, const vs_grid* grid, int quad_nodes,
+                     const double* r_dev, double* out_dev, int count, void* stream);
+
+/* ------------------------------------------------------------------------ */
+/* Steady solve (Eqs. 12-22; convergence loop of Sec. V-B).                  */
+/* ------------------------------------------------------------------------ */
+
+/* Solves u = L[P_dyn + P_leak0 (1 + beta theta)], theta = s u / (1 - alpha s u)
+ * for one map, where L is the convolution with the imaged Green's function.
+ * Iterates the mean/variation split (shift-invariant kernel
+ * K/(1 - beta mu K), Eq. 20 with alpha = 0) until max |dtheta| <= tol.
+ *   p_dyn, p_leak0: W per cell; s_kappa: conductivity multiplier (NULL => 1);
+ *   theta: output, K above ambient.
+ * info_host (may be NULL) is filled after an internal stream synchronisation.
+ * Returns the map's status (VS_OK, VS_ERR_NO_CONVERGENCE, VS_ERR_RUNAWAY,
+ * VS_ERR_NONFINITE) or an argument/CUDA error. */
+int vs_solve_steady(vs_kernel k, const float* p_dyn, const float* p_leak0,
+                    const float* s_kappa, const vs_solve_params* params,
+                    float* theta, vs_solve_info* info_host, void* stream);
+
+/* ------------------------------------------------------------------------ */
+/* Batched steady solve: many maps (possibly of different grid sizes) in one */
+/* persistent launch.                                                        */
+/* ------------------------------------------------------------------------ */
+
+typedef struct {
+  vs_kernel k;             /* Green's function of this map's geometry */
+  const float* p_dyn;      /* device, [n][n] */
+  const float* p_leak0;    /* device, [n][n] */
+  const float* s_kappa;    /* device, [n][n], or NULL => 1 */
+  float* theta;            /* device output, [n][n] */
+} vs_batch_item;
+
+/* Creates a plan for n_items maps: uploads the item table, allocates the
+ * scratch (4 bytes per cell plus small per-map state) and picks the launch
+ * shape (tuned once per mix of grid sizes and cached). The item pointers are
+ * retained until vs_plan_free. Synchronises `stream`. */
+int vs_plan_create(const vs_batch_item* items_host, int n_items,
+                   const vs_solve_params* params, vs_plan* out, void* stream);
+
+/* Runs the plan: one cooperative persistent launch that iterates every map to
+ * its own convergence. Asynchronous; makes no host allocation or
+ * synchronisation, so it can be captured in a CUDA graph. Per-map results go
+ * to the plan's device info array (vs_plan_info). */
+int vs_plan_run(vs_plan plan, void* stream);
+
+/* Copies the per-map vs_solve_info of the last run to host memory
+ * (n_items entries) after synchronising `stream`. Returns the worst status. */
+int vs_plan_info(vs_plan plan, vs_solve_info* info_host, void* stream);
+
+/* Number of kernel launches one vs_plan_run makes (for launch accounting). */
+int vs_plan_launches(vs_plan plan);
+
+void vs_plan_free(vs_plan plan);
+
+/* Convenience: create + run + info + free. info_host may be NULL.
+ * Returns the worst per-map status. */
+int vs_solve_batch(const vs_batch_item* items_host, int n_items,
+                   const vs_solve_params* params, vs_solve_info* info_host,
+                   void* stream);
+
+/* ------------------------------------------------------------------------ */
+/* Transient (Sec. III-D/E, Eqs. 23-31).                                     */
+/* ------------------------------------------------------------------------ */
+
+/* Time-varying power P_dyn,n (n = 1..n_steps, piecewise constant over steps
+ * of dt_s given at kernel build) with leakage lagged one step,
+ * P_n = P_dyn,n + P_leak0 (1 + beta theta_{n-1}), theta_0 = 0.
+ * Superposition of power differences (Eq. 30) with the single-pole step
+ * response g(k)(1 - exp(-t / (C g(k)))) of every cosine mode (Eq. 29), run as
+ * the equivalent per-mode recursion. The sub-cell alias part of the kernel is
+ * taken as settled within one step.
+ *   p_dyn_trace: [n_steps][n][n]; theta_trace: output [n_steps][n][n].
+ * info_host (may be NULL) filled after synchronisation; iterations = steps. */
+int vs_solve_transient(vs_kernel k, int n_steps, const float* p_dyn_trace,
+                       const float* p_leak0, const float* s_kappa,
+                       const vs_solve_params* params, float* theta_trace,
+                       vs_solve_info* info_host, void* stream);
+
+/* ------------------------------------------------------------------------ */
+
+const char* vs_status_string(int status);
+const char* vs_last_error(void);      /* thread-local, never NULL */
+const char* vs_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* VARSIM_H */

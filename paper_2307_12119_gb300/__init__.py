@@ -1,0 +1,356 @@
+"""Python binding of libvarsim (include/varsim.h): the GB300 (sm_103a)
+Green's-function thermal solver with leakage and conductivity variation.
+
+Argument marshalling only: every step of the solve runs in the CUDA library.
+PyTorch provides device memory and the current stream. Importing works
+without a GPU (so the C ABI can be inspected); any call that needs the library
+raises if libvarsim.so is missing -- there is no CPU fallback.
+
+Maps are float32 CUDA tensors [n, n] (row-major, x fastest), power in W per
+cell, temperatures in K above ambient.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+from dataclasses import dataclass, field
+from typing import Optional, Sequence
+
+__all__ = [
+    "VS_OK", "VS_ERR_INVALID_ARG", "VS_ERR_CUDA", "VS_ERR_OOM", "VS_ERR_NO_CONVERGENCE",
+    "VS_ERR_RUNAWAY", "VS_ERR_NONFINITE", "VS_ERR_TIMEOUT", "VarsimError", "Stack", "Grid",
+    "KernelOpts", "SolveParams", "Kernel", "Plan", "lib", "lib_path", "solve_steady",
+    "solve_batch", "solve_transient", "hankel_radial", "EXPORTS",
+]
+
+VS_OK, VS_ERR_INVALID_ARG, VS_ERR_CUDA, VS_ERR_OOM = 0, 1, 2, 3
+VS_ERR_NO_CONVERGENCE, VS_ERR_RUNAWAY, VS_ERR_NONFINITE, VS_ERR_TIMEOUT = 4, 5, 6, 7
+VS_MAX_LAYERS = 8
+
+EXPORTS = [
+    "vs_make_kernel", "vs_free_kernel", "vs_kernel_n", "vs_kernel_spectrum", "vs_kernel_radial",
+    "vs_hankel_radial", "vs_solve_steady", "vs_plan_create", "vs_plan_run", "vs_plan_info",
+    "vs_plan_launches", "vs_plan_free", "vs_solve_batch", "vs_solve_transient",
+    "vs_status_string", "vs_last_error", "vs_version",
+]
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+
+
+def lib_path() -> str:
+    return os.path.join(_HERE, "libvarsim.so")
+
+
+class VarsimError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__("%s (status %d)" % (msg, status))
+        self.status = status
+
+
+class _Stack(C.Structure):
+    _fields_ = [("n_layers", C.c_int), ("thickness_m", C.c_double * VS_MAX_LAYERS),
+                ("kappa_W_mK", C.c_double * VS_MAX_LAYERS), ("h_conv_W_m2K", C.c_double),
+                ("heat_cap_J_m2K", C.c_double)]
+
+
+class _Grid(C.Structure):
+    _fields_ = [("n", C.c_int), ("die_m", C.c_double)]
+
+
+class _KernelOpts(C.Structure):
+    _fields_ = [("quad_nodes", C.c_int), ("rel_tol", C.c_double), ("dt_s", C.c_double)]
+
+
+class _SolveParams(C.Structure):
+    _fields_ = [("beta_per_K", C.c_double), ("alpha_per_K", C.c_double), ("tol_K", C.c_double),
+                ("max_iter", C.c_int), ("precision", C.c_int)]
+
+
+class _SolveInfo(C.Structure):
+    _fields_ = [("status", C.c_int), ("iterations", C.c_int), ("residual_K", C.c_double),
+                ("mu_W", C.c_double)]
+
+
+class _BatchItem(C.Structure):
+    _fields_ = [("k", C.c_void_p), ("p_dyn", C.c_void_p), ("p_leak0", C.c_void_p),
+                ("s_kappa", C.c_void_p), ("theta", C.c_void_p)]
+
+
+_lib = None
+
+
+def lib():
+    """The loaded libvarsim (raises if it has not been built)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    path = lib_path()
+    if not os.path.exists(path):
+        raise RuntimeError("libvarsim.so not found at %s: build it with "
+                           "`python -c 'import __graft_entry__ as g; g.build()'`" % path)
+    L = C.CDLL(path)
+    vp, ip, dp = C.c_void_p, C.c_int, C.POINTER(C.c_double)
+    sig = {
+        "vs_make_kernel": (ip, [C.POINTER(_Stack), C.POINTER(_Grid), C.POINTER(_KernelOpts),
+                                C.POINTER(vp), vp]),
+        "vs_free_kernel": (None, [vp]),
+        "vs_kernel_n": (ip, [vp]),
+        "vs_kernel_spectrum": (ip, [vp, dp]),
+        "vs_kernel_radial": (ip, [vp, dp, C.POINTER(ip)]),
+        "vs_hankel_radial": (ip, [C.POINTER(_Stack), C.POINTER(_Grid), ip, vp, vp, ip, vp]),
+        "vs_solve_steady": (ip, [vp, vp, vp, vp, C.POINTER(_SolveParams), vp,
+                                 C.POINTER(_SolveInfo), vp]),
+        "vs_plan_create": (ip, [C.POINTER(_BatchItem), ip, C.POINTER(_SolveParams),
+                                C.POINTER(vp), vp]),
+        "vs_plan_run": (ip, [vp, vp]),
+        "vs_plan_info": (ip, [vp, C.POINTER(_SolveInfo), vp]),
+        "vs_plan_launches": (ip, [vp]),
+        "vs_plan_free": (None, [vp]),
+        "vs_solve_batch": (ip, [C.POINTER(_BatchItem), ip, C.POINTER(_SolveParams),
+                                C.POINTER(_SolveInfo), vp]),
+        "vs_solve_transient": (ip, [vp, ip, vp, vp, vp, C.POINTER(_SolveParams), vp,
+                                    C.POINTER(_SolveInfo), vp]),
+        "vs_status_string": (C.c_char_p, [ip]),
+        "vs_last_error": (C.c_char_p, []),
+        "vs_version": (C.c_char_p, []),
+    }
+    for name, (res, args) in sig.items():
+        f = getattr(L, name)
+        f.restype = res
+        f.argtypes = args
+    _lib = L
+    return L
+
+
+def _check(rc: int, what: str, ok=(VS_OK,)):
+    if rc not in ok:
+        L = lib()
+        raise VarsimError(rc, "%s: %s: %s" % (what, L.vs_status_string(rc).decode(),
+                                              L.vs_last_error().decode()))
+    return rc
+
+
+def _stream(stream) -> int:
+    import torch
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return s.cuda_stream
+
+
+def _ptr(t, n: Optional[int] = None, name: str = "map", allow_none=False):
+    import torch
+    if t is None:
+        if allow_none:
+            return None
+        raise ValueError("%s is required" % name)
+    if not isinstance(t, torch.Tensor) or not t.is_cuda or t.dtype != torch.float32:
+        raise TypeError("%s must be a float32 CUDA tensor" % name)
+    if not t.is_contiguous():
+        raise ValueError("%s must be contiguous" % name)
+    if n is not None and tuple(t.shape[-2:]) != (n, n):
+        raise ValueError("%s must be [..., %d, %d], got %s" % (name, n, n, tuple(t.shape)))
+    return t.data_ptr()
+
+
+@dataclass
+class Stack:
+    """Layer stack, top (source) layer first; SI units."""
+    thickness_m: Sequence[float] = (0.5e-3, 0.02e-3, 3.5e-3)
+    kappa_W_mK: Sequence[float] = (130.0, 4.0, 400.0)
+    h_conv_W_m2K: float = 2.0e4
+    heat_cap_J_m2K: float = 1.63e6 * 0.5e-3
+
+    def _c(self) -> _Stack:
+        s = _Stack()
+        s.n_layers = len(self.thickness_m)
+        for i, (t, k) in enumerate(zip(self.thickness_m, self.kappa_W_mK)):
+            s.thickness_m[i] = t
+            s.kappa_W_mK[i] = k
+        s.h_conv_W_m2K = self.h_conv_W_m2K
+        s.heat_cap_J_m2K = self.heat_cap_J_m2K
+        return s
+
+
+@dataclass
+class Grid:
+    n: int
+    die_m: float
+
+    def _c(self) -> _Grid:
+        return _Grid(self.n, self.die_m)
+
+
+@dataclass
+class KernelOpts:
+    quad_nodes: int = 256
+    rel_tol: float = 1e-13
+    dt_s: float = 0.0
+
+
+@dataclass
+class SolveParams:
+    beta_per_K: float = 0.0275
+    alpha_per_K: float = 0.3 * 1.3 / 318.15
+    tol_K: float = 1e-4
+    max_iter: int = 50
+    precision: int = 0
+
+    def _c(self) -> _SolveParams:
+        return _SolveParams(self.beta_per_K, self.alpha_per_K, self.tol_K, self.max_iter,
+                            self.precision)
+
+
+def _info(i: _SolveInfo) -> dict:
+    return {"status": i.status, "iterations": i.iterations, "residual_K": i.residual_K,
+            "mu_W": i.mu_W}
+
+
+class Kernel:
+    """Green's function of one (stack, grid) built on the GPU (vs_make_kernel)."""
+
+    def __init__(self, stack: Stack, grid: Grid, opts: Optional[KernelOpts] = None, stream=None):
+        L = lib()
+        o = opts or KernelOpts()
+        h = C.c_void_p()
+        self.stack, self.grid, self.opts = stack, grid, o
+        _check(L.vs_make_kernel(C.byref(stack._c()), C.byref(grid._c()),
+                                C.byref(_KernelOpts(o.quad_nodes, o.rel_tol, o.dt_s)),
+                                C.byref(h), _stream(stream)), "vs_make_kernel")
+        self.handle = h.value
+
+    @property
+    def n(self) -> int:
+        return lib().vs_kernel_n(self.handle)
+
+    def spectrum(self):
+        """FP64 cosine-basis kernel K[p][q] as a numpy array."""
+        import numpy as np
+        out = np.empty((self.n, self.n), dtype=np.float64)
+        _check(lib().vs_kernel_spectrum(self.handle, out.ctypes.data_as(C.POINTER(C.c_double))),
+               "vs_kernel_spectrum")
+        return out
+
+    def radial(self):
+        """Top-layer radial table G1(cell*sqrt(m)), m = 0..m_max (numpy)."""
+        import numpy as np
+        m = C.c_int()
+        _check(lib().vs_kernel_radial(self.handle, None, C.byref(m)), "vs_kernel_radial")
+        out = np.empty(m.value + 1, dtype=np.float64)
+        _check(lib().vs_kernel_radial(self.handle, out.ctypes.data_as(C.POINTER(C.c_double)),
+                                      C.byref(m)), "vs_kernel_radial")
+        return out
+
+    def close(self):
+        if getattr(self, "handle", None):
+            lib().vs_free_kernel(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def hankel_radial(stack: Stack, grid: Grid, r, quad_nodes: int = 256, stream=None):
+    """G1(r) for float64 CUDA radii r (vs_hankel_radial)."""
+    import torch
+    if r.dtype != torch.float64 or not r.is_cuda or not r.is_contiguous():
+        raise TypeError("r must be a contiguous float64 CUDA tensor")
+    out = torch.empty_like(r)
+    _check(lib().vs_hankel_radial(C.byref(stack._c()), C.byref(grid._c()), quad_nodes,
+                                  r.data_ptr(), out.data_ptr(), r.numel(), _stream(stream)),
+           "vs_hankel_radial")
+    return out
+
+
+_SOLVE_OK = (VS_OK, VS_ERR_NO_CONVERGENCE, VS_ERR_RUNAWAY, VS_ERR_NONFINITE)
+
+
+def solve_steady(kernel: Kernel, p_dyn, p_leak0, s_kappa=None, params: Optional[SolveParams] = None,
+                 theta=None, stream=None):
+    """One steady map. Returns (theta, info dict); raises on argument/CUDA errors."""
+    import torch
+    n = kernel.n
+    prm = params or SolveParams()
+    if theta is None:
+        theta = torch.empty_like(p_dyn)
+    info = _SolveInfo()
+    _check(lib().vs_solve_steady(kernel.handle, _ptr(p_dyn, n, "p_dyn"),
+                                 _ptr(p_leak0, n, "p_leak0"),
+                                 _ptr(s_kappa, n, "s_kappa", allow_none=True), C.byref(prm._c()),
+                                 _ptr(theta, n, "theta"), C.byref(info), _stream(stream)),
+           "vs_solve_steady", ok=_SOLVE_OK)
+    return theta, _info(info)
+
+
+class Plan:
+    """A batched solve over many maps (vs_plan_*): one persistent launch per run."""
+
+    def __init__(self, items, params: Optional[SolveParams] = None, stream=None):
+        """items: sequence of (Kernel, p_dyn, p_leak0, s_kappa or None, theta)."""
+        prm = params or SolveParams()
+        arr = (_BatchItem * len(items))()
+        self._keep = []
+        for i, (k, pd, pl, sk, th) in enumerate(items):
+            n = k.n
+            arr[i] = _BatchItem(k.handle, _ptr(pd, n, "p_dyn"), _ptr(pl, n, "p_leak0"),
+                                _ptr(sk, n, "s_kappa", allow_none=True), _ptr(th, n, "theta"))
+            self._keep.append((k, pd, pl, sk, th))
+        h = C.c_void_p()
+        _check(lib().vs_plan_create(arr, len(items), C.byref(prm._c()), C.byref(h),
+                                    _stream(stream)), "vs_plan_create")
+        self.handle = h.value
+        self.n_items = len(items)
+
+    def run(self, stream=None):
+        _check(lib().vs_plan_run(self.handle, _stream(stream)), "vs_plan_run")
+
+    def info(self, stream=None):
+        arr = (_SolveInfo * self.n_items)()
+        rc = lib().vs_plan_info(self.handle, arr, _stream(stream))
+        _check(rc, "vs_plan_info", ok=_SOLVE_OK)
+        return [_info(a) for a in arr]
+
+    @property
+    def launches(self) -> int:
+        return lib().vs_plan_launches(self.handle)
+
+    def close(self):
+        if getattr(self, "handle", None):
+            lib().vs_plan_free(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def solve_batch(items, params: Optional[SolveParams] = None, stream=None):
+    """Create a plan, run it once, return the per-map info list."""
+    p = Plan(items, params, stream)
+    try:
+        p.run(stream)
+        return p.info(stream)
+    finally:
+        p.close()
+
+
+def solve_transient(kernel: Kernel, p_dyn_trace, p_leak0, s_kappa=None,
+                    params: Optional[SolveParams] = None, theta_trace=None, stream=None):
+    """Transient over the trace [n_steps, n, n]; returns (theta_trace, info)."""
+    import torch
+    n = kernel.n
+    prm = params or SolveParams()
+    steps = p_dyn_trace.shape[0]
+    if theta_trace is None:
+        theta_trace = torch.empty_like(p_dyn_trace)
+    info = _SolveInfo()
+    _check(lib().vs_solve_transient(kernel.handle, steps, _ptr(p_dyn_trace, n, "p_dyn_trace"),
+                                    _ptr(p_leak0, n, "p_leak0"),
+                                    _ptr(s_kappa, n, "s_kappa", allow_none=True),
+                                    C.byref(prm._c()), _ptr(theta_trace, n, "theta_trace"),
+                                    C.byref(info), _stream(stream)),
+           "vs_solve_transient", ok=_SOLVE_OK)
+    return theta_trace, _info(info)

@@ -1,0 +1,73 @@
+// Internal declarations shared by the translation units of libvarsim.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+
+#include "varsim.h"
+
+// ---------------------------------------------------------------- errors
+
+int vs_set_error(int status, const char* fmt, ...);
+
+#define VS_CUDA_TRY(call)                                                    \
+  do {                                                                        \
+    cudaError_t e_ = (call);                                                  \
+    if (e_ != cudaSuccess) {                                                  \
+      return vs_set_error(e_ == cudaErrorMemoryAllocation ? VS_ERR_OOM        \
+                                                          : VS_ERR_CUDA,      \
+                          "%s failed: %s (%s:%d)", #call,                     \
+                          cudaGetErrorString(e_), __FILE__, __LINE__);        \
+    }                                                                         \
+  } while (0)
+
+// ---------------------------------------------------------------- stack
+
+struct vs_stack_dev {
+  int n_layers;
+  double t[VS_MAX_LAYERS];
+  double kappa[VS_MAX_LAYERS];
+  double h;
+  double heat_cap;
+};
+
+// ---------------------------------------------------------------- FFT tables
+// Per grid size n: twiddles W_{4n}^e = exp(-2 pi i e / (4n)), e in [0, 4n)
+// (float2), and the digit-reversal map of the in-place radix-16/8/4/2 FFT.
+struct vs_fft_tables {
+  int n;
+  float2* tw4n;      // device [4n]
+  int* digrev;       // device [n]
+};
+
+const vs_fft_tables* vs_get_fft_tables(int n, int* status);
+
+// ---------------------------------------------------------------- kernel
+struct vs_kernel_t {
+  int n;
+  double die_m;
+  vs_stack_dev st;
+  int quad_nodes;
+  double rel_tol;
+  double* Kt64;        // device [n][n] FP64 cosine-basis kernel
+  float* Kt32;         // device [n][n]
+  float kmax;          // max over modes of K (host)
+  double* radial;      // device [m_max + 1] top-layer radial table
+  int m_max;
+  double dt;           // transient step (0 = none)
+  float* trA;          // device [n][n] primary-mode weight cell^-2 g D
+  float* trRho;        // device [n][n] exp(-dt / (C g))
+  const vs_fft_tables* fft;
+};
+
+int vs_validate_stack(const vs_stack* s);
+int vs_validate_grid(const vs_grid* g);
+int vs_validate_params(const vs_solve_params* p);
+void vs_stack_to_dev(const vs_stack* s, vs_stack_dev* d);
+
+// Hankel quadrature of the top-layer radial Green's function at `count`
+// radii (device arrays), see vs_kernel_build.cu.
+int vs_hankel_eval(const vs_stack_dev& st, double cell_m, int quad_nodes,
+                   const double* r_dev, double* out_dev, int count, cudaStream_t s);

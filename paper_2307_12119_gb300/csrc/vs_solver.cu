@@ -1,0 +1,869 @@
+// Persistent batched solver of the leakage/conductivity fixed point
+// (Eqs. 12-22 with the convergence loop of Sec. V-B) and of the transient
+// superposition (Eqs. 23-31).
+//
+// One cooperative launch per solve. Every map is a set of tasks:
+//   row task  : RB consecutive rows of one map
+//     - inverse DCT along x of the column-phase output (transposed layout),
+//     - fused update: u -> theta = s u / (1 - alpha s u), residual
+//       max |theta - theta_prev|, source q = P_dyn + P_leak0
+//       + beta (P_leak0 theta - mu u) (mean/variation split, Sec. III-C),
+//     - forward DCT along x, stored transposed (x-frequency major);
+//   col task  : CB consecutive x-frequencies of one map
+//     - forward DCT along y, multiply by the shift-invariant modified kernel
+//       K / (1 - beta mu K) (Eq. 20 with alpha = 0), inverse DCT along y.
+// Phases are separated by a grid barrier; after each row phase one thread
+// per map decides convergence. Maps converge independently; the launch ends
+// when no map is active.
+#include <math.h>
+#include <stdio.h>
+#include <stdlib.h>
+#include <string.h>
+
+#include <algorithm>
+#include <chrono>
+#include <map>
+#include <mutex>
+#include <vector>
+
+#include "vs_fft.cuh"
+#include "vs_internal.cuh"
+
+using namespace vsfft;
+
+namespace {
+
+constexpr int kThreads = 256;
+constexpr int kMaxIter = 1000;
+constexpr int kFlagRunaway = 1;
+constexpr int kFlagNonfinite = 2;
+constexpr long long kSpinLimit = 20000000LL;  // ~ seconds at ~100 ns per spin
+
+struct MapDesc {
+  const float* p_dyn;
+  const float* p_leak0;
+  const float* s;
+  float* theta;
+  float* work;           // n*n, transposed spectral scratch
+  const float* Kt;       // n*n cosine-basis kernel
+  const float2* tw4n;
+  const int* digrev;
+  const float* trA;      // transient only
+  const float* trRho;
+  float* state;          // transient per-mode state, n*n
+  float kmax;
+  int n, rb, cb;
+  int row_off, col_off, part_off;
+};
+
+struct MapState {
+  double mu;
+  float mu_f;
+  unsigned resid_bits;
+  float prev_resid;
+  int growth;
+  int active;
+  int status;
+  int iters;
+  int flags;
+};
+
+struct Ctrl {
+  unsigned count;
+  unsigned gen;
+  unsigned abort;
+  unsigned pad_;
+  unsigned active[kMaxIter + 2];
+};
+
+struct PlanDev {
+  const MapDesc* maps;
+  MapState* st;
+  double* part;
+  vs_solve_info* info;
+  Ctrl* ctrl;
+  int n_maps, row_tasks, col_tasks;
+  int max_iter;
+  float beta, alpha, tol;
+  int n_steps;           // transient
+};
+
+// ------------------------------------------------------------ grid barrier
+
+__device__ __forceinline__ unsigned ld_acquire(const unsigned* p) {
+  unsigned v;
+  asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+
+// Returns false if the launch was aborted (a barrier timed out somewhere).
+__device__ bool grid_barrier(Ctrl* c) {
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    unsigned gen = ld_acquire(&c->gen);
+    __threadfence();
+    unsigned arrived = atomicAdd(&c->count, 1u) + 1u;
+    if (arrived == gridDim.x) {
+      atomicExch(&c->count, 0u);
+      __threadfence();
+      atomicAdd(&c->gen, 1u);
+    } else {
+      long long spins = 0;
+      while (ld_acquire(&c->gen) == gen) {
+        if (ld_acquire(&c->abort)) break;
+        __nanosleep(64);
+        if (++spins > kSpinLimit) {
+          atomicExch(&c->abort, 1u);
+          break;
+        }
+      }
+    }
+    __threadfence();
+  }
+  __syncthreads();
+  return ld_acquire(&c->abort) == 0u;
+}
+
+// ------------------------------------------------------------ reductions
+
+__device__ __forceinline__ double block_sum(double v, double* red) {
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+  int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+  if (l == 0) red[w] = v;
+  __syncthreads();
+  double r = 0.0;
+  if (threadIdx.x == 0)
+    for (int i = 0; i < (int)(blockDim.x >> 5); ++i) r += red[i];
+  __syncthreads();
+  return r;  // valid in thread 0
+}
+
+__device__ __forceinline__ float block_max(float v, float* red) {
+  for (int o = 16; o > 0; o >>= 1) v = fmaxf(v, __shfl_down_sync(0xffffffffu, v, o));
+  int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+  if (l == 0) red[w] = v;
+  __syncthreads();
+  float r = 0.f;
+  if (threadIdx.x == 0)
+    for (int i = 0; i < (int)(blockDim.x >> 5); ++i) r = fmaxf(r, red[i]);
+  __syncthreads();
+  return r;
+}
+
+__device__ __forceinline__ int block_or(int v, int* red) {
+  for (int o = 16; o > 0; o >>= 1) v |= __shfl_down_sync(0xffffffffu, v, o);
+  int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+  if (l == 0) red[w] = v;
+  __syncthreads();
+  int r = 0;
+  if (threadIdx.x == 0)
+    for (int i = 0; i < (int)(blockDim.x >> 5); ++i) r |= red[i];
+  __syncthreads();
+  return r;
+}
+
+__device__ __forceinline__ int find_map(const MapDesc* maps, int n_maps, int task, bool row) {
+  int lo = 0, hi = n_maps - 1;
+  while (lo < hi) {
+    int mid = (lo + hi + 1) >> 1;
+    int off = row ? maps[mid].row_off : maps[mid].col_off;
+    if (off <= task) lo = mid;
+    else hi = mid - 1;
+  }
+  return lo;
+}
+
+// ------------------------------------------------------------ row task
+// MODE 0: steady iteration `step` (0 = initial source). MODE 1: transient
+// step `step` (0 = first source, n_steps = last inverse only).
+template <int MODE>
+__device__ void row_task(const PlanDev& P, int task, int step, float2* buf) {
+  __shared__ double red_d[kThreads / 32];
+  __shared__ float red_f[kThreads / 32];
+  __shared__ int red_i[kThreads / 32];
+  const int b = find_map(P.maps, P.n_maps, task, true);
+  const MapDesc d = P.maps[b];
+  MapState* ms = P.st + b;
+  if (MODE == 0 && step > 0 && !ms->active) return;
+  const int n = d.n, F = d.rb >> 1, NP = padded_len(n), half = n >> 1;
+  const int chunk = task - d.row_off;
+  const int y0 = chunk * d.rb;
+  float* WT = d.work;
+  const float2* tw = d.tw4n;
+  const int* dr = d.digrev;
+  const bool first = (step == 0);
+  const bool last = (MODE == 1) && (step == P.n_steps);
+
+  if (!first) {
+    for (int it = threadIdx.x; it < F * (half + 1); it += blockDim.x) {
+      int f = it % F, k = it / F, nk = n - k;
+      float2 xk = *reinterpret_cast<const float2*>(WT + (size_t)k * n + y0 + 2 * f);
+      float2 xnk = (k == 0) ? make_float2(0.f, 0.f)
+                            : *reinterpret_cast<const float2*>(WT + (size_t)nk * n + y0 + 2 * f);
+      buf[f * NP + pad(__ldg(&dr[k]))] = dct_pre(xk.x, xnk.x, xk.y, xnk.y, __ldg(&tw[k]));
+      if (k != 0 && k != half)
+        buf[f * NP + pad(__ldg(&dr[nk]))] = dct_pre(xnk.x, xk.x, xnk.y, xk.y, __ldg(&tw[nk]));
+    }
+    __syncthreads();
+    fft_inverse(buf, n, F, NP, tw);
+  }
+
+  // fused elementwise update
+  const float beta = P.beta, alpha = P.alpha;
+  const float mu = (MODE == 0 && !first) ? ms->mu_f : 0.f;
+  double mu_acc = 0.0;
+  float resid = 0.f;
+  int flags = 0;
+  const size_t nn = (size_t)n * n;
+  for (int it = threadIdx.x; it < F * n; it += blockDim.x) {
+    int f = it / n, x = it - f * n;
+    int pos = f * NP + pad(makhoul_pos(x, n));
+    float2 uv = first ? make_float2(0.f, 0.f) : buf[pos];
+    float q[2];
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      size_t idx = (size_t)(y0 + 2 * f + h) * n + x;
+      float u = h ? uv.y : uv.x;
+      float pl = __ldg(&d.p_leak0[idx]);
+      float sk = d.s ? __ldg(&d.s[idx]) : 1.f;
+      if (MODE == 0) {
+        float pd = __ldg(&d.p_dyn[idx]);
+        if (first) {
+          d.theta[idx] = 0.f;
+          q[h] = pd + pl;
+          mu_acc += (double)pl;
+        } else {
+          float den = fmaf(-alpha * sk, u, 1.f);
+          if (!(den > 0.05f)) flags |= kFlagRunaway;
+          float th = sk * u / den;
+          float old = d.theta[idx];
+          if (!isfinite(th)) flags |= kFlagNonfinite;
+          else resid = fmaxf(resid, fabsf(th - old));
+          d.theta[idx] = th;
+          q[h] = pd + pl + beta * fmaf(pl, th, -mu * u);
+        }
+      } else {
+        float th = 0.f;
+        if (!first) {
+          float den = fmaf(-alpha * sk, u, 1.f);
+          if (!(den > 0.05f)) flags |= kFlagRunaway;
+          th = sk * u / den;
+          if (!isfinite(th)) flags |= kFlagNonfinite;
+          d.theta[(size_t)(step - 1) * nn + idx] = th;
+        }
+        q[h] = last ? 0.f : __ldg(&d.p_dyn[(size_t)step * nn + idx]) + pl * fmaf(beta, th, 1.f);
+      }
+    }
+    buf[pos] = make_float2(q[0], q[1]);
+  }
+  if (MODE == 0 && first) {
+    double tot = block_sum(mu_acc, red_d);
+    if (threadIdx.x == 0) P.part[d.part_off + chunk] = tot;
+  }
+  if (!first || MODE == 1) {
+    float r = block_max(resid, red_f);
+    int fl = block_or(flags, red_i);
+    if (threadIdx.x == 0) {
+      if (MODE == 0 && r > 0.f) atomicMax(&ms->resid_bits, __float_as_uint(r));
+      if (fl) atomicOr(&ms->flags, fl);
+    }
+  }
+  __syncthreads();
+  if (last) return;
+
+  fft_forward(buf, n, F, NP, tw);
+  for (int it = threadIdx.x; it < F * (half + 1); it += blockDim.x) {
+    int f = it % F, k = it / F, nk = n - k;
+    float2 zk = buf[f * NP + pad(__ldg(&dr[k]))];
+    float2 znk = buf[f * NP + pad(__ldg(&dr[k == 0 ? 0 : nk]))];
+    *reinterpret_cast<float2*>(WT + (size_t)k * n + y0 + 2 * f) = dct_post(zk, znk, __ldg(&tw[k]));
+    if (k != 0 && k != half)
+      *reinterpret_cast<float2*>(WT + (size_t)nk * n + y0 + 2 * f) = dct_post(znk, zk, __ldg(&tw[nk]));
+  }
+  __syncthreads();
+}
+
+// ------------------------------------------------------------ column task
+template <int MODE>
+__device__ void col_task(const PlanDev& P, int task, float2* buf) {
+  const int b = find_map(P.maps, P.n_maps, task, false);
+  const MapDesc d = P.maps[b];
+  MapState* ms = P.st + b;
+  if (MODE == 0 && !ms->active) return;
+  const int n = d.n, F = d.cb >> 1, NP = padded_len(n), half = n >> 1;
+  const int p0 = (task - d.col_off) * d.cb;
+  float* WT = d.work;
+  const float2* tw = d.tw4n;
+  const int* dr = d.digrev;
+
+  for (int it = threadIdx.x; it < F * n; it += blockDim.x) {
+    int f = it / n, j = it - f * n;
+    float a = WT[(size_t)(p0 + 2 * f) * n + j];
+    float c = WT[(size_t)(p0 + 2 * f + 1) * n + j];
+    buf[f * NP + pad(makhoul_pos(j, n))] = make_float2(a, c);
+  }
+  __syncthreads();
+  fft_forward(buf, n, F, NP, tw);
+
+  const float inv_n2 = 1.f / ((float)n * (float)n);
+  const float bm = P.beta * ((MODE == 0) ? ms->mu_f : 0.f);
+  for (int it = threadIdx.x; it < F * (half + 1); it += blockDim.x) {
+    int f = it % F, k = it / F, nk = n - k;
+    int ia = f * NP + pad(__ldg(&dr[k]));
+    int ib = f * NP + pad(__ldg(&dr[k == 0 ? 0 : nk]));
+    float2 zk = buf[ia], znk = buf[ib];
+    float2 xk = dct_post(zk, znk, __ldg(&tw[k]));
+    float2 xnk = (k == 0) ? make_float2(0.f, 0.f) : dct_post(znk, zk, __ldg(&tw[nk]));
+    const size_t ra = (size_t)(p0 + 2 * f) * n, rb = ra + n;
+    float2 yk, ynk;
+    if (MODE == 0) {
+      float ka = __ldg(&d.Kt[ra + k]), kb = __ldg(&d.Kt[rb + k]);
+      yk = make_float2(xk.x * ka / (1.f - bm * ka) * inv_n2, xk.y * kb / (1.f - bm * kb) * inv_n2);
+      if (k != 0) {
+        float ka2 = __ldg(&d.Kt[ra + nk]), kb2 = __ldg(&d.Kt[rb + nk]);
+        ynk = make_float2(xnk.x * ka2 / (1.f - bm * ka2) * inv_n2, xnk.y * kb2 / (1.f - bm * kb2) * inv_n2);
+      } else {
+        ynk = make_float2(0.f, 0.f);
+      }
+    } else {
+      // per-mode recursion: W = (1 - rho) X + rho W_prev;  Y = (K - A) X + A W
+      auto mode = [&](size_t idx, float x) {
+        float rho = __ldg(&d.trRho[idx]), A = __ldg(&d.trA[idx]), K = __ldg(&d.Kt[idx]);
+        float w = fmaf(rho, d.state[idx] - x, x);
+        d.state[idx] = w;
+        return fmaf(K - A, x, A * w) * inv_n2;
+      };
+      yk = make_float2(mode(ra + k, xk.x), mode(rb + k, xk.y));
+      if (k != 0 && k != half) ynk = make_float2(mode(ra + nk, xnk.x), mode(rb + nk, xnk.y));
+      else if (k == half) ynk = yk;
+      else ynk = make_float2(0.f, 0.f);
+    }
+    if (MODE == 0 && k == half) ynk = yk;
+    buf[ia] = dct_pre(yk.x, ynk.x, yk.y, ynk.y, __ldg(&tw[k]));
+    if (k != 0 && k != half) buf[ib] = dct_pre(ynk.x, yk.x, ynk.y, yk.y, __ldg(&tw[nk]));
+  }
+  __syncthreads();
+  fft_inverse(buf, n, F, NP, tw);
+  for (int it = threadIdx.x; it < F * n; it += blockDim.x) {
+    int f = it / n, j = it - f * n;
+    float2 v = buf[f * NP + pad(makhoul_pos(j, n))];
+    WT[(size_t)(p0 + 2 * f) * n + j] = v.x;
+    WT[(size_t)(p0 + 2 * f + 1) * n + j] = v.y;
+  }
+  __syncthreads();
+}
+
+// ------------------------------------------------------------ decision phase
+__device__ void write_info(const PlanDev& P, int b, const MapState& s) {
+  vs_solve_info* inf = P.info + b;
+  inf->status = s.status;
+  inf->iterations = s.iters;
+  inf->residual_K = (double)s.prev_resid;
+  inf->mu_W = s.mu;
+}
+
+__device__ void decide(const PlanDev& P, int it) {
+  for (int b = blockIdx.x * blockDim.x + threadIdx.x; b < P.n_maps; b += gridDim.x * blockDim.x) {
+    MapState s = P.st[b];
+    const MapDesc& d = P.maps[b];
+    if (it == 0) {
+      int tasks = d.n / d.rb;
+      double sum = 0.0;
+      for (int i = 0; i < tasks; ++i) sum += P.part[d.part_off + i];
+      s.mu = sum / ((double)d.n * d.n);
+      s.mu_f = (float)s.mu;
+      s.active = 1;
+      s.status = VS_OK;
+      s.iters = 0;
+      s.prev_resid = INFINITY;
+      if ((double)P.beta * s.mu * (double)d.kmax >= 0.999) {
+        s.active = 0;
+        s.status = VS_ERR_RUNAWAY;
+      }
+    } else {
+      if (!s.active) continue;
+      float r = __uint_as_float(s.resid_bits);
+      s.iters = it;
+      if (s.flags & kFlagNonfinite) {
+        s.active = 0;
+        s.status = VS_ERR_NONFINITE;
+      } else if (s.flags & kFlagRunaway) {
+        s.active = 0;
+        s.status = VS_ERR_RUNAWAY;
+      } else if (r <= P.tol) {
+        s.active = 0;
+        s.status = VS_OK;
+      } else {
+        s.growth = (it > 2 && r > s.prev_resid) ? s.growth + 1 : 0;
+        if (it >= P.max_iter || s.growth >= 5) {
+          s.active = 0;
+          s.status = VS_ERR_NO_CONVERGENCE;
+        }
+      }
+      s.prev_resid = r;
+    }
+    s.resid_bits = 0u;
+    P.st[b] = s;
+    write_info(P, b, s);
+    if (s.active) atomicAdd(&P.ctrl->active[it], 1u);
+  }
+}
+
+__global__ void __launch_bounds__(kThreads) k_solve_steady(PlanDev P) {
+  extern __shared__ float2 smem[];
+  for (int t = blockIdx.x; t < P.row_tasks; t += gridDim.x) row_task<0>(P, t, 0, smem);
+  if (!grid_barrier(P.ctrl)) return;
+  decide(P, 0);
+  if (!grid_barrier(P.ctrl)) return;
+  if (ld_acquire(&P.ctrl->active[0]) == 0u) return;
+  for (int it = 1; it <= P.max_iter; ++it) {
+    for (int t = blockIdx.x; t < P.col_tasks; t += gridDim.x) col_task<0>(P, t, smem);
+    if (!grid_barrier(P.ctrl)) return;
+    for (int t = blockIdx.x; t < P.row_tasks; t += gridDim.x) row_task<0>(P, t, it, smem);
+    if (!grid_barrier(P.ctrl)) return;
+    decide(P, it);
+    if (!grid_barrier(P.ctrl)) return;
+    if (ld_acquire(&P.ctrl->active[it]) == 0u) break;
+  }
+}
+
+__global__ void __launch_bounds__(kThreads) k_solve_transient(PlanDev P) {
+  extern __shared__ float2 smem[];
+  for (int t = blockIdx.x; t < P.row_tasks; t += gridDim.x) row_task<1>(P, t, 0, smem);
+  if (!grid_barrier(P.ctrl)) return;
+  for (int step = 1; step <= P.n_steps; ++step) {
+    for (int t = blockIdx.x; t < P.col_tasks; t += gridDim.x) col_task<1>(P, t, smem);
+    if (!grid_barrier(P.ctrl)) return;
+    for (int t = blockIdx.x; t < P.row_tasks; t += gridDim.x) row_task<1>(P, t, step, smem);
+    if (!grid_barrier(P.ctrl)) return;
+  }
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    for (int b = 0; b < P.n_maps; ++b) {
+      MapState s = P.st[b];
+      s.iters = P.n_steps;
+      s.status = (s.flags & kFlagNonfinite) ? VS_ERR_NONFINITE
+                 : (s.flags & kFlagRunaway) ? VS_ERR_RUNAWAY : VS_OK;
+      s.prev_resid = 0.f;
+      s.mu = 0.0;
+      P.st[b] = s;
+      write_info(P, b, s);
+    }
+  }
+}
+
+__global__ void k_twiddles(int n, float2* tw) {
+  int e = blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= 4 * n) return;
+  double sn, cs;
+  sincospi(-(double)e / (2.0 * n), &sn, &cs);
+  tw[e] = make_float2((float)cs, (float)sn);
+}
+
+// ------------------------------------------------------------ host side
+
+int pow2_log(int n) {
+  int l = 0;
+  while ((1 << l) < n) ++l;
+  return l;
+}
+
+std::vector<int> host_digrev(int n) {
+  std::vector<int> rad;
+  int rem = n;
+  while (rem > 1) {
+    int r = rem >= 16 ? 16 : rem;
+    rad.push_back(r);
+    rem /= r;
+  }
+  std::vector<int> out(n);
+  for (int k = 0; k < n; ++k) {
+    int kk = k, m = n, p = 0;
+    for (int r : rad) {
+      m /= r;
+      p += (kk % r) * m;
+      kk /= r;
+    }
+    out[k] = p;
+  }
+  return out;
+}
+
+std::mutex g_fft_mutex;
+std::map<std::pair<int, int>, vs_fft_tables*> g_fft;
+
+struct TaskShape {
+  int elems;   // target elements per task
+};
+
+int rows_for(int n, int elems) { return std::max(2, std::min(n, std::min(64, elems / n))); }
+int cols_for(int n, int elems) { return std::max(2, std::min(n, std::min(64, elems / n))); }
+
+}  // namespace
+
+const vs_fft_tables* vs_get_fft_tables(int n, int* status) {
+  int dev = 0;
+  cudaGetDevice(&dev);
+  std::lock_guard<std::mutex> lk(g_fft_mutex);
+  auto key = std::make_pair(dev, n);
+  auto it = g_fft.find(key);
+  if (it != g_fft.end()) return it->second;
+  vs_fft_tables* t = new vs_fft_tables();
+  t->n = n;
+  std::vector<int> dr = host_digrev(n);
+  cudaError_t e = cudaMalloc(&t->tw4n, sizeof(float2) * 4 * n);
+  if (e == cudaSuccess) e = cudaMalloc(&t->digrev, sizeof(int) * n);
+  if (e == cudaSuccess) e = cudaMemcpy(t->digrev, dr.data(), sizeof(int) * n, cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) {
+    k_twiddles<<<(4 * n + 255) / 256, 256>>>(n, t->tw4n);
+    e = cudaGetLastError();
+  }
+  if (e == cudaSuccess) e = cudaDeviceSynchronize();
+  if (e != cudaSuccess) {
+    cudaFree(t->tw4n);
+    cudaFree(t->digrev);
+    delete t;
+    *status = vs_set_error(e == cudaErrorMemoryAllocation ? VS_ERR_OOM : VS_ERR_CUDA,
+                           "FFT tables for n=%d: %s", n, cudaGetErrorString(e));
+    return nullptr;
+  }
+  g_fft[key] = t;
+  return t;
+}
+
+// ---------------------------------------------------------------- plans
+
+struct vs_plan_t {
+  int n_items;
+  std::vector<vs_batch_item> items;
+  vs_solve_params params;
+  int elems;                 // task size
+  int grid;
+  size_t smem;
+  int row_tasks, col_tasks, part_total;
+  MapDesc* d_maps = nullptr;
+  MapState* d_state = nullptr;
+  double* d_part = nullptr;
+  vs_solve_info* d_info = nullptr;
+  Ctrl* d_ctrl = nullptr;
+  float* d_work = nullptr;
+  float* d_trstate = nullptr;
+  int transient_steps = 0;
+};
+
+namespace {
+
+std::mutex g_tune_mutex;
+std::map<std::vector<int>, int> g_tuned;  // key: sorted n list + batch bucket
+
+void plan_release(vs_plan_t* p) {
+  cudaFree(p->d_maps);
+  cudaFree(p->d_state);
+  cudaFree(p->d_part);
+  cudaFree(p->d_info);
+  cudaFree(p->d_ctrl);
+  cudaFree(p->d_work);
+  cudaFree(p->d_trstate);
+  p->d_maps = nullptr;
+  p->d_state = nullptr;
+  p->d_part = nullptr;
+  p->d_info = nullptr;
+  p->d_ctrl = nullptr;
+  p->d_work = nullptr;
+  p->d_trstate = nullptr;
+}
+
+// Builds descriptors and scratch for task size `elems`.
+int plan_layout(vs_plan_t* p, int elems, cudaStream_t s, bool transient, int n_steps) {
+  plan_release(p);
+  p->elems = elems;
+  int n_items = p->n_items;
+  std::vector<MapDesc> maps(n_items);
+  size_t work_total = 0;
+  int row_off = 0, col_off = 0, part_off = 0;
+  size_t smem = 0;
+  for (int i = 0; i < n_items; ++i) {
+    const vs_batch_item& it = p->items[i];
+    vs_kernel k = it.k;
+    int n = k->n;
+    MapDesc& m = maps[i];
+    m.p_dyn = it.p_dyn;
+    m.p_leak0 = it.p_leak0;
+    m.s = it.s_kappa;
+    m.theta = it.theta;
+    m.Kt = k->Kt32;
+    m.tw4n = k->fft->tw4n;
+    m.digrev = k->fft->digrev;
+    m.trA = k->trA;
+    m.trRho = k->trRho;
+    m.kmax = k->kmax;
+    m.n = n;
+    m.rb = rows_for(n, elems);
+    m.cb = cols_for(n, elems);
+    m.row_off = row_off;
+    m.col_off = col_off;
+    m.part_off = part_off;
+    row_off += n / m.rb;
+    col_off += n / m.cb;
+    part_off += n / m.rb;
+    work_total += (size_t)n * n;
+    size_t sm = (size_t)(std::max(m.rb, m.cb) / 2) * padded_len(n) * sizeof(float2);
+    smem = std::max(smem, sm);
+  }
+  p->row_tasks = row_off;
+  p->col_tasks = col_off;
+  p->part_total = part_off;
+  p->smem = smem;
+  VS_CUDA_TRY(cudaMalloc(&p->d_work, work_total * sizeof(float)));
+  if (transient) VS_CUDA_TRY(cudaMalloc(&p->d_trstate, work_total * sizeof(float)));
+  size_t off = 0;
+  for (int i = 0; i < n_items; ++i) {
+    maps[i].work = p->d_work + off;
+    maps[i].state = transient ? p->d_trstate + off : nullptr;
+    off += (size_t)maps[i].n * maps[i].n;
+  }
+  VS_CUDA_TRY(cudaMalloc(&p->d_maps, sizeof(MapDesc) * n_items));
+  VS_CUDA_TRY(cudaMalloc(&p->d_state, sizeof(MapState) * n_items));
+  VS_CUDA_TRY(cudaMalloc(&p->d_part, sizeof(double) * std::max(1, part_off)));
+  VS_CUDA_TRY(cudaMalloc(&p->d_info, sizeof(vs_solve_info) * n_items));
+  VS_CUDA_TRY(cudaMalloc(&p->d_ctrl, sizeof(Ctrl)));
+  VS_CUDA_TRY(cudaMemcpyAsync(p->d_maps, maps.data(), sizeof(MapDesc) * n_items,
+                              cudaMemcpyHostToDevice, s));
+  VS_CUDA_TRY(cudaMemsetAsync(p->d_info, 0, sizeof(vs_solve_info) * n_items, s));
+
+  auto fn = transient ? (const void*)k_solve_transient : (const void*)k_solve_steady;
+  VS_CUDA_TRY(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  int per_sm = 0;
+  VS_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, kThreads, smem));
+  if (per_sm < 1) return vs_set_error(VS_ERR_INVALID_ARG, "no block fits on an SM (smem %zu)", smem);
+  int dev = 0, sms = 0;
+  VS_CUDA_TRY(cudaGetDevice(&dev));
+  VS_CUDA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+  int want = std::max(p->row_tasks, p->col_tasks);
+  p->grid = std::max(1, std::min(per_sm * sms, want));
+  p->transient_steps = n_steps;
+  VS_CUDA_TRY(cudaStreamSynchronize(s));  // host `maps` must outlive the copy
+  return VS_OK;
+}
+
+int plan_launch(vs_plan_t* p, cudaStream_t s, bool transient) {
+  VS_CUDA_TRY(cudaMemsetAsync(p->d_ctrl, 0, sizeof(Ctrl), s));
+  VS_CUDA_TRY(cudaMemsetAsync(p->d_state, 0, sizeof(MapState) * p->n_items, s));
+  PlanDev P;
+  P.maps = p->d_maps;
+  P.st = p->d_state;
+  P.part = p->d_part;
+  P.info = p->d_info;
+  P.ctrl = p->d_ctrl;
+  P.n_maps = p->n_items;
+  P.row_tasks = p->row_tasks;
+  P.col_tasks = p->col_tasks;
+  P.max_iter = p->params.max_iter;
+  P.beta = (float)p->params.beta_per_K;
+  P.alpha = (float)p->params.alpha_per_K;
+  P.tol = (float)p->params.tol_K;
+  P.n_steps = p->transient_steps;
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(p->grid);
+  cfg.blockDim = dim3(kThreads);
+  cfg.dynamicSmemBytes = p->smem;
+  cfg.stream = s;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeCooperative;
+  attr[0].val.cooperative = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  cudaError_t e = transient ? cudaLaunchKernelEx(&cfg, k_solve_transient, P)
+                            : cudaLaunchKernelEx(&cfg, k_solve_steady, P);
+  if (e != cudaSuccess)
+    return vs_set_error(VS_ERR_CUDA, "cooperative launch (grid %d, smem %zu): %s", p->grid,
+                        p->smem, cudaGetErrorString(e));
+  return VS_OK;
+}
+
+int timeout_status(vs_plan_t* p, cudaStream_t s) {
+  Ctrl c;
+  VS_CUDA_TRY(cudaMemcpyAsync(&c, p->d_ctrl, sizeof(unsigned) * 4, cudaMemcpyDeviceToHost, s));
+  VS_CUDA_TRY(cudaStreamSynchronize(s));
+  if (c.abort) return vs_set_error(VS_ERR_TIMEOUT, "grid barrier timed out");
+  return VS_OK;
+}
+
+double time_plan(vs_plan_t* p, cudaStream_t s, int reps) {
+  cudaEvent_t a, b;
+  cudaEventCreate(&a);
+  cudaEventCreate(&b);
+  if (plan_launch(p, s, false) != VS_OK) return 1e30;
+  cudaEventRecord(a, s);
+  for (int i = 0; i < reps; ++i)
+    if (plan_launch(p, s, false) != VS_OK) return 1e30;
+  cudaEventRecord(b, s);
+  cudaEventSynchronize(b);
+  float ms = 0.f;
+  cudaEventElapsedTime(&ms, a, b);
+  cudaEventDestroy(a);
+  cudaEventDestroy(b);
+  return ms;
+}
+
+}  // namespace
+
+extern "C" int vs_plan_create(const vs_batch_item* items_host, int n_items,
+                              const vs_solve_params* params, vs_plan* out, void* stream) {
+  if (!out) return vs_set_error(VS_ERR_INVALID_ARG, "out is NULL");
+  *out = nullptr;
+  if (!items_host || n_items <= 0) return vs_set_error(VS_ERR_INVALID_ARG, "no items");
+  int rc = vs_validate_params(params);
+  if (rc) return rc;
+  for (int i = 0; i < n_items; ++i) {
+    const vs_batch_item& it = items_host[i];
+    if (!it.k || !it.p_dyn || !it.p_leak0 || !it.theta)
+      return vs_set_error(VS_ERR_INVALID_ARG, "item %d has a NULL kernel or map", i);
+    uintptr_t al = (uintptr_t)it.p_dyn | (uintptr_t)it.p_leak0 | (uintptr_t)it.theta |
+                   (uintptr_t)it.s_kappa;
+    if (al & 15u) return vs_set_error(VS_ERR_INVALID_ARG, "item %d: maps must be 16-byte aligned", i);
+  }
+  cudaStream_t s = (cudaStream_t)stream;
+  vs_plan_t* p = new vs_plan_t();
+  p->n_items = n_items;
+  p->items.assign(items_host, items_host + n_items);
+  p->params = *params;
+
+  // task size: tuned once per mix of grid sizes when the batch is large
+  std::vector<int> key;
+  for (int i = 0; i < n_items; ++i) key.push_back(items_host[i].k->n);
+  std::sort(key.begin(), key.end());
+  key.erase(std::unique(key.begin(), key.end()), key.end());
+  key.push_back(n_items >= 256 ? 1 : 0);
+  int elems = 8192;
+  bool tune = n_items >= 64;
+  const char* env = getenv("VS_AUTOTUNE");
+  if (env && env[0] == '0') tune = false;
+  {
+    std::lock_guard<std::mutex> lk(g_tune_mutex);
+    auto itc = g_tuned.find(key);
+    if (itc != g_tuned.end()) {
+      elems = itc->second;
+      tune = false;
+    }
+  }
+  if (tune) {
+    double best = 1e30;
+    int best_e = elems;
+    const int cands[3] = {4096, 8192, 16384};
+    for (int e : cands) {
+      rc = plan_layout(p, e, s, false, 0);
+      if (rc) break;
+      double t = time_plan(p, s, 2);
+      if (t < best) {
+        best = t;
+        best_e = e;
+      }
+    }
+    if (rc == VS_OK) {
+      elems = best_e;
+      std::lock_guard<std::mutex> lk(g_tune_mutex);
+      g_tuned[key] = elems;
+    }
+    cudaError_t e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess && rc == VS_OK)
+      rc = vs_set_error(VS_ERR_CUDA, "autotune: %s", cudaGetErrorString(e));
+  }
+  if (rc == VS_OK) rc = plan_layout(p, elems, s, false, 0);
+  if (rc != VS_OK) {
+    plan_release(p);
+    delete p;
+    return rc;
+  }
+  *out = p;
+  return VS_OK;
+}
+
+extern "C" int vs_plan_run(vs_plan p, void* stream) {
+  if (!p) return vs_set_error(VS_ERR_INVALID_ARG, "NULL plan");
+  return plan_launch(p, (cudaStream_t)stream, false);
+}
+
+extern "C" int vs_plan_launches(vs_plan p) { return p ? 1 : 0; }
+
+extern "C" int vs_plan_info(vs_plan p, vs_solve_info* info_host, void* stream) {
+  if (!p || !info_host) return vs_set_error(VS_ERR_INVALID_ARG, "NULL plan or output");
+  cudaStream_t s = (cudaStream_t)stream;
+  VS_CUDA_TRY(cudaMemcpyAsync(info_host, p->d_info, sizeof(vs_solve_info) * p->n_items,
+                              cudaMemcpyDeviceToHost, s));
+  VS_CUDA_TRY(cudaStreamSynchronize(s));
+  int rc = timeout_status(p, s);
+  if (rc) return rc;
+  int worst = VS_OK;
+  for (int i = 0; i < p->n_items; ++i) worst = std::max(worst, info_host[i].status);
+  return worst;
+}
+
+extern "C" void vs_plan_free(vs_plan p) {
+  if (!p) return;
+  plan_release(p);
+  delete p;
+}
+
+extern "C" int vs_solve_batch(const vs_batch_item* items_host, int n_items,
+                              const vs_solve_params* params, vs_solve_info* info_host,
+                              void* stream) {
+  vs_plan p = nullptr;
+  int rc = vs_plan_create(items_host, n_items, params, &p, stream);
+  if (rc) return rc;
+  rc = vs_plan_run(p, stream);
+  if (rc == VS_OK) {
+    std::vector<vs_solve_info> tmp(n_items);
+    rc = vs_plan_info(p, info_host ? info_host : tmp.data(), stream);
+  }
+  cudaStreamSynchronize((cudaStream_t)stream);
+  vs_plan_free(p);
+  return rc;
+}
+
+extern "C" int vs_solve_steady(vs_kernel k, const float* p_dyn, const float* p_leak0,
+                               const float* s_kappa, const vs_solve_params* params, float* theta,
+                               vs_solve_info* info_host, void* stream) {
+  if (!k) return vs_set_error(VS_ERR_INVALID_ARG, "NULL kernel");
+  vs_batch_item it = {k, p_dyn, p_leak0, s_kappa, theta};
+  vs_solve_info inf;
+  int rc = vs_solve_batch(&it, 1, params, &inf, stream);
+  if (info_host && (rc == VS_OK || rc >= VS_ERR_NO_CONVERGENCE)) *info_host = inf;
+  return rc;
+}
+
+extern "C" int vs_solve_transient(vs_kernel k, int n_steps, const float* p_dyn_trace,
+                                  const float* p_leak0, const float* s_kappa,
+                                  const vs_solve_params* params, float* theta_trace,
+                                  vs_solve_info* info_host, void* stream) {
+  if (!k) return vs_set_error(VS_ERR_INVALID_ARG, "NULL kernel");
+  if (!(k->dt > 0.0) || !k->trA)
+    return vs_set_error(VS_ERR_INVALID_ARG, "kernel was built without a time step (dt_s = 0)");
+  if (n_steps < 1 || n_steps > 1000000) return vs_set_error(VS_ERR_INVALID_ARG, "n_steps %d", n_steps);
+  int rc = vs_validate_params(params);
+  if (rc) return rc;
+  if (!p_dyn_trace || !p_leak0 || !theta_trace)
+    return vs_set_error(VS_ERR_INVALID_ARG, "NULL map");
+  uintptr_t al = (uintptr_t)p_dyn_trace | (uintptr_t)p_leak0 | (uintptr_t)theta_trace |
+                 (uintptr_t)s_kappa;
+  if (al & 15u) return vs_set_error(VS_ERR_INVALID_ARG, "maps must be 16-byte aligned");
+  cudaStream_t s = (cudaStream_t)stream;
+  vs_plan_t* p = new vs_plan_t();
+  p->n_items = 1;
+  p->items.push_back(vs_batch_item{k, p_dyn_trace, p_leak0, s_kappa, theta_trace});
+  p->params = *params;
+  rc = plan_layout(p, 8192, s, true, n_steps);
+  if (rc == VS_OK) {
+    cudaError_t e = cudaMemsetAsync(p->d_trstate, 0, sizeof(float) * (size_t)k->n * k->n, s);
+    if (e != cudaSuccess) rc = vs_set_error(VS_ERR_CUDA, "memset: %s", cudaGetErrorString(e));
+  }
+  if (rc == VS_OK) rc = plan_launch(p, s, true);
+  if (rc == VS_OK) {
+    vs_solve_info inf;
+    rc = vs_plan_info(p, &inf, stream);
+    if (info_host) *info_host = inf;
+  }
+  cudaStreamSynchronize(s);
+  plan_release(p);
+  delete p;
+  return rc;
+}

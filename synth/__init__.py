@@ -229,3 +229,19 @@ def markov_trace(w: Workload, n_steps: int, seed: int = SEED, device="cpu",
             level = (w.floor_W_m2, 0.5 * dens, dens)[state[b]]
             out[t, y0:y0 + bh, x0:x0 + bw] = level * a_cell
     return out.to(dtype)
+
+
+def batch_workload(n: int = 256, count: int = 4096) -> Workload:
+    """Batched steady workload: `count` solves at n x n on a 20 x 20 mm die,
+    each with its own variation field (sigma 8 %, correlation length 2 mm)
+    over 64 floorplans of 32 blocks U[0.1, 3] W/mm^2 plus 4 hotspots of
+    5 W/mm^2 (0.5 mm)."""
+    w = Workload("batch_%d_x%d" % (n, count), n, 20 * MM, 32, 0.1e6, 3.0e6, n_hot=4,
+                 sigma=(0.08, 0.08), corr_len_m=(2 * MM, 2 * MM), config_id=5)
+    return w
+
+
+def batch_inputs(n: int = 256, count: int = 4096, device="cuda", seed: int = SEED):
+    w = batch_workload(n, count)
+    pd, pl, s = steady_inputs(w, count, seed=seed, n_floorplans=64, device=device)
+    return w, pd, pl, s

@@ -1,0 +1,64 @@
+"""The C-ABI library builds, loads and exports every symbol include/varsim.h
+declares (CPU only: no compute call is made)."""
+import ctypes
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _declared():
+    src = open(os.path.join(ROOT, "include", "varsim.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"\b(vs_[a-z_0-9]+)\s*\(", src)))
+
+
+@pytest.fixture(scope="module")
+def libpath():
+    from paper_2307_12119_gb300 import build
+    return build.build()
+
+
+def test_header_declares_the_boundary():
+    names = _declared()
+    for required in ("vs_make_kernel", "vs_solve_steady", "vs_solve_transient", "vs_solve_batch"):
+        assert required in names
+
+
+def test_library_exports_every_declared_symbol(libpath):
+    lib = ctypes.CDLL(libpath)
+    missing = [n for n in _declared() if not hasattr(lib, n)]
+    assert not missing, missing
+
+
+def test_binding_lists_every_export(libpath):
+    import paper_2307_12119_gb300 as vs
+    assert sorted(vs.EXPORTS) == _declared()
+    L = vs.lib()
+    assert L.vs_version().decode().startswith("varsim-gb300")
+    assert L.vs_status_string(vs.VS_ERR_RUNAWAY).decode() == "thermal or conductivity runaway"
+
+
+def test_argument_errors_need_no_gpu(libpath):
+    import paper_2307_12119_gb300 as vs
+    L = vs.lib()
+    h = ctypes.c_void_p()
+    st = vs.Stack()._c()
+    bad_grid = vs.Grid(100, 0.01)._c()          # not a power of two
+    rc = L.vs_make_kernel(ctypes.byref(st), ctypes.byref(bad_grid), None, ctypes.byref(h), None)
+    assert rc == vs.VS_ERR_INVALID_ARG
+    assert "power of two" in L.vs_last_error().decode()
+    st.n_layers = 0
+    rc = L.vs_make_kernel(ctypes.byref(st), ctypes.byref(vs.Grid(64, 0.01)._c()), None,
+                          ctypes.byref(h), None)
+    assert rc == vs.VS_ERR_INVALID_ARG and h.value is None
+
+
+def test_missing_library_fails_loudly(monkeypatch, tmp_path):
+    import paper_2307_12119_gb300 as vs
+    monkeypatch.setattr(vs, "_lib", None)
+    monkeypatch.setattr(vs, "lib_path", lambda: str(tmp_path / "nope.so"))
+    with pytest.raises(RuntimeError, match="libvarsim.so not found"):
+        vs.lib()
