@@ -11,7 +11,8 @@
 // the same passes undone in reverse order (digit-reversed in, natural out).
 // Radix 16 passes first, then one radix-8/4/2 pass for the remaining factor.
 // Complex index i of an FFT buffer is stored at i + (i >> 4) (one pad slot per
-// 16) to spread the strided accesses of the late passes over banks.
+// 16) to spread the strided accesses of the late passes over banks, and
+// consecutive FFTs of a buffer start an odd number of slots apart.
 #pragma once
 
 #include <cuda_runtime.h>
@@ -19,7 +20,9 @@
 namespace vsfft {
 
 __device__ __forceinline__ int pad(int i) { return i + (i >> 4); }
-__host__ __device__ inline int padded_len(int n) { return n + (n >> 4); }
+// Odd stride (in float2) between the FFTs of a buffer, so that the same
+// element of consecutive FFTs falls in different banks.
+__host__ __device__ inline int padded_len(int n) { return n + (n >> 4) + 1; }
 
 __device__ __forceinline__ float2 cadd(float2 a, float2 b) { return make_float2(a.x + b.x, a.y + b.y); }
 __device__ __forceinline__ float2 csub(float2 a, float2 b) { return make_float2(a.x - b.x, a.y - b.y); }
@@ -143,15 +146,18 @@ __device__ __forceinline__ void dftR(float2* v) {
 template <int R, bool FWD>
 __device__ __forceinline__ void fft_pass(float2* buf, int n, int L, int nfft, int stride,
                                          const float2* __restrict__ tw4n, int tid, int nthr) {
+  // all sizes are powers of two: index math by shifts and masks
   const int m = L / R;
+  const int lg_m = __ffs(m) - 1;
   const int per_fft = n / R;
+  const int lg_per = __ffs(per_fft) - 1;
   const int total = nfft * per_fft;
   const int tws = 4 * (n / L);
   for (int b = tid; b < total; b += nthr) {
-    int f = b / per_fft;
-    int rem = b - f * per_fft;
-    int blk = rem / m;
-    int j = rem - blk * m;
+    int f = b >> lg_per;
+    int rem = b & (per_fft - 1);
+    int blk = rem >> lg_m;
+    int j = rem & (m - 1);
     float2* base = buf + f * stride;
     int i0 = blk * L + j;
     float2 v[R];
@@ -159,11 +165,15 @@ __device__ __forceinline__ void fft_pass(float2* buf, int n, int L, int nfft, in
     for (int r = 0; r < R; ++r) v[r] = base[pad(i0 + r * m)];
     if (FWD) {
       dftR<R, true>(v);
+      if (m > 1) {
 #pragma unroll
-      for (int r = 1; r < R; ++r) v[r] = cmul(v[r], __ldg(&tw4n[j * r * tws]));
+        for (int r = 1; r < R; ++r) v[r] = cmul(v[r], __ldg(&tw4n[j * r * tws]));
+      }
     } else {
+      if (m > 1) {
 #pragma unroll
-      for (int r = 1; r < R; ++r) v[r] = cmulc(v[r], __ldg(&tw4n[j * r * tws]));
+        for (int r = 1; r < R; ++r) v[r] = cmulc(v[r], __ldg(&tw4n[j * r * tws]));
+      }
       dftR<R, false>(v);
     }
 #pragma unroll

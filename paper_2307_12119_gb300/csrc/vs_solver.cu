@@ -34,6 +34,7 @@ using namespace vsfft;
 namespace {
 
 constexpr int kThreads = 256;
+constexpr int kU = 4;          // items per thread with loads issued together
 constexpr int kMaxIter = 1000;
 constexpr int kFlagRunaway = 1;
 constexpr int kFlagNonfinite = 2;
@@ -78,6 +79,8 @@ struct Ctrl {
 
 struct PlanDev {
   const MapDesc* maps;
+  const int* row_map;    // task -> map index
+  const int* col_map;
   MapState* st;
   double* part;
   vs_solve_info* info;
@@ -162,15 +165,8 @@ __device__ __forceinline__ int block_or(int v, int* red) {
   return r;
 }
 
-__device__ __forceinline__ int find_map(const MapDesc* maps, int n_maps, int task, bool row) {
-  int lo = 0, hi = n_maps - 1;
-  while (lo < hi) {
-    int mid = (lo + hi + 1) >> 1;
-    int off = row ? maps[mid].row_off : maps[mid].col_off;
-    if (off <= task) lo = mid;
-    else hi = mid - 1;
-  }
-  return lo;
+__device__ __forceinline__ int find_map(const PlanDev& P, int task, bool row) {
+  return __ldg(row ? &P.row_map[task] : &P.col_map[task]);
 }
 
 // ------------------------------------------------------------ row task
@@ -181,11 +177,12 @@ __device__ void row_task(const PlanDev& P, int task, int step, float2* buf) {
   __shared__ double red_d[kThreads / 32];
   __shared__ float red_f[kThreads / 32];
   __shared__ int red_i[kThreads / 32];
-  const int b = find_map(P.maps, P.n_maps, task, true);
+  const int b = find_map(P, task, true);
   const MapDesc d = P.maps[b];
   MapState* ms = P.st + b;
   if (MODE == 0 && step > 0 && !ms->active) return;
   const int n = d.n, F = d.rb >> 1, NP = padded_len(n), half = n >> 1;
+  const int lgF = __ffs(F) - 1, lgn = __ffs(n) - 1;
   const int chunk = task - d.row_off;
   const int y0 = chunk * d.rb;
   float* WT = d.work;
@@ -195,14 +192,29 @@ __device__ void row_task(const PlanDev& P, int task, int step, float2* buf) {
   const bool last = (MODE == 1) && (step == P.n_steps);
 
   if (!first) {
-    for (int it = threadIdx.x; it < F * (half + 1); it += blockDim.x) {
-      int f = it % F, k = it / F, nk = n - k;
-      float2 xk = *reinterpret_cast<const float2*>(WT + (size_t)k * n + y0 + 2 * f);
-      float2 xnk = (k == 0) ? make_float2(0.f, 0.f)
-                            : *reinterpret_cast<const float2*>(WT + (size_t)nk * n + y0 + 2 * f);
-      buf[f * NP + pad(__ldg(&dr[k]))] = dct_pre(xk.x, xnk.x, xk.y, xnk.y, __ldg(&tw[k]));
-      if (k != 0 && k != half)
-        buf[f * NP + pad(__ldg(&dr[nk]))] = dct_pre(xnk.x, xk.x, xnk.y, xk.y, __ldg(&tw[nk]));
+    const int total = F * (half + 1);
+    for (int base = threadIdx.x; base < total; base += kU * blockDim.x) {
+      float2 xk[kU], xnk[kU];
+#pragma unroll
+      for (int u = 0; u < kU; ++u) {
+        int it = base + u * blockDim.x;
+        xk[u] = xnk[u] = make_float2(0.f, 0.f);
+        if (it < total) {
+          int f = it & (F - 1), k = it >> lgF;
+          xk[u] = *reinterpret_cast<const float2*>(WT + (size_t)k * n + y0 + 2 * f);
+          if (k != 0) xnk[u] = *reinterpret_cast<const float2*>(WT + (size_t)(n - k) * n + y0 + 2 * f);
+        }
+      }
+#pragma unroll
+      for (int u = 0; u < kU; ++u) {
+        int it = base + u * blockDim.x;
+        if (it < total) {
+          int f = it & (F - 1), k = it >> lgF, nk = n - k;
+          buf[f * NP + pad(__ldg(&dr[k]))] = dct_pre(xk[u].x, xnk[u].x, xk[u].y, xnk[u].y, __ldg(&tw[k]));
+          if (k != 0 && k != half)
+            buf[f * NP + pad(__ldg(&dr[nk]))] = dct_pre(xnk[u].x, xk[u].x, xnk[u].y, xk[u].y, __ldg(&tw[nk]));
+        }
+      }
     }
     __syncthreads();
     fft_inverse(buf, n, F, NP, tw);
@@ -215,46 +227,71 @@ __device__ void row_task(const PlanDev& P, int task, int step, float2* buf) {
   float resid = 0.f;
   int flags = 0;
   const size_t nn = (size_t)n * n;
-  for (int it = threadIdx.x; it < F * n; it += blockDim.x) {
-    int f = it / n, x = it - f * n;
-    int pos = f * NP + pad(makhoul_pos(x, n));
-    float2 uv = first ? make_float2(0.f, 0.f) : buf[pos];
-    float q[2];
+  const int total = F * n;
+  for (int base = threadIdx.x; base < total; base += kU * blockDim.x) {
+    float pl[kU][2], pd[kU][2], sk[kU][2], old[kU][2];
+    float2 uv[kU];
 #pragma unroll
-    for (int h = 0; h < 2; ++h) {
-      size_t idx = (size_t)(y0 + 2 * f + h) * n + x;
-      float u = h ? uv.y : uv.x;
-      float pl = __ldg(&d.p_leak0[idx]);
-      float sk = d.s ? __ldg(&d.s[idx]) : 1.f;
-      if (MODE == 0) {
-        float pd = __ldg(&d.p_dyn[idx]);
-        if (first) {
-          d.theta[idx] = 0.f;
-          q[h] = pd + pl;
-          mu_acc += (double)pl;
-        } else {
-          float den = fmaf(-alpha * sk, u, 1.f);
-          if (!(den > 0.05f)) flags |= kFlagRunaway;
-          float th = sk * u / den;
-          float old = d.theta[idx];
-          if (!isfinite(th)) flags |= kFlagNonfinite;
-          else resid = fmaxf(resid, fabsf(th - old));
-          d.theta[idx] = th;
-          q[h] = pd + pl + beta * fmaf(pl, th, -mu * u);
+    for (int u = 0; u < kU; ++u) {
+      int it = base + u * blockDim.x;
+      uv[u] = make_float2(0.f, 0.f);
+#pragma unroll
+      for (int h = 0; h < 2; ++h) pl[u][h] = pd[u][h] = old[u][h] = 0.f, sk[u][h] = 1.f;
+      if (it < total) {
+        int f = it >> lgn, x = it & (n - 1);
+        if (!first) uv[u] = buf[f * NP + pad(makhoul_pos(x, n))];
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+          size_t idx = (size_t)(y0 + 2 * f + h) * n + x;
+          pl[u][h] = __ldg(&d.p_leak0[idx]);
+          if (d.s) sk[u][h] = __ldg(&d.s[idx]);
+          if (MODE == 0) {
+            pd[u][h] = __ldg(&d.p_dyn[idx]);
+            if (!first) old[u][h] = d.theta[idx];
+          } else if (!last) {
+            pd[u][h] = __ldg(&d.p_dyn[(size_t)step * nn + idx]);
+          }
         }
-      } else {
-        float th = 0.f;
-        if (!first) {
-          float den = fmaf(-alpha * sk, u, 1.f);
-          if (!(den > 0.05f)) flags |= kFlagRunaway;
-          th = sk * u / den;
-          if (!isfinite(th)) flags |= kFlagNonfinite;
-          d.theta[(size_t)(step - 1) * nn + idx] = th;
-        }
-        q[h] = last ? 0.f : __ldg(&d.p_dyn[(size_t)step * nn + idx]) + pl * fmaf(beta, th, 1.f);
       }
     }
-    buf[pos] = make_float2(q[0], q[1]);
+#pragma unroll
+    for (int u = 0; u < kU; ++u) {
+      int it = base + u * blockDim.x;
+      if (it >= total) continue;
+      int f = it >> lgn, x = it & (n - 1);
+      float q[2];
+#pragma unroll
+      for (int h = 0; h < 2; ++h) {
+        size_t idx = (size_t)(y0 + 2 * f + h) * n + x;
+        float uu = h ? uv[u].y : uv[u].x;
+        if (MODE == 0) {
+          if (first) {
+            d.theta[idx] = 0.f;
+            q[h] = pd[u][h] + pl[u][h];
+            mu_acc += (double)pl[u][h];
+          } else {
+            float den = fmaf(-alpha * sk[u][h], uu, 1.f);
+            if (!(den > 0.05f)) flags |= kFlagRunaway;
+            float th = sk[u][h] * uu / den;
+            if (!isfinite(th)) flags |= kFlagNonfinite;
+            else resid = fmaxf(resid, fabsf(th - old[u][h]));
+            d.theta[idx] = th;
+            q[h] = pd[u][h] + pl[u][h] + beta * fmaf(pl[u][h], th, -mu * uu);
+          }
+        } else {
+          float th = 0.f;
+          if (!first) {
+            float den = fmaf(-alpha * sk[u][h], uu, 1.f);
+            if (!(den > 0.05f)) flags |= kFlagRunaway;
+            th = sk[u][h] * uu / den;
+            if (!isfinite(th)) flags |= kFlagNonfinite;
+            d.theta[(size_t)(step - 1) * nn + idx] = th;
+          }
+          q[h] = last ? 0.f : pd[u][h] + pl[u][h] * fmaf(beta, th, 1.f);
+        }
+      }
+      buf[f * NP + pad(makhoul_pos(x, n))] = make_float2(q[0], q[1]);
+    }
   }
   if (MODE == 0 && first) {
     double tot = block_sum(mu_acc, red_d);
@@ -273,7 +310,7 @@ __device__ void row_task(const PlanDev& P, int task, int step, float2* buf) {
 
   fft_forward(buf, n, F, NP, tw);
   for (int it = threadIdx.x; it < F * (half + 1); it += blockDim.x) {
-    int f = it % F, k = it / F, nk = n - k;
+    int f = it & (F - 1), k = it >> lgF, nk = n - k;
     float2 zk = buf[f * NP + pad(__ldg(&dr[k]))];
     float2 znk = buf[f * NP + pad(__ldg(&dr[k == 0 ? 0 : nk]))];
     *reinterpret_cast<float2*>(WT + (size_t)k * n + y0 + 2 * f) = dct_post(zk, znk, __ldg(&tw[k]));
@@ -286,21 +323,38 @@ __device__ void row_task(const PlanDev& P, int task, int step, float2* buf) {
 // ------------------------------------------------------------ column task
 template <int MODE>
 __device__ void col_task(const PlanDev& P, int task, float2* buf) {
-  const int b = find_map(P.maps, P.n_maps, task, false);
+  const int b = find_map(P, task, false);
   const MapDesc d = P.maps[b];
   MapState* ms = P.st + b;
   if (MODE == 0 && !ms->active) return;
   const int n = d.n, F = d.cb >> 1, NP = padded_len(n), half = n >> 1;
+  const int lgF = __ffs(F) - 1, lgn = __ffs(n) - 1;
   const int p0 = (task - d.col_off) * d.cb;
   float* WT = d.work;
   const float2* tw = d.tw4n;
   const int* dr = d.digrev;
 
-  for (int it = threadIdx.x; it < F * n; it += blockDim.x) {
-    int f = it / n, j = it - f * n;
-    float a = WT[(size_t)(p0 + 2 * f) * n + j];
-    float c = WT[(size_t)(p0 + 2 * f + 1) * n + j];
-    buf[f * NP + pad(makhoul_pos(j, n))] = make_float2(a, c);
+  const int total = F * n;
+  for (int base = threadIdx.x; base < total; base += kU * blockDim.x) {
+    float a[kU], c[kU];
+#pragma unroll
+    for (int u = 0; u < kU; ++u) {
+      int it = base + u * blockDim.x;
+      a[u] = c[u] = 0.f;
+      if (it < total) {
+        int f = it >> lgn, j = it & (n - 1);
+        a[u] = WT[(size_t)(p0 + 2 * f) * n + j];
+        c[u] = WT[(size_t)(p0 + 2 * f + 1) * n + j];
+      }
+    }
+#pragma unroll
+    for (int u = 0; u < kU; ++u) {
+      int it = base + u * blockDim.x;
+      if (it < total) {
+        int f = it >> lgn, j = it & (n - 1);
+        buf[f * NP + pad(makhoul_pos(j, n))] = make_float2(a[u], c[u]);
+      }
+    }
   }
   __syncthreads();
   fft_forward(buf, n, F, NP, tw);
@@ -308,7 +362,7 @@ __device__ void col_task(const PlanDev& P, int task, float2* buf) {
   const float inv_n2 = 1.f / ((float)n * (float)n);
   const float bm = P.beta * ((MODE == 0) ? ms->mu_f : 0.f);
   for (int it = threadIdx.x; it < F * (half + 1); it += blockDim.x) {
-    int f = it % F, k = it / F, nk = n - k;
+    int f = it & (F - 1), k = it >> lgF, nk = n - k;
     int ia = f * NP + pad(__ldg(&dr[k]));
     int ib = f * NP + pad(__ldg(&dr[k == 0 ? 0 : nk]));
     float2 zk = buf[ia], znk = buf[ib];
@@ -345,7 +399,7 @@ __device__ void col_task(const PlanDev& P, int task, float2* buf) {
   __syncthreads();
   fft_inverse(buf, n, F, NP, tw);
   for (int it = threadIdx.x; it < F * n; it += blockDim.x) {
-    int f = it / n, j = it - f * n;
+    int f = it >> lgn, j = it & (n - 1);
     float2 v = buf[f * NP + pad(makhoul_pos(j, n))];
     WT[(size_t)(p0 + 2 * f) * n + j] = v.x;
     WT[(size_t)(p0 + 2 * f + 1) * n + j] = v.y;
@@ -409,7 +463,7 @@ __device__ void decide(const PlanDev& P, int it) {
   }
 }
 
-__global__ void __launch_bounds__(kThreads) k_solve_steady(PlanDev P) {
+__global__ void __launch_bounds__(kThreads, 3) k_solve_steady(PlanDev P) {
   extern __shared__ float2 smem[];
   for (int t = blockIdx.x; t < P.row_tasks; t += gridDim.x) row_task<0>(P, t, 0, smem);
   if (!grid_barrier(P.ctrl)) return;
@@ -427,7 +481,7 @@ __global__ void __launch_bounds__(kThreads) k_solve_steady(PlanDev P) {
   }
 }
 
-__global__ void __launch_bounds__(kThreads) k_solve_transient(PlanDev P) {
+__global__ void __launch_bounds__(kThreads, 3) k_solve_transient(PlanDev P) {
   extern __shared__ float2 smem[];
   for (int t = blockIdx.x; t < P.row_tasks; t += gridDim.x) row_task<1>(P, t, 0, smem);
   if (!grid_barrier(P.ctrl)) return;
@@ -460,12 +514,6 @@ __global__ void k_twiddles(int n, float2* tw) {
 }
 
 // ------------------------------------------------------------ host side
-
-int pow2_log(int n) {
-  int l = 0;
-  while ((1 << l) < n) ++l;
-  return l;
-}
 
 std::vector<int> host_digrev(int n) {
   std::vector<int> rad;
@@ -541,6 +589,8 @@ struct vs_plan_t {
   size_t smem;
   int row_tasks, col_tasks, part_total;
   MapDesc* d_maps = nullptr;
+  int* d_row_map = nullptr;
+  int* d_col_map = nullptr;
   MapState* d_state = nullptr;
   double* d_part = nullptr;
   vs_solve_info* d_info = nullptr;
@@ -553,10 +603,14 @@ struct vs_plan_t {
 namespace {
 
 std::mutex g_tune_mutex;
+std::mutex g_attr_mutex;
+size_t g_smem_attr_steady = 0, g_smem_attr_transient = 0;
 std::map<std::vector<int>, int> g_tuned;  // key: sorted n list + batch bucket
 
 void plan_release(vs_plan_t* p) {
   cudaFree(p->d_maps);
+  cudaFree(p->d_row_map);
+  cudaFree(p->d_col_map);
   cudaFree(p->d_state);
   cudaFree(p->d_part);
   cudaFree(p->d_info);
@@ -564,6 +618,8 @@ void plan_release(vs_plan_t* p) {
   cudaFree(p->d_work);
   cudaFree(p->d_trstate);
   p->d_maps = nullptr;
+  p->d_row_map = nullptr;
+  p->d_col_map = nullptr;
   p->d_state = nullptr;
   p->d_part = nullptr;
   p->d_info = nullptr;
@@ -628,10 +684,31 @@ int plan_layout(vs_plan_t* p, int elems, cudaStream_t s, bool transient, int n_s
   VS_CUDA_TRY(cudaMalloc(&p->d_ctrl, sizeof(Ctrl)));
   VS_CUDA_TRY(cudaMemcpyAsync(p->d_maps, maps.data(), sizeof(MapDesc) * n_items,
                               cudaMemcpyHostToDevice, s));
+  std::vector<int> rmap(p->row_tasks), cmap(p->col_tasks);
+  for (int i = 0; i < n_items; ++i) {
+    for (int t = 0; t < maps[i].n / maps[i].rb; ++t) rmap[maps[i].row_off + t] = i;
+    for (int t = 0; t < maps[i].n / maps[i].cb; ++t) cmap[maps[i].col_off + t] = i;
+  }
+  VS_CUDA_TRY(cudaMalloc(&p->d_row_map, sizeof(int) * p->row_tasks));
+  VS_CUDA_TRY(cudaMalloc(&p->d_col_map, sizeof(int) * p->col_tasks));
+  VS_CUDA_TRY(cudaMemcpyAsync(p->d_row_map, rmap.data(), sizeof(int) * p->row_tasks,
+                              cudaMemcpyHostToDevice, s));
+  VS_CUDA_TRY(cudaMemcpyAsync(p->d_col_map, cmap.data(), sizeof(int) * p->col_tasks,
+                              cudaMemcpyHostToDevice, s));
   VS_CUDA_TRY(cudaMemsetAsync(p->d_info, 0, sizeof(vs_solve_info) * n_items, s));
 
   auto fn = transient ? (const void*)k_solve_transient : (const void*)k_solve_steady;
-  VS_CUDA_TRY(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  {
+    // Function attributes are process-wide: only ever raise the limit, so a
+    // plan with a smaller footprint never invalidates a larger one.
+    std::lock_guard<std::mutex> lk(g_attr_mutex);
+    size_t& cur = transient ? g_smem_attr_transient : g_smem_attr_steady;
+    if (smem > cur) {
+      VS_CUDA_TRY(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+      VS_CUDA_TRY(cudaFuncSetAttribute(fn, cudaFuncAttributePreferredSharedMemoryCarveout, 100));
+      cur = smem;
+    }
+  }
   int per_sm = 0;
   VS_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, kThreads, smem));
   if (per_sm < 1) return vs_set_error(VS_ERR_INVALID_ARG, "no block fits on an SM (smem %zu)", smem);
@@ -650,6 +727,8 @@ int plan_launch(vs_plan_t* p, cudaStream_t s, bool transient) {
   VS_CUDA_TRY(cudaMemsetAsync(p->d_state, 0, sizeof(MapState) * p->n_items, s));
   PlanDev P;
   P.maps = p->d_maps;
+  P.row_map = p->d_row_map;
+  P.col_map = p->d_col_map;
   P.st = p->d_state;
   P.part = p->d_part;
   P.info = p->d_info;

@@ -181,3 +181,21 @@ def test_argument_checks():
         vs.solve_steady(k, pd[0][:32], pl[0], s[0], vs_params(w))
     with pytest.raises(vs.VarsimError):                     # transient needs dt
         vs.solve_transient(k, pd, pl[0], s[0], vs_params(w))
+
+
+def test_plans_with_different_footprints_coexist():
+    # a small plan created after a large one must not break the large one
+    vs = _vs()
+    big, small = synth.workload("c3_512"), synth.workload("tiny_16")
+    kb, ks = _kernel(big), _kernel(small)
+    pd, pl, s = inputs(big, count=2)
+    th = torch.empty_like(pd)
+    plan = vs.Plan([(kb, pd[i], pl[i], s[i], th[i]) for i in range(2)], vs_params(big))
+    plan.run()
+    a = th.clone()
+    qd, ql, qs = inputs(small)
+    vs.solve_steady(ks, qd[0], ql[0], qs[0], vs_params(small))
+    th.zero_()
+    plan.run()
+    torch.cuda.synchronize()
+    assert torch.equal(a, th)
