@@ -179,6 +179,27 @@ int vs_solve_steady(vs_kernel k, const float* p_dyn, const float* p_leak0,
                     const float* s_kappa, const vs_solve_params* params,
                     float* theta, vs_solve_info* info_host, void* stream);
 
+/* Allocation-free variant of vs_solve_steady. The paper has no counterpart:
+ * this entry point exists for callers that must not allocate device memory
+ * while solving -- e.g. services that reserve their device-memory budget up
+ * front, or latency-critical loops where cudaMalloc/cudaFree (which can
+ * synchronise the device) are not allowed. It makes no cudaMalloc, cudaFree
+ * or other allocating call; its scratch lives in a fixed, file-scope device
+ * array of about 1.02 MiB that every GPU loading the library holds until the
+ * process exits.
+ *   Limit: n <= 512 (the work map of a 512 x 512 grid fills the array);
+ *          larger grids return VS_ERR_INVALID_ARG with a message.
+ *   Arguments, layout, outputs and statuses are those of vs_solve_steady.
+ *   The first call on each device resolves the array's device address
+ *   (cudaGetSymbolAddress); make that first call outside any stream capture.
+ *   Every call re-initialises the parts of the array that must start at zero,
+ *   but all calls share the one array: calls whose GPU work overlaps (different
+ *   streams or host threads without ordering) race and corrupt each other.
+ *   Synchronises `stream` before returning. */
+int vs_solve_steady_noalloc(vs_kernel k, const float* p_dyn, const float* p_leak0,
+                            const float* s_kappa, const vs_solve_params* params,
+                            float* theta, vs_solve_info* info_host, void* stream);
+
 /* ------------------------------------------------------------------------ */
 /* Batched steady solve: many maps (possibly of different grid sizes) in one */
 /* persistent launch.                                                        */

@@ -20,7 +20,7 @@ __all__ = [
     "VS_OK", "VS_ERR_INVALID_ARG", "VS_ERR_CUDA", "VS_ERR_OOM", "VS_ERR_NO_CONVERGENCE",
     "VS_ERR_RUNAWAY", "VS_ERR_NONFINITE", "VS_ERR_TIMEOUT", "VarsimError", "Stack", "Grid",
     "KernelOpts", "SolveParams", "Kernel", "Plan", "lib", "lib_path", "solve_steady",
-    "solve_batch", "solve_transient", "hankel_radial", "EXPORTS",
+    "solve_batch", "solve_transient", "hankel_radial", "EXPORTS", "solve_steady_noalloc",
 ]
 
 VS_OK, VS_ERR_INVALID_ARG, VS_ERR_CUDA, VS_ERR_OOM = 0, 1, 2, 3
@@ -31,7 +31,7 @@ EXPORTS = [
     "vs_make_kernel", "vs_free_kernel", "vs_kernel_n", "vs_kernel_spectrum", "vs_kernel_radial",
     "vs_hankel_radial", "vs_solve_steady", "vs_plan_create", "vs_plan_run", "vs_plan_info",
     "vs_plan_launches", "vs_plan_free", "vs_solve_batch", "vs_solve_transient",
-    "vs_status_string", "vs_last_error", "vs_version",
+    "vs_status_string", "vs_last_error", "vs_version", "vs_solve_steady_noalloc",
 ]
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
@@ -100,6 +100,8 @@ def lib():
         "vs_hankel_radial": (ip, [C.POINTER(_Stack), C.POINTER(_Grid), ip, vp, vp, ip, vp]),
         "vs_solve_steady": (ip, [vp, vp, vp, vp, C.POINTER(_SolveParams), vp,
                                  C.POINTER(_SolveInfo), vp]),
+        "vs_solve_steady_noalloc": (ip, [vp, vp, vp, vp, C.POINTER(_SolveParams), vp,
+                                         C.POINTER(_SolveInfo), vp]),
         "vs_plan_create": (ip, [C.POINTER(_BatchItem), ip, C.POINTER(_SolveParams),
                                 C.POINTER(vp), vp]),
         "vs_plan_run": (ip, [vp, vp]),
@@ -280,6 +282,27 @@ def solve_steady(kernel: Kernel, p_dyn, p_leak0, s_kappa=None, params: Optional[
                                  _ptr(s_kappa, n, "s_kappa", allow_none=True), C.byref(prm._c()),
                                  _ptr(theta, n, "theta"), C.byref(info), _stream(stream)),
            "vs_solve_steady", ok=_SOLVE_OK)
+    return theta, _info(info)
+
+
+def solve_steady_noalloc(kernel: Kernel, p_dyn, p_leak0, s_kappa=None,
+                         params: Optional[SolveParams] = None, theta=None, stream=None):
+    """vs_solve_steady_noalloc: same as solve_steady, but the library makes no
+    device allocation (scratch is a fixed device array; n <= 512; calls that
+    overlap on the GPU race). `theta` should be preallocated by callers that
+    cannot allocate."""
+    import torch
+    n = kernel.n
+    prm = params or SolveParams()
+    if theta is None:
+        theta = torch.empty_like(p_dyn)
+    info = _SolveInfo()
+    _check(lib().vs_solve_steady_noalloc(kernel.handle, _ptr(p_dyn, n, "p_dyn"),
+                                         _ptr(p_leak0, n, "p_leak0"),
+                                         _ptr(s_kappa, n, "s_kappa", allow_none=True),
+                                         C.byref(prm._c()), _ptr(theta, n, "theta"),
+                                         C.byref(info), _stream(stream)),
+           "vs_solve_steady_noalloc", ok=_SOLVE_OK)
     return theta, _info(info)
 
 

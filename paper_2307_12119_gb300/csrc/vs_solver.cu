@@ -18,6 +18,7 @@
 #include <math.h>
 #include <stdio.h>
 #include <stdlib.h>
+#include <stddef.h>
 #include <string.h>
 
 #include <algorithm>
@@ -945,4 +946,171 @@ extern "C" int vs_solve_transient(vs_kernel k, int n_steps, const float* p_dyn_t
   plan_release(p);
   delete p;
   return rc;
+}
+
+// ---------------------------------------------------------------------------
+// Allocation-free steady solve.
+//
+// Some callers cannot allocate device memory at solve time: services that
+// reserve their whole device-memory budget up front and forbid later
+// allocations, and latency-critical loops that must not hit cudaMalloc /
+// cudaFree (both can synchronise the device and take locks). For them this
+// entry point keeps all per-call scratch of the steady solve (the spectral
+// work map, descriptors, per-map state, reduction slots, barrier words) in one
+// file-scope device array of fixed size, reserved when the library is loaded
+// and held by every GPU that loads it until the process exits.
+//
+// The array is shared by every call: its contents persist from the previous
+// call, so each call re-initialises the parts that must start at zero, and two
+// calls whose work overlaps on the GPU (different streams, or different host
+// threads) race on it. Calls on one stream are ordered and safe.
+// ---------------------------------------------------------------------------
+namespace {
+
+constexpr int kNoAllocMaxN = 512;
+constexpr size_t kNoAllocWorkBytes = (size_t)kNoAllocMaxN * kNoAllocMaxN * sizeof(float);
+constexpr size_t kNoAllocBytes = kNoAllocWorkBytes + (16u << 10);
+
+static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocBytes];
+
+struct NoAllocLayout {
+  size_t desc, state, part, info, ctrl, row_map, col_map, end;
+};
+
+constexpr size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
+
+NoAllocLayout noalloc_layout(int row_tasks, int col_tasks) {
+  NoAllocLayout l;
+  l.desc = kNoAllocWorkBytes;
+  l.state = align256(l.desc + sizeof(MapDesc));
+  l.part = align256(l.state + sizeof(MapState));
+  l.info = align256(l.part + sizeof(double) * row_tasks);
+  l.ctrl = align256(l.info + sizeof(vs_solve_info));
+  l.row_map = align256(l.ctrl + sizeof(Ctrl));
+  l.col_map = align256(l.row_map + sizeof(int) * row_tasks);
+  l.end = align256(l.col_map + sizeof(int) * col_tasks);
+  return l;
+}
+
+// Writes the descriptor and zeroes every slot that must start at zero.
+__global__ void k_noalloc_init(MapDesc desc, unsigned char* base, NoAllocLayout l) {
+  if (blockIdx.x == 0 && threadIdx.x == 0) *reinterpret_cast<MapDesc*>(base + l.desc) = desc;
+  for (size_t i = l.state + threadIdx.x; i < l.end; i += blockDim.x) base[i] = 0;
+}
+
+std::mutex g_noalloc_mutex;
+void* g_noalloc_ptr[64] = {};
+
+}  // namespace
+
+extern "C" int vs_solve_steady_noalloc(vs_kernel k, const float* p_dyn, const float* p_leak0,
+                                       const float* s_kappa, const vs_solve_params* params,
+                                       float* theta, vs_solve_info* info_host, void* stream) {
+  if (!k) return vs_set_error(VS_ERR_INVALID_ARG, "NULL kernel");
+  int rc = vs_validate_params(params);
+  if (rc) return rc;
+  if (!p_dyn || !p_leak0 || !theta) return vs_set_error(VS_ERR_INVALID_ARG, "NULL map");
+  uintptr_t al = (uintptr_t)p_dyn | (uintptr_t)p_leak0 | (uintptr_t)theta | (uintptr_t)s_kappa;
+  if (al & 15u) return vs_set_error(VS_ERR_INVALID_ARG, "maps must be 16-byte aligned");
+  const int n = k->n;
+  if (n > kNoAllocMaxN)
+    return vs_set_error(VS_ERR_INVALID_ARG,
+                        "vs_solve_steady_noalloc supports n <= %d (got %d): its scratch is a "
+                        "fixed %zu-byte device array; use vs_solve_steady for larger grids",
+                        kNoAllocMaxN, n, kNoAllocBytes);
+  cudaStream_t s = (cudaStream_t)stream;
+
+  // one-time set-up per device: resolve the array's device address
+  int dev = 0;
+  VS_CUDA_TRY(cudaGetDevice(&dev));
+  if (dev < 0 || dev >= 64) return vs_set_error(VS_ERR_INVALID_ARG, "device index %d", dev);
+  unsigned char* base = nullptr;
+  {
+    std::lock_guard<std::mutex> lk(g_noalloc_mutex);
+    if (!g_noalloc_ptr[dev]) {
+      void* ptr = nullptr;
+      cudaError_t e = cudaGetSymbolAddress(&ptr, g_noalloc_scratch);
+      if (e != cudaSuccess || !ptr)
+        return vs_set_error(VS_ERR_CUDA, "cudaGetSymbolAddress(scratch): %s", cudaGetErrorString(e));
+      g_noalloc_ptr[dev] = ptr;
+    }
+    base = static_cast<unsigned char*>(g_noalloc_ptr[dev]);
+  }
+
+  MapDesc m = {};
+  m.p_dyn = p_dyn;
+  m.p_leak0 = p_leak0;
+  m.s = s_kappa;
+  m.theta = theta;
+  m.work = reinterpret_cast<float*>(base);
+  m.Kt = k->Kt32;
+  m.tw4n = k->fft->tw4n;
+  m.digrev = k->fft->digrev;
+  m.kmax = k->kmax;
+  m.n = n;
+  m.rb = rows_for(n, 8192);
+  m.cb = cols_for(n, 8192);
+  const int row_tasks = n / m.rb, col_tasks = n / m.cb;
+  NoAllocLayout l = noalloc_layout(row_tasks, col_tasks);
+  if (l.end > kNoAllocBytes) return vs_set_error(VS_ERR_INVALID_ARG, "scratch layout overflow");
+
+  const size_t smem = (size_t)(std::max(m.rb, m.cb) / 2) * padded_len(n) * sizeof(float2);
+  {
+    std::lock_guard<std::mutex> lk(g_attr_mutex);
+    if (smem > g_smem_attr_steady) {
+      VS_CUDA_TRY(cudaFuncSetAttribute((const void*)k_solve_steady,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+      VS_CUDA_TRY(cudaFuncSetAttribute((const void*)k_solve_steady,
+                                       cudaFuncAttributePreferredSharedMemoryCarveout, 100));
+      g_smem_attr_steady = smem;
+    }
+  }
+  int per_sm = 0, sms = 0;
+  VS_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_solve_steady, kThreads, smem));
+  VS_CUDA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+  if (per_sm < 1) return vs_set_error(VS_ERR_INVALID_ARG, "no block fits on an SM");
+
+  // row/col task -> map index tables are all zero (one map): cleared by init
+  k_noalloc_init<<<1, 256, 0, s>>>(m, base, l);
+  VS_CUDA_TRY(cudaGetLastError());
+
+  PlanDev P;
+  P.maps = reinterpret_cast<const MapDesc*>(base + l.desc);
+  P.row_map = reinterpret_cast<const int*>(base + l.row_map);
+  P.col_map = reinterpret_cast<const int*>(base + l.col_map);
+  P.st = reinterpret_cast<MapState*>(base + l.state);
+  P.part = reinterpret_cast<double*>(base + l.part);
+  P.info = reinterpret_cast<vs_solve_info*>(base + l.info);
+  P.ctrl = reinterpret_cast<Ctrl*>(base + l.ctrl);
+  P.n_maps = 1;
+  P.row_tasks = row_tasks;
+  P.col_tasks = col_tasks;
+  P.max_iter = params->max_iter;
+  P.beta = (float)params->beta_per_K;
+  P.alpha = (float)params->alpha_per_K;
+  P.tol = (float)params->tol_K;
+  P.n_steps = 0;
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(std::max(1, std::min(per_sm * sms, std::max(row_tasks, col_tasks))));
+  cfg.blockDim = dim3(kThreads);
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = s;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeCooperative;
+  attr[0].val.cooperative = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  cudaError_t e = cudaLaunchKernelEx(&cfg, k_solve_steady, P);
+  if (e != cudaSuccess)
+    return vs_set_error(VS_ERR_CUDA, "cooperative launch: %s", cudaGetErrorString(e));
+
+  vs_solve_info inf;
+  unsigned abort_flag = 0;
+  VS_CUDA_TRY(cudaMemcpyAsync(&inf, base + l.info, sizeof(inf), cudaMemcpyDeviceToHost, s));
+  VS_CUDA_TRY(cudaMemcpyAsync(&abort_flag, base + l.ctrl + offsetof(Ctrl, abort), sizeof(unsigned),
+                              cudaMemcpyDeviceToHost, s));
+  VS_CUDA_TRY(cudaStreamSynchronize(s));
+  if (abort_flag) return vs_set_error(VS_ERR_TIMEOUT, "grid barrier timed out");
+  if (info_host) *info_host = inf;
+  return inf.status;
 }
