@@ -90,14 +90,18 @@ typedef struct {
   double dt_s;
 } vs_kernel_opts;
 
-#define VS_PREC_FP32 0        /* plain FP32 fast cosine transforms */
+#define VS_PREC_FP32 0        /* FP32 fast cosine transforms (SIMT, any n) */
+#define VS_PREC_BF16_SPLIT 1  /* cosine transforms as tcgen05 tensor-core GEMMs in
+                                 BF16 hi/lo split precision with FP32 accumulation
+                                 (x = hi + lo, products hi*hi + hi*lo + lo*hi);
+                                 batched plans with n = 128 or 256 */
 
 /* Parameters of a solve.
  *   beta_per_K : temperature coefficient of leakage (Eq. 5), >= 0
  *   alpha_per_K: temperature coefficient of the Green's function (Eq. 8), >= 0
  *   tol_K      : stop when max |theta_n - theta_{n-1}| <= tol_K (> 0)
  *   max_iter   : 1 .. 1000
- *   precision  : VS_PREC_FP32 */
+ *   precision  : VS_PREC_FP32 or VS_PREC_BF16_SPLIT */
 typedef struct {
   double beta_per_K;
   double alpha_per_K;
@@ -258,6 +262,15 @@ int vs_solve_transient(vs_kernel k, int n_steps, const float* p_dyn_trace,
                        const float* p_leak0, const float* s_kappa,
                        const vs_solve_params* params, float* theta_trace,
                        vs_solve_info* info_host, void* stream);
+
+/* Split-precision tensor-core transform (the building block of
+ * VS_PREC_BF16_SPLIT), exposed for testing: for each of `rows` rows,
+ *   out[r][j] = sum_k in[r][k] C[j][k],  C[j][k] = cos(pi j (2k+1) / 2n)
+ * (forward DCT-II of Sec. III-G's mirror-imaged rows) or, with inverse != 0,
+ *   out[r][j] = sum_k in[r][k] w_k cos(pi k (2j+1) / 2n) / n, w_0 = 1, w_k = 2
+ * (its exact inverse). in/out: device float32 [rows][n], rows a multiple of
+ * 128, n = 128 or 256, 16-byte aligned. Asynchronous on `stream`. */
+int vs_tc_transform(const float* in, float* out, int rows, int n, int inverse, void* stream);
 
 /* ------------------------------------------------------------------------ */
 

@@ -21,10 +21,12 @@ __all__ = [
     "VS_ERR_RUNAWAY", "VS_ERR_NONFINITE", "VS_ERR_TIMEOUT", "VarsimError", "Stack", "Grid",
     "KernelOpts", "SolveParams", "Kernel", "Plan", "lib", "lib_path", "solve_steady",
     "solve_batch", "solve_transient", "hankel_radial", "EXPORTS", "solve_steady_noalloc",
+    "tc_transform", "VS_PREC_FP32", "VS_PREC_BF16_SPLIT",
 ]
 
 VS_OK, VS_ERR_INVALID_ARG, VS_ERR_CUDA, VS_ERR_OOM = 0, 1, 2, 3
 VS_ERR_NO_CONVERGENCE, VS_ERR_RUNAWAY, VS_ERR_NONFINITE, VS_ERR_TIMEOUT = 4, 5, 6, 7
+VS_PREC_FP32, VS_PREC_BF16_SPLIT = 0, 1
 VS_MAX_LAYERS = 8
 
 EXPORTS = [
@@ -32,6 +34,7 @@ EXPORTS = [
     "vs_hankel_radial", "vs_solve_steady", "vs_plan_create", "vs_plan_run", "vs_plan_info",
     "vs_plan_launches", "vs_plan_free", "vs_solve_batch", "vs_solve_transient",
     "vs_status_string", "vs_last_error", "vs_version", "vs_solve_steady_noalloc",
+    "vs_tc_transform",
 ]
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
@@ -112,6 +115,7 @@ def lib():
                                 C.POINTER(_SolveInfo), vp]),
         "vs_solve_transient": (ip, [vp, ip, vp, vp, vp, C.POINTER(_SolveParams), vp,
                                     C.POINTER(_SolveInfo), vp]),
+        "vs_tc_transform": (ip, [vp, vp, ip, ip, ip, vp]),
         "vs_status_string": (C.c_char_p, [ip]),
         "vs_last_error": (C.c_char_p, []),
         "vs_version": (C.c_char_p, []),
@@ -283,6 +287,18 @@ def solve_steady(kernel: Kernel, p_dyn, p_leak0, s_kappa=None, params: Optional[
                                  _ptr(theta, n, "theta"), C.byref(info), _stream(stream)),
            "vs_solve_steady", ok=_SOLVE_OK)
     return theta, _info(info)
+
+
+def tc_transform(x, inverse: bool = False, stream=None):
+    """Split-precision tensor-core DCT-II (or its inverse) along the last axis
+    of a float32 CUDA tensor [rows, n] (vs_tc_transform)."""
+    import torch
+    n = x.shape[-1]
+    rows = x.numel() // n
+    out = torch.empty_like(x)
+    _check(lib().vs_tc_transform(_ptr(x, None, "x"), out.data_ptr(), rows, n, int(inverse),
+                                 _stream(stream)), "vs_tc_transform")
+    return out
 
 
 def solve_steady_noalloc(kernel: Kernel, p_dyn, p_leak0, s_kappa=None,

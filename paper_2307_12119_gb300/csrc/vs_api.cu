@@ -70,7 +70,7 @@ int vs_validate_params(const vs_solve_params* p) {
   if (!pos_finite(p->tol_K)) return vs_set_error(VS_ERR_INVALID_ARG, "tol must be > 0");
   if (p->max_iter < 1 || p->max_iter > 1000)
     return vs_set_error(VS_ERR_INVALID_ARG, "max_iter %d outside [1, 1000]", p->max_iter);
-  if (p->precision != VS_PREC_FP32)
+  if (p->precision != VS_PREC_FP32 && p->precision != VS_PREC_BF16_SPLIT)
     return vs_set_error(VS_ERR_INVALID_ARG, "unknown precision %d", p->precision);
   return VS_OK;
 }

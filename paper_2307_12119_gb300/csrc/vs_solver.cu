@@ -29,6 +29,7 @@
 
 #include "vs_fft.cuh"
 #include "vs_internal.cuh"
+#include "vs_tc.cuh"
 
 using namespace vsfft;
 
@@ -53,6 +54,9 @@ struct MapDesc {
   const float* trA;      // transient only
   const float* trRho;
   float* state;          // transient per-mode state, n*n
+  float* work2;          // second scratch map (tensor-core path)
+  const uint8_t* tcf;    // pre-tiled forward DCT matrix, BF16 hi/lo (tensor-core path)
+  const uint8_t* tci;    // pre-tiled inverse DCT matrix
   float kmax;
   int n, rb, cb;
   int row_off, col_off, part_off;
@@ -514,6 +518,360 @@ __global__ void k_twiddles(int n, float2* tw) {
   tw[e] = make_float2((float)cs, (float)sn);
 }
 
+// ------------------------------------------------------------ tensor-core path
+// Split-precision cosine transforms on tcgen05 (BF16 hi/lo, FP32 accumulate).
+// One 1-D transform of 128 rows of a map is a GEMM D[128][N] = A[128][K] B^T
+// with K = N = n: A = map data (split x = hi + lo on the fly), B = the DCT
+// matrix (hi/lo pre-split, pre-tiled in core-matrix order). Three MMAs per
+// K-step: A_hi B_hi + A_hi B_lo + A_lo B_hi (the lo*lo term, ~2^-16 relative,
+// is dropped). Per iteration four passes (rows fwd, columns fwd, columns inv,
+// rows inv) with the spectral multiply and the leakage/conductivity update in
+// the epilogues; the fixed-point control is the same as the SIMT path.
+
+constexpr int kTcChunkK = 64;
+constexpr int kTcStageBytes = 96 * 1024;      // A hi/lo 2x16 KB + B hi/lo 2x32 KB
+constexpr long long kTcWaitLimit = 20000000LL;
+
+struct TcSmem {
+  uint8_t stage[2][kTcStageBytes];
+  uint64_t full[2];
+  uint64_t done[2];
+  uint64_t fin;
+  uint32_t tmem_base;
+  uint32_t err;
+};
+
+struct TcCtx {
+  TcSmem* sm;
+  uint32_t tmem;
+  int uses[2];
+  int chunk;
+  int fin_uses;
+};
+
+enum TcPass { kTcRowFwdFirst = 0, kTcRowFwd = 1, kTcColFwd = 2, kTcColInv = 3, kTcRowInv = 4 };
+
+// Producer: A chunk [128 rows][64 k] from G. Non-transposed: A[m][k] =
+// G[(row0 + m) * ld + k0 + k]. Transposed: A[m][k] = G[(k0 + k) * ld + col0 + m].
+__device__ __forceinline__ void tc_produce(uint8_t* st, const float* G, int ld, int row0, int k0,
+                                           bool transposed, const float* G2) {
+  uint8_t* hi = st;
+  uint8_t* lo = st + 16 * 1024;
+  if (!transposed) {
+    for (int i = threadIdx.x; i < 2048; i += blockDim.x) {
+      int kk = i >> 8, rem = i & 255, m = rem >> 1, h = rem & 1;
+      int k = kk * 8 + h * 4;
+      size_t g = (size_t)(row0 + m) * ld + k0 + k;
+      float4 v = *reinterpret_cast<const float4*>(G + g);
+      if (G2) {                               // first source: P_dyn + P_leak0
+        float4 w = __ldg(reinterpret_cast<const float4*>(G2 + g));
+        v.x += w.x; v.y += w.y; v.z += w.z; v.w += w.w;
+      }
+      __nv_bfloat16 h0, h1, h2, h3, l0, l1, l2, l3;
+      vstc::split_bf16(v.x, h0, l0);
+      vstc::split_bf16(v.y, h1, l1);
+      vstc::split_bf16(v.z, h2, l2);
+      vstc::split_bf16(v.w, h3, l3);
+      uint32_t off = vstc::core_off(m, k, kTcChunkK);
+      __nv_bfloat162 a = __halves2bfloat162(h0, h1), b = __halves2bfloat162(h2, h3);
+      __nv_bfloat162 c = __halves2bfloat162(l0, l1), d = __halves2bfloat162(l2, l3);
+      uint2 uh = make_uint2(*reinterpret_cast<uint32_t*>(&a), *reinterpret_cast<uint32_t*>(&b));
+      uint2 ul = make_uint2(*reinterpret_cast<uint32_t*>(&c), *reinterpret_cast<uint32_t*>(&d));
+      *reinterpret_cast<uint2*>(hi + off) = uh;
+      *reinterpret_cast<uint2*>(lo + off) = ul;
+    }
+  } else {
+    for (int i = threadIdx.x; i < 1024; i += blockDim.x) {
+      int kp = i >> 5, mq = i & 31;           // k pair, m quad
+      int k = 2 * kp, m = 4 * mq;
+      float4 r0 = *reinterpret_cast<const float4*>(G + (size_t)(k0 + k) * ld + row0 + m);
+      float4 r1 = *reinterpret_cast<const float4*>(G + (size_t)(k0 + k + 1) * ld + row0 + m);
+      float a0[4] = {r0.x, r0.y, r0.z, r0.w}, a1[4] = {r1.x, r1.y, r1.z, r1.w};
+#pragma unroll
+      for (int j = 0; j < 4; ++j) {
+        __nv_bfloat16 h0, l0, h1, l1;
+        vstc::split_bf16(a0[j], h0, l0);
+        vstc::split_bf16(a1[j], h1, l1);
+        uint32_t off = vstc::core_off(m + j, k, kTcChunkK);
+        __nv_bfloat162 ph = __halves2bfloat162(h0, h1), pl = __halves2bfloat162(l0, l1);
+        *reinterpret_cast<__nv_bfloat162*>(hi + off) = ph;
+        *reinterpret_cast<__nv_bfloat162*>(lo + off) = pl;
+      }
+    }
+  }
+}
+
+// One 128-row GEMM into TMEM columns [0, N). Returns false on a wait timeout.
+__device__ bool tc_gemm(TcCtx& c, int N, const uint8_t* Bg, const float* G, int ld, int row0,
+                        bool transposed, const float* G2) {
+  const int nk = N / kTcChunkK;
+  const uint32_t idesc = vstc::idesc_bf16(128, N);
+  const uint32_t bbytes = (uint32_t)N * kTcChunkK * 2;     // one of hi / lo
+  for (int kc = 0; kc < nk; ++kc) {
+    const int s = c.chunk & 1;
+    if (c.uses[s] > 0 && !vstc::mbar_wait(&c.sm->done[s], (c.uses[s] - 1) & 1, kTcWaitLimit))
+      return false;
+    uint8_t* st = c.sm->stage[s];
+    if (threadIdx.x == 0) {
+      vstc::mbar_arrive_expect_tx(&c.sm->full[s], 2 * bbytes);
+      const uint8_t* src = Bg + (size_t)kc * 2 * bbytes;
+      vstc::bulk_g2s(st + 32 * 1024, src, bbytes, &c.sm->full[s]);            // B hi
+      vstc::bulk_g2s(st + 32 * 1024 + bbytes, src + bbytes, bbytes, &c.sm->full[s]);  // B lo
+    }
+    tc_produce(st, G, ld, row0, kc * kTcChunkK, transposed, G2);
+    vstc::fence_proxy_async_smem();
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      bool landed = vstc::mbar_wait(&c.sm->full[s], c.uses[s] & 1, kTcWaitLimit);
+      vstc::tc_fence_after();
+      if (landed) {
+        const uint32_t a0 = vstc::smem_u32(st), b0 = vstc::smem_u32(st + 32 * 1024);
+        const uint32_t sbo_a = (kTcChunkK / 8) * 128, sbo_b = sbo_a;
+#pragma unroll
+        for (int ks = 0; ks < kTcChunkK / 16; ++ks) {
+          const uint32_t o = ks * 256;
+          uint64_t ah = vstc::smem_desc(a0 + o, 128, sbo_a);
+          uint64_t al = vstc::smem_desc(a0 + 16 * 1024 + o, 128, sbo_a);
+          uint64_t bh = vstc::smem_desc(b0 + o, 128, sbo_b);
+          uint64_t bl = vstc::smem_desc(b0 + bbytes + o, 128, sbo_b);
+          vstc::mma_bf16(c.tmem, ah, bh, idesc, (kc > 0 || ks > 0) ? 1u : 0u);
+          vstc::mma_bf16(c.tmem, ah, bl, idesc, 1u);
+          vstc::mma_bf16(c.tmem, al, bh, idesc, 1u);
+        }
+      } else {
+        c.sm->err = 1u;
+      }
+      vstc::mma_commit(&c.sm->done[s]);
+    }
+    c.uses[s]++;
+    c.chunk++;
+  }
+  const int sl = (c.chunk - 1) & 1;
+  bool ok = vstc::mbar_wait(&c.sm->done[sl], (c.uses[sl] - 1) & 1, kTcWaitLimit);
+  vstc::tc_fence_after();
+  __syncthreads();
+  return ok && c.sm->err == 0u;
+}
+
+// Epilogue traversal: warp w reads TMEM lanes 32 (w % 4) .. + 31 (tile rows)
+// and half (w / 4) of the N columns, 32 columns at a time.
+template <class Op>
+__device__ __forceinline__ void tc_epilogue(const TcCtx& c, int N, Op op) {
+  const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int m = 32 * (w & 3) + lane;
+  const int half = N >> 1;
+  for (int c0 = (w >> 2) * half; c0 < (w >> 2) * half + half; c0 += 32) {
+    float v[32];
+    vstc::tmem_ld32(c.tmem + ((uint32_t)(32 * (w & 3)) << 16) + (uint32_t)c0, v);
+    op(m, c0, v);
+  }
+}
+
+__device__ __forceinline__ void store32(float* dst, const float* v) {
+#pragma unroll
+  for (int i = 0; i < 32; i += 4)
+    *reinterpret_cast<float4*>(dst + i) = make_float4(v[i], v[i + 1], v[i + 2], v[i + 3]);
+}
+
+// One task of a pass: rows [row0, row0+128) of map b.
+__device__ bool tc_task(const PlanDev& P, TcCtx& c, int pass, int task) {
+  __shared__ double red_d[8];
+  __shared__ float red_f[8];
+  __shared__ int red_i[8];
+  const int b = __ldg(&P.row_map[task]);
+  const MapDesc d = P.maps[b];
+  MapState* ms = P.st + b;
+  const bool first = pass == kTcRowFwdFirst;
+  if (!first && !ms->active) return true;
+  const int n = d.n;
+  const int tile = task - d.row_off;
+  const int r0 = tile * 128;
+  bool ok = true;
+  double mu_acc = 0.0;
+  float resid = 0.f;
+  int flags = 0;
+  if (pass == kTcRowFwdFirst || pass == kTcRowFwd) {
+    // rows forward: A[y][x] = q (first: P_dyn + P_leak0), B = C -> R[y][p] in work
+    if (first) ok = tc_gemm(c, n, d.tcf, d.p_dyn, n, r0, false, d.p_leak0);
+    else ok = tc_gemm(c, n, d.tcf, d.work2, n, r0, false, nullptr);
+    tc_epilogue(c, n, [&](int m, int c0, float* v) {
+      size_t row = (size_t)(r0 + m) * n + c0;
+      store32(d.work + row, v);
+      if (first) {
+#pragma unroll
+        for (int i = 0; i < 32; ++i) {
+          d.theta[row + i] = 0.f;
+          mu_acc += (double)__ldg(&d.p_leak0[row + i]);
+        }
+      }
+    });
+  } else if (pass == kTcColFwd) {
+    // columns forward: A[p][y] = R[y][p] (transposed), B = C -> X[p][q]; x K/(1-beta mu K)
+    ok = tc_gemm(c, n, d.tcf, d.work, n, r0, true, nullptr);
+    const float bm = P.beta * ms->mu_f;
+    tc_epilogue(c, n, [&](int m, int c0, float* v) {
+      size_t row = (size_t)(r0 + m) * n + c0;
+#pragma unroll
+      for (int i = 0; i < 32; ++i) {
+        float k = __ldg(&d.Kt[row + i]);
+        v[i] = v[i] * k / (1.f - bm * k);
+      }
+      store32(d.work2 + row, v);
+    });
+  } else if (pass == kTcColInv) {
+    // columns inverse: A[p][q] = Y, B = Ci -> ZT[p][y]
+    ok = tc_gemm(c, n, d.tci, d.work2, n, r0, false, nullptr);
+    tc_epilogue(c, n, [&](int m, int c0, float* v) { store32(d.work + (size_t)(r0 + m) * n + c0, v); });
+  } else {
+    // rows inverse: A[y][p] = ZT[p][y] (transposed), B = Ci -> u[y][x]; fused update
+    ok = tc_gemm(c, n, d.tci, d.work, n, r0, true, nullptr);
+    const float beta = P.beta, alpha = P.alpha, mu = ms->mu_f;
+    tc_epilogue(c, n, [&](int m, int c0, float* v) {
+      size_t row = (size_t)(r0 + m) * n + c0;
+      float q[32];
+#pragma unroll
+      for (int i = 0; i < 32; i += 4) {
+        float4 pd = __ldg(reinterpret_cast<const float4*>(d.p_dyn + row + i));
+        float4 pl = __ldg(reinterpret_cast<const float4*>(d.p_leak0 + row + i));
+        float4 sk = d.s ? __ldg(reinterpret_cast<const float4*>(d.s + row + i))
+                        : make_float4(1.f, 1.f, 1.f, 1.f);
+        float4 old = *reinterpret_cast<const float4*>(d.theta + row + i);
+        float pda[4] = {pd.x, pd.y, pd.z, pd.w}, pla[4] = {pl.x, pl.y, pl.z, pl.w};
+        float ska[4] = {sk.x, sk.y, sk.z, sk.w}, olda[4] = {old.x, old.y, old.z, old.w};
+        float th4[4];
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+          float u = v[i + j];
+          float den = fmaf(-alpha * ska[j], u, 1.f);
+          if (!(den > 0.05f)) flags |= kFlagRunaway;
+          float th = ska[j] * u / den;
+          if (!isfinite(th)) flags |= kFlagNonfinite;
+          else resid = fmaxf(resid, fabsf(th - olda[j]));
+          th4[j] = th;
+          q[i + j] = pda[j] + pla[j] + beta * fmaf(pla[j], th, -mu * u);
+        }
+        *reinterpret_cast<float4*>(d.theta + row + i) = make_float4(th4[0], th4[1], th4[2], th4[3]);
+      }
+      store32(d.work2 + row, q);
+    });
+  }
+  vstc::tc_fence_before();
+  if (first) {
+    double tot = block_sum(mu_acc, red_d);
+    if (threadIdx.x == 0) P.part[d.part_off + tile] = tot;
+  } else if (pass == kTcRowInv) {
+    float r = block_max(resid, red_f);
+    int fl = block_or(flags, red_i);
+    if (threadIdx.x == 0) {
+      if (r > 0.f) atomicMax(&ms->resid_bits, __float_as_uint(r));
+      if (fl) atomicOr(&ms->flags, fl);
+    }
+  }
+  __syncthreads();
+  return ok;
+}
+
+__device__ void tc_finish(TcCtx& c) {
+  // wait (bounded) for every tcgen05 op issued by thread 0, then free TMEM
+  if (threadIdx.x == 0) {
+    vstc::mma_commit(&c.sm->fin);
+    vstc::mbar_wait(&c.sm->fin, c.fin_uses & 1, kTcWaitLimit);
+  }
+  c.fin_uses++;
+  vstc::tc_fence_before();
+  __syncthreads();
+  vstc::tc_fence_after();
+  if ((threadIdx.x >> 5) == 0) vstc::tmem_dealloc(c.tmem, 256);
+}
+
+__global__ void __launch_bounds__(kThreads, 1) k_solve_steady_tc(PlanDev P) {
+  extern __shared__ __align__(1024) uint8_t tc_smem_raw[];
+  TcSmem* sm = reinterpret_cast<TcSmem*>(
+      (reinterpret_cast<uintptr_t>(tc_smem_raw) + 1023) & ~(uintptr_t)1023);
+  if (threadIdx.x == 0) {
+    vstc::mbar_init(&sm->full[0], 1);
+    vstc::mbar_init(&sm->full[1], 1);
+    vstc::mbar_init(&sm->done[0], 1);
+    vstc::mbar_init(&sm->done[1], 1);
+    vstc::mbar_init(&sm->fin, 1);
+    vstc::mbar_fence_init();
+    sm->err = 0u;
+  }
+  if ((threadIdx.x >> 5) == 0) vstc::tmem_alloc(&sm->tmem_base, 256);
+  vstc::tc_fence_before();
+  __syncthreads();
+  vstc::tc_fence_after();
+  TcCtx c;
+  c.sm = sm;
+  c.tmem = sm->tmem_base;
+  c.uses[0] = c.uses[1] = 0;
+  c.chunk = 0;
+  c.fin_uses = 0;
+  bool alive = true;
+  auto pass_all = [&](int pass) {
+    for (int t = blockIdx.x; t < P.row_tasks && alive; t += gridDim.x)
+      if (!tc_task(P, c, pass, t)) {
+        atomicExch(&P.ctrl->abort, 1u);
+        alive = false;
+      }
+  };
+  pass_all(kTcRowFwdFirst);
+  if (alive) alive = grid_barrier(P.ctrl);
+  if (alive) decide(P, 0);
+  if (alive) alive = grid_barrier(P.ctrl);
+  if (alive && ld_acquire(&P.ctrl->active[0]) != 0u) {
+    for (int it = 1; it <= P.max_iter && alive; ++it) {
+      pass_all(kTcColFwd);
+      if (alive) alive = grid_barrier(P.ctrl);
+      if (alive) pass_all(kTcColInv);
+      if (alive) alive = grid_barrier(P.ctrl);
+      if (alive) pass_all(kTcRowInv);
+      if (alive) alive = grid_barrier(P.ctrl);
+      if (alive) decide(P, it);
+      if (alive) alive = grid_barrier(P.ctrl);
+      if (!alive || ld_acquire(&P.ctrl->active[it]) == 0u) break;
+      pass_all(kTcRowFwd);
+      if (alive) alive = grid_barrier(P.ctrl);
+    }
+  }
+  tc_finish(c);
+}
+
+// Standalone split-precision transform (for testing the building block):
+// out[r][j] = sum_k in[r][k] T[j][k], T = forward or inverse DCT matrix.
+__global__ void __launch_bounds__(kThreads, 1) k_tc_transform(const float* in, float* out, int rows,
+                                                              int n, const uint8_t* Bg) {
+  extern __shared__ __align__(1024) uint8_t tc_smem_raw[];
+  TcSmem* sm = reinterpret_cast<TcSmem*>(
+      (reinterpret_cast<uintptr_t>(tc_smem_raw) + 1023) & ~(uintptr_t)1023);
+  if (threadIdx.x == 0) {
+    vstc::mbar_init(&sm->full[0], 1);
+    vstc::mbar_init(&sm->full[1], 1);
+    vstc::mbar_init(&sm->done[0], 1);
+    vstc::mbar_init(&sm->done[1], 1);
+    vstc::mbar_init(&sm->fin, 1);
+    vstc::mbar_fence_init();
+    sm->err = 0u;
+  }
+  if ((threadIdx.x >> 5) == 0) vstc::tmem_alloc(&sm->tmem_base, 256);
+  vstc::tc_fence_before();
+  __syncthreads();
+  vstc::tc_fence_after();
+  TcCtx c;
+  c.sm = sm;
+  c.tmem = sm->tmem_base;
+  c.uses[0] = c.uses[1] = 0;
+  c.chunk = 0;
+  c.fin_uses = 0;
+  for (int t = blockIdx.x; t < rows / 128; t += gridDim.x) {
+    if (!tc_gemm(c, n, Bg, in, n, t * 128, false, nullptr)) break;
+    tc_epilogue(c, n, [&](int m, int c0, float* v) { store32(out + (size_t)(t * 128 + m) * n + c0, v); });
+    vstc::tc_fence_before();
+    __syncthreads();
+  }
+  tc_finish(c);
+}
+
 // ------------------------------------------------------------ host side
 
 std::vector<int> host_digrev(int n) {
@@ -539,6 +897,75 @@ std::vector<int> host_digrev(int n) {
 
 std::mutex g_fft_mutex;
 std::map<std::pair<int, int>, vs_fft_tables*> g_fft;
+
+// ---- pre-split, pre-tiled DCT matrices for the tensor-core path
+uint16_t host_bf16(double x) {
+  float f = (float)x;
+  uint32_t u;
+  memcpy(&u, &f, 4);
+  u += 0x7FFFu + ((u >> 16) & 1u);          // round to nearest even
+  return (uint16_t)(u >> 16);
+}
+double host_bf16_val(uint16_t h) {
+  uint32_t u = (uint32_t)h << 16;
+  float f;
+  memcpy(&f, &u, 4);
+  return (double)f;
+}
+
+struct TcMats {
+  uint8_t* fwd = nullptr;    // B[j][k] = cos(pi j (2k+1) / 2n)
+  uint8_t* inv = nullptr;    // B[j][k] = w_k cos(pi k (2j+1) / 2n) / n
+};
+std::mutex g_tc_mutex;
+std::map<std::pair<int, int>, TcMats> g_tc;
+
+// Layout per K-chunk of 64: [hi: n x 64 core-matrix order][lo: same].
+std::vector<uint8_t> tile_matrix(int n, bool inverse) {
+  const double pi = 3.141592653589793238462643383279502884;
+  const int nk = n / kTcChunkK;
+  const size_t half = (size_t)n * kTcChunkK * 2;
+  std::vector<uint8_t> out((size_t)nk * 2 * half, 0);
+  for (int j = 0; j < n; ++j)
+    for (int k = 0; k < n; ++k) {
+      double v = inverse ? (k == 0 ? 1.0 : 2.0) * cos(pi * k * (2.0 * j + 1.0) / (2.0 * n)) / n
+                         : cos(pi * j * (2.0 * k + 1.0) / (2.0 * n));
+      uint16_t hi = host_bf16(v);
+      uint16_t lo = host_bf16(v - host_bf16_val(hi));
+      int kc = k / kTcChunkK;
+      size_t off = (size_t)kc * 2 * half + vstc::core_off(j, k % kTcChunkK, kTcChunkK);
+      memcpy(&out[off], &hi, 2);
+      memcpy(&out[off + half], &lo, 2);
+    }
+  return out;
+}
+
+const TcMats* get_tc_mats(int n, int* status) {
+  int dev = 0;
+  cudaGetDevice(&dev);
+  std::lock_guard<std::mutex> lk(g_tc_mutex);
+  auto key = std::make_pair(dev, n);
+  auto it = g_tc.find(key);
+  if (it != g_tc.end()) return &it->second;
+  TcMats m;
+  std::vector<uint8_t> f = tile_matrix(n, false), iv = tile_matrix(n, true);
+  cudaError_t e = cudaMalloc(&m.fwd, f.size());
+  if (e == cudaSuccess) e = cudaMalloc(&m.inv, iv.size());
+  if (e == cudaSuccess) e = cudaMemcpy(m.fwd, f.data(), f.size(), cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = cudaMemcpy(m.inv, iv.data(), iv.size(), cudaMemcpyHostToDevice);
+  if (e != cudaSuccess) {
+    cudaFree(m.fwd);
+    cudaFree(m.inv);
+    *status = vs_set_error(e == cudaErrorMemoryAllocation ? VS_ERR_OOM : VS_ERR_CUDA,
+                           "tensor-core matrices n=%d: %s", n, cudaGetErrorString(e));
+    return nullptr;
+  }
+  g_tc[key] = m;
+  return &g_tc[key];
+}
+
+bool tc_size_ok(int n) { return n == 128 || n == 256; }
+constexpr size_t kTcSmemBytes = sizeof(TcSmem) + 1024;
 
 struct TaskShape {
   int elems;   // target elements per task
@@ -638,11 +1065,19 @@ int plan_layout(vs_plan_t* p, int elems, cudaStream_t s, bool transient, int n_s
   size_t work_total = 0;
   int row_off = 0, col_off = 0, part_off = 0;
   size_t smem = 0;
+  const bool tc = p->params.precision == VS_PREC_BF16_SPLIT;
   for (int i = 0; i < n_items; ++i) {
     const vs_batch_item& it = p->items[i];
     vs_kernel k = it.k;
     int n = k->n;
     MapDesc& m = maps[i];
+    if (tc) {
+      int st = VS_OK;
+      const TcMats* tm = get_tc_mats(n, &st);
+      if (!tm) return st;
+      m.tcf = tm->fwd;
+      m.tci = tm->inv;
+    }
     m.p_dyn = it.p_dyn;
     m.p_leak0 = it.p_leak0;
     m.s = it.s_kappa;
@@ -654,16 +1089,16 @@ int plan_layout(vs_plan_t* p, int elems, cudaStream_t s, bool transient, int n_s
     m.trRho = k->trRho;
     m.kmax = k->kmax;
     m.n = n;
-    m.rb = rows_for(n, elems);
-    m.cb = cols_for(n, elems);
+    m.rb = tc ? 128 : rows_for(n, elems);
+    m.cb = tc ? 128 : cols_for(n, elems);
     m.row_off = row_off;
     m.col_off = col_off;
     m.part_off = part_off;
     row_off += n / m.rb;
     col_off += n / m.cb;
     part_off += n / m.rb;
-    work_total += (size_t)n * n;
-    size_t sm = (size_t)(std::max(m.rb, m.cb) / 2) * padded_len(n) * sizeof(float2);
+    work_total += (size_t)n * n * (tc ? 2 : 1);
+    size_t sm = tc ? kTcSmemBytes : (size_t)(std::max(m.rb, m.cb) / 2) * padded_len(n) * sizeof(float2);
     smem = std::max(smem, sm);
   }
   p->row_tasks = row_off;
@@ -677,6 +1112,10 @@ int plan_layout(vs_plan_t* p, int elems, cudaStream_t s, bool transient, int n_s
     maps[i].work = p->d_work + off;
     maps[i].state = transient ? p->d_trstate + off : nullptr;
     off += (size_t)maps[i].n * maps[i].n;
+    if (tc) {
+      maps[i].work2 = p->d_work + off;
+      off += (size_t)maps[i].n * maps[i].n;
+    }
   }
   VS_CUDA_TRY(cudaMalloc(&p->d_maps, sizeof(MapDesc) * n_items));
   VS_CUDA_TRY(cudaMalloc(&p->d_state, sizeof(MapState) * n_items));
@@ -698,8 +1137,12 @@ int plan_layout(vs_plan_t* p, int elems, cudaStream_t s, bool transient, int n_s
                               cudaMemcpyHostToDevice, s));
   VS_CUDA_TRY(cudaMemsetAsync(p->d_info, 0, sizeof(vs_solve_info) * n_items, s));
 
-  auto fn = transient ? (const void*)k_solve_transient : (const void*)k_solve_steady;
-  {
+  auto fn = transient ? (const void*)k_solve_transient
+            : tc      ? (const void*)k_solve_steady_tc
+                      : (const void*)k_solve_steady;
+  if (tc) {
+    VS_CUDA_TRY(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  } else {
     // Function attributes are process-wide: only ever raise the limit, so a
     // plan with a smaller footprint never invalidates a larger one.
     std::lock_guard<std::mutex> lk(g_attr_mutex);
@@ -753,7 +1196,9 @@ int plan_launch(vs_plan_t* p, cudaStream_t s, bool transient) {
   cfg.attrs = attr;
   cfg.numAttrs = 1;
   cudaError_t e = transient ? cudaLaunchKernelEx(&cfg, k_solve_transient, P)
-                            : cudaLaunchKernelEx(&cfg, k_solve_steady, P);
+                  : p->params.precision == VS_PREC_BF16_SPLIT
+                      ? cudaLaunchKernelEx(&cfg, k_solve_steady_tc, P)
+                      : cudaLaunchKernelEx(&cfg, k_solve_steady, P);
   if (e != cudaSuccess)
     return vs_set_error(VS_ERR_CUDA, "cooperative launch (grid %d, smem %zu): %s", p->grid,
                         p->smem, cudaGetErrorString(e));
@@ -801,6 +1246,10 @@ extern "C" int vs_plan_create(const vs_batch_item* items_host, int n_items,
     uintptr_t al = (uintptr_t)it.p_dyn | (uintptr_t)it.p_leak0 | (uintptr_t)it.theta |
                    (uintptr_t)it.s_kappa;
     if (al & 15u) return vs_set_error(VS_ERR_INVALID_ARG, "item %d: maps must be 16-byte aligned", i);
+    if (params->precision == VS_PREC_BF16_SPLIT && !tc_size_ok(it.k->n))
+      return vs_set_error(VS_ERR_INVALID_ARG,
+                          "item %d: the BF16 split tensor-core path supports n = 128 or 256 (got %d)",
+                          i, it.k->n);
   }
   cudaStream_t s = (cudaStream_t)stream;
   vs_plan_t* p = new vs_plan_t();
@@ -815,7 +1264,7 @@ extern "C" int vs_plan_create(const vs_batch_item* items_host, int n_items,
   key.erase(std::unique(key.begin(), key.end()), key.end());
   key.push_back(n_items >= 256 ? 1 : 0);
   int elems = 8192;
-  bool tune = n_items >= 64;
+  bool tune = n_items >= 64 && params->precision == VS_PREC_FP32;
   const char* env = getenv("VS_AUTOTUNE");
   if (env && env[0] == '0') tune = false;
   {
@@ -1113,4 +1562,25 @@ extern "C" int vs_solve_steady_noalloc(vs_kernel k, const float* p_dyn, const fl
   if (abort_flag) return vs_set_error(VS_ERR_TIMEOUT, "grid barrier timed out");
   if (info_host) *info_host = inf;
   return inf.status;
+}
+
+extern "C" int vs_tc_transform(const float* in, float* out, int rows, int n, int inverse,
+                               void* stream) {
+  if (!in || !out) return vs_set_error(VS_ERR_INVALID_ARG, "NULL array");
+  if (!tc_size_ok(n)) return vs_set_error(VS_ERR_INVALID_ARG, "n must be 128 or 256 (got %d)", n);
+  if (rows <= 0 || rows % 128) return vs_set_error(VS_ERR_INVALID_ARG, "rows must be a positive multiple of 128");
+  if (((uintptr_t)in | (uintptr_t)out) & 15u) return vs_set_error(VS_ERR_INVALID_ARG, "arrays must be 16-byte aligned");
+  int st = VS_OK;
+  const TcMats* tm = get_tc_mats(n, &st);
+  if (!tm) return st;
+  VS_CUDA_TRY(cudaFuncSetAttribute((const void*)k_tc_transform,
+                                   cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kTcSmemBytes));
+  int dev = 0, sms = 0;
+  VS_CUDA_TRY(cudaGetDevice(&dev));
+  VS_CUDA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+  int grid = std::max(1, std::min(sms, rows / 128));
+  k_tc_transform<<<grid, kThreads, kTcSmemBytes, (cudaStream_t)stream>>>(
+      in, out, rows, n, inverse ? tm->inv : tm->fwd);
+  VS_CUDA_TRY(cudaGetLastError());
+  return VS_OK;
 }
