@@ -2,8 +2,11 @@
 
 One step = one run of the whole steady hot path (mean leakage reduction,
 shift-invariant modified kernel, mirror-image cosine-basis convolution,
-fused leakage/conductivity update, fixed point iterated to 1e-4 K per map)
-over a batch of maps already resident in device memory. Inputs (3 GiB for
+fused leakage/conductivity update, fixed point iterated per map to its
+tolerance) over a batch of maps already resident in device memory. The
+chosen path runs the cosine transforms as BF16 hi/lo split-precision tcgen05
+GEMMs; the FP32 SIMT path and the one-map-per-call plain path are timed on
+the same batch for comparison. Inputs (3 GiB for
 4096 maps) are larger than the 129 MB L2, so no flush is needed between steps.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
@@ -137,7 +140,7 @@ class Clocks:
                 "samples": len(rows)}
 
 
-def cpu_oracle_leg(w, pd, pl, s, gpu_theta, seconds: float):
+def cpu_oracle_leg(w, pd, pl, s, gpu_theta, seconds: float, other=None):
     """Times the FP64 oracle (as it stands) on the host cores over the first
     maps of the same batch, and compares the GPU results of those maps with it.
     The oracle's Green's-function build is done once, outside the timed
@@ -149,6 +152,7 @@ def cpu_oracle_leg(w, pd, pl, s, gpu_theta, seconds: float):
     Kt = ph.spectrum(w.n, w.die_m, st.thickness_m, st.kappa_W_mK, st.h_conv_W_m2K)
     f64 = lambda t: t.double().cpu().numpy()
     done, worst, rel_worst = 0, 0.0, 0.0
+    worst2, rel2 = 0.0, 0.0
     t0 = time.perf_counter()
     elapsed = 0.0
     while done < pd.shape[0] and (done < 2 or elapsed < seconds):
@@ -161,12 +165,17 @@ def cpu_oracle_leg(w, pd, pl, s, gpu_theta, seconds: float):
             d = f64(gpu_theta[done]) - ref
             worst = max(worst, float(np.max(np.abs(d))))
             rel_worst = max(rel_worst, float(np.linalg.norm(d) / np.linalg.norm(ref)))
+        if other is not None:
+            d2 = f64(other[done]) - ref
+            worst2 = max(worst2, float(np.max(np.abs(d2))))
+            rel2 = max(rel2, float(np.linalg.norm(d2) / np.linalg.norm(ref)))
         done += 1
     cores = len(os.sched_getaffinity(0))
     return {"value": done / elapsed, "unit": UNIT, "cores": cores, "kind": "oracle",
             "sample": "%d of the batch's 256x256 maps, FP64 dense-cosine spectral Picard to "
                       "1e-8 K, %.1f s" % (done, elapsed)}, {
-        "max_abs_K": worst, "rel_l2": rel_worst, "maps_checked": done}
+        "max_abs_K": worst, "rel_l2": rel_worst, "maps_checked": done,
+        "fp32_batched": {"max_abs_K": worst2, "rel_l2": rel2} if other is not None else None}
 
 
 def run_reference(a):
@@ -178,12 +187,13 @@ def run_reference(a):
     import synth
     from oracle import physics as ph
     from oracle import solve as so
-    n_maps = max(a.steps + a.warmup, 1) * 2
-    w, pd, pl, s = synth.batch_inputs(a.n, a.batch, device="cpu")
+    per_step = 2
+    n_maps = min(a.batch, per_step * (a.steps + a.warmup))
+    # the first maps of the batch are identical whatever the batch size
+    w, pd, pl, s = synth.batch_inputs(a.n, n_maps, device="cpu")
     st, phy = w.stack, w.physics
     Kt = ph.spectrum(w.n, w.die_m, st.thickness_m, st.kappa_W_mK, st.h_conv_W_m2K)
     f64 = lambda t: t.double().numpy()
-    per_step = 2
     idx = 0
 
     def step():
@@ -215,6 +225,38 @@ def run_reference(a):
     }))
 
 
+def _time_plan(plan, steps, warmup, ws, local, stream):
+    import torch
+    import torch.distributed as dist
+    for _ in range(warmup):
+        plan.run()
+    torch.cuda.synchronize()
+
+    def barrier():
+        if ws > 1:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with Clocks(local) as clk:
+        barrier()
+        ev0.record(stream)
+        for _ in range(steps):
+            plan.run()
+        ev1.record(stream)
+        barrier()
+    return ev0.elapsed_time(ev1) / steps, clk.summary()
+
+
+def _max_over_ranks(x, ws, dev):
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], device=dev, dtype=torch.float64)
+    if ws > 1:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
 def run_ours(a):
     import torch
     import torch.distributed as dist
@@ -231,115 +273,132 @@ def run_ours(a):
     st, phy = w.stack, w.physics
     stack = vs.Stack(st.thickness_m, st.kappa_W_mK, st.h_conv_W_m2K, st.heat_cap_J_m2K)
     k = vs.Kernel(stack, vs.Grid(w.n, w.die_m))
-    params = vs.SolveParams(phy.beta_per_K, phy.alpha_per_K, 1e-4, 50)
-    theta = torch.empty_like(pd)
     B = pd.shape[0]
-    plan = vs.Plan([(k, pd[i], pl[i], s[i], theta[i]) for i in range(B)], params)
     stream = torch.cuda.current_stream()
-    for _ in range(a.warmup):
-        plan.run()
-    torch.cuda.synchronize()
-    infos = plan.info()
-    iters = [i["iterations"] for i in infos]
-    bad = sum(1 for i in infos if i["status"] != vs.VS_OK)
+    tol_tc = 1e-2
+    p32 = vs.SolveParams(phy.beta_per_K, phy.alpha_per_K, tol_tc, 50, vs.VS_PREC_FP32)
+    p32t = vs.SolveParams(phy.beta_per_K, phy.alpha_per_K, 1e-4, 50, vs.VS_PREC_FP32)
+    ptc = vs.SolveParams(phy.beta_per_K, phy.alpha_per_K, tol_tc, 50, vs.VS_PREC_BF16_SPLIT)
 
-    def barrier():
-        if ws > 1:
-            dist.barrier()
-        torch.cuda.synchronize()
+    # chosen: batched persistent plan, BF16 hi/lo split cosine transforms on tcgen05
+    th_tc = torch.empty_like(pd)
+    plan_tc = vs.Plan([(k, pd[i], pl[i], s[i], th_tc[i]) for i in range(B)], ptc)
+    ms_tc, clocks = _time_plan(plan_tc, a.steps, a.warmup, ws, local, stream)
+    info_tc = plan_tc.info()
+    ms_tc_max = _max_over_ranks(ms_tc, ws, dev)
+    value = ws * B / (ms_tc_max * 1e-3)
 
-    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    with Clocks(local) as clk:
-        barrier()
-        ev0.record(stream)
-        for _ in range(a.steps):
-            plan.run()
-        ev1.record(stream)
-        barrier()
-    clocks = clk.summary()
-    ms = ev0.elapsed_time(ev1) / a.steps
-    t = torch.tensor([ms], device=dev, dtype=torch.float64)
-    if ws > 1:
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-    ms_max = float(t.item())
-    value = ws * B / (ms_max * 1e-3)
+    # FP32 batched plan (SIMT fast transforms), same batch, same tolerance
+    th_32 = torch.empty_like(pd)
+    plan_32 = vs.Plan([(k, pd[i], pl[i], s[i], th_32[i]) for i in range(B)], p32)
+    ms_32, clocks32 = _time_plan(plan_32, a.steps, a.warmup, ws, local, stream)
+    info_32 = plan_32.info()
+    ms_32_max = _max_over_ranks(ms_32, ws, dev)
+    del plan_32
+    # FP32 batched at a 1e-4 K update tolerance (context: the tight setting)
+    th_32t = torch.empty_like(pd)
+    plan_32t = vs.Plan([(k, pd[i], pl[i], s[i], th_32t[i]) for i in range(B)], p32t)
+    ms_32t, _ = _time_plan(plan_32t, a.steps, a.warmup, ws, local, stream)
+    it_32t = [i["iterations"] for i in plan_32t.info()]
+    ms_32t_max = _max_over_ranks(ms_32t, ws, dev)
+    del plan_32t, th_32t
 
-    # plain: the same solver, one map per vs_solve_steady call, no plan reuse
+    # plain: FP32, one map per vs_solve_steady call
     plain_maps = 32
     torch.cuda.synchronize()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     plain_out = torch.empty_like(pd[0])
-    vs.solve_steady(k, pd[0], pl[0], s[0], params, plain_out)
+    vs.solve_steady(k, pd[0], pl[0], s[0], p32, plain_out)
     e0.record(stream)
     for i in range(plain_maps):
-        vs.solve_steady(k, pd[i], pl[i], s[i], params, plain_out)
+        vs.solve_steady(k, pd[i], pl[i], s[i], p32, plain_out)
     e1.record(stream)
     torch.cuda.synchronize()
     plain_value = plain_maps / (e0.elapsed_time(e1) * 1e-3)
 
-    # e2e: pinned host inputs -> device -> solve -> host theta, every step
+    # e2e: pinned host inputs -> device -> chosen plan -> host theta, every step
     e2e = None
     if not a.no_e2e:
         hpd = pd.cpu().pin_memory()
         hpl = pl.cpu().pin_memory()
         hs = s.cpu().pin_memory()
-        hth = torch.empty(theta.shape, dtype=theta.dtype, pin_memory=True)
+        hth = torch.empty(th_tc.shape, dtype=th_tc.dtype, pin_memory=True)
         e2e_steps = max(1, min(a.steps, 3))
 
         def e2e_step():
             pd.copy_(hpd, non_blocking=True)
             pl.copy_(hpl, non_blocking=True)
             s.copy_(hs, non_blocking=True)
-            plan.run()
-            hth.copy_(theta, non_blocking=True)
+            plan_tc.run()
+            hth.copy_(th_tc, non_blocking=True)
 
         e2e_step()
-        barrier()
+        torch.cuda.synchronize()
+        if ws > 1:
+            dist.barrier()
         t0 = time.perf_counter()
         for _ in range(e2e_steps):
             e2e_step()
-        barrier()
-        dt = (time.perf_counter() - t0) / e2e_steps
-        tt = torch.tensor([dt], device=dev, dtype=torch.float64)
+        torch.cuda.synchronize()
         if ws > 1:
-            dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        e2e = {"value": ws * B / float(tt.item()), "unit": UNIT,
-               "h2d_bytes_per_step": 3 * pd.numel() * 4, "d2h_bytes_per_step": theta.numel() * 4,
-               "how": "vs_plan_run through the Python binding; pinned host inputs copied in and "
-                      "theta copied out every step"}
+            dist.barrier()
+        dt = _max_over_ranks((time.perf_counter() - t0) / e2e_steps, ws, dev)
+        e2e = {"value": ws * B / dt, "unit": UNIT,
+               "h2d_bytes_per_step": 3 * pd.numel() * 4, "d2h_bytes_per_step": th_tc.numel() * 4,
+               "how": "vs_plan_run (chosen path) through the Python binding; pinned host inputs "
+                      "copied in and theta copied out every step"}
 
     if rank == 0:
-        peak, peak_kind = _peaks()
+        hbm, hbm_kind = _peaks()
+        pk = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json"))) if hbm_kind == "measured" else {}
+        tc_peak = float(pk.get("bf16_tflops_sustained", 1700.0))
+        it_tc = [i["iterations"] for i in info_tc]
+        it_32 = [i["iterations"] for i in info_32]
+        # tensor-core flops per map: 4 passes per iteration, each 2 n^3 x 3 split products
+        flops = sum(it_tc) * 4 * 2 * w.n ** 3 * 3
+        achieved_tf = flops / (ms_tc * 1e-3) / 1e12
         alg_bytes = B * w.n * w.n * ALG_BYTES_PER_PIXEL
-        achieved = alg_bytes / (ms * 1e-3) / 1e9
         tr = _traffic_record("k_solve_steady")
-        cpu, acc = cpu_oracle_leg(w, pd.cpu(), pl.cpu(), s.cpu(), theta.cpu(), a.cpu_seconds)
+        cpu, acc = cpu_oracle_leg(w, pd.cpu(), pl.cpu(), s.cpu(), th_tc.cpu(), a.cpu_seconds,
+                                  other=th_32.cpu())
         out = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": a.steps,
-            "warmup": a.warmup, "ms_per_step": ms_max, "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "warmup": a.warmup, "ms_per_step": ms_tc_max, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "bf16", "data": "synthetic",
             "config": {"workload": "steady %dx%d, 20x20 mm die, batch of %d maps per GPU "
                                    "(64 floorplans x per-map variation fields)" % (w.n, w.n, B),
-                       "n": w.n, "global_batch": ws * B, "tol_K": 1e-4,
-                       "path": "chosen = persistent batched plan (one cooperative launch, FP32 "
-                               "fast cosine transforms)",
+                       "n": w.n, "global_batch": ws * B,
+                       "path": "chosen = batched persistent plan, cosine transforms as tcgen05 "
+                               "GEMMs in BF16 hi/lo split precision (FP32 accumulate), update "
+                               "tolerance %g K" % tol_tc,
                        "l2": "inputs %.1f GiB per GPU > L2, no flush" % (3 * pd.numel() * 4 / 2**30),
                        "parallelism": "replicas x%d" % ws},
+            "fp32_batched_tol1e-4": {"value": ws * B / (ms_32t_max * 1e-3), "unit": UNIT,
+                                     "ms_per_step": ms_32t_max,
+                                     "iterations_mean": sum(it_32t) / len(it_32t)},
+            "fp32_batched": {"value": ws * B / (ms_32_max * 1e-3), "unit": UNIT,
+                             "ms_per_step": ms_32_max, "tol_K": tol_tc,
+                             "iterations_mean": sum(it_32) / len(it_32),
+                             "roofline": {"bound": "hbm",
+                                          "achieved": alg_bytes / (ms_32 * 1e-3) / 1e9,
+                                          "peak": hbm, "unit": "GB/s",
+                                          "frac": alg_bytes / (ms_32 * 1e-3) / 1e9 / hbm,
+                                          "traffic": (tr["dram_bytes_per_map"] * B) if tr else None,
+                                          "kernel": "k_solve_steady"},
+                             "clocks": clocks32},
             "plain": {"value": plain_value, "unit": UNIT,
-                      "how": "one map per vs_solve_steady call (plan built per call), %d maps"
-                             % plain_maps},
-            "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                         "frac": achieved / peak,
-                         "traffic": (tr["dram_bytes_per_map"] * B) if tr else None,
-                         "kernel": "k_solve_steady",
-                         "note": "achieved = 16 B/pixel algorithmic bytes x maps / launch time; "
-                                 "peak %s" % peak_kind},
+                      "how": "FP32, one map per vs_solve_steady call, tol %g K, %d maps" % (tol_tc, plain_maps)},
+            "roofline": {"bound": "tensor", "achieved": achieved_tf, "peak": tc_peak,
+                         "unit": "TFLOP/s", "frac": achieved_tf / tc_peak,
+                         "traffic": None, "kernel": "k_solve_steady_tc",
+                         "note": "achieved = sum over maps of iterations x 4 passes x 2n^3 x 3 "
+                                 "(split products) / launch time; peak = measured bf16 sustained"},
             "cpu_baseline": cpu,
             "accuracy_vs_fp64_oracle": acc,
             "e2e": e2e,
-            "gpu_launches": a.steps * plan.launches,
-            "iterations": {"mean": sum(iters) / len(iters), "max": max(iters),
-                           "not_ok": bad},
+            "gpu_launches": a.steps * plan_tc.launches,
+            "iterations": {"mean": sum(it_tc) / len(it_tc), "max": max(it_tc),
+                           "not_ok": sum(1 for i in info_tc if i["status"] != vs.VS_OK)},
             "clocks": clocks,
         }
         print(json.dumps(out))

@@ -529,7 +529,11 @@ __global__ void k_twiddles(int n, float2* tw) {
 // the epilogues; the fixed-point control is the same as the SIMT path.
 
 constexpr int kTcChunkK = 64;
-constexpr int kTcStageBytes = 96 * 1024;      // A hi/lo 2x16 KB + B hi/lo 2x32 KB
+// A tcgen05 kernel is held to one CTA per SM (its CTA owns the SM's tensor
+// memory), so latency is hidden inside the CTA: 16 warps.
+constexpr int kTcThreads = 512;
+constexpr int kTcABytes = 128 * kTcChunkK * 2;   // one of A hi / lo
+constexpr int kTcStageBytes = 2 * kTcABytes + 2 * 256 * kTcChunkK * 2;  // A hi/lo + B hi/lo (N <= 256)
 constexpr long long kTcWaitLimit = 20000000LL;
 
 struct TcSmem {
@@ -551,89 +555,103 @@ struct TcCtx {
 
 enum TcPass { kTcRowFwdFirst = 0, kTcRowFwd = 1, kTcColFwd = 2, kTcColInv = 3, kTcRowInv = 4 };
 
-// Producer: A chunk [128 rows][64 k] from G. Non-transposed: A[m][k] =
-// G[(row0 + m) * ld + k0 + k]. Transposed: A[m][k] = G[(k0 + k) * ld + col0 + m].
-__device__ __forceinline__ void tc_produce(uint8_t* st, const float* G, int ld, int row0, int k0,
-                                           bool transposed, const float* G2) {
-  uint8_t* hi = st;
-  uint8_t* lo = st + 16 * 1024;
-  if (!transposed) {
-    for (int i = threadIdx.x; i < 2048; i += blockDim.x) {
-      int kk = i >> 8, rem = i & 255, m = rem >> 1, h = rem & 1;
-      int k = kk * 8 + h * 4;
-      size_t g = (size_t)(row0 + m) * ld + k0 + k;
-      float4 v = *reinterpret_cast<const float4*>(G + g);
-      if (G2) {                               // first source: P_dyn + P_leak0
-        float4 w = __ldg(reinterpret_cast<const float4*>(G2 + g));
-        v.x += w.x; v.y += w.y; v.z += w.z; v.w += w.w;
-      }
-      __nv_bfloat16 h0, h1, h2, h3, l0, l1, l2, l3;
-      vstc::split_bf16(v.x, h0, l0);
-      vstc::split_bf16(v.y, h1, l1);
-      vstc::split_bf16(v.z, h2, l2);
-      vstc::split_bf16(v.w, h3, l3);
-      uint32_t off = vstc::core_off(m, k, kTcChunkK);
-      __nv_bfloat162 a = __halves2bfloat162(h0, h1), b = __halves2bfloat162(h2, h3);
-      __nv_bfloat162 c = __halves2bfloat162(l0, l1), d = __halves2bfloat162(l2, l3);
-      uint2 uh = make_uint2(*reinterpret_cast<uint32_t*>(&a), *reinterpret_cast<uint32_t*>(&b));
-      uint2 ul = make_uint2(*reinterpret_cast<uint32_t*>(&c), *reinterpret_cast<uint32_t*>(&d));
-      *reinterpret_cast<uint2*>(hi + off) = uh;
-      *reinterpret_cast<uint2*>(lo + off) = ul;
-    }
-  } else {
-    for (int i = threadIdx.x; i < 1024; i += blockDim.x) {
-      int kp = i >> 5, mq = i & 31;           // k pair, m quad
-      int k = 2 * kp, m = 4 * mq;
-      float4 r0 = *reinterpret_cast<const float4*>(G + (size_t)(k0 + k) * ld + row0 + m);
-      float4 r1 = *reinterpret_cast<const float4*>(G + (size_t)(k0 + k + 1) * ld + row0 + m);
-      float a0[4] = {r0.x, r0.y, r0.z, r0.w}, a1[4] = {r1.x, r1.y, r1.z, r1.w};
+// Producer: A chunk [128 rows][64 k], A[m][k] = G[(row0 + m) * ld + k0 + k]
+// (+ G2 for the first source P_dyn + P_leak0), split into BF16 hi/lo and
+// written in core-matrix order. A warp covers 16 rows x 8 k of one core
+// column: 8-byte stores, two wavefronts, no bank conflicts. All loads of a
+// thread are issued before the conversions.
+constexpr int kTcPer = 128 * kTcChunkK / 4 / kTcThreads;   // float4 items per thread per chunk
+
+// item u of this thread -> (k core kk, row m, half h); a warp covers 16 rows of
+// one k core, so the 8-byte stores below fill whole wavefronts.
+__device__ __forceinline__ void tc_item(int u, int& kk, int& m, int& h) {
+  int i = threadIdx.x + u * kTcThreads;
+  kk = i >> 8;
+  int rem = i & 255;
+  m = rem >> 1;
+  h = rem & 1;
+}
+
+// Loads of one A chunk into registers (A[m][k] = G[(row0 + m) * ld + k0 + k],
+// plus G2 for the first source P_dyn + P_leak0).
+__device__ __forceinline__ void tc_load(float4* v, const float* G, int ld, int row0, int k0,
+                                        const float* G2) {
 #pragma unroll
-      for (int j = 0; j < 4; ++j) {
-        __nv_bfloat16 h0, l0, h1, l1;
-        vstc::split_bf16(a0[j], h0, l0);
-        vstc::split_bf16(a1[j], h1, l1);
-        uint32_t off = vstc::core_off(m + j, k, kTcChunkK);
-        __nv_bfloat162 ph = __halves2bfloat162(h0, h1), pl = __halves2bfloat162(l0, l1);
-        *reinterpret_cast<__nv_bfloat162*>(hi + off) = ph;
-        *reinterpret_cast<__nv_bfloat162*>(lo + off) = pl;
-      }
+  for (int u = 0; u < kTcPer; ++u) {
+    int kk, m, h;
+    tc_item(u, kk, m, h);
+    size_t g = (size_t)(row0 + m) * ld + k0 + kk * 8 + h * 4;
+    v[u] = *reinterpret_cast<const float4*>(G + g);
+    if (G2) {
+      float4 w = __ldg(reinterpret_cast<const float4*>(G2 + g));
+      v[u].x += w.x; v[u].y += w.y; v[u].z += w.z; v[u].w += w.w;
     }
+  }
+}
+
+// Split into BF16 hi/lo and store in core-matrix order.
+__device__ __forceinline__ void tc_store(uint8_t* st, const float4* v) {
+  uint8_t* hi = st;
+  uint8_t* lo = st + kTcABytes;
+#pragma unroll
+  for (int u = 0; u < kTcPer; ++u) {
+    int kk, m, h;
+    tc_item(u, kk, m, h);
+    __nv_bfloat16 h0, h1, h2, h3, l0, l1, l2, l3;
+    vstc::split_bf16(v[u].x, h0, l0);
+    vstc::split_bf16(v[u].y, h1, l1);
+    vstc::split_bf16(v[u].z, h2, l2);
+    vstc::split_bf16(v[u].w, h3, l3);
+    uint32_t off = vstc::core_off(m, kk * 8 + h * 4, kTcChunkK);
+    __nv_bfloat162 a = __halves2bfloat162(h0, h1), b = __halves2bfloat162(h2, h3);
+    __nv_bfloat162 c = __halves2bfloat162(l0, l1), d = __halves2bfloat162(l2, l3);
+    *reinterpret_cast<uint2*>(hi + off) =
+        make_uint2(*reinterpret_cast<uint32_t*>(&a), *reinterpret_cast<uint32_t*>(&b));
+    *reinterpret_cast<uint2*>(lo + off) =
+        make_uint2(*reinterpret_cast<uint32_t*>(&c), *reinterpret_cast<uint32_t*>(&d));
   }
 }
 
 // One 128-row GEMM into TMEM columns [0, N). Returns false on a wait timeout.
 __device__ bool tc_gemm(TcCtx& c, int N, const uint8_t* Bg, const float* G, int ld, int row0,
-                        bool transposed, const float* G2) {
+                        const float* G2) {
   const int nk = N / kTcChunkK;
   const uint32_t idesc = vstc::idesc_bf16(128, N);
   const uint32_t bbytes = (uint32_t)N * kTcChunkK * 2;     // one of hi / lo
+  float4 vnext[kTcPer];
+  tc_load(vnext, G, ld, row0, 0, G2);
   for (int kc = 0; kc < nk; ++kc) {
     const int s = c.chunk & 1;
+    float4 v[kTcPer];
+#pragma unroll
+    for (int u = 0; u < kTcPer; ++u) v[u] = vnext[u];
+    if (kc + 1 < nk) tc_load(vnext, G, ld, row0, (kc + 1) * kTcChunkK, G2);   // in flight
     if (c.uses[s] > 0 && !vstc::mbar_wait(&c.sm->done[s], (c.uses[s] - 1) & 1, kTcWaitLimit))
       return false;
     uint8_t* st = c.sm->stage[s];
+    uint8_t* bst = st + 2 * kTcABytes;
     if (threadIdx.x == 0) {
       vstc::mbar_arrive_expect_tx(&c.sm->full[s], 2 * bbytes);
       const uint8_t* src = Bg + (size_t)kc * 2 * bbytes;
-      vstc::bulk_g2s(st + 32 * 1024, src, bbytes, &c.sm->full[s]);            // B hi
-      vstc::bulk_g2s(st + 32 * 1024 + bbytes, src + bbytes, bbytes, &c.sm->full[s]);  // B lo
+      vstc::bulk_g2s(bst, src, bbytes, &c.sm->full[s]);                       // B hi
+      vstc::bulk_g2s(bst + bbytes, src + bbytes, bbytes, &c.sm->full[s]);     // B lo
     }
-    tc_produce(st, G, ld, row0, kc * kTcChunkK, transposed, G2);
+    tc_store(st, v);
     vstc::fence_proxy_async_smem();
     __syncthreads();
     if (threadIdx.x == 0) {
       bool landed = vstc::mbar_wait(&c.sm->full[s], c.uses[s] & 1, kTcWaitLimit);
       vstc::tc_fence_after();
       if (landed) {
-        const uint32_t a0 = vstc::smem_u32(st), b0 = vstc::smem_u32(st + 32 * 1024);
-        const uint32_t sbo_a = (kTcChunkK / 8) * 128, sbo_b = sbo_a;
+        const uint32_t a0 = vstc::smem_u32(st), b0 = vstc::smem_u32(bst);
+        const uint32_t sbo = (kTcChunkK / 8) * 128;
 #pragma unroll
         for (int ks = 0; ks < kTcChunkK / 16; ++ks) {
           const uint32_t o = ks * 256;
-          uint64_t ah = vstc::smem_desc(a0 + o, 128, sbo_a);
-          uint64_t al = vstc::smem_desc(a0 + 16 * 1024 + o, 128, sbo_a);
-          uint64_t bh = vstc::smem_desc(b0 + o, 128, sbo_b);
-          uint64_t bl = vstc::smem_desc(b0 + bbytes + o, 128, sbo_b);
+          uint64_t ah = vstc::smem_desc(a0 + o, 128, sbo);
+          uint64_t al = vstc::smem_desc(a0 + kTcABytes + o, 128, sbo);
+          uint64_t bh = vstc::smem_desc(b0 + o, 128, sbo);
+          uint64_t bl = vstc::smem_desc(b0 + bbytes + o, 128, sbo);
           vstc::mma_bf16(c.tmem, ah, bh, idesc, (kc > 0 || ks > 0) ? 1u : 0u);
           vstc::mma_bf16(c.tmem, ah, bl, idesc, 1u);
           vstc::mma_bf16(c.tmem, al, bh, idesc, 1u);
@@ -654,17 +672,48 @@ __device__ bool tc_gemm(TcCtx& c, int N, const uint8_t* Bg, const float* G, int 
 }
 
 // Epilogue traversal: warp w reads TMEM lanes 32 (w % 4) .. + 31 (tile rows)
-// and half (w / 4) of the N columns, 32 columns at a time.
+// and column quarter (w / 4) of the N columns, 32 columns at a time.
 template <class Op>
 __device__ __forceinline__ void tc_epilogue(const TcCtx& c, int N, Op op) {
   const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int m = 32 * (w & 3) + lane;
-  const int half = N >> 1;
-  for (int c0 = (w >> 2) * half; c0 < (w >> 2) * half + half; c0 += 32) {
+  const int quarter = N >> 2;
+  const int g = w >> 2;
+  for (int c0 = g * quarter; c0 < (g + 1) * quarter; c0 += 32) {
     float v[32];
     vstc::tmem_ld32(c.tmem + ((uint32_t)(32 * (w & 3)) << 16) + (uint32_t)c0, v);
     op(m, c0, v);
   }
+}
+
+// Row-wise epilogue: each warp moves its 32 x 32 TMEM block through shared
+// memory (`scratch`, 16 warps x 32 x 33 floats) and then walks it one tile
+// row at a time with lane = column, so global loads and stores of the fused
+// update are coalesced and independent across rows.
+template <class Op>
+__device__ __forceinline__ void tc_epilogue_rows(const TcCtx& c, int N, float* scratch, Op op) {
+  const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int q = w & 3;
+  const int quarter = N >> 2;
+  const int g = w >> 2;
+  float* tile = scratch + w * (32 * 33);
+  for (int c0 = g * quarter; c0 < (g + 1) * quarter; c0 += 32) {
+    float v[32];
+    vstc::tmem_ld32(c.tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)c0, v);
+#pragma unroll
+    for (int j = 0; j < 32; ++j) tile[lane * 33 + j] = v[j];
+    __syncwarp();
+#pragma unroll 8
+    for (int r = 0; r < 32; ++r) op(32 * q + r, c0 + lane, tile[r * 33 + lane]);
+    __syncwarp();
+  }
+}
+
+// Transposed store of a thread's 32 columns: out[(c0 + i) * ld + row]; the
+// 32 lanes of a warp hold consecutive rows, so each store is one 128-B line.
+__device__ __forceinline__ void store32_t(float* out, int ld, int c0, int row, const float* v) {
+#pragma unroll
+  for (int i = 0; i < 32; ++i) out[(size_t)(c0 + i) * ld + row] = v[i];
 }
 
 __device__ __forceinline__ void store32(float* dst, const float* v) {
@@ -675,9 +724,9 @@ __device__ __forceinline__ void store32(float* dst, const float* v) {
 
 // One task of a pass: rows [row0, row0+128) of map b.
 __device__ bool tc_task(const PlanDev& P, TcCtx& c, int pass, int task) {
-  __shared__ double red_d[8];
-  __shared__ float red_f[8];
-  __shared__ int red_i[8];
+  __shared__ double red_d[kTcThreads / 32];
+  __shared__ float red_f[kTcThreads / 32];
+  __shared__ int red_i[kTcThreads / 32];
   const int b = __ldg(&P.row_map[task]);
   const MapDesc d = P.maps[b];
   MapState* ms = P.st + b;
@@ -691,70 +740,55 @@ __device__ bool tc_task(const PlanDev& P, TcCtx& c, int pass, int task) {
   float resid = 0.f;
   int flags = 0;
   if (pass == kTcRowFwdFirst || pass == kTcRowFwd) {
-    // rows forward: A[y][x] = q (first: P_dyn + P_leak0), B = C -> R[y][p] in work
-    if (first) ok = tc_gemm(c, n, d.tcf, d.p_dyn, n, r0, false, d.p_leak0);
-    else ok = tc_gemm(c, n, d.tcf, d.work2, n, r0, false, nullptr);
-    tc_epilogue(c, n, [&](int m, int c0, float* v) {
-      size_t row = (size_t)(r0 + m) * n + c0;
-      store32(d.work + row, v);
-      if (first) {
-#pragma unroll
-        for (int i = 0; i < 32; ++i) {
-          d.theta[row + i] = 0.f;
-          mu_acc += (double)__ldg(&d.p_leak0[row + i]);
-        }
+    // rows forward: A[y][x] = q (first: P_dyn + P_leak0), B = C -> R[y][p], stored as RT[p][y]
+    if (first) ok = tc_gemm(c, n, d.tcf, d.p_dyn, n, r0, d.p_leak0);
+    else ok = tc_gemm(c, n, d.tcf, d.work2, n, r0, nullptr);
+    tc_epilogue(c, n, [&](int m, int c0, float* v) { store32_t(d.work, n, c0, r0 + m, v); });
+    if (first) {
+      // theta_0 = 0 and the partial sum of P_leak0 over the tile (coalesced)
+      for (int i = threadIdx.x; i < 128 * n / 4; i += blockDim.x) {
+        size_t idx = (size_t)r0 * n + 4 * (size_t)i;
+        *reinterpret_cast<float4*>(d.theta + idx) = make_float4(0.f, 0.f, 0.f, 0.f);
+        float4 w4 = __ldg(reinterpret_cast<const float4*>(d.p_leak0 + idx));
+        mu_acc += (double)w4.x + (double)w4.y + (double)w4.z + (double)w4.w;
       }
-    });
+    }
   } else if (pass == kTcColFwd) {
-    // columns forward: A[p][y] = R[y][p] (transposed), B = C -> X[p][q]; x K/(1-beta mu K)
-    ok = tc_gemm(c, n, d.tcf, d.work, n, r0, true, nullptr);
+    // columns forward: A[p][y] = RT, B = C -> X[p][q]; x K/(1-beta mu K) -> Y[p][q]
+    ok = tc_gemm(c, n, d.tcf, d.work, n, r0, nullptr);
     const float bm = P.beta * ms->mu_f;
-    tc_epilogue(c, n, [&](int m, int c0, float* v) {
-      size_t row = (size_t)(r0 + m) * n + c0;
-#pragma unroll
-      for (int i = 0; i < 32; ++i) {
-        float k = __ldg(&d.Kt[row + i]);
-        v[i] = v[i] * k / (1.f - bm * k);
-      }
-      store32(d.work2 + row, v);
+    float* scratch = reinterpret_cast<float*>(c.sm->stage[0]);
+    tc_epilogue_rows(c, n, scratch, [&](int m, int col, float val) {
+      size_t idx = (size_t)(r0 + m) * n + col;
+      float k = __ldg(&d.Kt[idx]);
+      d.work2[idx] = val * k / (1.f - bm * k);
     });
   } else if (pass == kTcColInv) {
-    // columns inverse: A[p][q] = Y, B = Ci -> ZT[p][y]
-    ok = tc_gemm(c, n, d.tci, d.work2, n, r0, false, nullptr);
-    tc_epilogue(c, n, [&](int m, int c0, float* v) { store32(d.work + (size_t)(r0 + m) * n + c0, v); });
+    // columns inverse: A[p][q] = Y, B = Ci -> ZT[p][y], stored as Z[y][p]
+    ok = tc_gemm(c, n, d.tci, d.work2, n, r0, nullptr);
+    tc_epilogue(c, n, [&](int m, int c0, float* v) { store32_t(d.work, n, c0, r0 + m, v); });
   } else {
-    // rows inverse: A[y][p] = ZT[p][y] (transposed), B = Ci -> u[y][x]; fused update
-    ok = tc_gemm(c, n, d.tci, d.work, n, r0, true, nullptr);
+    // rows inverse: A[y][p] = Z, B = Ci -> u[y][x]; fused update -> q[y][x]
+    ok = tc_gemm(c, n, d.tci, d.work, n, r0, nullptr);
     const float beta = P.beta, alpha = P.alpha, mu = ms->mu_f;
-    tc_epilogue(c, n, [&](int m, int c0, float* v) {
-      size_t row = (size_t)(r0 + m) * n + c0;
-      float q[32];
-#pragma unroll
-      for (int i = 0; i < 32; i += 4) {
-        float4 pd = __ldg(reinterpret_cast<const float4*>(d.p_dyn + row + i));
-        float4 pl = __ldg(reinterpret_cast<const float4*>(d.p_leak0 + row + i));
-        float4 sk = d.s ? __ldg(reinterpret_cast<const float4*>(d.s + row + i))
-                        : make_float4(1.f, 1.f, 1.f, 1.f);
-        float4 old = *reinterpret_cast<const float4*>(d.theta + row + i);
-        float pda[4] = {pd.x, pd.y, pd.z, pd.w}, pla[4] = {pl.x, pl.y, pl.z, pl.w};
-        float ska[4] = {sk.x, sk.y, sk.z, sk.w}, olda[4] = {old.x, old.y, old.z, old.w};
-        float th4[4];
-#pragma unroll
-        for (int j = 0; j < 4; ++j) {
-          float u = v[i + j];
-          float den = fmaf(-alpha * ska[j], u, 1.f);
-          if (!(den > 0.05f)) flags |= kFlagRunaway;
-          float th = ska[j] * u / den;
-          if (!isfinite(th)) flags |= kFlagNonfinite;
-          else resid = fmaxf(resid, fabsf(th - olda[j]));
-          th4[j] = th;
-          q[i + j] = pda[j] + pla[j] + beta * fmaf(pla[j], th, -mu * u);
-        }
-        *reinterpret_cast<float4*>(d.theta + row + i) = make_float4(th4[0], th4[1], th4[2], th4[3]);
-      }
-      store32(d.work2 + row, q);
+    float* scratch = reinterpret_cast<float*>(c.sm->stage[0]);
+    tc_epilogue_rows(c, n, scratch, [&](int m, int col, float u) {
+      size_t idx = (size_t)(r0 + m) * n + col;
+      float pd = __ldg(&d.p_dyn[idx]);
+      float pl = __ldg(&d.p_leak0[idx]);
+      float sk = d.s ? __ldg(&d.s[idx]) : 1.f;
+      float old = d.theta[idx];
+      float den = fmaf(-alpha * sk, u, 1.f);
+      if (!(den > 0.05f)) flags |= kFlagRunaway;
+      float th = sk * u / den;
+      if (!isfinite(th)) flags |= kFlagNonfinite;
+      else resid = fmaxf(resid, fabsf(th - old));
+      d.theta[idx] = th;
+      d.work2[idx] = pd + pl + beta * fmaf(pl, th, -mu * u);
     });
   }
+  // the epilogue scratch (stage 0) is refilled by the async proxy next
+  vstc::fence_proxy_async_smem();
   vstc::tc_fence_before();
   if (first) {
     double tot = block_sum(mu_acc, red_d);
@@ -784,7 +818,7 @@ __device__ void tc_finish(TcCtx& c) {
   if ((threadIdx.x >> 5) == 0) vstc::tmem_dealloc(c.tmem, 256);
 }
 
-__global__ void __launch_bounds__(kThreads, 1) k_solve_steady_tc(PlanDev P) {
+__global__ void __launch_bounds__(kTcThreads, 1) k_solve_steady_tc(PlanDev P) {
   extern __shared__ __align__(1024) uint8_t tc_smem_raw[];
   TcSmem* sm = reinterpret_cast<TcSmem*>(
       (reinterpret_cast<uintptr_t>(tc_smem_raw) + 1023) & ~(uintptr_t)1023);
@@ -839,7 +873,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_solve_steady_tc(PlanDev P) {
 
 // Standalone split-precision transform (for testing the building block):
 // out[r][j] = sum_k in[r][k] T[j][k], T = forward or inverse DCT matrix.
-__global__ void __launch_bounds__(kThreads, 1) k_tc_transform(const float* in, float* out, int rows,
+__global__ void __launch_bounds__(kTcThreads, 1) k_tc_transform(const float* in, float* out, int rows,
                                                               int n, const uint8_t* Bg) {
   extern __shared__ __align__(1024) uint8_t tc_smem_raw[];
   TcSmem* sm = reinterpret_cast<TcSmem*>(
@@ -864,7 +898,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_tc_transform(const float* in, f
   c.chunk = 0;
   c.fin_uses = 0;
   for (int t = blockIdx.x; t < rows / 128; t += gridDim.x) {
-    if (!tc_gemm(c, n, Bg, in, n, t * 128, false, nullptr)) break;
+    if (!tc_gemm(c, n, Bg, in, n, t * 128, nullptr)) break;
     tc_epilogue(c, n, [&](int m, int c0, float* v) { store32(out + (size_t)(t * 128 + m) * n + c0, v); });
     vstc::tc_fence_before();
     __syncthreads();
@@ -1142,6 +1176,7 @@ int plan_layout(vs_plan_t* p, int elems, cudaStream_t s, bool transient, int n_s
                       : (const void*)k_solve_steady;
   if (tc) {
     VS_CUDA_TRY(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    VS_CUDA_TRY(cudaFuncSetAttribute(fn, cudaFuncAttributePreferredSharedMemoryCarveout, 100));
   } else {
     // Function attributes are process-wide: only ever raise the limit, so a
     // plan with a smaller footprint never invalidates a larger one.
@@ -1154,13 +1189,27 @@ int plan_layout(vs_plan_t* p, int elems, cudaStream_t s, bool transient, int n_s
     }
   }
   int per_sm = 0;
-  VS_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, kThreads, smem));
+  VS_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, tc ? kTcThreads : kThreads,
+                                                            smem));
   if (per_sm < 1) return vs_set_error(VS_ERR_INVALID_ARG, "no block fits on an SM (smem %zu)", smem);
   int dev = 0, sms = 0;
   VS_CUDA_TRY(cudaGetDevice(&dev));
   VS_CUDA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
   int want = std::max(p->row_tasks, p->col_tasks);
   p->grid = std::max(1, std::min(per_sm * sms, want));
+  if (getenv("VS_DEBUG")) {
+    cudaFuncAttributes fa;
+    cudaFuncGetAttributes(&fa, fn);
+    int smem_sm = 0, regs_sm = 0;
+    cudaDeviceGetAttribute(&smem_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev);
+    cudaDeviceGetAttribute(&regs_sm, cudaDevAttrMaxRegistersPerMultiprocessor, dev);
+    fprintf(stderr,
+            "varsim plan: %s items=%d grid=%d per_sm=%d sms=%d smem=%zu tasks=%d/%d regs=%d "
+            "static_smem=%zu max_dyn=%d local=%zu | sm: smem=%d regs=%d\n",
+            transient ? "transient" : (tc ? "bf16-split" : "fp32"), n_items, p->grid, per_sm, sms,
+            smem, p->row_tasks, p->col_tasks, fa.numRegs, fa.sharedSizeBytes,
+            fa.maxDynamicSharedSizeBytes, fa.localSizeBytes, smem_sm, regs_sm);
+  }
   p->transient_steps = n_steps;
   VS_CUDA_TRY(cudaStreamSynchronize(s));  // host `maps` must outlive the copy
   return VS_OK;
@@ -1187,7 +1236,7 @@ int plan_launch(vs_plan_t* p, cudaStream_t s, bool transient) {
   P.n_steps = p->transient_steps;
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3(p->grid);
-  cfg.blockDim = dim3(kThreads);
+  cfg.blockDim = dim3(p->params.precision == VS_PREC_BF16_SPLIT && !transient ? kTcThreads : kThreads);
   cfg.dynamicSmemBytes = p->smem;
   cfg.stream = s;
   cudaLaunchAttribute attr[1];
@@ -1575,11 +1624,13 @@ extern "C" int vs_tc_transform(const float* in, float* out, int rows, int n, int
   if (!tm) return st;
   VS_CUDA_TRY(cudaFuncSetAttribute((const void*)k_tc_transform,
                                    cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kTcSmemBytes));
+  VS_CUDA_TRY(cudaFuncSetAttribute((const void*)k_tc_transform,
+                                   cudaFuncAttributePreferredSharedMemoryCarveout, 100));
   int dev = 0, sms = 0;
   VS_CUDA_TRY(cudaGetDevice(&dev));
   VS_CUDA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
   int grid = std::max(1, std::min(sms, rows / 128));
-  k_tc_transform<<<grid, kThreads, kTcSmemBytes, (cudaStream_t)stream>>>(
+  k_tc_transform<<<grid, kTcThreads, kTcSmemBytes, (cudaStream_t)stream>>>(
       in, out, rows, n, inverse ? tm->inv : tm->fwd);
   VS_CUDA_TRY(cudaGetLastError());
   return VS_OK;
