@@ -122,6 +122,7 @@ typedef struct {
 
 typedef struct vs_kernel_t* vs_kernel;
 typedef struct vs_plan_t* vs_plan;
+typedef struct vs_model_t* vs_model;
 
 /* ------------------------------------------------------------------------ */
 /* Green's function build (Sec. II-B, Eq. 2; Sec. II-F Eq. 10; Theorem I;    */
@@ -215,6 +216,8 @@ typedef struct {
   const float* p_leak0;    /* device, [n][n] */
   const float* s_kappa;    /* device, [n][n], or NULL => 1 */
   float* theta;            /* device output, [n][n] */
+  const float* theta_init; /* device [n][n] initial temperature (warm start of the
+                              fixed point, e.g. from vs_model_predict), or NULL => 0 */
 } vs_batch_item;
 
 /* Creates a plan for n_items maps: uploads the item table, allocates the
@@ -262,6 +265,55 @@ int vs_solve_transient(vs_kernel k, int n_steps, const float* p_dyn_trace,
                        const float* p_leak0, const float* s_kappa,
                        const vs_solve_params* params, float* theta_trace,
                        vs_solve_info* info_host, void* stream);
+
+/* ------------------------------------------------------------------------ */
+/* Learned warm start of the fixed point. The paper iterates power ->        */
+/* temperature -> leakage until convergence (Sec. V-B); these calls predict  */
+/* most of the remaining correction after the first iterate so that the     */
+/* iteration can start closer to its fixed point. The solve still decides   */
+/* convergence, so a poor prediction costs iterations, not accuracy.         */
+/* ------------------------------------------------------------------------ */
+
+/* Small U-Net on resolution x resolution inputs (3 channels -> 1): convs
+ * 3->C, C->C, pool, C->2C, 2C->2C, pool, 2C->2C, up + skip -> C, up + skip -> C,
+ * C->1 (3x3, zero padding, ReLU except the last). BF16 weights, FP32
+ * activations and accumulation; He-uniform initialisation from `seed`.
+ * base_channels C in [1, 64]; resolution a multiple of 4 in [8, 256].
+ * Parameters are laid out as all weights [co][ci][3][3] layer by layer, then
+ * all biases. */
+int vs_model_create(int base_channels, int resolution, unsigned long long seed, vs_model* out);
+void vs_free_model(vs_model m);
+long long vs_model_nparams(vs_model m);
+/* Host FP32 copies of the master parameters (n = vs_model_nparams). Setting
+ * them also resets the optimiser state. Blocking. */
+int vs_model_get_params(vs_model m, float* host);
+int vs_model_set_params(vs_model m, const float* host);
+/* y[b][0][R][R] = net(x[b][3][R][R]) for `batch` samples (device arrays). */
+int vs_model_forward(vs_model m, const float* x, float* y, int batch, void* stream);
+/* Mean-squared-error loss against t[b][1][R][R] and its parameter gradient
+ * (host arrays; grad_host may be NULL). No update. Blocking. */
+int vs_model_loss_grad(vs_model m, const float* x, const float* t, int batch,
+                       double* loss_host, float* grad_host, void* stream);
+/* Adam training (lr, beta1 0.9, beta2 0.999) on n_samples pairs (x, t) in
+ * device memory for `epochs` shuffled passes of `batch`; *loss_host = MSE of
+ * the last batch. Blocking. */
+int vs_model_train(vs_model m, const float* x, const float* t, int n_samples, int epochs,
+                   int batch, float lr, unsigned long long seed, double* loss_host, void* stream);
+/* Checkpoint (base channels, resolution, parameters) to / from a file. */
+int vs_model_save(vs_model m, const char* path);
+int vs_model_load(const char* path, vs_model* out);
+
+/* Features of `count` maps [count][n][n] for the warm start, averaged over
+ * (n/R)^2 blocks: x[b] = {theta1/100, 10 (P_leak0/mean - 1), 30 (s - 1)}
+ * ([count][3][R][R]); s_kappa may be NULL. */
+int vs_warm_features(const float* theta1, const float* p_leak0, const float* s_kappa,
+                     int count, int n, int resolution, float* x_out, void* stream);
+/* Training target t[b] = block average of (theta_star - theta1) / 10. */
+int vs_warm_target(const float* theta_star, const float* theta1, int count, int n,
+                   int resolution, float* t_out, void* stream);
+/* theta_init = theta1 + 10 * bilinear upsampling of y to n x n. */
+int vs_warm_apply(const float* theta1, const float* y, int count, int n, int resolution,
+                  float* theta_init, void* stream);
 
 /* Split-precision tensor-core transform (the building block of
  * VS_PREC_BF16_SPLIT), exposed for testing: for each of `rows` rows,

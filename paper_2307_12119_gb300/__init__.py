@@ -21,7 +21,8 @@ __all__ = [
     "VS_ERR_RUNAWAY", "VS_ERR_NONFINITE", "VS_ERR_TIMEOUT", "VarsimError", "Stack", "Grid",
     "KernelOpts", "SolveParams", "Kernel", "Plan", "lib", "lib_path", "solve_steady",
     "solve_batch", "solve_transient", "hankel_radial", "EXPORTS", "solve_steady_noalloc",
-    "tc_transform", "VS_PREC_FP32", "VS_PREC_BF16_SPLIT",
+    "tc_transform", "VS_PREC_FP32", "VS_PREC_BF16_SPLIT", "Model", "WarmPlan",
+    "warm_features", "warm_target", "warm_apply",
 ]
 
 VS_OK, VS_ERR_INVALID_ARG, VS_ERR_CUDA, VS_ERR_OOM = 0, 1, 2, 3
@@ -34,7 +35,10 @@ EXPORTS = [
     "vs_hankel_radial", "vs_solve_steady", "vs_plan_create", "vs_plan_run", "vs_plan_info",
     "vs_plan_launches", "vs_plan_free", "vs_solve_batch", "vs_solve_transient",
     "vs_status_string", "vs_last_error", "vs_version", "vs_solve_steady_noalloc",
-    "vs_tc_transform",
+    "vs_tc_transform", "vs_model_create", "vs_free_model", "vs_model_nparams",
+    "vs_model_get_params", "vs_model_set_params", "vs_model_forward", "vs_model_loss_grad",
+    "vs_model_train", "vs_model_save", "vs_model_load", "vs_warm_features", "vs_warm_target",
+    "vs_warm_apply",
 ]
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
@@ -76,7 +80,7 @@ class _SolveInfo(C.Structure):
 
 class _BatchItem(C.Structure):
     _fields_ = [("k", C.c_void_p), ("p_dyn", C.c_void_p), ("p_leak0", C.c_void_p),
-                ("s_kappa", C.c_void_p), ("theta", C.c_void_p)]
+                ("s_kappa", C.c_void_p), ("theta", C.c_void_p), ("theta_init", C.c_void_p)]
 
 
 _lib = None
@@ -116,6 +120,20 @@ def lib():
         "vs_solve_transient": (ip, [vp, ip, vp, vp, vp, C.POINTER(_SolveParams), vp,
                                     C.POINTER(_SolveInfo), vp]),
         "vs_tc_transform": (ip, [vp, vp, ip, ip, ip, vp]),
+        "vs_model_create": (ip, [ip, ip, C.c_ulonglong, C.POINTER(vp)]),
+        "vs_free_model": (None, [vp]),
+        "vs_model_nparams": (C.c_longlong, [vp]),
+        "vs_model_get_params": (ip, [vp, vp]),
+        "vs_model_set_params": (ip, [vp, vp]),
+        "vs_model_forward": (ip, [vp, vp, vp, ip, vp]),
+        "vs_model_loss_grad": (ip, [vp, vp, vp, ip, C.POINTER(C.c_double), vp, vp]),
+        "vs_model_train": (ip, [vp, vp, vp, ip, ip, ip, C.c_float, C.c_ulonglong,
+                                C.POINTER(C.c_double), vp]),
+        "vs_model_save": (ip, [vp, C.c_char_p]),
+        "vs_model_load": (ip, [C.c_char_p, C.POINTER(vp)]),
+        "vs_warm_features": (ip, [vp, vp, vp, ip, ip, ip, vp, vp]),
+        "vs_warm_target": (ip, [vp, vp, ip, ip, ip, vp, vp]),
+        "vs_warm_apply": (ip, [vp, vp, ip, ip, ip, vp, vp]),
         "vs_status_string": (C.c_char_p, [ip]),
         "vs_last_error": (C.c_char_p, []),
         "vs_version": (C.c_char_p, []),
@@ -326,15 +344,19 @@ class Plan:
     """A batched solve over many maps (vs_plan_*): one persistent launch per run."""
 
     def __init__(self, items, params: Optional[SolveParams] = None, stream=None):
-        """items: sequence of (Kernel, p_dyn, p_leak0, s_kappa or None, theta)."""
+        """items: sequence of (Kernel, p_dyn, p_leak0, s_kappa or None, theta
+        [, theta_init or None])."""
         prm = params or SolveParams()
         arr = (_BatchItem * len(items))()
         self._keep = []
-        for i, (k, pd, pl, sk, th) in enumerate(items):
+        for i, item in enumerate(items):
+            k, pd, pl, sk, th = item[:5]
+            ti = item[5] if len(item) > 5 else None
             n = k.n
             arr[i] = _BatchItem(k.handle, _ptr(pd, n, "p_dyn"), _ptr(pl, n, "p_leak0"),
-                                _ptr(sk, n, "s_kappa", allow_none=True), _ptr(th, n, "theta"))
-            self._keep.append((k, pd, pl, sk, th))
+                                _ptr(sk, n, "s_kappa", allow_none=True), _ptr(th, n, "theta"),
+                                _ptr(ti, n, "theta_init", allow_none=True))
+            self._keep.append(item)
         h = C.c_void_p()
         _check(lib().vs_plan_create(arr, len(items), C.byref(prm._c()), C.byref(h),
                                     _stream(stream)), "vs_plan_create")
@@ -393,3 +415,167 @@ def solve_transient(kernel: Kernel, p_dyn_trace, p_leak0, s_kappa=None,
                                     C.byref(info), _stream(stream)),
            "vs_solve_transient", ok=_SOLVE_OK)
     return theta_trace, _info(info)
+
+
+# --------------------------------------------------------------------------
+# Learned warm start (vs_model_*, vs_warm_*)
+# --------------------------------------------------------------------------
+
+class Model:
+    """The warm-start U-Net (vs_model_create); parameters live on the GPU."""
+
+    def __init__(self, base_channels: int = 16, resolution: int = 64, seed: int = 1,
+                 _handle=None):
+        if _handle is not None:
+            self.handle = _handle
+        else:
+            h = C.c_void_p()
+            _check(lib().vs_model_create(base_channels, resolution, seed, C.byref(h)),
+                   "vs_model_create")
+            self.handle = h.value
+        self.base_channels = base_channels
+        self.resolution = resolution
+
+    @classmethod
+    def load(cls, path: str, base_channels: int, resolution: int):
+        h = C.c_void_p()
+        _check(lib().vs_model_load(path.encode(), C.byref(h)), "vs_model_load")
+        return cls(base_channels, resolution, _handle=h.value)
+
+    def save(self, path: str):
+        _check(lib().vs_model_save(self.handle, path.encode()), "vs_model_save")
+
+    @property
+    def nparams(self) -> int:
+        return int(lib().vs_model_nparams(self.handle))
+
+    def get_params(self):
+        import numpy as np
+        out = np.empty(self.nparams, dtype=np.float32)
+        _check(lib().vs_model_get_params(self.handle, out.ctypes.data), "vs_model_get_params")
+        return out
+
+    def set_params(self, p):
+        import numpy as np
+        a = np.ascontiguousarray(p, dtype=np.float32)
+        assert a.size == self.nparams
+        _check(lib().vs_model_set_params(self.handle, a.ctypes.data), "vs_model_set_params")
+
+    def forward(self, x, stream=None):
+        import torch
+        y = torch.empty(x.shape[0], 1, self.resolution, self.resolution, device=x.device)
+        _check(lib().vs_model_forward(self.handle, _ptr(x, None, "x"), y.data_ptr(), x.shape[0],
+                                      _stream(stream)), "vs_model_forward")
+        return y
+
+    def loss_grad(self, x, t, stream=None):
+        import numpy as np
+        loss = C.c_double()
+        g = np.empty(self.nparams, dtype=np.float32)
+        _check(lib().vs_model_loss_grad(self.handle, _ptr(x, None, "x"), _ptr(t, None, "t"),
+                                        x.shape[0], C.byref(loss), g.ctypes.data,
+                                        _stream(stream)), "vs_model_loss_grad")
+        return loss.value, g
+
+    def train(self, x, t, epochs: int = 8, batch: int = 64, lr: float = 1e-3, seed: int = 7,
+              stream=None) -> float:
+        loss = C.c_double()
+        _check(lib().vs_model_train(self.handle, _ptr(x, None, "x"), _ptr(t, None, "t"),
+                                    x.shape[0], epochs, batch, lr, seed, C.byref(loss),
+                                    _stream(stream)), "vs_model_train")
+        return loss.value
+
+    def close(self):
+        if getattr(self, "handle", None):
+            lib().vs_free_model(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def warm_features(theta1, p_leak0, s_kappa, resolution: int, stream=None):
+    import torch
+    B, n = theta1.shape[0], theta1.shape[-1]
+    x = torch.empty(B, 3, resolution, resolution, device=theta1.device)
+    _check(lib().vs_warm_features(_ptr(theta1, n, "theta1"), _ptr(p_leak0, n, "p_leak0"),
+                                  _ptr(s_kappa, n, "s", allow_none=True), B, n, resolution,
+                                  x.data_ptr(), _stream(stream)), "vs_warm_features")
+    return x
+
+
+def warm_target(theta_star, theta1, resolution: int, stream=None):
+    import torch
+    B, n = theta1.shape[0], theta1.shape[-1]
+    t = torch.empty(B, 1, resolution, resolution, device=theta1.device)
+    _check(lib().vs_warm_target(_ptr(theta_star, n, "theta_star"), _ptr(theta1, n, "theta1"), B,
+                                n, resolution, t.data_ptr(), _stream(stream)), "vs_warm_target")
+    return t
+
+
+def warm_apply(theta1, y, out=None, stream=None):
+    import torch
+    B, n = theta1.shape[0], theta1.shape[-1]
+    R = y.shape[-1]
+    if out is None:
+        out = torch.empty_like(theta1)
+    _check(lib().vs_warm_apply(_ptr(theta1, n, "theta1"), _ptr(y, None, "y"), B, n, R,
+                               out.data_ptr(), _stream(stream)), "vs_warm_apply")
+    return out
+
+
+class WarmPlan:
+    """Warm-started batched solve of maps [B, n, n] with one kernel:
+    a one-iteration plan gives the first iterate theta_1; the network predicts
+    the remaining correction at reduced resolution; the main plan starts from
+    theta_init = theta_1 + correction. Maps that do not converge from the warm
+    start are re-solved from theta_0 = 0 (`fallback`)."""
+
+    def __init__(self, kernel: Kernel, p_dyn, p_leak0, s_kappa, theta, model: Model,
+                 params: Optional[SolveParams] = None, stream=None):
+        import copy
+        import torch
+        prm = params or SolveParams()
+        one = copy.copy(prm)
+        one.max_iter = 1
+        B = p_dyn.shape[0]
+        self.B, self.model, self.stream = B, model, stream
+        self.kernel, self.p_dyn, self.p_leak0, self.s, self.theta = kernel, p_dyn, p_leak0, s_kappa, theta
+        self.theta1 = torch.empty_like(p_dyn)
+        self.theta_init = torch.empty_like(p_dyn)
+        sk = (lambda i: s_kappa[i]) if s_kappa is not None else (lambda i: None)
+        self.first = Plan([(kernel, p_dyn[i], p_leak0[i], sk(i), self.theta1[i]) for i in range(B)],
+                          one, stream)
+        self.warm = Plan([(kernel, p_dyn[i], p_leak0[i], sk(i), theta[i], self.theta_init[i])
+                          for i in range(B)], prm, stream)
+        self.params = prm
+        self.fallbacks = 0
+
+    @property
+    def launches(self) -> int:
+        # first plan, features, network (8 convs, 2 pools, 2 upsamplings), apply, warm plan
+        return self.first.launches + 1 + 12 + 1 + self.warm.launches
+
+    def run(self, stream=None):
+        st = stream if stream is not None else self.stream
+        self.first.run(st)
+        x = warm_features(self.theta1, self.p_leak0, self.s, self.model.resolution, st)
+        y = self.model.forward(x, st)
+        warm_apply(self.theta1, y, self.theta_init, st)
+        self.warm.run(st)
+
+    def info(self, fallback: bool = True):
+        infos = self.warm.info(self.stream)
+        bad = [i for i, inf in enumerate(infos) if inf["status"] != VS_OK]
+        self.fallbacks = len(bad)
+        if fallback and bad:
+            sk = (lambda i: self.s[i]) if self.s is not None else (lambda i: None)
+            items = [(self.kernel, self.p_dyn[i], self.p_leak0[i], sk(i), self.theta[i]) for i in bad]
+            redo = solve_batch(items, self.params, self.stream)
+            for j, i in enumerate(bad):
+                redo[j]["fell_back"] = True
+                infos[i] = redo[j]
+        return infos

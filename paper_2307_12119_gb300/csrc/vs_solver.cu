@@ -47,6 +47,7 @@ struct MapDesc {
   const float* p_leak0;
   const float* s;
   float* theta;
+  const float* theta_init;  // warm start (nullable)
   float* work;           // n*n, transposed spectral scratch
   const float* Kt;       // n*n cosine-basis kernel
   const float2* tw4n;
@@ -94,6 +95,7 @@ struct PlanDev {
   int max_iter;
   float beta, alpha, tol;
   int n_steps;           // transient
+  int warm;              // some map has a warm start
 };
 
 // ------------------------------------------------------------ grid barrier
@@ -175,8 +177,9 @@ __device__ __forceinline__ int find_map(const PlanDev& P, int task, bool row) {
 }
 
 // ------------------------------------------------------------ row task
-// MODE 0: steady iteration `step` (0 = initial source). MODE 1: transient
-// step `step` (0 = first source, n_steps = last inverse only).
+// MODE 0: steady iteration `step` (0 = initial source from theta_0 = 0,
+// -1 = initial source from a warm start theta_0, -2 = mean leakage only).
+// MODE 1: transient step `step` (0 = first source, n_steps = last inverse only).
 template <int MODE>
 __device__ void row_task(const PlanDev& P, int task, int step, float2* buf) {
   __shared__ double red_d[kThreads / 32];
@@ -185,7 +188,7 @@ __device__ void row_task(const PlanDev& P, int task, int step, float2* buf) {
   const int b = find_map(P, task, true);
   const MapDesc d = P.maps[b];
   MapState* ms = P.st + b;
-  if (MODE == 0 && step > 0 && !ms->active) return;
+  if (MODE == 0 && (step > 0 || step == -1) && !ms->active) return;
   const int n = d.n, F = d.rb >> 1, NP = padded_len(n), half = n >> 1;
   const int lgF = __ffs(F) - 1, lgn = __ffs(n) - 1;
   const int chunk = task - d.row_off;
@@ -193,8 +196,19 @@ __device__ void row_task(const PlanDev& P, int task, int step, float2* buf) {
   float* WT = d.work;
   const float2* tw = d.tw4n;
   const int* dr = d.digrev;
-  const bool first = (step == 0);
+  const bool first = (step <= 0);
+  const bool warm = (MODE == 0) && (step == -1);
+  const bool muonly = (MODE == 0) && (step == -2);
   const bool last = (MODE == 1) && (step == P.n_steps);
+  if (muonly) {
+    double acc = 0.0;
+    for (int i = threadIdx.x; i < d.rb * n; i += blockDim.x)
+      acc += (double)__ldg(&d.p_leak0[(size_t)y0 * n + i]);
+    double tot = block_sum(acc, red_d);
+    if (threadIdx.x == 0) P.part[d.part_off + chunk] = tot;
+    __syncthreads();
+    return;
+  }
 
   if (!first) {
     const int total = F * (half + 1);
@@ -227,7 +241,7 @@ __device__ void row_task(const PlanDev& P, int task, int step, float2* buf) {
 
   // fused elementwise update
   const float beta = P.beta, alpha = P.alpha;
-  const float mu = (MODE == 0 && !first) ? ms->mu_f : 0.f;
+  const float mu = (MODE == 0 && (!first || warm)) ? ms->mu_f : 0.f;
   double mu_acc = 0.0;
   float resid = 0.f;
   int flags = 0;
@@ -253,6 +267,7 @@ __device__ void row_task(const PlanDev& P, int task, int step, float2* buf) {
           if (MODE == 0) {
             pd[u][h] = __ldg(&d.p_dyn[idx]);
             if (!first) old[u][h] = d.theta[idx];
+            else if (warm && d.theta_init) old[u][h] = __ldg(&d.theta_init[idx]);
           } else if (!last) {
             pd[u][h] = __ldg(&d.p_dyn[(size_t)step * nn + idx]);
           }
@@ -270,7 +285,13 @@ __device__ void row_task(const PlanDev& P, int task, int step, float2* buf) {
         size_t idx = (size_t)(y0 + 2 * f + h) * n + x;
         float uu = h ? uv[u].y : uv[u].x;
         if (MODE == 0) {
-          if (first) {
+          if (warm) {
+            // theta_0 from the warm start; u_0 = theta_0 / (s (1 + alpha theta_0))
+            float t0 = old[u][h];
+            float u0 = t0 / (sk[u][h] * fmaf(alpha, t0, 1.f));
+            d.theta[idx] = t0;
+            q[h] = pd[u][h] + pl[u][h] + beta * fmaf(pl[u][h], t0, -mu * u0);
+          } else if (first) {
             d.theta[idx] = 0.f;
             q[h] = pd[u][h] + pl[u][h];
             mu_acc += (double)pl[u][h];
@@ -298,7 +319,7 @@ __device__ void row_task(const PlanDev& P, int task, int step, float2* buf) {
       buf[f * NP + pad(makhoul_pos(x, n))] = make_float2(q[0], q[1]);
     }
   }
-  if (MODE == 0 && first) {
+  if (MODE == 0 && first && !warm) {
     double tot = block_sum(mu_acc, red_d);
     if (threadIdx.x == 0) P.part[d.part_off + chunk] = tot;
   }
@@ -470,11 +491,16 @@ __device__ void decide(const PlanDev& P, int it) {
 
 __global__ void __launch_bounds__(kThreads, 3) k_solve_steady(PlanDev P) {
   extern __shared__ float2 smem[];
-  for (int t = blockIdx.x; t < P.row_tasks; t += gridDim.x) row_task<0>(P, t, 0, smem);
+  const int first = P.warm ? -2 : 0;
+  for (int t = blockIdx.x; t < P.row_tasks; t += gridDim.x) row_task<0>(P, t, first, smem);
   if (!grid_barrier(P.ctrl)) return;
   decide(P, 0);
   if (!grid_barrier(P.ctrl)) return;
   if (ld_acquire(&P.ctrl->active[0]) == 0u) return;
+  if (P.warm) {
+    for (int t = blockIdx.x; t < P.row_tasks; t += gridDim.x) row_task<0>(P, t, -1, smem);
+    if (!grid_barrier(P.ctrl)) return;
+  }
   for (int it = 1; it <= P.max_iter; ++it) {
     for (int t = blockIdx.x; t < P.col_tasks; t += gridDim.x) col_task<0>(P, t, smem);
     if (!grid_barrier(P.ctrl)) return;
@@ -553,7 +579,8 @@ struct TcCtx {
   int fin_uses;
 };
 
-enum TcPass { kTcRowFwdFirst = 0, kTcRowFwd = 1, kTcColFwd = 2, kTcColInv = 3, kTcRowInv = 4 };
+enum TcPass { kTcRowFwdFirst = 0, kTcRowFwd = 1, kTcColFwd = 2, kTcColInv = 3, kTcRowInv = 4,
+              kTcMu = 5, kTcWarm = 6 };
 
 // Producer: A chunk [128 rows][64 k], A[m][k] = G[(row0 + m) * ld + k0 + k]
 // (+ G2 for the first source P_dyn + P_leak0), split into BF16 hi/lo and
@@ -731,7 +758,7 @@ __device__ bool tc_task(const PlanDev& P, TcCtx& c, int pass, int task) {
   const MapDesc d = P.maps[b];
   MapState* ms = P.st + b;
   const bool first = pass == kTcRowFwdFirst;
-  if (!first && !ms->active) return true;
+  if (!first && pass != kTcMu && !ms->active) return true;
   const int n = d.n;
   const int tile = task - d.row_off;
   const int r0 = tile * 128;
@@ -739,6 +766,29 @@ __device__ bool tc_task(const PlanDev& P, TcCtx& c, int pass, int task) {
   double mu_acc = 0.0;
   float resid = 0.f;
   int flags = 0;
+  if (pass == kTcMu || pass == kTcWarm) {
+    // warm start: mean leakage of the tile, then the first source from theta_0
+    const float beta = P.beta, alpha = P.alpha, mu = ms->mu_f;
+    for (int i = threadIdx.x; i < 128 * n; i += blockDim.x) {
+      size_t idx = (size_t)r0 * n + i;
+      float pl = __ldg(&d.p_leak0[idx]);
+      if (pass == kTcMu) {
+        mu_acc += (double)pl;
+      } else {
+        float t0 = d.theta_init ? __ldg(&d.theta_init[idx]) : 0.f;
+        float sk = d.s ? __ldg(&d.s[idx]) : 1.f;
+        float u0 = t0 / (sk * fmaf(alpha, t0, 1.f));
+        d.theta[idx] = t0;
+        d.work2[idx] = __ldg(&d.p_dyn[idx]) + pl + beta * fmaf(pl, t0, -mu * u0);
+      }
+    }
+    if (pass == kTcMu) {
+      double tot = block_sum(mu_acc, red_d);
+      if (threadIdx.x == 0) P.part[d.part_off + tile] = tot;
+    }
+    __syncthreads();
+    return true;
+  }
   if (pass == kTcRowFwdFirst || pass == kTcRowFwd) {
     // rows forward: A[y][x] = q (first: P_dyn + P_leak0), B = C -> R[y][p], stored as RT[p][y]
     if (first) ok = tc_gemm(c, n, d.tcf, d.p_dyn, n, r0, d.p_leak0);
@@ -849,10 +899,16 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_solve_steady_tc(PlanDev P) {
         alive = false;
       }
   };
-  pass_all(kTcRowFwdFirst);
+  pass_all(P.warm ? kTcMu : kTcRowFwdFirst);
   if (alive) alive = grid_barrier(P.ctrl);
   if (alive) decide(P, 0);
   if (alive) alive = grid_barrier(P.ctrl);
+  if (alive && P.warm && ld_acquire(&P.ctrl->active[0]) != 0u) {
+    pass_all(kTcWarm);
+    if (alive) alive = grid_barrier(P.ctrl);
+    if (alive) pass_all(kTcRowFwd);
+    if (alive) alive = grid_barrier(P.ctrl);
+  }
   if (alive && ld_acquire(&P.ctrl->active[0]) != 0u) {
     for (int it = 1; it <= P.max_iter && alive; ++it) {
       pass_all(kTcColFwd);
@@ -1060,6 +1116,7 @@ struct vs_plan_t {
   float* d_work = nullptr;
   float* d_trstate = nullptr;
   int transient_steps = 0;
+  int warm = 0;
 };
 
 namespace {
@@ -1116,6 +1173,8 @@ int plan_layout(vs_plan_t* p, int elems, cudaStream_t s, bool transient, int n_s
     m.p_leak0 = it.p_leak0;
     m.s = it.s_kappa;
     m.theta = it.theta;
+    m.theta_init = it.theta_init;
+    if (it.theta_init) p->warm = 1;
     m.Kt = k->Kt32;
     m.tw4n = k->fft->tw4n;
     m.digrev = k->fft->digrev;
@@ -1234,6 +1293,7 @@ int plan_launch(vs_plan_t* p, cudaStream_t s, bool transient) {
   P.alpha = (float)p->params.alpha_per_K;
   P.tol = (float)p->params.tol_K;
   P.n_steps = p->transient_steps;
+  P.warm = p->warm;
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3(p->grid);
   cfg.blockDim = dim3(p->params.precision == VS_PREC_BF16_SPLIT && !transient ? kTcThreads : kThreads);
@@ -1293,7 +1353,7 @@ extern "C" int vs_plan_create(const vs_batch_item* items_host, int n_items,
     if (!it.k || !it.p_dyn || !it.p_leak0 || !it.theta)
       return vs_set_error(VS_ERR_INVALID_ARG, "item %d has a NULL kernel or map", i);
     uintptr_t al = (uintptr_t)it.p_dyn | (uintptr_t)it.p_leak0 | (uintptr_t)it.theta |
-                   (uintptr_t)it.s_kappa;
+                   (uintptr_t)it.s_kappa | (uintptr_t)it.theta_init;
     if (al & 15u) return vs_set_error(VS_ERR_INVALID_ARG, "item %d: maps must be 16-byte aligned", i);
     if (params->precision == VS_PREC_BF16_SPLIT && !tc_size_ok(it.k->n))
       return vs_set_error(VS_ERR_INVALID_ARG,
@@ -1402,7 +1462,7 @@ extern "C" int vs_solve_steady(vs_kernel k, const float* p_dyn, const float* p_l
                                const float* s_kappa, const vs_solve_params* params, float* theta,
                                vs_solve_info* info_host, void* stream) {
   if (!k) return vs_set_error(VS_ERR_INVALID_ARG, "NULL kernel");
-  vs_batch_item it = {k, p_dyn, p_leak0, s_kappa, theta};
+  vs_batch_item it = {k, p_dyn, p_leak0, s_kappa, theta, nullptr};
   vs_solve_info inf;
   int rc = vs_solve_batch(&it, 1, params, &inf, stream);
   if (info_host && (rc == VS_OK || rc >= VS_ERR_NO_CONVERGENCE)) *info_host = inf;
@@ -1427,7 +1487,7 @@ extern "C" int vs_solve_transient(vs_kernel k, int n_steps, const float* p_dyn_t
   cudaStream_t s = (cudaStream_t)stream;
   vs_plan_t* p = new vs_plan_t();
   p->n_items = 1;
-  p->items.push_back(vs_batch_item{k, p_dyn_trace, p_leak0, s_kappa, theta_trace});
+  p->items.push_back(vs_batch_item{k, p_dyn_trace, p_leak0, s_kappa, theta_trace, nullptr});
   p->params = *params;
   rc = plan_layout(p, 8192, s, true, n_steps);
   if (rc == VS_OK) {
@@ -1588,6 +1648,7 @@ extern "C" int vs_solve_steady_noalloc(vs_kernel k, const float* p_dyn, const fl
   P.alpha = (float)params->alpha_per_K;
   P.tol = (float)params->tol_K;
   P.n_steps = 0;
+  P.warm = 0;
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3(std::max(1, std::min(per_sm * sms, std::max(row_tasks, col_tasks))));
   cfg.blockDim = dim3(kThreads);

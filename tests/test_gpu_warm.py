@@ -1,0 +1,140 @@
+"""Learned warm start: the network's forward pass and gradients against the
+FP64 oracle network, training, checkpoints, and what the trained network
+gains over starting the fixed point from zero."""
+import os
+
+import numpy as np
+import pytest
+import torch
+
+import synth
+from oracle import cnn
+
+from _util import vs_params, vs_stack
+
+pytestmark = pytest.mark.gpu
+
+
+def _bf16_exact(a):
+    """Round float32 values to the nearest BF16 (ties to even), as float32."""
+    u = np.ascontiguousarray(a, dtype=np.float32).view(np.uint32).astype(np.uint64)
+    u = ((u + 0x7FFF + ((u >> 16) & 1)) & 0xFFFF0000).astype(np.uint32)
+    return u.view(np.float32)
+
+
+def test_network_forward_and_gradient_match_oracle():
+    import paper_2307_12119_gb300 as vs
+    C, R, B = 4, 16, 3
+    m = vs.Model(C, R, seed=3)
+    rng = np.random.default_rng(0)
+    p = rng.normal(0, 0.3, m.nparams).astype(np.float32)
+    nw = sum(co * ci * 9 for co, ci in cnn.layer_shapes(C))
+    p[:nw] = _bf16_exact(p[:nw])                  # the GPU computes with BF16 weights
+    m.set_params(p)
+    assert np.array_equal(m.get_params(), p)
+    x = rng.normal(0, 1, (B, 3, R, R)).astype(np.float32)
+    t = rng.normal(0, 1, (B, 1, R, R)).astype(np.float32)
+    xd, td = torch.tensor(x, device="cuda"), torch.tensor(t, device="cuda")
+    y = m.forward(xd).cpu().numpy()
+    p64 = p.astype(np.float64)
+    y_ref = cnn.forward(p64, C, x.astype(np.float64))
+    assert np.max(np.abs(y - y_ref)) <= 1e-4 * np.max(np.abs(y_ref))
+    loss, g = m.loss_grad(xd, td)
+    loss_ref, g_ref = cnn.loss_and_grad(p64, C, x.astype(np.float64), t.astype(np.float64))
+    assert loss == pytest.approx(loss_ref, rel=1e-5)
+    assert np.max(np.abs(g - g_ref)) <= 1e-4 * np.max(np.abs(g_ref))
+    rel = np.linalg.norm(g - g_ref) / np.linalg.norm(g_ref)
+    assert rel <= 1e-5
+
+
+def test_training_reduces_loss_and_checkpoint_round_trip(tmp_path):
+    import paper_2307_12119_gb300 as vs
+    C, R = 4, 16
+    m = vs.Model(C, R, seed=5)
+    g = torch.Generator(device="cuda").manual_seed(1)
+    x = torch.randn(256, 3, R, R, device="cuda", generator=g)
+    # a smooth target the network can learn: a local average of channel 0
+    t = torch.nn.functional.avg_pool2d(x[:, :1], 3, 1, 1).contiguous()
+    l0, _ = m.loss_grad(x[:64].contiguous(), t[:64].contiguous())
+    m.train(x, t, epochs=30, batch=32, lr=3e-3)
+    l1, _ = m.loss_grad(x[:64].contiguous(), t[:64].contiguous())
+    assert l1 < 0.3 * l0
+    path = str(tmp_path / "m.bin")
+    m.save(path)
+    m2 = vs.Model.load(path, C, R)
+    assert np.array_equal(m2.get_params(), m.get_params())
+    assert torch.equal(m2.forward(x[:8].contiguous()), m.forward(x[:8].contiguous()))
+
+
+def _dataset(vs, k, w, count, first, prm_cold, prm_one, R):
+    pd, pl, s = synth.steady_inputs(w, count, first=first, n_floorplans=64, device="cuda")
+    ths = torch.empty_like(pd)
+    th1 = torch.empty_like(pd)
+    vs.solve_batch([(k, pd[i], pl[i], s[i], ths[i]) for i in range(count)], prm_cold)
+    vs.solve_batch([(k, pd[i], pl[i], s[i], th1[i]) for i in range(count)], prm_one)
+    x = vs.warm_features(th1, pl, s, R)
+    t = vs.warm_target(ths, th1, R)
+    return pd, pl, s, ths, th1, x, t
+
+
+def test_warm_start_gain_over_cold_start():
+    import paper_2307_12119_gb300 as vs
+    w = synth.batch_workload(256, 2048)
+    k = vs.Kernel(vs_stack(w), vs.Grid(w.n, w.die_m))
+    R = 64
+    tol = 1e-2
+    prm = vs_params(w, tol_K=tol)
+    tight = vs_params(w, tol_K=1e-5)
+    one = vs_params(w, max_iter=1)
+    _, _, _, _, _, x, t = _dataset(vs, k, w, 1536, 0, tight, one, R)
+    m = vs.Model(16, R, seed=11)
+    loss = m.train(x, t, epochs=12, batch=32, lr=2e-3)
+    assert np.isfinite(loss)
+    # held-out maps
+    pd, pl, s, ths, th1, xv, tv = _dataset(vs, k, w, 256, 100000, tight, one, R)
+    lv, _ = m.loss_grad(xv, tv)
+    lz, _ = m.loss_grad(xv, torch.zeros_like(tv))
+    assert lv < 0.5 * lz                       # predicts most of the correction
+    # warm-started solves: same answers, fewer iterations in the main plan
+    th_w = torch.empty_like(pd)
+    wp = vs.WarmPlan(k, pd, pl, s, th_w, m, prm)
+    wp.run()
+    iw = wp.info()
+    assert all(i["status"] == vs.VS_OK for i in iw)
+    th_c = torch.empty_like(pd)
+    ic = vs.solve_batch([(k, pd[i], pl[i], s[i], th_c[i]) for i in range(256)], prm)
+    assert float((th_w - ths).abs().max()) <= 2 * tol
+    assert float((th_c - ths).abs().max()) <= 2 * tol
+    init_err = float((wp.theta_init - ths).abs().mean())
+    first_err = float((th1 - ths).abs().mean())
+    assert init_err < 0.5 * first_err
+    cold_it = np.mean([i["iterations"] for i in ic])
+    warm_it = 1 + np.mean([i["iterations"] for i in iw])     # + the first-iterate plan
+    print("warm start: cold %.2f iterations, warm %.2f (incl. first iterate); "
+          "mean |theta_init - theta*| %.3f K vs |theta_1 - theta*| %.3f K"
+          % (cold_it, warm_it, init_err, first_err))
+    assert warm_it <= cold_it + 0.5
+
+
+def test_bad_warm_start_falls_back_to_cold_solve():
+    import paper_2307_12119_gb300 as vs
+    w = synth.workload("c1_64")
+    k = vs.Kernel(vs_stack(w), vs.Grid(w.n, w.die_m))
+    pd, pl, s = synth.steady_inputs(w, 2, device="cuda")
+    th = torch.empty_like(pd)
+    crazy = torch.full_like(pd, 5000.0)                 # far beyond the runaway guard
+    infos = vs.solve_batch([(k, pd[0], pl[0], s[0], th[0], crazy[0]),
+                            (k, pd[1], pl[1], s[1], th[1], None)], vs_params(w))
+    assert infos[1]["status"] == vs.VS_OK
+    assert infos[0]["status"] in (vs.VS_ERR_RUNAWAY, vs.VS_ERR_NONFINITE, vs.VS_ERR_NO_CONVERGENCE,
+                                  vs.VS_OK)
+    m = vs.Model(4, 16, seed=1)
+    wp = vs.WarmPlan(k, pd, pl, s, th, m, vs_params(w))
+    wp.run()
+    wp.theta_init.fill_(5000.0)                         # poison the prediction
+    wp.warm.run()
+    infos = wp.info(fallback=True)
+    assert all(i["status"] == vs.VS_OK for i in infos)
+    assert wp.fallbacks == 2
+    ref, _ = vs.solve_steady(k, pd[0], pl[0], s[0], vs_params(w))
+    assert float((th[0] - ref).abs().max()) <= 1e-3

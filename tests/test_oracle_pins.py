@@ -344,3 +344,25 @@ def test_defaults_follow_paper_chip_parameter_table():
     assert st.kappa_W_mK == (g["si_conductivity_W_mK"], g["tim_conductivity_W_mK"],
                              g["spreader_conductivity_W_mK"])
     assert st.thickness_m[1:] == (g["tim_thickness_mm"] * 1e-3, g["spreader_thickness_mm"] * 1e-3)
+
+
+# ------------------------------------------- warm-start network reference
+
+def test_cnn_oracle_gradient_matches_finite_differences():
+    from oracle import cnn
+    rng = np.random.default_rng(4)
+    C, R, B = 2, 8, 2
+    p = rng.normal(0, 0.4, cnn.n_params(C))
+    x = rng.normal(0, 1, (B, 3, R, R))
+    t = rng.normal(0, 1, (B, 1, R, R))
+    loss, g = cnn.loss_and_grad(p, C, x, t)
+    idx = rng.choice(p.size, 40, replace=False)
+    h = 1e-6
+    for i in idx:
+        e = np.zeros_like(p)
+        e[i] = h
+        lp = np.mean((cnn.forward(p + e, C, x) - t) ** 2)
+        lm = np.mean((cnn.forward(p - e, C, x) - t) ** 2)
+        fd = (lp - lm) / (2 * h)
+        assert abs(fd - g[i]) <= 1e-6 * max(1.0, abs(fd)), (i, fd, g[i])
+    assert loss == pytest.approx(np.mean((cnn.forward(p, C, x) - t) ** 2), rel=1e-14)
