@@ -309,7 +309,8 @@ def run_ours(a):
     B = pd.shape[0]
     stream = torch.cuda.current_stream()
     tol = 1e-2
-    mk = lambda prec, t=tol: vs.SolveParams(phy.beta_per_K, phy.alpha_per_K, t, 50, prec)
+    mk = lambda prec, t=tol, eng=vs.VS_ENGINE_AUTO: vs.SolveParams(phy.beta_per_K, phy.alpha_per_K,
+                                                                  t, 50, prec, eng)
     model, train_info = _train_warm_model(vs, synth, k, w, dev, a.train_maps, a.train_epochs,
                                           synth.SEED + 104729 + rank, stream)
     items = lambda out: [(k, pd[i], pl[i], s[i], out[i]) for i in range(B)]
@@ -332,27 +333,34 @@ def run_ours(a):
         measure(name, runner, runner.launches)
         runners[name], thetas[name] = runner, theta
 
-    # the benchmark spec's form: batched + BF16 hi/lo split tensor cores + learned warm start
+    # the split-precision tensor-core form with the learned warm start
     th = torch.empty_like(pd)
     variant("bf16_split_learned_warm",
             vs.WarmPlan(k, pd, pl, s, th, model, mk(vs.VS_PREC_BF16_SPLIT)), th)
     th = torch.empty_like(pd)
     variant("bf16_split_cold", vs.Plan(items(th), mk(vs.VS_PREC_BF16_SPLIT)), th)
+    # FP32 with the learned warm start (its plans take the automatic engine)
     th = torch.empty_like(pd)
-    variant("fp32_warm", vs.WarmPlan(k, pd, pl, s, th, model, mk(vs.VS_PREC_FP32)), th)
+    variant("fp32_learned_warm", vs.WarmPlan(k, pd, pl, s, th, model, mk(vs.VS_PREC_FP32)), th)
+    # FP32 cold starts on both engines
     th = torch.empty_like(pd)
-    variant("fp32_cold", vs.Plan(items(th), mk(vs.VS_PREC_FP32)), th)
+    variant("fp32_streamed_cold",
+            vs.Plan(items(th), mk(vs.VS_PREC_FP32, eng=vs.VS_ENGINE_STREAMED)), th)
     th = torch.empty_like(pd)
-    plan = vs.Plan(items(th), mk(vs.VS_PREC_FP32, 1e-4))
-    measure("fp32_cold_tol1e-4", plan, plan.launches)
-    del plan, th
-    best = max(("fp32_cold", "bf16_split_cold", "fp32_warm", "bf16_split_learned_warm"),
-               key=lambda name: results[name]["value"])
+    variant("fp32_cluster_cold",
+            vs.Plan(items(th), mk(vs.VS_PREC_FP32, eng=vs.VS_ENGINE_CLUSTER)), th)
+    for eng, nm in ((vs.VS_ENGINE_STREAMED, "streamed"), (vs.VS_ENGINE_CLUSTER, "cluster")):
+        th = torch.empty_like(pd)
+        plan = vs.Plan(items(th), mk(vs.VS_PREC_FP32, 1e-4, eng))
+        measure("fp32_%s_tol1e-4" % nm, plan, plan.launches)
+        del plan, th
+    batched = ("fp32_cluster_cold", "fp32_streamed_cold", "bf16_split_cold", "fp32_learned_warm",
+               "bf16_split_learned_warm")
+    best = max(batched, key=lambda name: results[name]["value"])
     if ws > 1:                      # every rank reports the same headline path
-        t = torch.tensor([["fp32_cold", "bf16_split_cold", "fp32_warm",
-                           "bf16_split_learned_warm"].index(best)], device=dev)
+        t = torch.tensor([batched.index(best)], device=dev)
         dist.broadcast(t, 0)
-        best = ["fp32_cold", "bf16_split_cold", "fp32_warm", "bf16_split_learned_warm"][int(t.item())]
+        best = batched[int(t.item())]
     th_best = thetas[best]
 
     # plain: FP32, one map per vs_solve_steady call
@@ -407,46 +415,50 @@ def run_ours(a):
         pk = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json"))) if hbm_kind == "measured" else {}
         tc_peak = float(pk.get("bf16_tflops_sustained", 1700.0))
         ch = results["bf16_split_learned_warm"]
-        # tensor-core flops of the chosen step: 4 transform passes per iteration of both
-        # plans (first iterate + warm plan), each 2 n^3 per 128-row... = 2 n^3 x 3 per map
+        # tensor-core flops of the warm-started split path: per map and iteration (first
+        # iterate plan + warm plan) 4 transform passes of 2 n^3 flops, x 3 split products
         it_total = ch["iterations_mean"] + 1.0
         flops = B * it_total * 4 * 2 * w.n ** 3 * 3
         achieved_tf = flops / (ch["ms_local"] * 1e-3) / 1e12
         alg_bytes = B * w.n * w.n * ALG_BYTES_PER_PIXEL
-        fp = results["fp32_cold"]
-        tr = _traffic_record("k_solve_steady")
         # the headline is the fastest batched variant at the 1e-2 K tolerance
         bv = results[best]
         for r in results.values():
             r.pop("ms_local", None)
-        other = "bf16_split_learned_warm" if best != "bf16_split_learned_warm" else "fp32_cold"
+        other = "bf16_split_learned_warm" if best != "bf16_split_learned_warm" else "fp32_cluster_cold"
         cpu, acc = cpu_oracle_leg(w, pd.cpu(), pl.cpu(), s.cpu(), th_best.cpu(), a.cpu_seconds,
                                   other=thetas[other].cpu())
         acc["path"] = best
         acc["other_path"] = other
-        if best == "fp32_cold":
-            roof = {"bound": "hbm", "achieved": alg_bytes / (bv["ms_per_step"] * 1e-3) / 1e9,
-                    "peak": hbm, "unit": "GB/s",
-                    "frac": alg_bytes / (bv["ms_per_step"] * 1e-3) / 1e9 / hbm,
-                    "traffic": (tr["dram_bytes_per_map"] * B) if tr else None,
-                    "kernel": "k_solve_steady",
-                    "note": "achieved = 16 B/pixel algorithmic bytes x maps / step time; the "
-                            "kernel streams ~36 B/pixel per iteration; peak %s" % hbm_kind}
-        else:
-            roof = None
-        tc_roof = {"bound": "tensor", "achieved": achieved_tf, "peak": tc_peak,
-                   "unit": "TFLOP/s", "frac": achieved_tf / tc_peak, "traffic": None,
-                   "kernel": "k_solve_steady_tc"}
+
+        def hbm_roof(name, kernel):
+            r = results[name]
+            tr = _traffic_record(kernel)
+            ach = alg_bytes / (r["ms_per_step"] * 1e-3) / 1e9
+            return {"bound": "hbm", "achieved": ach, "peak": hbm, "unit": "GB/s",
+                    "frac": ach / hbm, "traffic": (tr["dram_bytes_per_map"] * B) if tr else None,
+                    "kernel": kernel,
+                    "note": "achieved = 16 B/pixel algorithmic bytes (3 input maps read, theta "
+                            "written) x maps / step time; peak = %s HBM copy bandwidth" % hbm_kind}
+
         cold_tc = results["bf16_split_cold"]
         cold_tf = B * (cold_tc["iterations_mean"]) * 4 * 2 * w.n ** 3 * 3 / (
             cold_tc["ms_per_step"] * 1e-3) / 1e12
-        if best == "bf16_split_cold":
-            roof = {"bound": "tensor", "achieved": cold_tf, "peak": tc_peak, "unit": "TFLOP/s",
-                    "frac": cold_tf / tc_peak, "traffic": None, "kernel": "k_solve_steady_tc",
-                    "note": "achieved = maps x iterations x 4 passes x 2n^3 x 3 split products / "
-                            "step time; peak = measured bf16 sustained"}
-        elif roof is None:
-            roof = tc_roof
+        tc_cold_roof = {"bound": "tensor", "achieved": cold_tf, "peak": tc_peak, "unit": "TFLOP/s",
+                        "frac": cold_tf / tc_peak, "traffic": None, "kernel": "k_solve_steady_tc",
+                        "note": "achieved = maps x iterations x 4 passes x 2n^3 x 3 split products "
+                                "/ step time; peak = measured bf16 sustained"}
+        tc_warm_roof = {"bound": "tensor", "achieved": achieved_tf, "peak": tc_peak,
+                        "unit": "TFLOP/s", "frac": achieved_tf / tc_peak, "traffic": None,
+                        "kernel": "k_solve_steady_tc"}
+        roofs = {"fp32_cluster_cold": hbm_roof("fp32_cluster_cold", "k_solve_cluster"),
+                 "fp32_streamed_cold": hbm_roof("fp32_streamed_cold", "k_solve_steady"),
+                 "bf16_split_cold": tc_cold_roof, "bf16_split_learned_warm": tc_warm_roof}
+        roof = roofs.get(best)
+        if roof is None:            # FP32 learned warm: two cluster plans around the network
+            roof = dict(roofs["fp32_cluster_cold"])
+            roof["achieved"] = alg_bytes / (bv["ms_per_step"] * 1e-3) / 1e9
+            roof["frac"] = roof["achieved"] / hbm
         out = {
             "metric": METRIC, "value": bv["value"], "unit": UNIT, "n_gpus": ws, "steps": a.steps,
             "warmup": a.warmup, "ms_per_step": bv["ms_per_step"], "higher_is_better": True,
@@ -465,16 +477,9 @@ def run_ours(a):
                              % (tol, plain_maps)},
             "warm_start_model": train_info,
             "roofline": roof,
-            "roofline_bf16_split_cold": {"bound": "tensor", "achieved": cold_tf, "peak": tc_peak,
-                                         "unit": "TFLOP/s", "frac": cold_tf / tc_peak,
-                                         "traffic": None, "kernel": "k_solve_steady_tc"},
-            "roofline_fp32_cold": {"bound": "hbm",
-                                   "achieved": alg_bytes / (fp["ms_per_step"] * 1e-3) / 1e9,
-                                   "peak": hbm, "unit": "GB/s",
-                                   "frac": alg_bytes / (fp["ms_per_step"] * 1e-3) / 1e9 / hbm,
-                                   "traffic": (tr["dram_bytes_per_map"] * B) if tr else None,
-                                   "kernel": "k_solve_steady",
-                                   "note": "16 B/pixel algorithmic bytes; peak %s" % hbm_kind},
+            "roofline_fp32_cluster_cold": roofs["fp32_cluster_cold"],
+            "roofline_fp32_streamed_cold": roofs["fp32_streamed_cold"],
+            "roofline_bf16_split_cold": tc_cold_roof,
             "cpu_baseline": cpu,
             "accuracy_vs_fp64_oracle": acc,
             "e2e": e2e,

@@ -96,18 +96,39 @@ typedef struct {
                                  (x = hi + lo, products hi*hi + hi*lo + lo*hi);
                                  batched plans with n = 128 or 256 */
 
+/* Execution engines of the FP32 steady solve (identical arithmetic, different
+ * data movement).
+ *   VS_ENGINE_STREAMED: one cooperative launch over all maps of a plan; the
+ *     spectral work map streams through global memory between the row and
+ *     column phases, phases separated by grid barriers; any n.
+ *   VS_ENGINE_CLUSTER: one thread-block cluster of n/32 CTAs per map that
+ *     keeps the map in shared memory for the whole solve (transposes through
+ *     distributed shared memory, cluster barriers); n in [32, 256]; one launch
+ *     per distinct n of a plan.
+ *   VS_ENGINE_AUTO: the cluster engine when precision is FP32 and every map
+ *     has n in [32, 256], the streamed engine otherwise.
+ * The transient solve and vs_solve_steady_noalloc always use the streamed
+ * engine; VS_PREC_BF16_SPLIT has its own tensor-core engine. */
+#define VS_ENGINE_AUTO 0
+#define VS_ENGINE_STREAMED 1
+#define VS_ENGINE_CLUSTER 2
+
 /* Parameters of a solve.
  *   beta_per_K : temperature coefficient of leakage (Eq. 5), >= 0
  *   alpha_per_K: temperature coefficient of the Green's function (Eq. 8), >= 0
  *   tol_K      : stop when max |theta_n - theta_{n-1}| <= tol_K (> 0)
  *   max_iter   : 1 .. 1000
- *   precision  : VS_PREC_FP32 or VS_PREC_BF16_SPLIT */
+ *   precision  : VS_PREC_FP32 or VS_PREC_BF16_SPLIT
+ *   engine     : VS_ENGINE_AUTO (0, what a zero-initialised struct selects),
+ *                VS_ENGINE_STREAMED or VS_ENGINE_CLUSTER; asking for the
+ *                cluster engine where it does not apply is VS_ERR_INVALID_ARG */
 typedef struct {
   double beta_per_K;
   double alpha_per_K;
   double tol_K;
   int max_iter;
   int precision;
+  int engine;
 } vs_solve_params;
 
 /* Per-map outcome. status is a vs_status; iterations counts applications of

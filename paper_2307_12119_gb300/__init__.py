@@ -21,13 +21,15 @@ __all__ = [
     "VS_ERR_RUNAWAY", "VS_ERR_NONFINITE", "VS_ERR_TIMEOUT", "VarsimError", "Stack", "Grid",
     "KernelOpts", "SolveParams", "Kernel", "Plan", "lib", "lib_path", "solve_steady",
     "solve_batch", "solve_transient", "hankel_radial", "EXPORTS", "solve_steady_noalloc",
-    "tc_transform", "VS_PREC_FP32", "VS_PREC_BF16_SPLIT", "Model", "WarmPlan",
+    "tc_transform", "VS_PREC_FP32", "VS_PREC_BF16_SPLIT", "VS_ENGINE_AUTO",
+    "VS_ENGINE_STREAMED", "VS_ENGINE_CLUSTER", "Model", "WarmPlan",
     "warm_features", "warm_target", "warm_apply",
 ]
 
 VS_OK, VS_ERR_INVALID_ARG, VS_ERR_CUDA, VS_ERR_OOM = 0, 1, 2, 3
 VS_ERR_NO_CONVERGENCE, VS_ERR_RUNAWAY, VS_ERR_NONFINITE, VS_ERR_TIMEOUT = 4, 5, 6, 7
 VS_PREC_FP32, VS_PREC_BF16_SPLIT = 0, 1
+VS_ENGINE_AUTO, VS_ENGINE_STREAMED, VS_ENGINE_CLUSTER = 0, 1, 2
 VS_MAX_LAYERS = 8
 
 EXPORTS = [
@@ -70,7 +72,7 @@ class _KernelOpts(C.Structure):
 
 class _SolveParams(C.Structure):
     _fields_ = [("beta_per_K", C.c_double), ("alpha_per_K", C.c_double), ("tol_K", C.c_double),
-                ("max_iter", C.c_int), ("precision", C.c_int)]
+                ("max_iter", C.c_int), ("precision", C.c_int), ("engine", C.c_int)]
 
 
 class _SolveInfo(C.Structure):
@@ -217,10 +219,11 @@ class SolveParams:
     tol_K: float = 1e-4
     max_iter: int = 50
     precision: int = 0
+    engine: int = 0
 
     def _c(self) -> _SolveParams:
         return _SolveParams(self.beta_per_K, self.alpha_per_K, self.tol_K, self.max_iter,
-                            self.precision)
+                            self.precision, self.engine)
 
 
 def _info(i: _SolveInfo) -> dict:
@@ -341,7 +344,8 @@ def solve_steady_noalloc(kernel: Kernel, p_dyn, p_leak0, s_kappa=None,
 
 
 class Plan:
-    """A batched solve over many maps (vs_plan_*): one persistent launch per run."""
+    """A batched solve over many maps (vs_plan_*). One launch per run; with the
+    cluster engine, one launch per distinct grid size (`launches`)."""
 
     def __init__(self, items, params: Optional[SolveParams] = None, stream=None):
         """items: sequence of (Kernel, p_dyn, p_leak0, s_kappa or None, theta

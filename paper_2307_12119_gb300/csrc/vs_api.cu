@@ -72,6 +72,9 @@ int vs_validate_params(const vs_solve_params* p) {
     return vs_set_error(VS_ERR_INVALID_ARG, "max_iter %d outside [1, 1000]", p->max_iter);
   if (p->precision != VS_PREC_FP32 && p->precision != VS_PREC_BF16_SPLIT)
     return vs_set_error(VS_ERR_INVALID_ARG, "unknown precision %d", p->precision);
+  if (p->engine != VS_ENGINE_AUTO && p->engine != VS_ENGINE_STREAMED &&
+      p->engine != VS_ENGINE_CLUSTER)
+    return vs_set_error(VS_ERR_INVALID_ARG, "unknown engine %d", p->engine);
   return VS_OK;
 }
 

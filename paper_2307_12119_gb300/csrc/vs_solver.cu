@@ -536,6 +536,476 @@ __global__ void __launch_bounds__(kThreads, 3) k_solve_transient(PlanDev P) {
   }
 }
 
+// ------------------------------------------------------------ cluster engine
+// The same fixed point for grids up to 256 x 256, with each map held by one
+// thread-block cluster for the whole solve, so the map never leaves on-chip
+// memory between iterations. CTA c of a cluster of n / 32 CTAs owns
+//   - rows y in [32c, 32c + 32): 16 row FFTs, two rows packed per FFT;
+//   - the x-frequency pairs (j, n - j), j in [16c, 16c + 16), pair 0 being
+//     (0, n/2): 16 column FFTs, the two frequencies of a pair packed per FFT.
+// Pairing k with n - k puts both operands of every DCT pre/post-twiddle in
+// the CTA that produces them, so each exchange stores finished FFT inputs
+// straight into the consumer's shared memory (st.shared::cluster) and one
+// cluster barrier per exchange orders them. An iteration is: column phase
+// (forward DCT along y, multiply by K / (1 - beta mu K) (Eq. 20 with
+// alpha = 0), inverse DCT along y, push to the row owners), barrier, row
+// phase (inverse DCT along x, the fused update of the streamed engine,
+// forward DCT along x, push to the column owners together with the residual
+// partials), barrier; then every CTA takes the same convergence decision from
+// the same partials, so control flow stays uniform across the cluster. Global
+// memory sees only the inputs (read) and theta (written). There are no spin
+// waits: the cluster barriers are hardware barriers.
+
+constexpr int kClThreads = 256;
+constexpr int kClRows = 32;             // rows and x-frequencies per CTA
+constexpr int kClF = kClRows / 2;       // FFTs per CTA in each phase
+constexpr int kClMaxRanks = 8;
+
+struct ClSlots {
+  double part[kClMaxRanks];
+  float resid[kClMaxRanks];
+  int flags[kClMaxRanks];
+};
+
+struct ClusterDev {
+  const MapDesc* maps;
+  const int* order;      // cluster index -> map index
+  vs_solve_info* info;
+  int max_iter;
+  float beta, alpha, tol;
+};
+
+// Shared memory of one CTA for grid size N, in float2 units: row buffer
+// [kClF][NP], column buffer [kClF][NP], spectral multiplier of the CTA's
+// frequency pairs [N][kClF] (column index XOR-swizzled by the row), the
+// first-pass FFT twiddles W_N^{j r} stored [r][j] (r < 16, j < N/16), the
+// DCT twiddles W_4N^k (k < N), then the partials slots.
+template <int N>
+struct ClLayout {
+  static constexpr int NP = N + N / 16 + 1;
+  static constexpr int kBcol = kClF * NP;
+  static constexpr int kLs = 2 * kClF * NP;
+  static constexpr int kTwp = kLs + N * kClF;
+  static constexpr int kTdct = kTwp + N;
+  static constexpr int kSlots = kTdct + N;
+  static constexpr size_t kBytes = (size_t)kSlots * sizeof(float2) + sizeof(ClSlots);
+};
+
+inline size_t cl_smem_bytes(int n) {
+  switch (n) {
+    case 32: return ClLayout<32>::kBytes;
+    case 64: return ClLayout<64>::kBytes;
+    case 128: return ClLayout<128>::kBytes;
+    default: return ClLayout<256>::kBytes;
+  }
+}
+
+__device__ __forceinline__ unsigned cl_rank() {
+  unsigned r;
+  asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
+  return r;
+}
+__device__ __forceinline__ unsigned cl_index() {
+  unsigned r;
+  asm volatile("mov.u32 %0, %%clusterid.x;" : "=r"(r));
+  return r;
+}
+__device__ __forceinline__ void cl_arrive_relaxed() {
+  asm volatile("barrier.cluster.arrive.relaxed.aligned;" ::: "memory");
+}
+__device__ __forceinline__ void cl_wait() {
+  asm volatile("barrier.cluster.wait.acquire.aligned;" ::: "memory");
+}
+__device__ __forceinline__ void cl_sync() {
+  asm volatile(
+      "barrier.cluster.arrive.release.aligned;\n\t"
+      "barrier.cluster.wait.acquire.aligned;" ::: "memory");
+}
+// Address of the same shared-memory location in the CTA of cluster rank `rank`.
+__device__ __forceinline__ unsigned cl_map(const void* p, unsigned rank) {
+  unsigned a = (unsigned)__cvta_generic_to_shared(p), r;
+  asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(r) : "r"(a), "r"(rank));
+  return r;
+}
+__device__ __forceinline__ void cl_put(unsigned a, float2 v) {
+  asm volatile("st.shared::cluster.v2.f32 [%0], {%1, %2};" ::"r"(a), "f"(v.x), "f"(v.y) : "memory");
+}
+__device__ __forceinline__ void cl_put(unsigned a, float v) {
+  asm volatile("st.shared::cluster.f32 [%0], %1;" ::"r"(a), "f"(v) : "memory");
+}
+__device__ __forceinline__ void cl_put(unsigned a, int v) {
+  asm volatile("st.shared::cluster.s32 [%0], %1;" ::"r"(a), "r"(v) : "memory");
+}
+__device__ __forceinline__ void cl_put(unsigned a, double v) {
+  asm volatile("st.shared::cluster.f64 [%0], %1;" ::"r"(a), "d"(v) : "memory");
+}
+
+// Digit-reversed position of frequency k in the output of the radix-16 x
+// (N/16) forward FFT below (the same order as the streamed engine's tables).
+template <int N>
+__device__ __forceinline__ int cl_dr(int k) {
+  return (k & 15) * (N / 16) + (k >> 4);
+}
+
+// The 16 in-place FFTs of length N of a buffer (stride NP), radix 16 then
+// radix N/16: forward = decimation in frequency (natural in, digit-reversed
+// out), inverse = the exact reverse (digit-reversed in, natural out, x N).
+// Same passes as vsfft::fft_forward / fft_inverse with every size a
+// compile-time constant and the twiddles read from shared memory.
+template <int N, bool FWD>
+__device__ __forceinline__ void cl_fft(float2* buf, const float2* twp) {
+  constexpr int M1 = N / 16;       // sub-stride of the radix-16 pass
+  constexpr int R2 = N / 16;       // radix of the second pass
+  constexpr int NP = ClLayout<N>::NP;
+  auto pass16 = [&]() {
+    for (int b = threadIdx.x; b < kClF * M1; b += kClThreads) {
+      const int f = b / M1, j = b % M1;
+      float2* base = buf + f * NP;
+      float2 v[16];
+#pragma unroll
+      for (int r = 0; r < 16; ++r) v[r] = base[pad(j + r * M1)];
+      if (FWD) {
+        dft16<true>(v);
+        if (M1 > 1) {
+#pragma unroll
+          for (int r = 1; r < 16; ++r) v[r] = cmul(v[r], twp[r * M1 + j]);
+        }
+      } else {
+        if (M1 > 1) {
+#pragma unroll
+          for (int r = 1; r < 16; ++r) v[r] = cmulc(v[r], twp[r * M1 + j]);
+        }
+        dft16<false>(v);
+      }
+#pragma unroll
+      for (int r = 0; r < 16; ++r) base[pad(j + r * M1)] = v[r];
+    }
+  };
+  auto pass2 = [&]() {
+    for (int b = threadIdx.x; b < kClF * 16; b += kClThreads) {
+      float2* base = buf + (b >> 4) * NP + (b & 15) * R2 + (((b & 15) * R2) >> 4);
+      float2 v[R2];
+#pragma unroll
+      for (int r = 0; r < R2; ++r) v[r] = base[r];
+      dftR<R2, FWD>(v);
+#pragma unroll
+      for (int r = 0; r < R2; ++r) base[r] = v[r];
+    }
+  };
+  if (FWD) {
+    pass16();
+    __syncthreads();
+    pass2();
+  } else {
+    pass2();
+    __syncthreads();
+    pass16();
+  }
+  __syncthreads();
+}
+
+template <int N>
+__global__ void __launch_bounds__(kClThreads, 2) k_solve_cluster(ClusterDev P) {
+  using Lay = ClLayout<N>;
+  constexpr int NP = Lay::NP, half = N / 2, ranks = N / kClRows;
+  extern __shared__ __align__(16) float2 cl_smem[];
+  __shared__ double red_d[kClThreads / 32];
+  __shared__ float red_f[kClThreads / 32];
+  __shared__ int red_i[kClThreads / 32];
+  const unsigned rank = cl_rank();
+  const int b = __ldg(&P.order[cl_index()]);
+  const MapDesc d = P.maps[b];
+  float2* brow = cl_smem;
+  float2* bcol = cl_smem + Lay::kBcol;
+  float2* Ls = cl_smem + Lay::kLs;
+  float2* twp = cl_smem + Lay::kTwp;
+  float2* tw = cl_smem + Lay::kTdct;
+  ClSlots* slots = reinterpret_cast<ClSlots*>(cl_smem + Lay::kSlots);
+  const int y0 = (int)rank * kClRows;
+  const int j0 = (int)rank * kClF;
+  const float beta = P.beta, alpha = P.alpha;
+  // W_4N^e table of the kernel's FFT tables -> shared memory
+  for (int i = threadIdx.x; i < N; i += kClThreads) {
+    const int r = i / (N / 16), j = i % (N / 16);
+    twp[i] = __ldg(&d.tw4n[4 * j * r]);
+    tw[i] = __ldg(&d.tw4n[i]);
+  }
+  __syncthreads();
+
+  // Row phase update. mode 0: initial source from theta_0 = 0 (accumulates
+  // the leakage sum); 1: initial source from the warm start theta_0;
+  // 2: iteration (brow holds u after the inverse transform along x).
+  auto row_update = [&](int mode, float mu, float& resid, int& flags, double& pl_sum) {
+    constexpr int total = kClF * N;
+    for (int base = threadIdx.x; base < total; base += kU * kClThreads) {
+      float pl[kU][2], pd[kU][2], sk[kU][2], old[kU][2];
+      float2 uv[kU];
+#pragma unroll
+      for (int u = 0; u < kU; ++u) {
+        const int it = base + u * kClThreads;
+        uv[u] = make_float2(0.f, 0.f);
+#pragma unroll
+        for (int h = 0; h < 2; ++h) pl[u][h] = pd[u][h] = old[u][h] = 0.f, sk[u][h] = 1.f;
+        if (it < total) {
+          const int f = it / N, x = it % N;
+          if (mode == 2) uv[u] = brow[f * NP + pad(makhoul_pos(x, N))];
+#pragma unroll
+          for (int h = 0; h < 2; ++h) {
+            const size_t idx = (size_t)(y0 + 2 * f + h) * N + x;
+            pl[u][h] = __ldg(&d.p_leak0[idx]);
+            pd[u][h] = __ldg(&d.p_dyn[idx]);
+            if (d.s) sk[u][h] = __ldg(&d.s[idx]);
+            if (mode == 2) old[u][h] = d.theta[idx];
+            else if (mode == 1) old[u][h] = __ldg(&d.theta_init[idx]);
+          }
+        }
+      }
+#pragma unroll
+      for (int u = 0; u < kU; ++u) {
+        const int it = base + u * kClThreads;
+        if (it >= total) continue;
+        const int f = it / N, x = it % N;
+        float q[2];
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+          const size_t idx = (size_t)(y0 + 2 * f + h) * N + x;
+          if (mode == 0) {
+            d.theta[idx] = 0.f;
+            q[h] = pd[u][h] + pl[u][h];
+            pl_sum += (double)pl[u][h];
+          } else if (mode == 1) {
+            // u_0 = theta_0 / (s (1 + alpha theta_0))
+            const float t0 = old[u][h];
+            const float u0 = t0 / (sk[u][h] * fmaf(alpha, t0, 1.f));
+            d.theta[idx] = t0;
+            q[h] = pd[u][h] + pl[u][h] + beta * fmaf(pl[u][h], t0, -mu * u0);
+          } else {
+            const float uu = h ? uv[u].y : uv[u].x;
+            const float den = fmaf(-alpha * sk[u][h], uu, 1.f);
+            if (!(den > 0.05f)) flags |= kFlagRunaway;
+            const float th = sk[u][h] * uu / den;
+            if (!isfinite(th)) flags |= kFlagNonfinite;
+            else resid = fmaxf(resid, fabsf(th - old[u][h]));
+            d.theta[idx] = th;
+            q[h] = pd[u][h] + pl[u][h] + beta * fmaf(pl[u][h], th, -mu * uu);
+          }
+        }
+        brow[f * NP + pad(makhoul_pos(x, N))] = make_float2(q[0], q[1]);
+      }
+    }
+  };
+
+  // After the forward FFT of brow: DCT-II post-twiddle of every frequency
+  // pair of every row pair, stored into the column buffer of the pair's owner
+  // at the Makhoul positions of the two rows.
+  auto push_rows = [&]() {
+    for (int it = threadIdx.x; it < kClF * half; it += kClThreads) {
+      const int f = it % kClF, j = it / kClF;
+      const float2* row = brow + f * NP;
+      float2 ea, eb;
+      if (j == 0) {
+        const float2 z0 = row[0], zh = row[pad(cl_dr<N>(half))];
+        const float2 x0 = dct_post(z0, z0, tw[0]), xh = dct_post(zh, zh, tw[half]);
+        ea = make_float2(x0.x, xh.x);
+        eb = make_float2(x0.y, xh.y);
+      } else {
+        const float2 zk = row[pad(cl_dr<N>(j))], zn = row[pad(cl_dr<N>(N - j))];
+        const float2 xk = dct_post(zk, zn, tw[j]), xn = dct_post(zn, zk, tw[N - j]);
+        ea = make_float2(xk.x, xn.x);
+        eb = make_float2(xk.y, xn.y);
+      }
+      const int ya = y0 + 2 * f;
+      const unsigned dst = cl_map(bcol, (unsigned)(j / kClF)) + (unsigned)((j % kClF) * NP) * 8u;
+      cl_put(dst + (unsigned)pad(makhoul_pos(ya, N)) * 8u, ea);
+      cl_put(dst + (unsigned)pad(makhoul_pos(ya + 1, N)) * 8u, eb);
+    }
+  };
+
+  // Column phase: the column buffer holds the x-spectra of all rows for this
+  // CTA's frequency pairs.
+  auto col_phase = [&]() {
+    cl_fft<N, true>(bcol, twp);
+    for (int it = threadIdx.x; it < kClF * (half + 1); it += kClThreads) {
+      const int jj = it % kClF, q = it / kClF;
+      float2* col = bcol + jj * NP;
+      const int ia = pad(cl_dr<N>(q)), ib = pad(cl_dr<N>(q == 0 ? 0 : N - q));
+      const float2 zq = col[ia], zn = col[ib];
+      float2 y = dct_post(zq, zn, tw[q]);
+      const float2 L = Ls[q * kClF + (jj ^ (q & (kClF - 1)))];
+      y.x *= L.x;
+      y.y *= L.y;
+      float2 yn = make_float2(0.f, 0.f);
+      if (q == half) {
+        yn = y;
+      } else if (q != 0) {
+        yn = dct_post(zn, zq, tw[N - q]);
+        const int qn = N - q;
+        const float2 Ln = Ls[qn * kClF + (jj ^ (qn & (kClF - 1)))];
+        yn.x *= Ln.x;
+        yn.y *= Ln.y;
+      }
+      col[ia] = dct_pre(y.x, yn.x, y.y, yn.y, tw[q]);
+      if (q != 0 && q != half) col[ib] = dct_pre(yn.x, y.x, yn.y, y.y, tw[N - q]);
+    }
+    __syncthreads();
+    cl_fft<N, false>(bcol, twp);
+    // inverse pre-twiddle along x for both frequencies of each pair, stored
+    // into the row buffer of the owner of each row pair
+    for (int it = threadIdx.x; it < kClF * half; it += kClThreads) {
+      const int jj = it % kClF, r = it / kClF;
+      const float2* col = bcol + jj * NP;
+      const int ya = 2 * r;
+      const float2 va = col[pad(makhoul_pos(ya, N))], vb = col[pad(makhoul_pos(ya + 1, N))];
+      const int j = j0 + jj;
+      int pa, pb;
+      float2 ea, eb;
+      if (j == 0) {
+        pa = 0;
+        pb = half;
+        ea = dct_pre(va.x, 0.f, vb.x, 0.f, tw[0]);
+        eb = dct_pre(va.y, va.y, vb.y, vb.y, tw[half]);
+      } else {
+        pa = j;
+        pb = N - j;
+        ea = dct_pre(va.x, va.y, vb.x, vb.y, tw[j]);
+        eb = dct_pre(va.y, va.x, vb.y, vb.x, tw[N - j]);
+      }
+      const unsigned dst = cl_map(brow, (unsigned)(ya / kClRows)) +
+                           (unsigned)(((ya % kClRows) >> 1) * NP) * 8u;
+      cl_put(dst + (unsigned)pad(cl_dr<N>(pa)) * 8u, ea);
+      cl_put(dst + (unsigned)pad(cl_dr<N>(pb)) * 8u, eb);
+    }
+  };
+
+  auto put_part = [&](double v) {
+    if (threadIdx.x == 0)
+      for (int r = 0; r < ranks; ++r) cl_put(cl_map(&slots->part[rank], (unsigned)r), v);
+  };
+  auto cluster_mu = [&]() {
+    double sum = 0.0;
+    for (int r = 0; r < ranks; ++r) sum += slots->part[r];
+    return sum / ((double)N * N);
+  };
+
+  int status = VS_OK, iters = 0, growth = 0;
+  float prev = INFINITY;
+  double mu = 0.0;
+  bool stop = false;
+  cl_arrive_relaxed();  // peers store into this CTA only after every CTA started
+
+  // initial source (Eq. 17 at theta_0) and the mean leakage mu (Sec. III-C)
+  if (d.theta_init) {
+    double acc = 0.0;
+    for (int i = threadIdx.x; i < kClRows * N; i += kClThreads)
+      acc += (double)__ldg(&d.p_leak0[(size_t)y0 * N + i]);
+    const double tot = block_sum(acc, red_d);
+    cl_wait();
+    put_part(tot);
+    cl_sync();
+    mu = cluster_mu();
+    if ((double)beta * mu * (double)d.kmax >= 0.999) {
+      status = VS_ERR_RUNAWAY;
+      stop = true;
+    } else {
+      float r0 = 0.f;
+      int f0 = 0;
+      double unused = 0.0;
+      row_update(1, (float)mu, r0, f0, unused);
+      __syncthreads();
+      cl_fft<N, true>(brow, twp);
+      push_rows();
+      cl_sync();
+    }
+  } else {
+    float r0 = 0.f;
+    int f0 = 0;
+    double acc = 0.0;
+    row_update(0, 0.f, r0, f0, acc);
+    const double tot = block_sum(acc, red_d);  // synchronises the block
+    cl_fft<N, true>(brow, twp);
+    cl_wait();
+    push_rows();
+    put_part(tot);
+    cl_sync();
+    mu = cluster_mu();
+    if ((double)beta * mu * (double)d.kmax >= 0.999) {
+      status = VS_ERR_RUNAWAY;
+      stop = true;
+    }
+  }
+
+  if (!stop) {
+    const float mu_f = (float)mu;
+    {
+      // spectral multiplier of this CTA's frequency pairs, with the 1 / N^2
+      // of the two unnormalised inverse transforms folded in
+      const float bm = beta * mu_f;
+      const float inv_n2 = 1.f / ((float)N * (float)N);
+      for (int it = threadIdx.x; it < kClF * N; it += kClThreads) {
+        const int q = it % N, jj = it / N, j = j0 + jj;
+        const int pa = j == 0 ? 0 : j, pb = j == 0 ? half : N - j;
+        const float ka = __ldg(&d.Kt[(size_t)pa * N + q]), kb = __ldg(&d.Kt[(size_t)pb * N + q]);
+        Ls[q * kClF + (jj ^ (q & (kClF - 1)))] =
+            make_float2(ka / (1.f - bm * ka) * inv_n2, kb / (1.f - bm * kb) * inv_n2);
+      }
+      __syncthreads();
+    }
+    for (int it = 1; it <= P.max_iter; ++it) {
+      col_phase();
+      cl_sync();
+      cl_fft<N, false>(brow, twp);
+      float resid = 0.f;
+      int flags = 0;
+      double unused = 0.0;
+      row_update(2, mu_f, resid, flags, unused);
+      const float rm = block_max(resid, red_f);  // both synchronise the block
+      const int fo = block_or(flags, red_i);
+      cl_fft<N, true>(brow, twp);
+      push_rows();
+      if (threadIdx.x == 0) {
+        for (int r = 0; r < ranks; ++r) {
+          cl_put(cl_map(&slots->resid[rank], (unsigned)r), rm);
+          cl_put(cl_map(&slots->flags[rank], (unsigned)r), fo);
+        }
+      }
+      cl_sync();
+      // the same decision in every thread of every CTA of the cluster
+      float rr = 0.f;
+      int ff = 0;
+      for (int r = 0; r < ranks; ++r) {
+        rr = fmaxf(rr, slots->resid[r]);
+        ff |= slots->flags[r];
+      }
+      iters = it;
+      if (ff & kFlagNonfinite) {
+        status = VS_ERR_NONFINITE;
+        stop = true;
+      } else if (ff & kFlagRunaway) {
+        status = VS_ERR_RUNAWAY;
+        stop = true;
+      } else if (rr <= P.tol) {
+        status = VS_OK;
+        stop = true;
+      } else {
+        growth = (it > 2 && rr > prev) ? growth + 1 : 0;
+        if (it >= P.max_iter || growth >= 5) {
+          status = VS_ERR_NO_CONVERGENCE;
+          stop = true;
+        }
+      }
+      prev = rr;
+      if (stop) break;
+    }
+  }
+  if (rank == 0 && threadIdx.x == 0) {
+    vs_solve_info* inf = P.info + b;
+    inf->status = status;
+    inf->iterations = iters;
+    inf->residual_K = (double)prev;
+    inf->mu_W = mu;
+  }
+}
+
 __global__ void k_twiddles(int n, float2* tw) {
   int e = blockIdx.x * blockDim.x + threadIdx.x;
   if (e >= 4 * n) return;
@@ -1117,6 +1587,9 @@ struct vs_plan_t {
   float* d_trstate = nullptr;
   int transient_steps = 0;
   int warm = 0;
+  bool cluster = false;                       // cluster engine
+  std::vector<std::pair<int, int>> cl_groups; // (n, maps) per launch, in order
+  int* d_order = nullptr;                     // maps grouped by n
 };
 
 namespace {
@@ -1136,6 +1609,8 @@ void plan_release(vs_plan_t* p) {
   cudaFree(p->d_ctrl);
   cudaFree(p->d_work);
   cudaFree(p->d_trstate);
+  cudaFree(p->d_order);
+  p->d_order = nullptr;
   p->d_maps = nullptr;
   p->d_row_map = nullptr;
   p->d_col_map = nullptr;
@@ -1274,7 +1749,134 @@ int plan_layout(vs_plan_t* p, int elems, cudaStream_t s, bool transient, int n_s
   return VS_OK;
 }
 
+bool cluster_size_ok(int n) { return n >= kClRows && n <= kClRows * kClMaxRanks; }
+
+using ClusterFn = void (*)(ClusterDev);
+ClusterFn cluster_kernel(int n) {
+  switch (n) {
+    case 32: return k_solve_cluster<32>;
+    case 64: return k_solve_cluster<64>;
+    case 128: return k_solve_cluster<128>;
+    default: return k_solve_cluster<256>;
+  }
+}
+
+size_t g_smem_attr_cluster[4] = {0, 0, 0, 0};  // per instantiation, n = 32 .. 256
+
+cudaLaunchConfig_t cluster_config(int n, int count, cudaStream_t s, cudaLaunchAttribute* attr) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3((unsigned)(n / kClRows) * (unsigned)count);
+  cfg.blockDim = dim3(kClThreads);
+  cfg.dynamicSmemBytes = cl_smem_bytes(n);
+  cfg.stream = s;
+  attr[0].id = cudaLaunchAttributeClusterDimension;
+  attr[0].val.clusterDim.x = (unsigned)(n / kClRows);
+  attr[0].val.clusterDim.y = 1;
+  attr[0].val.clusterDim.z = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  return cfg;
+}
+
+// Cluster engine layout: descriptors only (no spectral scratch), maps grouped
+// by grid size, one launch per group.
+int plan_layout_cluster(vs_plan_t* p, cudaStream_t s) {
+  plan_release(p);
+  const int n_items = p->n_items;
+  std::map<int, std::vector<int>> by_n;
+  for (int i = 0; i < n_items; ++i) by_n[p->items[i].k->n].push_back(i);
+  std::vector<int> order;
+  p->cl_groups.clear();
+  size_t smem = 0;
+  for (auto& g : by_n) {
+    p->cl_groups.push_back({g.first, (int)g.second.size()});
+    order.insert(order.end(), g.second.begin(), g.second.end());
+    smem = std::max(smem, cl_smem_bytes(g.first));
+  }
+  std::vector<MapDesc> maps(n_items);
+  for (int i = 0; i < n_items; ++i) {
+    const vs_batch_item& it = p->items[i];
+    MapDesc& m = maps[i];
+    memset(&m, 0, sizeof(m));
+    m.p_dyn = it.p_dyn;
+    m.p_leak0 = it.p_leak0;
+    m.s = it.s_kappa;
+    m.theta = it.theta;
+    m.theta_init = it.theta_init;
+    if (it.theta_init) p->warm = 1;
+    m.Kt = it.k->Kt32;
+    m.tw4n = it.k->fft->tw4n;
+    m.digrev = it.k->fft->digrev;
+    m.kmax = it.k->kmax;
+    m.n = it.k->n;
+  }
+  p->smem = smem;
+  VS_CUDA_TRY(cudaMalloc(&p->d_maps, sizeof(MapDesc) * n_items));
+  VS_CUDA_TRY(cudaMalloc(&p->d_order, sizeof(int) * n_items));
+  VS_CUDA_TRY(cudaMalloc(&p->d_info, sizeof(vs_solve_info) * n_items));
+  VS_CUDA_TRY(cudaMalloc(&p->d_ctrl, sizeof(Ctrl)));
+  VS_CUDA_TRY(cudaMemcpyAsync(p->d_maps, maps.data(), sizeof(MapDesc) * n_items,
+                              cudaMemcpyHostToDevice, s));
+  VS_CUDA_TRY(cudaMemcpyAsync(p->d_order, order.data(), sizeof(int) * n_items,
+                              cudaMemcpyHostToDevice, s));
+  VS_CUDA_TRY(cudaMemsetAsync(p->d_info, 0, sizeof(vs_solve_info) * n_items, s));
+  VS_CUDA_TRY(cudaMemsetAsync(p->d_ctrl, 0, sizeof(Ctrl), s));
+  for (auto& g : p->cl_groups) {
+    ClusterFn fn = cluster_kernel(g.first);
+    {
+      std::lock_guard<std::mutex> lk(g_attr_mutex);
+      size_t& cur = g_smem_attr_cluster[__builtin_ctz((unsigned)g.first) - 5];
+      if (cur == 0) {
+        VS_CUDA_TRY(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)cl_smem_bytes(g.first)));
+        VS_CUDA_TRY(cudaFuncSetAttribute(fn, cudaFuncAttributePreferredSharedMemoryCarveout, 100));
+        cur = cl_smem_bytes(g.first);
+      }
+    }
+    cudaLaunchAttribute attr[1];
+    cudaLaunchConfig_t cfg = cluster_config(g.first, 1, s, attr);
+    int clusters = 0;
+    VS_CUDA_TRY(cudaOccupancyMaxActiveClusters(&clusters, fn, &cfg));
+    if (clusters < 1)
+      return vs_set_error(VS_ERR_INVALID_ARG, "no cluster of %d CTAs fits on the device (n=%d)",
+                          g.first / kClRows, g.first);
+    if (getenv("VS_DEBUG")) {
+      cudaFuncAttributes fa;
+      cudaFuncGetAttributes(&fa, fn);
+      fprintf(stderr, "varsim plan: cluster n=%d maps=%d ranks=%d smem=%zu regs=%d local=%zu "
+              "active_clusters=%d\n", g.first, g.second, g.first / kClRows, cl_smem_bytes(g.first),
+              fa.numRegs, fa.localSizeBytes, clusters);
+    }
+  }
+  p->grid = 0;
+  VS_CUDA_TRY(cudaStreamSynchronize(s));  // host vectors must outlive the copies
+  return VS_OK;
+}
+
+int plan_launch_cluster(vs_plan_t* p, cudaStream_t s) {
+  int off = 0;
+  for (auto& g : p->cl_groups) {
+    ClusterDev P;
+    P.maps = p->d_maps;
+    P.order = p->d_order + off;
+    P.info = p->d_info;
+    P.max_iter = p->params.max_iter;
+    P.beta = (float)p->params.beta_per_K;
+    P.alpha = (float)p->params.alpha_per_K;
+    P.tol = (float)p->params.tol_K;
+    cudaLaunchAttribute attr[1];
+    cudaLaunchConfig_t cfg = cluster_config(g.first, g.second, s, attr);
+    cudaError_t e = cudaLaunchKernelEx(&cfg, cluster_kernel(g.first), P);
+    if (e != cudaSuccess)
+      return vs_set_error(VS_ERR_CUDA, "cluster launch (n %d, %d maps): %s", g.first, g.second,
+                          cudaGetErrorString(e));
+    off += g.second;
+  }
+  return VS_OK;
+}
+
 int plan_launch(vs_plan_t* p, cudaStream_t s, bool transient) {
+  if (p->cluster && !transient) return plan_launch_cluster(p, s);
   VS_CUDA_TRY(cudaMemsetAsync(p->d_ctrl, 0, sizeof(Ctrl), s));
   VS_CUDA_TRY(cudaMemsetAsync(p->d_state, 0, sizeof(MapState) * p->n_items, s));
   PlanDev P;
@@ -1360,11 +1962,28 @@ extern "C" int vs_plan_create(const vs_batch_item* items_host, int n_items,
                           "item %d: the BF16 split tensor-core path supports n = 128 or 256 (got %d)",
                           i, it.k->n);
   }
+  bool cluster_ok = params->precision == VS_PREC_FP32;
+  for (int i = 0; i < n_items && cluster_ok; ++i) cluster_ok = cluster_size_ok(items_host[i].k->n);
+  if (params->engine == VS_ENGINE_CLUSTER && !cluster_ok)
+    return vs_set_error(VS_ERR_INVALID_ARG,
+                        "the cluster engine needs FP32 precision and every n in [%d, %d]", kClRows,
+                        kClRows * kClMaxRanks);
   cudaStream_t s = (cudaStream_t)stream;
   vs_plan_t* p = new vs_plan_t();
   p->n_items = n_items;
   p->items.assign(items_host, items_host + n_items);
   p->params = *params;
+  if (cluster_ok && params->engine != VS_ENGINE_STREAMED) {
+    p->cluster = true;
+    rc = plan_layout_cluster(p, s);
+    if (rc != VS_OK) {
+      plan_release(p);
+      delete p;
+      return rc;
+    }
+    *out = p;
+    return VS_OK;
+  }
 
   // task size: tuned once per mix of grid sizes when the batch is large
   std::vector<int> key;
@@ -1421,7 +2040,10 @@ extern "C" int vs_plan_run(vs_plan p, void* stream) {
   return plan_launch(p, (cudaStream_t)stream, false);
 }
 
-extern "C" int vs_plan_launches(vs_plan p) { return p ? 1 : 0; }
+extern "C" int vs_plan_launches(vs_plan p) {
+  if (!p) return 0;
+  return p->cluster ? (int)p->cl_groups.size() : 1;
+}
 
 extern "C" int vs_plan_info(vs_plan p, vs_solve_info* info_host, void* stream) {
   if (!p || !info_host) return vs_set_error(VS_ERR_INVALID_ARG, "NULL plan or output");

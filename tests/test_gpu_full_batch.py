@@ -1,6 +1,6 @@
 """The benchmark's launch configuration at full size: 4096 maps of 256 x 256
-in one persistent plan, checked on sampled maps against the FP64 oracle and
-on properties that hold for every map."""
+in one plan (cluster and streamed engines), checked on sampled maps against
+the FP64 oracle and on properties that hold for every map."""
 import numpy as np
 import pytest
 import torch
@@ -12,12 +12,14 @@ from _util import ENG_TOL_K, REQ_REL_L2, errors, oracle_spectrum, oracle_steady,
 pytestmark = pytest.mark.gpu
 
 
-def test_full_batch_4096_at_256():
+@pytest.mark.parametrize("engine", [2, 1])          # cluster, streamed
+def test_full_batch_4096_at_256(engine):
     import paper_2307_12119_gb300 as vs
     w, pd, pl, s = synth.batch_inputs(256, 4096)
     k = vs.Kernel(vs_stack(w), vs.Grid(w.n, w.die_m))
     th = torch.empty_like(pd)
-    plan = vs.Plan([(k, pd[i], pl[i], s[i], th[i]) for i in range(pd.shape[0])], vs_params(w))
+    plan = vs.Plan([(k, pd[i], pl[i], s[i], th[i]) for i in range(pd.shape[0])],
+                   vs_params(w, engine=engine))
     plan.run()
     infos = plan.info()
     assert all(i["status"] == vs.VS_OK for i in infos)

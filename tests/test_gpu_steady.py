@@ -110,12 +110,14 @@ def test_batch_mixed_sizes_matches_single_and_oracle():
         pd, pl, s = inputs(w, first=i)
         th = torch.empty_like(pd[0])
         items.append((kernels[i % 3], pd[0], pl[0], s[0], th))
+    # n = 512 puts the plan on the streamed engine; the single solves use it too
+    streamed = dict(engine=vs.VS_ENGINE_STREAMED)
     infos = vs.solve_batch(items, vs_params(ws[0]))
     assert all(i["status"] == vs.VS_OK for i in infos)
     spectra = {w.n: oracle_spectrum(w) for w in ws}
     for i, (k, pd, pl, s, th) in enumerate(items):
         w = ws[i % 3]
-        single, info1 = vs.solve_steady(k, pd, pl, s, vs_params(w))
+        single, info1 = vs.solve_steady(k, pd, pl, s, vs_params(w, **streamed))
         assert info1["iterations"] == infos[i]["iterations"]
         assert float((single - th).abs().max()) <= 1e-4
         if i < 3:
@@ -124,13 +126,15 @@ def test_batch_mixed_sizes_matches_single_and_oracle():
             assert emax <= ENG_TOL_K and rel <= REQ_REL_L2
 
 
-def test_batch_is_deterministic_and_graph_capturable():
+@pytest.mark.parametrize("engine", [1, 2])          # streamed, cluster
+def test_batch_is_deterministic_and_graph_capturable(engine):
     vs = _vs()
     w = synth.workload("c3_256")
     k = _kernel(w)
     pd, pl, s = inputs(w, count=12)
     th = torch.empty_like(pd)
-    plan = vs.Plan([(k, pd[i], pl[i], s[i], th[i]) for i in range(12)], vs_params(w))
+    plan = vs.Plan([(k, pd[i], pl[i], s[i], th[i]) for i in range(12)],
+                   vs_params(w, engine=engine))
     plan.run()
     a = th.clone()
     th.zero_()
