@@ -556,10 +556,22 @@ __global__ void __launch_bounds__(kThreads, 3) k_solve_transient(PlanDev P) {
 // memory sees only the inputs (read) and theta (written). There are no spin
 // waits: the cluster barriers are hardware barriers.
 
-constexpr int kClThreads = 256;
-constexpr int kClRows = 32;             // rows and x-frequencies per CTA
-constexpr int kClF = kClRows / 2;       // FFTs per CTA in each phase
+// Rows (and x-frequencies) a CTA owns at most; the cluster holds N / rows CTAs.
+#ifndef VS_CL_ROWS
+#define VS_CL_ROWS 32
+#endif
+constexpr int kClMaxN = 256;
 constexpr int kClMaxRanks = 8;
+constexpr int kClBatch = 2;            // positions whose inputs are loaded together
+
+template <int N>
+struct ClShape {
+  static constexpr int ROWS = N < VS_CL_ROWS ? N : VS_CL_ROWS;
+  static constexpr int F = ROWS / 2;         // FFTs per CTA in each phase
+  static constexpr int THREADS = 16 * F;     // one radix-16 butterfly per thread
+  static constexpr int RANKS = N / ROWS;
+  static constexpr int MIN_BLOCKS = THREADS <= 256 ? 2 : 1;
+};
 
 struct ClSlots {
   double part[kClMaxRanks];
@@ -576,16 +588,17 @@ struct ClusterDev {
 };
 
 // Shared memory of one CTA for grid size N, in float2 units: row buffer
-// [kClF][NP], column buffer [kClF][NP], spectral multiplier of the CTA's
-// frequency pairs [N][kClF] (column index XOR-swizzled by the row), the
-// first-pass FFT twiddles W_N^{j r} stored [r][j] (r < 16, j < N/16), the
-// DCT twiddles W_4N^k (k < N), then the partials slots.
+// [F][NP], column buffer [F][NP], spectral multiplier of the CTA's frequency
+// pairs [N][F] (column index XOR-swizzled by the row), the first-pass FFT
+// twiddles W_N^{j r} stored [r][j] (r < 16, j < N/16), the DCT twiddles
+// W_4N^k (k < N), then the partials slots.
 template <int N>
 struct ClLayout {
+  static constexpr int F = ClShape<N>::F;
   static constexpr int NP = N + N / 16 + 1;
-  static constexpr int kBcol = kClF * NP;
-  static constexpr int kLs = 2 * kClF * NP;
-  static constexpr int kTwp = kLs + N * kClF;
+  static constexpr int kBcol = F * NP;
+  static constexpr int kLs = 2 * F * NP;
+  static constexpr int kTwp = kLs + N * F;
   static constexpr int kTdct = kTwp + N;
   static constexpr int kSlots = kTdct + N;
   static constexpr size_t kBytes = (size_t)kSlots * sizeof(float2) + sizeof(ClSlots);
@@ -647,239 +660,307 @@ __device__ __forceinline__ int cl_dr(int k) {
   return (k & 15) * (N / 16) + (k >> 4);
 }
 
-// The 16 in-place FFTs of length N of a buffer (stride NP), radix 16 then
-// radix N/16: forward = decimation in frequency (natural in, digit-reversed
-// out), inverse = the exact reverse (digit-reversed in, natural out, x N).
-// Same passes as vsfft::fft_forward / fft_inverse with every size a
-// compile-time constant and the twiddles read from shared memory.
-template <int N, bool FWD>
-__device__ __forceinline__ void cl_fft(float2* buf, const float2* twp) {
-  constexpr int M1 = N / 16;       // sub-stride of the radix-16 pass
-  constexpr int R2 = N / 16;       // radix of the second pass
-  constexpr int NP = ClLayout<N>::NP;
-  auto pass16 = [&]() {
-    for (int b = threadIdx.x; b < kClF * M1; b += kClThreads) {
-      const int f = b / M1, j = b % M1;
-      float2* base = buf + f * NP;
-      float2 v[16];
-#pragma unroll
-      for (int r = 0; r < 16; ++r) v[r] = base[pad(j + r * M1)];
-      if (FWD) {
-        dft16<true>(v);
-        if (M1 > 1) {
-#pragma unroll
-          for (int r = 1; r < 16; ++r) v[r] = cmul(v[r], twp[r * M1 + j]);
-        }
-      } else {
-        if (M1 > 1) {
-#pragma unroll
-          for (int r = 1; r < 16; ++r) v[r] = cmulc(v[r], twp[r * M1 + j]);
-        }
-        dft16<false>(v);
-      }
-#pragma unroll
-      for (int r = 0; r < 16; ++r) base[pad(j + r * M1)] = v[r];
-    }
-  };
-  auto pass2 = [&]() {
-    for (int b = threadIdx.x; b < kClF * 16; b += kClThreads) {
-      float2* base = buf + (b >> 4) * NP + (b & 15) * R2 + (((b & 15) * R2) >> 4);
-      float2 v[R2];
-#pragma unroll
-      for (int r = 0; r < R2; ++r) v[r] = base[r];
-      dftR<R2, FWD>(v);
-#pragma unroll
-      for (int r = 0; r < R2; ++r) base[r] = v[r];
-    }
-  };
-  if (FWD) {
-    pass16();
-    __syncthreads();
-    pass2();
-  } else {
-    pass2();
-    __syncthreads();
-    pass16();
-  }
-  __syncthreads();
-}
-
+// Thread roles of the transforms (16 FFTs of length N = 16 R2 per buffer):
+//   radix-16 role (the first 16 M1 threads, M1 = N/16): FFT f = t / M1 and
+//     its positions j + M1 r, r < 16, j = t % M1;
+//   radix-R2 role (all 256 threads): FFT f = t / 16 and its positions
+//     16 b + r... stored as b R2 + r, r < R2, b = t % 16 (after the forward
+//     pass these hold the frequencies k = 16 r + b).
+// Forward transform = radix-16 pass (decimation in frequency, twiddled by
+// W_N^{j r}) then radix-R2 pass; the inverse undoes them in reverse order.
+// The radix-16 role keeps its 16 values in registers between the inverse and
+// the forward transform along x, so the fixed-point update runs on them
+// in place; the frequency k and its mirror N - k sit in lanes b and 16 - b of
+// one half-warp and are paired with shuffles.
 template <int N>
-__global__ void __launch_bounds__(kClThreads, 2) k_solve_cluster(ClusterDev P) {
+__global__ void __launch_bounds__(ClShape<N>::THREADS, ClShape<N>::MIN_BLOCKS)
+    k_solve_cluster(ClusterDev P) {
   using Lay = ClLayout<N>;
-  constexpr int NP = Lay::NP, half = N / 2, ranks = N / kClRows;
+  constexpr int kClRows = ClShape<N>::ROWS, kClF = ClShape<N>::F;
+  constexpr int kClThreads = ClShape<N>::THREADS, ranks = ClShape<N>::RANKS;
+  constexpr int NP = Lay::NP, half = N / 2;
+  constexpr int M1 = N / 16, R2 = N / 16;
+  constexpr int kP16 = kClF * M1;
   extern __shared__ __align__(16) float2 cl_smem[];
   __shared__ double red_d[kClThreads / 32];
   __shared__ float red_f[kClThreads / 32];
   __shared__ int red_i[kClThreads / 32];
   const unsigned rank = cl_rank();
   const int b = __ldg(&P.order[cl_index()]);
-  const MapDesc d = P.maps[b];
+  const MapDesc& d = P.maps[b];   // fields are read where used
   float2* brow = cl_smem;
   float2* bcol = cl_smem + Lay::kBcol;
   float2* Ls = cl_smem + Lay::kLs;
   float2* twp = cl_smem + Lay::kTwp;
   float2* tw = cl_smem + Lay::kTdct;
   ClSlots* slots = reinterpret_cast<ClSlots*>(cl_smem + Lay::kSlots);
+  const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
+  const bool p16 = t < kP16;
+  const int f16 = t / M1, j16 = t % M1;
+  const int f2 = t >> 4, blk = t & 15;
+  const int partner2 = (lane & 16) | ((16 - blk) & 15);
+  const int partner16 = (lane & ~(M1 - 1)) | (M1 - 1 - j16);
   const int y0 = (int)rank * kClRows;
   const int j0 = (int)rank * kClF;
   const float beta = P.beta, alpha = P.alpha;
-  // W_4N^e table of the kernel's FFT tables -> shared memory
-  for (int i = threadIdx.x; i < N; i += kClThreads) {
-    const int r = i / (N / 16), j = i % (N / 16);
+  for (int i = t; i < N; i += kClThreads) {
+    const int r = i / M1, j = i % M1;
     twp[i] = __ldg(&d.tw4n[4 * j * r]);
     tw[i] = __ldg(&d.tw4n[i]);
   }
   __syncthreads();
 
-  // Row phase update. mode 0: initial source from theta_0 = 0 (accumulates
-  // the leakage sum); 1: initial source from the warm start theta_0;
-  // 2: iteration (brow holds u after the inverse transform along x).
-  auto row_update = [&](int mode, float mu, float& resid, int& flags, double& pl_sum) {
-    constexpr int total = kClF * N;
-    for (int base = threadIdx.x; base < total; base += kU * kClThreads) {
-      float pl[kU][2], pd[kU][2], sk[kU][2], old[kU][2];
-      float2 uv[kU];
+  auto load16 = [&](const float2* buf, float2* v) {
 #pragma unroll
-      for (int u = 0; u < kU; ++u) {
-        const int it = base + u * kClThreads;
-        uv[u] = make_float2(0.f, 0.f);
+    for (int r = 0; r < 16; ++r) v[r] = buf[f16 * NP + pad(j16 + r * M1)];
+  };
+  auto store16 = [&](float2* buf, const float2* v) {
 #pragma unroll
-        for (int h = 0; h < 2; ++h) pl[u][h] = pd[u][h] = old[u][h] = 0.f, sk[u][h] = 1.f;
-        if (it < total) {
-          const int f = it / N, x = it % N;
-          if (mode == 2) uv[u] = brow[f * NP + pad(makhoul_pos(x, N))];
+    for (int r = 0; r < 16; ++r) buf[f16 * NP + pad(j16 + r * M1)] = v[r];
+  };
+  auto base2 = [&](float2* buf) { return buf + f2 * NP + blk * R2 + ((blk * R2) >> 4); };
+  auto fwd16 = [&](float2* v) {
+    dft16<true>(v);
+    if (M1 > 1) {
 #pragma unroll
-          for (int h = 0; h < 2; ++h) {
-            const size_t idx = (size_t)(y0 + 2 * f + h) * N + x;
-            pl[u][h] = __ldg(&d.p_leak0[idx]);
-            pd[u][h] = __ldg(&d.p_dyn[idx]);
-            if (d.s) sk[u][h] = __ldg(&d.s[idx]);
-            if (mode == 2) old[u][h] = d.theta[idx];
-            else if (mode == 1) old[u][h] = __ldg(&d.theta_init[idx]);
-          }
-        }
-      }
-#pragma unroll
-      for (int u = 0; u < kU; ++u) {
-        const int it = base + u * kClThreads;
-        if (it >= total) continue;
-        const int f = it / N, x = it % N;
-        float q[2];
-#pragma unroll
-        for (int h = 0; h < 2; ++h) {
-          const size_t idx = (size_t)(y0 + 2 * f + h) * N + x;
-          if (mode == 0) {
-            d.theta[idx] = 0.f;
-            q[h] = pd[u][h] + pl[u][h];
-            pl_sum += (double)pl[u][h];
-          } else if (mode == 1) {
-            // u_0 = theta_0 / (s (1 + alpha theta_0))
-            const float t0 = old[u][h];
-            const float u0 = t0 / (sk[u][h] * fmaf(alpha, t0, 1.f));
-            d.theta[idx] = t0;
-            q[h] = pd[u][h] + pl[u][h] + beta * fmaf(pl[u][h], t0, -mu * u0);
-          } else {
-            const float uu = h ? uv[u].y : uv[u].x;
-            const float den = fmaf(-alpha * sk[u][h], uu, 1.f);
-            if (!(den > 0.05f)) flags |= kFlagRunaway;
-            const float th = sk[u][h] * uu / den;
-            if (!isfinite(th)) flags |= kFlagNonfinite;
-            else resid = fmaxf(resid, fabsf(th - old[u][h]));
-            d.theta[idx] = th;
-            q[h] = pd[u][h] + pl[u][h] + beta * fmaf(pl[u][h], th, -mu * uu);
-          }
-        }
-        brow[f * NP + pad(makhoul_pos(x, N))] = make_float2(q[0], q[1]);
-      }
+      for (int r = 1; r < 16; ++r) v[r] = cmul(v[r], twp[r * M1 + j16]);
     }
   };
+  auto inv16 = [&](float2* v) {
+    if (M1 > 1) {
+#pragma unroll
+      for (int r = 1; r < 16; ++r) v[r] = cmulc(v[r], twp[r * M1 + j16]);
+    }
+    dft16<false>(v);
+  };
+  auto shfl2 = [&](float2 v, int src) {
+    return make_float2(__shfl_sync(0xffffffffu, v.x, src), __shfl_sync(0xffffffffu, v.y, src));
+  };
 
-  // After the forward FFT of brow: DCT-II post-twiddle of every frequency
-  // pair of every row pair, stored into the column buffer of the pair's owner
-  // at the Makhoul positions of the two rows.
-  auto push_rows = [&]() {
-    for (int it = threadIdx.x; it < kClF * half; it += kClThreads) {
-      const int f = it % kClF, j = it / kClF;
-      const float2* row = brow + f * NP;
+  // Row phase. mode 0: initial source from theta_0 = 0 (leakage sum into
+  // pl_sum); 1: initial source from the warm start; 2: iteration (brow holds
+  // the spectra of the column phase, pre-twiddled, at digit-reversed places).
+  auto row_phase = [&](int mode, float mu, float& resid, int& flags, double& pl_sum) {
+    if (mode == 2) {
+      float2* p = base2(brow);
+      float2 w[R2];
+#pragma unroll
+      for (int r = 0; r < R2; ++r) w[r] = p[r];
+      dftR<R2, false>(w);
+#pragma unroll
+      for (int r = 0; r < R2; ++r) p[r] = w[r];
+      __syncthreads();
+    }
+    if (p16) {
+      float2 v[16];
+      if (mode == 2) {
+        load16(brow, v);
+        inv16(v);       // v[r] = u at Makhoul position j + M1 r of rows ya, ya + 1
+      }
+      // Positions m (< N/2, x = 2m) of this lane and N - 1 - m (x + 1) of the
+      // mirror lane are updated together, so every input is read as a
+      // coalesced float2 (x, x + 1); u and q of x + 1 travel by shuffle.
+      const size_t row_a = (size_t)(y0 + 2 * f16) * N;
+      auto ld2 = [&](const float* p, size_t idx) { return __ldg(reinterpret_cast<const float2*>(p + idx)); };
+#pragma unroll
+      for (int r0 = 0; r0 < 8; r0 += kClBatch) {
+        float2 pl[kClBatch][2], pd[kClBatch][2], sk[kClBatch][2], old[kClBatch][2];
+#pragma unroll
+        for (int u = 0; u < kClBatch; ++u) {
+          const int x = 2 * (j16 + (r0 + u) * M1);
+#pragma unroll
+          for (int h = 0; h < 2; ++h) {
+            const size_t idx = row_a + (size_t)h * N + x;
+            pl[u][h] = ld2(d.p_leak0, idx);
+            pd[u][h] = ld2(d.p_dyn, idx);
+            sk[u][h] = d.s ? ld2(d.s, idx) : make_float2(1.f, 1.f);
+            old[u][h] = mode == 2 ? *reinterpret_cast<const float2*>(d.theta + idx)
+                        : mode == 1 ? ld2(d.theta_init, idx) : make_float2(0.f, 0.f);
+          }
+        }
+#pragma unroll
+        for (int u = 0; u < kClBatch; ++u) {
+          const int r = r0 + u;
+          const int x = 2 * (j16 + r * M1);
+          const float2 um = shfl2(v[15 - r], partner16);   // u at x + 1 (mirror lane)
+          float qe[2], qo[2];
+#pragma unroll
+          for (int h = 0; h < 2; ++h) {
+            const size_t idx = row_a + (size_t)h * N + x;
+            float th[2];
+#pragma unroll
+            for (int e = 0; e < 2; ++e) {
+              const float PL = e ? pl[u][h].y : pl[u][h].x, PD = e ? pd[u][h].y : pd[u][h].x;
+              const float S = e ? sk[u][h].y : sk[u][h].x, O = e ? old[u][h].y : old[u][h].x;
+              float q;
+              if (mode == 0) {
+                th[e] = 0.f;
+                q = PD + PL;
+                pl_sum += (double)PL;
+              } else if (mode == 1) {
+                // u_0 = theta_0 / (s (1 + alpha theta_0))
+                const float u0 = O / (S * fmaf(alpha, O, 1.f));
+                th[e] = O;
+                q = PD + PL + beta * fmaf(PL, O, -mu * u0);
+              } else {
+                const float uu = e ? (h ? um.y : um.x) : (h ? v[r].y : v[r].x);
+                const float den = fmaf(-alpha * S, uu, 1.f);
+                if (!(den > 0.05f)) flags |= kFlagRunaway;
+                th[e] = S * uu / den;
+                if (!isfinite(th[e])) flags |= kFlagNonfinite;
+                else resid = fmaxf(resid, fabsf(th[e] - O));
+                q = PD + PL + beta * fmaf(PL, th[e], -mu * uu);
+              }
+              (e ? qo : qe)[h] = q;
+            }
+            *reinterpret_cast<float2*>(d.theta + idx) = make_float2(th[0], th[1]);
+          }
+          v[r] = make_float2(qe[0], qe[1]);
+          v[15 - r] = shfl2(make_float2(qo[0], qo[1]), partner16);
+        }
+      }
+      fwd16(v);
+      store16(brow, v);
+    }
+    // per-warp partials of the residual, flags and leakage sum
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      resid = fmaxf(resid, __shfl_down_sync(0xffffffffu, resid, o));
+      flags |= __shfl_down_sync(0xffffffffu, flags, o);
+      pl_sum += __shfl_down_sync(0xffffffffu, pl_sum, o);
+    }
+    if (lane == 0) {
+      red_f[warp] = resid;
+      red_i[warp] = flags;
+      red_d[warp] = pl_sum;
+    }
+    __syncthreads();
+    // radix-R2 pass: Z[k], k = 16 r + blk; pair with N - k from the partner
+    // lane, DCT-II post-twiddle, store into the column owner
+    float2 z[R2];
+    {
+      const float2* p = base2(brow);
+#pragma unroll
+      for (int r = 0; r < R2; ++r) z[r] = p[r];
+    }
+    dftR<R2, true>(z);
+    const int ya = y0 + 2 * f2;
+    const unsigned oa = (unsigned)pad(makhoul_pos(ya, N)) * 8u;
+    const unsigned ob = (unsigned)pad(makhoul_pos(ya + 1, N)) * 8u;
+#pragma unroll
+    for (int r = 0; r < R2 / 2; ++r) {
+      // what the partner needs at its index r: Z[N - k'] for its k' = 16 r + (16 - blk)
+      const float2 give = blk == 0 ? z[r == 0 ? R2 / 2 : R2 - r] : z[R2 - 1 - r];
+      const float2 zn = shfl2(give, partner2);
+      const int k = 16 * r + blk;
       float2 ea, eb;
-      if (j == 0) {
-        const float2 z0 = row[0], zh = row[pad(cl_dr<N>(half))];
-        const float2 x0 = dct_post(z0, z0, tw[0]), xh = dct_post(zh, zh, tw[half]);
+      if (k == 0) {
+        const float2 x0 = dct_post(z[0], z[0], tw[0]), xh = dct_post(zn, zn, tw[half]);
         ea = make_float2(x0.x, xh.x);
         eb = make_float2(x0.y, xh.y);
       } else {
-        const float2 zk = row[pad(cl_dr<N>(j))], zn = row[pad(cl_dr<N>(N - j))];
-        const float2 xk = dct_post(zk, zn, tw[j]), xn = dct_post(zn, zk, tw[N - j]);
+        const float2 xk = dct_post(z[r], zn, tw[k]), xn = dct_post(zn, z[r], tw[N - k]);
         ea = make_float2(xk.x, xn.x);
         eb = make_float2(xk.y, xn.y);
       }
-      const int ya = y0 + 2 * f;
-      const unsigned dst = cl_map(bcol, (unsigned)(j / kClF)) + (unsigned)((j % kClF) * NP) * 8u;
-      cl_put(dst + (unsigned)pad(makhoul_pos(ya, N)) * 8u, ea);
-      cl_put(dst + (unsigned)pad(makhoul_pos(ya + 1, N)) * 8u, eb);
+      const unsigned dst = cl_map(bcol, (unsigned)(k / kClF)) + (unsigned)((k % kClF) * NP) * 8u;
+      cl_put(dst + oa, ea);
+      cl_put(dst + ob, eb);
     }
   };
 
-  // Column phase: the column buffer holds the x-spectra of all rows for this
-  // CTA's frequency pairs.
+  // Column phase: bcol holds, for this CTA's frequency pairs, the x-spectra
+  // of all rows at the Makhoul positions of y.
   auto col_phase = [&]() {
-    cl_fft<N, true>(bcol, twp);
-    for (int it = threadIdx.x; it < kClF * (half + 1); it += kClThreads) {
-      const int jj = it % kClF, q = it / kClF;
-      float2* col = bcol + jj * NP;
-      const int ia = pad(cl_dr<N>(q)), ib = pad(cl_dr<N>(q == 0 ? 0 : N - q));
-      const float2 zq = col[ia], zn = col[ib];
-      float2 y = dct_post(zq, zn, tw[q]);
-      const float2 L = Ls[q * kClF + (jj ^ (q & (kClF - 1)))];
-      y.x *= L.x;
-      y.y *= L.y;
-      float2 yn = make_float2(0.f, 0.f);
-      if (q == half) {
-        yn = y;
-      } else if (q != 0) {
-        yn = dct_post(zn, zq, tw[N - q]);
-        const int qn = N - q;
-        const float2 Ln = Ls[qn * kClF + (jj ^ (qn & (kClF - 1)))];
-        yn.x *= Ln.x;
-        yn.y *= Ln.y;
-      }
-      col[ia] = dct_pre(y.x, yn.x, y.y, yn.y, tw[q]);
-      if (q != 0 && q != half) col[ib] = dct_pre(yn.x, y.x, yn.y, y.y, tw[N - q]);
+    if (p16) {
+      float2 v[16];
+      load16(bcol, v);
+      fwd16(v);
+      store16(bcol, v);
     }
     __syncthreads();
-    cl_fft<N, false>(bcol, twp);
-    // inverse pre-twiddle along x for both frequencies of each pair, stored
-    // into the row buffer of the owner of each row pair
-    for (int it = threadIdx.x; it < kClF * half; it += kClThreads) {
-      const int jj = it % kClF, r = it / kClF;
-      const float2* col = bcol + jj * NP;
-      const int ya = 2 * r;
-      const float2 va = col[pad(makhoul_pos(ya, N))], vb = col[pad(makhoul_pos(ya + 1, N))];
-      const int j = j0 + jj;
-      int pa, pb;
-      float2 ea, eb;
-      if (j == 0) {
-        pa = 0;
-        pb = half;
-        ea = dct_pre(va.x, 0.f, vb.x, 0.f, tw[0]);
-        eb = dct_pre(va.y, va.y, vb.y, vb.y, tw[half]);
-      } else {
-        pa = j;
-        pb = N - j;
-        ea = dct_pre(va.x, va.y, vb.x, vb.y, tw[j]);
-        eb = dct_pre(va.y, va.x, vb.y, vb.x, tw[N - j]);
+    {
+      float2* p = base2(bcol);
+      float2 z[R2], e[R2];
+#pragma unroll
+      for (int r = 0; r < R2; ++r) z[r] = p[r];
+      dftR<R2, true>(z);
+      const int jj = f2;
+#pragma unroll
+      for (int r = 0; r < R2; ++r) {
+        const float2 give = blk == 0 ? z[(R2 - r) % R2] : z[R2 - 1 - r];
+        const float2 zn = shfl2(give, partner2);   // Z[N - q]
+        const int q = 16 * r + blk, qn = N - q;
+        const float2 L = Ls[q * kClF + (jj ^ (q & (kClF - 1)))];
+        float2 y = dct_post(z[r], zn, tw[q]);
+        y.x *= L.x;
+        y.y *= L.y;
+        float2 yn;
+        if (q == 0) {
+          yn = make_float2(0.f, 0.f);
+        } else if (q == half) {
+          yn = y;
+        } else {
+          const float2 Ln = Ls[qn * kClF + (jj ^ (qn & (kClF - 1)))];
+          yn = dct_post(zn, z[r], tw[qn]);
+          yn.x *= Ln.x;
+          yn.y *= Ln.y;
+        }
+        e[r] = dct_pre(y.x, yn.x, y.y, yn.y, tw[q]);
       }
-      const unsigned dst = cl_map(brow, (unsigned)(ya / kClRows)) +
-                           (unsigned)(((ya % kClRows) >> 1) * NP) * 8u;
-      cl_put(dst + (unsigned)pad(cl_dr<N>(pa)) * 8u, ea);
-      cl_put(dst + (unsigned)pad(cl_dr<N>(pb)) * 8u, eb);
+      dftR<R2, false>(e);
+#pragma unroll
+      for (int r = 0; r < R2; ++r) p[r] = e[r];
+    }
+    __syncthreads();
+    if (p16) {
+      float2 v[16];
+      load16(bcol, v);
+      inv16(v);         // v[r] = column data at Makhoul position j + M1 r of y
+      const int j = j0 + f16;
+      const int pa = j == 0 ? 0 : j, pb = j == 0 ? half : N - j;
+      const float2 twa = tw[pa], twb = tw[pb];
+      const unsigned ra = (unsigned)pad(cl_dr<N>(pa)) * 8u, rb = (unsigned)pad(cl_dr<N>(pb)) * 8u;
+#pragma unroll
+      for (int r = 0; r < 8; ++r) {
+        const float2 vb = shfl2(v[15 - r], partner16);   // the row ya + 1
+        const float2 va = v[r];
+        const int ya = 2 * (j16 + r * M1);
+        float2 ea, eb;
+        if (j == 0) {
+          ea = dct_pre(va.x, 0.f, vb.x, 0.f, twa);
+          eb = dct_pre(va.y, va.y, vb.y, vb.y, twb);
+        } else {
+          ea = dct_pre(va.x, va.y, vb.x, vb.y, twa);
+          eb = dct_pre(va.y, va.x, vb.y, vb.x, twb);
+        }
+        const unsigned dst = cl_map(brow, (unsigned)(ya / kClRows)) +
+                             (unsigned)(((ya % kClRows) >> 1) * NP) * 8u;
+        cl_put(dst + ra, ea);
+        cl_put(dst + rb, eb);
+      }
     }
   };
 
-  auto put_part = [&](double v) {
-    if (threadIdx.x == 0)
-      for (int r = 0; r < ranks; ++r) cl_put(cl_map(&slots->part[rank], (unsigned)r), v);
+  auto put_slots = [&](bool part) {
+    if (t == 0) {
+      float rm = 0.f;
+      int fo = 0;
+      double ps = 0.0;
+      for (int w = 0; w < kClThreads / 32; ++w) {
+        rm = fmaxf(rm, red_f[w]);
+        fo |= red_i[w];
+        ps += red_d[w];
+      }
+      for (int r = 0; r < ranks; ++r) {
+        if (part) {
+          cl_put(cl_map(&slots->part[rank], (unsigned)r), ps);
+        } else {
+          cl_put(cl_map(&slots->resid[rank], (unsigned)r), rm);
+          cl_put(cl_map(&slots->flags[rank], (unsigned)r), fo);
+        }
+      }
+    }
   };
   auto cluster_mu = [&]() {
     double sum = 0.0;
@@ -896,11 +977,12 @@ __global__ void __launch_bounds__(kClThreads, 2) k_solve_cluster(ClusterDev P) {
   // initial source (Eq. 17 at theta_0) and the mean leakage mu (Sec. III-C)
   if (d.theta_init) {
     double acc = 0.0;
-    for (int i = threadIdx.x; i < kClRows * N; i += kClThreads)
+    for (int i = t; i < kClRows * N; i += kClThreads)
       acc += (double)__ldg(&d.p_leak0[(size_t)y0 * N + i]);
     const double tot = block_sum(acc, red_d);
     cl_wait();
-    put_part(tot);
+    if (t == 0)
+      for (int r = 0; r < ranks; ++r) cl_put(cl_map(&slots->part[rank], (unsigned)r), tot);
     cl_sync();
     mu = cluster_mu();
     if ((double)beta * mu * (double)d.kmax >= 0.999) {
@@ -910,22 +992,17 @@ __global__ void __launch_bounds__(kClThreads, 2) k_solve_cluster(ClusterDev P) {
       float r0 = 0.f;
       int f0 = 0;
       double unused = 0.0;
-      row_update(1, (float)mu, r0, f0, unused);
-      __syncthreads();
-      cl_fft<N, true>(brow, twp);
-      push_rows();
+      // the peers' start is already established by the barrier above
+      row_phase(1, (float)mu, r0, f0, unused);
       cl_sync();
     }
   } else {
     float r0 = 0.f;
     int f0 = 0;
     double acc = 0.0;
-    row_update(0, 0.f, r0, f0, acc);
-    const double tot = block_sum(acc, red_d);  // synchronises the block
-    cl_fft<N, true>(brow, twp);
     cl_wait();
-    push_rows();
-    put_part(tot);
+    row_phase(0, 0.f, r0, f0, acc);
+    put_slots(true);
     cl_sync();
     mu = cluster_mu();
     if ((double)beta * mu * (double)d.kmax >= 0.999) {
@@ -941,7 +1018,7 @@ __global__ void __launch_bounds__(kClThreads, 2) k_solve_cluster(ClusterDev P) {
       // of the two unnormalised inverse transforms folded in
       const float bm = beta * mu_f;
       const float inv_n2 = 1.f / ((float)N * (float)N);
-      for (int it = threadIdx.x; it < kClF * N; it += kClThreads) {
+      for (int it = t; it < kClF * N; it += kClThreads) {
         const int q = it % N, jj = it / N, j = j0 + jj;
         const int pa = j == 0 ? 0 : j, pb = j == 0 ? half : N - j;
         const float ka = __ldg(&d.Kt[(size_t)pa * N + q]), kb = __ldg(&d.Kt[(size_t)pb * N + q]);
@@ -953,21 +1030,11 @@ __global__ void __launch_bounds__(kClThreads, 2) k_solve_cluster(ClusterDev P) {
     for (int it = 1; it <= P.max_iter; ++it) {
       col_phase();
       cl_sync();
-      cl_fft<N, false>(brow, twp);
       float resid = 0.f;
       int flags = 0;
       double unused = 0.0;
-      row_update(2, mu_f, resid, flags, unused);
-      const float rm = block_max(resid, red_f);  // both synchronise the block
-      const int fo = block_or(flags, red_i);
-      cl_fft<N, true>(brow, twp);
-      push_rows();
-      if (threadIdx.x == 0) {
-        for (int r = 0; r < ranks; ++r) {
-          cl_put(cl_map(&slots->resid[rank], (unsigned)r), rm);
-          cl_put(cl_map(&slots->flags[rank], (unsigned)r), fo);
-        }
-      }
+      row_phase(2, mu_f, resid, flags, unused);
+      put_slots(false);
       cl_sync();
       // the same decision in every thread of every CTA of the cluster
       float rr = 0.f;
@@ -997,7 +1064,7 @@ __global__ void __launch_bounds__(kClThreads, 2) k_solve_cluster(ClusterDev P) {
       if (stop) break;
     }
   }
-  if (rank == 0 && threadIdx.x == 0) {
+  if (rank == 0 && t == 0) {
     vs_solve_info* inf = P.info + b;
     inf->status = status;
     inf->iterations = iters;
@@ -1749,7 +1816,20 @@ int plan_layout(vs_plan_t* p, int elems, cudaStream_t s, bool transient, int n_s
   return VS_OK;
 }
 
-bool cluster_size_ok(int n) { return n >= kClRows && n <= kClRows * kClMaxRanks; }
+bool cluster_size_ok(int n) { return n >= 32 && n <= kClMaxN; }
+
+struct ClHost {
+  int ranks, threads;
+  size_t smem;
+};
+ClHost cluster_shape(int n) {
+  switch (n) {
+    case 32: return {ClShape<32>::RANKS, ClShape<32>::THREADS, ClLayout<32>::kBytes};
+    case 64: return {ClShape<64>::RANKS, ClShape<64>::THREADS, ClLayout<64>::kBytes};
+    case 128: return {ClShape<128>::RANKS, ClShape<128>::THREADS, ClLayout<128>::kBytes};
+    default: return {ClShape<256>::RANKS, ClShape<256>::THREADS, ClLayout<256>::kBytes};
+  }
+}
 
 using ClusterFn = void (*)(ClusterDev);
 ClusterFn cluster_kernel(int n) {
@@ -1765,12 +1845,13 @@ size_t g_smem_attr_cluster[4] = {0, 0, 0, 0};  // per instantiation, n = 32 .. 2
 
 cudaLaunchConfig_t cluster_config(int n, int count, cudaStream_t s, cudaLaunchAttribute* attr) {
   cudaLaunchConfig_t cfg = {};
-  cfg.gridDim = dim3((unsigned)(n / kClRows) * (unsigned)count);
-  cfg.blockDim = dim3(kClThreads);
-  cfg.dynamicSmemBytes = cl_smem_bytes(n);
+  const ClHost h = cluster_shape(n);
+  cfg.gridDim = dim3((unsigned)h.ranks * (unsigned)count);
+  cfg.blockDim = dim3((unsigned)h.threads);
+  cfg.dynamicSmemBytes = h.smem;
   cfg.stream = s;
   attr[0].id = cudaLaunchAttributeClusterDimension;
-  attr[0].val.clusterDim.x = (unsigned)(n / kClRows);
+  attr[0].val.clusterDim.x = (unsigned)h.ranks;
   attr[0].val.clusterDim.y = 1;
   attr[0].val.clusterDim.z = 1;
   cfg.attrs = attr;
@@ -1839,12 +1920,12 @@ int plan_layout_cluster(vs_plan_t* p, cudaStream_t s) {
     VS_CUDA_TRY(cudaOccupancyMaxActiveClusters(&clusters, fn, &cfg));
     if (clusters < 1)
       return vs_set_error(VS_ERR_INVALID_ARG, "no cluster of %d CTAs fits on the device (n=%d)",
-                          g.first / kClRows, g.first);
+                          cluster_shape(g.first).ranks, g.first);
     if (getenv("VS_DEBUG")) {
       cudaFuncAttributes fa;
       cudaFuncGetAttributes(&fa, fn);
       fprintf(stderr, "varsim plan: cluster n=%d maps=%d ranks=%d smem=%zu regs=%d local=%zu "
-              "active_clusters=%d\n", g.first, g.second, g.first / kClRows, cl_smem_bytes(g.first),
+              "active_clusters=%d\n", g.first, g.second, cluster_shape(g.first).ranks, cl_smem_bytes(g.first),
               fa.numRegs, fa.localSizeBytes, clusters);
     }
   }
@@ -1966,8 +2047,7 @@ extern "C" int vs_plan_create(const vs_batch_item* items_host, int n_items,
   for (int i = 0; i < n_items && cluster_ok; ++i) cluster_ok = cluster_size_ok(items_host[i].k->n);
   if (params->engine == VS_ENGINE_CLUSTER && !cluster_ok)
     return vs_set_error(VS_ERR_INVALID_ARG,
-                        "the cluster engine needs FP32 precision and every n in [%d, %d]", kClRows,
-                        kClRows * kClMaxRanks);
+                        "the cluster engine needs FP32 precision and every n in [32, %d]", kClMaxN);
   cudaStream_t s = (cudaStream_t)stream;
   vs_plan_t* p = new vs_plan_t();
   p->n_items = n_items;
