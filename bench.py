@@ -3,11 +3,12 @@
 One step = one run of the whole steady hot path (mean leakage reduction,
 shift-invariant modified kernel, mirror-image cosine-basis convolution,
 fused leakage/conductivity update, fixed point iterated per map to its
-tolerance) over a batch of maps already resident in device memory. The
-chosen path runs the cosine transforms as BF16 hi/lo split-precision tcgen05
-GEMMs; the FP32 SIMT path and the one-map-per-call plain path are timed on
-the same batch for comparison. Inputs (3 GiB for
-4096 maps) are larger than the 129 MB L2, so no flush is needed between steps.
+tolerance) over a batch of maps already resident in device memory. Every
+batched variant (FP32 on the cluster and streamed engines, BF16 hi/lo split
+precision on tcgen05 tensor cores, each cold and with the learned warm start)
+is timed on the same batch and the fastest is reported; the one-map-per-call
+plain path is timed for comparison. Inputs (3 GiB for 4096 maps) are larger
+than the 129 MB L2, so no flush is needed between steps.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 
@@ -34,6 +35,27 @@ METRIC = ("thermal maps/s at 256² (max ΔT ≤0.05 K vs FP64), "
           "chosen vs plain; % roofline")
 UNIT = "maps/s"
 ALG_BYTES_PER_PIXEL = 16      # read P_dyn, P_leak0, s; write theta (FP32)
+# FP32 peak: 152 SMs x 128 FP32 lanes x 2 flops (FMA) x 2.07 GHz maximum SM clock
+FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
+
+
+def fp32_flops_per_map(n: int, iterations: float) -> float:
+    """FP32 operations of one steady solve on the FP32 engines, counted from
+    the arithmetic the kernels perform: per iteration four 1-D transform
+    stages (inverse and forward along x, forward and inverse along y), each
+    n/2 complex FFTs of length n (two real lines packed per FFT) plus the DCT
+    pre/post-twiddle (7 flops per real value); the spectral multiply (1 per
+    value) and the fused update (13 per value). The initial source costs one
+    forward stage and the source sum. Radix-16 butterfly: 8 radix-4 DFTs
+    (16 adds each) + 9 inner twiddle products (6 flops each) = 182 flops, plus
+    15 outer twiddle products (90) in the twiddled pass."""
+    lg = int(math.log2(n))
+    r2 = n >> 4 if lg >= 4 else 1
+    dft = {16: 182, 8: 72, 4: 16, 2: 4}
+    fft = (n // 16) * (dft[16] + (90 if n > 16 else 0)) + 16 * dft.get(r2, 0)
+    stage = (n // 2) * fft + 7 * n * n
+    per_iter = 4 * stage + n * n * (1 + 13)
+    return iterations * per_iter + stage + 2 * n * n
 
 
 def _args():
@@ -48,6 +70,13 @@ def _args():
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--train-maps", type=int, default=4096)
     ap.add_argument("--train-epochs", type=int, default=8)
+    ap.add_argument("--record-traffic", metavar="NCU_RAW_CSV", default="",
+                    help="write profiles/traffic.json for --kernel from an ncu raw CSV export "
+                         "of a capture over --batch maps (no GPU needed) and exit")
+    ap.add_argument("--kernel", default="k_solve_cluster")
+    ap.add_argument("--how", default="")
+    ap.add_argument("--variants", default="",
+                    help="comma-separated subset of the variants to time (default: all)")
     return ap.parse_args()
 
 
@@ -66,24 +95,56 @@ def _peaks():
     return 6800.0, "fallback"
 
 
-def _kernel_source_hash() -> str:
+# Source files that define each timed kernel: a traffic record taken with ncu
+# is used only while none of them has changed since.
+_SOLVER_SOURCES = ["paper_2307_12119_gb300/csrc/vs_solver.cu", "paper_2307_12119_gb300/csrc/vs_fft.cuh",
+                   "paper_2307_12119_gb300/csrc/vs_internal.cuh", "include/varsim.h"]
+KERNEL_SOURCES = {"k_solve_cluster": _SOLVER_SOURCES, "k_solve_steady": _SOLVER_SOURCES,
+                  "k_solve_steady_tc": _SOLVER_SOURCES + ["paper_2307_12119_gb300/csrc/vs_tc.cuh"]}
+TRAFFIC_JSON = os.path.join(ROOT, "profiles", "traffic.json")
+
+
+def _source_hash(files) -> str:
     h = hashlib.sha256()
-    csrc = os.path.join(ROOT, "paper_2307_12119_gb300", "csrc")
-    for f in sorted(os.listdir(csrc)):
-        h.update(open(os.path.join(csrc, f), "rb").read())
+    for f in files:
+        h.update(open(os.path.join(ROOT, f), "rb").read())
     return h.hexdigest()[:16]
 
 
 def _traffic_record(kernel: str):
-    """DRAM bytes per launch of `kernel` from a committed ncu summary, or None
-    if the kernel sources changed since it was taken."""
-    p = os.path.join(ROOT, "profiles", "traffic.json")
-    if not os.path.exists(p):
+    """DRAM bytes per map of `kernel` from a committed ncu capture, or None if
+    the kernel's sources changed since it was taken."""
+    if not os.path.exists(TRAFFIC_JSON) or kernel not in KERNEL_SOURCES:
         return None
-    d = json.load(open(p)).get(kernel)
-    if not d or d.get("source_hash") != _kernel_source_hash():
+    d = json.load(open(TRAFFIC_JSON)).get(kernel)
+    if not d or d.get("source_hash") != _source_hash(KERNEL_SOURCES[kernel]):
         return None
     return d
+
+
+def record_traffic(csv_path: str, kernel: str, maps: int, how: str):
+    """Writes the traffic record of `kernel` from `ncu -i <report> --page raw
+    --csv` output: dram__bytes_read.sum + dram__bytes_write.sum of the first
+    captured launch of that kernel, divided by the maps the launch solved."""
+    import csv
+    rows = list(csv.reader(open(csv_path)))
+    head, units = rows[0], rows[1]
+    col = {name: i for i, name in enumerate(head)}
+    scale = {"byte": 1.0, "Kbyte": 1e3, "Mbyte": 1e6, "Gbyte": 1e9, "KB": 1e3, "MB": 1e6, "GB": 1e9}
+    for r in rows[2:]:
+        if kernel not in r[col["Kernel Name"]]:
+            continue
+        get = lambda m: float(r[col[m]].replace(",", "")) * scale.get(units[col[m]], 1.0)
+        rd, wr = get("dram__bytes_read.sum"), get("dram__bytes_write.sum")
+        d = json.load(open(TRAFFIC_JSON)) if os.path.exists(TRAFFIC_JSON) else {}
+        d[kernel] = {"source_hash": _source_hash(KERNEL_SOURCES[kernel]),
+                     "dram_bytes_per_map": (rd + wr) / maps, "captured_maps": maps,
+                     "dram_read_bytes": rd, "dram_write_bytes": wr, "how": how}
+        json.dump(d, open(TRAFFIC_JSON, "w"), indent=1)
+        print("%s: %.3f MB per map (read %.1f MB, write %.1f MB over %d maps)"
+              % (kernel, (rd + wr) / maps / 1e6, rd / 1e6, wr / 1e6, maps))
+        return
+    raise SystemExit("no launch of %s in %s" % (kernel, csv_path))
 
 
 class Clocks:
@@ -290,6 +351,11 @@ def _train_warm_model(vs, synth, k, w, dev, n_train, epochs, seed_base, stream):
                "train_s": round(time.perf_counter() - t1, 2)}
 
 
+ALL_VARIANTS = ("fp32_cluster_cold", "fp32_streamed_cold", "bf16_split_cold", "fp32_learned_warm",
+                "bf16_split_learned_warm", "fp32_cluster_tol1e-4", "fp32_streamed_tol1e-4")
+BATCHED = ALL_VARIANTS[:5]          # candidates for the headline (tolerance 1e-2 K)
+
+
 def run_ours(a):
     import torch
     import torch.distributed as dist
@@ -301,6 +367,10 @@ def run_ours(a):
     import paper_2307_12119_gb300 as vs
     import synth
 
+    wanted = [v for v in (a.variants.split(",") if a.variants else ALL_VARIANTS)]
+    for v in wanted:
+        if v not in ALL_VARIANTS:
+            raise SystemExit("unknown variant %r (known: %s)" % (v, ", ".join(ALL_VARIANTS)))
     # every rank solves its own shard of the sample space (weak scaling)
     w, pd, pl, s = synth.batch_inputs(a.n, a.batch, device=dev, seed=synth.SEED + 7919 * rank)
     st, phy = w.stack, w.physics
@@ -311,51 +381,54 @@ def run_ours(a):
     tol = 1e-2
     mk = lambda prec, t=tol, eng=vs.VS_ENGINE_AUTO: vs.SolveParams(phy.beta_per_K, phy.alpha_per_K,
                                                                   t, 50, prec, eng)
-    model, train_info = _train_warm_model(vs, synth, k, w, dev, a.train_maps, a.train_epochs,
-                                          synth.SEED + 104729 + rank, stream)
+    model, train_info = None, None
+    if any(v.endswith("learned_warm") for v in wanted):
+        model, train_info = _train_warm_model(vs, synth, k, w, dev, a.train_maps, a.train_epochs,
+                                              synth.SEED + 104729 + rank, stream)
     items = lambda out: [(k, pd[i], pl[i], s[i], out[i]) for i in range(B)]
-    results = {}
+    results, runners, thetas = {}, {}, {}
 
-    def measure(name, runner, launches):
+    def measure(name, runner):
         ms, clk = _time_plan(runner, a.steps, a.warmup, ws, local, stream)
         infos = runner.info()
         msx = _max_over_ranks(ms, ws, dev)
         its = [i["iterations"] for i in infos]
         results[name] = {"value": ws * B / (msx * 1e-3), "unit": UNIT, "ms_per_step": msx,
-                         "ms_local": ms, "iterations_mean": sum(its) / len(its),
+                         "iterations_mean": sum(its) / len(its),
                          "not_ok": sum(1 for i in infos if i["status"] != vs.VS_OK),
                          "fell_back": sum(1 for i in infos if i.get("fell_back")),
-                         "gpu_launches_per_step": launches, "clocks": clk}
+                         "gpu_launches_per_step": runner.launches, "clocks": clk}
 
-    runners, thetas = {}, {}
-
-    def variant(name, runner, theta):
-        measure(name, runner, runner.launches)
-        runners[name], thetas[name] = runner, theta
-
-    # the split-precision tensor-core form with the learned warm start
-    th = torch.empty_like(pd)
-    variant("bf16_split_learned_warm",
-            vs.WarmPlan(k, pd, pl, s, th, model, mk(vs.VS_PREC_BF16_SPLIT)), th)
-    th = torch.empty_like(pd)
-    variant("bf16_split_cold", vs.Plan(items(th), mk(vs.VS_PREC_BF16_SPLIT)), th)
-    # FP32 with the learned warm start (its plans take the automatic engine)
-    th = torch.empty_like(pd)
-    variant("fp32_learned_warm", vs.WarmPlan(k, pd, pl, s, th, model, mk(vs.VS_PREC_FP32)), th)
-    # FP32 cold starts on both engines
-    th = torch.empty_like(pd)
-    variant("fp32_streamed_cold",
-            vs.Plan(items(th), mk(vs.VS_PREC_FP32, eng=vs.VS_ENGINE_STREAMED)), th)
-    th = torch.empty_like(pd)
-    variant("fp32_cluster_cold",
-            vs.Plan(items(th), mk(vs.VS_PREC_FP32, eng=vs.VS_ENGINE_CLUSTER)), th)
-    for eng, nm in ((vs.VS_ENGINE_STREAMED, "streamed"), (vs.VS_ENGINE_CLUSTER, "cluster")):
+    builders = {
+        # BF16 hi/lo split precision on tcgen05, with and without the learned warm start
+        "bf16_split_learned_warm":
+            lambda th: vs.WarmPlan(k, pd, pl, s, th, model, mk(vs.VS_PREC_BF16_SPLIT)),
+        "bf16_split_cold": lambda th: vs.Plan(items(th), mk(vs.VS_PREC_BF16_SPLIT)),
+        # FP32 with the learned warm start (its plans take the automatic engine)
+        "fp32_learned_warm": lambda th: vs.WarmPlan(k, pd, pl, s, th, model, mk(vs.VS_PREC_FP32)),
+        # FP32 cold starts on both engines, at the headline tolerance and at 1e-4 K
+        "fp32_streamed_cold":
+            lambda th: vs.Plan(items(th), mk(vs.VS_PREC_FP32, eng=vs.VS_ENGINE_STREAMED)),
+        "fp32_cluster_cold":
+            lambda th: vs.Plan(items(th), mk(vs.VS_PREC_FP32, eng=vs.VS_ENGINE_CLUSTER)),
+        "fp32_streamed_tol1e-4":
+            lambda th: vs.Plan(items(th), mk(vs.VS_PREC_FP32, 1e-4, vs.VS_ENGINE_STREAMED)),
+        "fp32_cluster_tol1e-4":
+            lambda th: vs.Plan(items(th), mk(vs.VS_PREC_FP32, 1e-4, vs.VS_ENGINE_CLUSTER)),
+    }
+    for name in ALL_VARIANTS:
+        if name not in wanted:
+            continue
         th = torch.empty_like(pd)
-        plan = vs.Plan(items(th), mk(vs.VS_PREC_FP32, 1e-4, eng))
-        measure("fp32_%s_tol1e-4" % nm, plan, plan.launches)
-        del plan, th
-    batched = ("fp32_cluster_cold", "fp32_streamed_cold", "bf16_split_cold", "fp32_learned_warm",
-               "bf16_split_learned_warm")
+        runner = builders[name](th)
+        measure(name, runner)
+        if name in BATCHED:
+            runners[name], thetas[name] = runner, th
+        else:
+            del runner, th
+    batched = [v for v in BATCHED if v in results]
+    if not batched:
+        raise SystemExit("no batched variant at the headline tolerance was selected")
     best = max(batched, key=lambda name: results[name]["value"])
     if ws > 1:                      # every rank reports the same headline path
         t = torch.tensor([batched.index(best)], device=dev)
@@ -364,7 +437,7 @@ def run_ours(a):
     th_best = thetas[best]
 
     # plain: FP32, one map per vs_solve_steady call
-    plain_maps = 32
+    plain_maps = min(32, B)
     torch.cuda.synchronize()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     plain_out = torch.empty_like(pd[0])
@@ -414,51 +487,53 @@ def run_ours(a):
         hbm, hbm_kind = _peaks()
         pk = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json"))) if hbm_kind == "measured" else {}
         tc_peak = float(pk.get("bf16_tflops_sustained", 1700.0))
-        ch = results["bf16_split_learned_warm"]
-        # tensor-core flops of the warm-started split path: per map and iteration (first
-        # iterate plan + warm plan) 4 transform passes of 2 n^3 flops, x 3 split products
-        it_total = ch["iterations_mean"] + 1.0
-        flops = B * it_total * 4 * 2 * w.n ** 3 * 3
-        achieved_tf = flops / (ch["ms_local"] * 1e-3) / 1e12
         alg_bytes = B * w.n * w.n * ALG_BYTES_PER_PIXEL
-        # the headline is the fastest batched variant at the 1e-2 K tolerance
         bv = results[best]
-        for r in results.values():
-            r.pop("ms_local", None)
-        other = "bf16_split_learned_warm" if best != "bf16_split_learned_warm" else "fp32_cluster_cold"
-        cpu, acc = cpu_oracle_leg(w, pd.cpu(), pl.cpu(), s.cpu(), th_best.cpu(), a.cpu_seconds,
-                                  other=thetas[other].cpu())
-        acc["path"] = best
-        acc["other_path"] = other
 
-        def hbm_roof(name, kernel):
+        def alu_roof(name, kernel):
             r = results[name]
             tr = _traffic_record(kernel)
-            ach = alg_bytes / (r["ms_per_step"] * 1e-3) / 1e9
-            return {"bound": "hbm", "achieved": ach, "peak": hbm, "unit": "GB/s",
-                    "frac": ach / hbm, "traffic": (tr["dram_bytes_per_map"] * B) if tr else None,
-                    "kernel": kernel,
-                    "note": "achieved = 16 B/pixel algorithmic bytes (3 input maps read, theta "
-                            "written) x maps / step time; peak = %s HBM copy bandwidth" % hbm_kind}
+            fl = B * fp32_flops_per_map(w.n, r["iterations_mean"])
+            ach = fl / (r["ms_per_step"] * 1e-3) / 1e12
+            hb = alg_bytes / (r["ms_per_step"] * 1e-3) / 1e9
+            return {"bound": "alu", "achieved": ach, "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s",
+                    "frac": ach / FP32_PEAK_TFLOPS,
+                    "traffic": (tr["dram_bytes_per_map"] * B) if tr else None, "kernel": kernel,
+                    "note": "achieved = FP32 operations of the FFT-based cosine transforms, "
+                            "twiddles, multiply and update (bench.fp32_flops_per_map) / step "
+                            "time; peak = 152 SMs x 128 lanes x 2 x 2.07 GHz. HBM view: %.0f "
+                            "GB/s of algorithmic bytes (16 B/pixel) = %.3f of the %s %.0f GB/s"
+                            % (hb, hb / hbm, hbm_kind, hbm)}
 
-        cold_tc = results["bf16_split_cold"]
-        cold_tf = B * (cold_tc["iterations_mean"]) * 4 * 2 * w.n ** 3 * 3 / (
-            cold_tc["ms_per_step"] * 1e-3) / 1e12
-        tc_cold_roof = {"bound": "tensor", "achieved": cold_tf, "peak": tc_peak, "unit": "TFLOP/s",
-                        "frac": cold_tf / tc_peak, "traffic": None, "kernel": "k_solve_steady_tc",
-                        "note": "achieved = maps x iterations x 4 passes x 2n^3 x 3 split products "
-                                "/ step time; peak = measured bf16 sustained"}
-        tc_warm_roof = {"bound": "tensor", "achieved": achieved_tf, "peak": tc_peak,
-                        "unit": "TFLOP/s", "frac": achieved_tf / tc_peak, "traffic": None,
-                        "kernel": "k_solve_steady_tc"}
-        roofs = {"fp32_cluster_cold": hbm_roof("fp32_cluster_cold", "k_solve_cluster"),
-                 "fp32_streamed_cold": hbm_roof("fp32_streamed_cold", "k_solve_steady"),
-                 "bf16_split_cold": tc_cold_roof, "bf16_split_learned_warm": tc_warm_roof}
-        roof = roofs.get(best)
-        if roof is None:            # FP32 learned warm: two cluster plans around the network
-            roof = dict(roofs["fp32_cluster_cold"])
-            roof["achieved"] = alg_bytes / (bv["ms_per_step"] * 1e-3) / 1e9
-            roof["frac"] = roof["achieved"] / hbm
+        def tc_roof(name, extra_iteration):
+            # per map and iteration 4 transform passes of 2 n^3 flops, x 3 split products
+            r = results[name]
+            it = r["iterations_mean"] + (1.0 if extra_iteration else 0.0)
+            ach = B * it * 4 * 2 * w.n ** 3 * 3 / (r["ms_per_step"] * 1e-3) / 1e12
+            return {"bound": "tensor", "achieved": ach, "peak": tc_peak, "unit": "TFLOP/s",
+                    "frac": ach / tc_peak, "traffic": None, "kernel": "k_solve_steady_tc",
+                    "note": "achieved = maps x iterations x 4 passes x 2n^3 x 3 split products "
+                            "/ step time; peak = measured bf16 sustained"}
+
+        roofs = {}
+        if "fp32_cluster_cold" in results:
+            roofs["fp32_cluster_cold"] = alu_roof("fp32_cluster_cold", "k_solve_cluster")
+        if "fp32_streamed_cold" in results:
+            roofs["fp32_streamed_cold"] = alu_roof("fp32_streamed_cold", "k_solve_steady")
+        if "fp32_learned_warm" in results:
+            roofs["fp32_learned_warm"] = alu_roof("fp32_learned_warm", "k_solve_cluster")
+        if "bf16_split_cold" in results:
+            roofs["bf16_split_cold"] = tc_roof("bf16_split_cold", False)
+        if "bf16_split_learned_warm" in results:
+            roofs["bf16_split_learned_warm"] = tc_roof("bf16_split_learned_warm", True)
+        acc, cpu = None, None
+        if a.cpu_seconds > 0:
+            other = next((v for v in ("bf16_split_learned_warm", "fp32_cluster_cold") if v != best
+                          and v in thetas), None)
+            cpu, acc = cpu_oracle_leg(w, pd.cpu(), pl.cpu(), s.cpu(), th_best.cpu(), a.cpu_seconds,
+                                      other=thetas[other].cpu() if other else None)
+            acc["path"] = best
+            acc["other_path"] = other
         out = {
             "metric": METRIC, "value": bv["value"], "unit": UNIT, "n_gpus": ws, "steps": a.steps,
             "warmup": a.warmup, "ms_per_step": bv["ms_per_step"], "higher_is_better": True,
@@ -476,10 +551,8 @@ def run_ours(a):
                       "how": "FP32, one map per vs_solve_steady call, tol %g K, %d maps"
                              % (tol, plain_maps)},
             "warm_start_model": train_info,
-            "roofline": roof,
-            "roofline_fp32_cluster_cold": roofs["fp32_cluster_cold"],
-            "roofline_fp32_streamed_cold": roofs["fp32_streamed_cold"],
-            "roofline_bf16_split_cold": tc_cold_roof,
+            "roofline": roofs[best],
+            "rooflines": roofs,
             "cpu_baseline": cpu,
             "accuracy_vs_fp64_oracle": acc,
             "e2e": e2e,
@@ -495,7 +568,9 @@ def run_ours(a):
 
 if __name__ == "__main__":
     args = _args()
-    if args.impl == "reference":
+    if args.record_traffic:
+        record_traffic(args.record_traffic, args.kernel, args.batch, args.how)
+    elif args.impl == "reference":
         run_reference(args)
     else:
         run_ours(args)
