@@ -8,16 +8,16 @@
  *   - T = f_sp * P: temperature is the Green's function convolved with the
  *     power map (Sec. II-B, Eq. 2);
  *   - the radially symmetric Green's function is obtained from its Hankel
- *     transform (Sec. II-F, Eq. 10; Appendix, Theorem I);
- *   - die edges are handled by mirror images (Sec. III-G);
- *   - leakage P = P_dyn + P_leak0 (1 + beta dT) (Eqs. 5, 12) and the
- *     conductivity factor f_sp(T) = f_sp0 (1 + alpha dT) (Eq. 8) are resolved
+ *     transform (Sec. II-F, Eq. 8; Appendix, Theorem I);
+ *   - die edges are handled by mirror images (Sec. IV-F);
+ *   - leakage P = P_dyn + P_leak0 (1 + beta dT) (Eqs. 5, 13) and the
+ *     conductivity factor f_sp(T) = f_sp0 (1 + alpha dT) (Eq. 12) are resolved
  *     by iterating power -> temperature -> leakage/conductivity to a stated
- *     tolerance (the convergence loop of Sec. V-B), preconditioned by the
+ *     tolerance (the convergence loop of Sec. V-C), preconditioned by the
  *     mean/variation split into a shift-invariant and a shift-variant part
- *     (Sec. III-C, Eqs. 17-22);
+ *     (Sec. IV-C, Eqs. 18-26);
  *   - the transient uses a single-pole response per spatial frequency and
- *     superposition of power differences (Sec. III-D/E, Eqs. 23-31).
+ *     superposition of power differences (Sec. IV-D/E, Eqs. 27-37).
  *
  * Conventions for every call:
  *   - Maps are row-major float32 [n][n] (x fastest), one value per grid cell.
@@ -62,7 +62,7 @@ typedef enum {
  * top plane. Layers are in perfect contact; the bottom of the last layer sees
  * a convective coefficient h; the top surface and the side walls are
  * adiabatic. heat_cap_J_m2K is the areal thermal capacitance C of the
- * transient model (Eq. 23); it is only used when a time step is given. */
+ * transient model (Eq. 27); it is only used when a time step is given. */
 typedef struct {
   int n_layers;                          /* 1 .. VS_MAX_LAYERS */
   double thickness_m[VS_MAX_LAYERS];     /* > 0 */
@@ -115,7 +115,7 @@ typedef struct {
 
 /* Parameters of a solve.
  *   beta_per_K : temperature coefficient of leakage (Eq. 5), >= 0
- *   alpha_per_K: temperature coefficient of the Green's function (Eq. 8), >= 0
+ *   alpha_per_K: temperature coefficient of the Green's function (Eq. 12), >= 0
  *   tol_K      : stop when max |theta_n - theta_{n-1}| <= tol_K (> 0)
  *   max_iter   : 1 .. 1000
  *   precision  : VS_PREC_FP32 or VS_PREC_BF16_SPLIT
@@ -146,15 +146,15 @@ typedef struct vs_plan_t* vs_plan;
 typedef struct vs_model_t* vs_model;
 
 /* ------------------------------------------------------------------------ */
-/* Green's function build (Sec. II-B, Eq. 2; Sec. II-F Eq. 10; Theorem I;    */
-/* images Sec. III-G).                                                       */
+/* Green's function build (Sec. II-B, Eq. 2; Sec. II-F Eq. 8; Theorem I;    */
+/* images Sec. IV-F).                                                       */
 /* ------------------------------------------------------------------------ */
 
 /* Builds the imaged, cell-averaged Green's function of (stack, grid) in the
  * cosine basis of the die, K[p][q], p,q in [0,n), on the GPU:
  *   1. stack spectrum g(k) (impedance recursion of the heat equation, Eq. 1);
- *   2. Hankel quadrature (Eq. 10, Theorem I normalisation) of the top-layer
- *      ("rapidly decaying", Sec. II-B) Green's function at every lattice
+ *   2. Hankel quadrature (Eq. 8, Theorem I normalisation) of the top-layer
+ *      (fast-decaying part, Sec. II-B) Green's function at every lattice
  *      radius, FP64: G1(r) = halfspace_disc(r) - sum_i w_i J0(k_i r);
  *   3. fold of the lattice into the 2n-periodic mirror-imaged kernel and its
  *      cosine transform;
@@ -189,13 +189,13 @@ int vs_hankel_radial(const vs_stack* stack, const vs_grid* grid, int quad_nodes,
                      const double* r_dev, double* out_dev, int count, void* stream);
 
 /* ------------------------------------------------------------------------ */
-/* Steady solve (Eqs. 12-22; convergence loop of Sec. V-B).                  */
+/* Steady solve (Eqs. 13-26; convergence loop of Sec. V-C).                 */
 /* ------------------------------------------------------------------------ */
 
 /* Solves u = L[P_dyn + P_leak0 (1 + beta theta)], theta = s u / (1 - alpha s u)
  * for one map, where L is the convolution with the imaged Green's function.
  * Iterates the mean/variation split (shift-invariant kernel
- * K/(1 - beta mu K), Eq. 20 with alpha = 0) until max |dtheta| <= tol.
+ * K/(1 - beta mu K), Eq. 21 with alpha = 0) until max |dtheta| <= tol.
  *   p_dyn, p_leak0: W per cell; s_kappa: conductivity multiplier (NULL => 1);
  *   theta: output, K above ambient.
  * info_host (may be NULL) is filled after an internal stream synchronisation.
@@ -227,8 +227,8 @@ int vs_solve_steady_noalloc(vs_kernel k, const float* p_dyn, const float* p_leak
                             float* theta, vs_solve_info* info_host, void* stream);
 
 /* ------------------------------------------------------------------------ */
-/* Batched steady solve: many maps (possibly of different grid sizes) in one */
-/* persistent launch.                                                        */
+/* Batched steady solve: many maps (possibly of different grid sizes), one  */
+/* launch per run (cluster engine: one per distinct grid size).             */
 /* ------------------------------------------------------------------------ */
 
 typedef struct {
@@ -241,17 +241,20 @@ typedef struct {
                               fixed point, e.g. from vs_model_predict), or NULL => 0 */
 } vs_batch_item;
 
-/* Creates a plan for n_items maps: uploads the item table, allocates the
- * scratch (4 bytes per cell plus small per-map state) and picks the launch
- * shape (tuned once per mix of grid sizes and cached). The item pointers are
- * retained until vs_plan_free. Synchronises `stream`. */
+/* Creates a plan for n_items maps: uploads the item table and picks the
+ * engine (params->engine). Streamed engine: allocates the scratch (4 bytes per
+ * cell plus small per-map state) and picks the launch shape (tuned once per
+ * mix of grid sizes and cached). Cluster engine: no spectral scratch, maps
+ * grouped by grid size. The item pointers are retained until vs_plan_free.
+ * Synchronises `stream`. */
 int vs_plan_create(const vs_batch_item* items_host, int n_items,
                    const vs_solve_params* params, vs_plan* out, void* stream);
 
-/* Runs the plan: one cooperative persistent launch that iterates every map to
- * its own convergence. Asynchronous; makes no host allocation or
- * synchronisation, so it can be captured in a CUDA graph. Per-map results go
- * to the plan's device info array (vs_plan_info). */
+/* Runs the plan: one launch (streamed engine: cooperative and persistent;
+ * cluster engine: one per distinct grid size, a cluster per map) that
+ * iterates every map to its own convergence. Asynchronous; makes no host
+ * allocation or synchronisation, so it can be captured in a CUDA graph.
+ * Per-map results go to the plan's device info array (vs_plan_info). */
 int vs_plan_run(vs_plan plan, void* stream);
 
 /* Copies the per-map vs_solve_info of the last run to host memory
@@ -270,14 +273,14 @@ int vs_solve_batch(const vs_batch_item* items_host, int n_items,
                    void* stream);
 
 /* ------------------------------------------------------------------------ */
-/* Transient (Sec. III-D/E, Eqs. 23-31).                                     */
+/* Transient (Sec. IV-D/E, Eqs. 27-37).                                     */
 /* ------------------------------------------------------------------------ */
 
 /* Time-varying power P_dyn,n (n = 1..n_steps, piecewise constant over steps
  * of dt_s given at kernel build) with leakage lagged one step,
  * P_n = P_dyn,n + P_leak0 (1 + beta theta_{n-1}), theta_0 = 0.
- * Superposition of power differences (Eq. 30) with the single-pole step
- * response g(k)(1 - exp(-t / (C g(k)))) of every cosine mode (Eq. 29), run as
+ * Superposition of power differences (Eq. 36) with the single-pole step
+ * response g(k)(1 - exp(-t / (C g(k)))) of every cosine mode (Eq. 35), run as
  * the equivalent per-mode recursion. The sub-cell alias part of the kernel is
  * taken as settled within one step.
  *   p_dyn_trace: [n_steps][n][n]; theta_trace: output [n_steps][n][n].
@@ -288,11 +291,11 @@ int vs_solve_transient(vs_kernel k, int n_steps, const float* p_dyn_trace,
                        vs_solve_info* info_host, void* stream);
 
 /* ------------------------------------------------------------------------ */
-/* Learned warm start of the fixed point. The paper iterates power ->        */
-/* temperature -> leakage until convergence (Sec. V-B); these calls predict  */
+/* Learned warm start of the fixed point. The paper iterates power ->       */
+/* temperature -> leakage until convergence (Sec. V-C); these calls predict */
 /* most of the remaining correction after the first iterate so that the     */
 /* iteration can start closer to its fixed point. The solve still decides   */
-/* convergence, so a poor prediction costs iterations, not accuracy.         */
+/* convergence, so a poor prediction costs iterations, not accuracy.        */
 /* ------------------------------------------------------------------------ */
 
 /* Small U-Net on resolution x resolution inputs (3 channels -> 1): convs
@@ -339,7 +342,7 @@ int vs_warm_apply(const float* theta1, const float* y, int count, int n, int res
 /* Split-precision tensor-core transform (the building block of
  * VS_PREC_BF16_SPLIT), exposed for testing: for each of `rows` rows,
  *   out[r][j] = sum_k in[r][k] C[j][k],  C[j][k] = cos(pi j (2k+1) / 2n)
- * (forward DCT-II of Sec. III-G's mirror-imaged rows) or, with inverse != 0,
+ * (forward DCT-II of Sec. IV-F's mirror-imaged rows) or, with inverse != 0,
  *   out[r][j] = sum_k in[r][k] w_k cos(pi k (2j+1) / 2n) / n, w_0 = 1, w_k = 2
  * (its exact inverse). in/out: device float32 [rows][n], rows a multiple of
  * 128, n = 128 or 256, 16-byte aligned. Asynchronous on `stream`. */

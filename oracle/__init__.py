@@ -7,7 +7,7 @@ point and the CPU-baseline leg of the benchmark may import it; the product path
 
 Modules
 -------
-physics : layer-stack spectrum g^(k), the top-layer ("rapidly decaying")
+physics : layer-stack spectrum g^(k), the fast-decaying top-layer
           Green's function by its eigenfunction series, the disc-source
           half-space closed form, and the spectral kernel K~ of the imaged die.
 solve   : the mirror-image convolution (direct summation and dense-cosine

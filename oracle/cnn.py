@@ -1,7 +1,7 @@
 """FP64 reference of the warm-start network (test infrastructure only).
 
 The learned warm start is this project's addition to the method (the paper
-iterates to convergence, Sec. V-B, and has no learned part). This module holds
+iterates to convergence, Sec. V-C, and has no learned part). This module holds
 the plain definition of the network the CUDA library trains, written in numpy
 FP64 with its own forward and backward passes, so the GPU gradients can be
 checked against it; its own backward is pinned by finite differences.

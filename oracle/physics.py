@@ -3,7 +3,7 @@
 Test infrastructure only (see the package docstring). All arithmetic is FP64.
 
 Model (the paper measures its baseline Green's function with a modified
-HotSpot, Sec. V-B; the analytic layered model below is this project's reading
+HotSpot, Sec. V-C; the analytic layered model below is this project's reading
 of the heat equation, Eq. 1, for the stack of the chip parameter table):
 
 * layers i = 0..M-1 from the source plane down, thickness t_i, conductivity
@@ -13,12 +13,12 @@ of the heat equation, Eq. 1, for the stack of the chip parameter table):
   temperature of a unit point source (Eq. 2 with f_sp the Green's function);
 * every grid cell is a uniform disc source of the cell's area (radius
   a = cell/sqrt(pi)), temperatures are read at cell centres;
-* the die walls are handled by mirror images (Sec. III-G), i.e. even
+* the die walls are handled by mirror images (Sec. IV-F), i.e. even
   reflection at both walls in x and y, which makes the imaged kernel
   2L-periodic.
 
-The radial Green's function is split as in Sec. II-B ("a rapidly decaying part
-f_silic plus the part redistributed by the spreader"):
+The radial Green's function is split as Sec. II-B describes it, into a part that
+decays fast with r and a part carried by the heat spreader:
   g^(k) = g1(k) + R(k),  g1(k) = tanh(k t0)/(kappa0 k)
 g1 is the top layer on an isothermal base; its radial function decays like
 K0(pi r / 2 t0) and is summed in real space. R(k) decays like exp(-2 k t0) and
@@ -73,7 +73,7 @@ def ghat(k, t, kappa, h):
 
 def ghat_top(k, t, kappa):
     """g1(k) = tanh(k t0)/(kappa0 k): the source layer alone on an isothermal
-    base (the 'rapidly decaying' part of the Green's function, Sec. II-B)."""
+    base (the fast-decaying part of the Green's function, Sec. II-B)."""
     return (t[0] / kappa[0]) * _tanhc(np.asarray(k, dtype=np.float64) * t[0])
 
 
@@ -108,7 +108,7 @@ def ghat_transfer_matrix(k: float, t, kappa, h) -> float:
 
 
 # --------------------------------------------------------------------------- #
-# Radial Green's functions (inverse Hankel transform, Eq. 10 / Theorem I)     #
+# Radial Green's functions (inverse Hankel transform, Eq. 8 / Theorem I)      #
 # --------------------------------------------------------------------------- #
 
 def disc_radius(cell_m: float) -> float:
@@ -201,7 +201,7 @@ def spectrum(n: int, die_m: float, t, kappa, h, n_modes: int | None = None,
              rel: float = 1e-18):
     """K~[p, q] for p, q in [0, n_modes) (n_modes defaults to n).
 
-    Definition (Sec. III-G images + Eq. 2): with all mirror images the imaged
+    Definition (Sec. IV-F images + Eq. 2): with all mirror images the imaged
     kernel is the lattice sum of the cell Green's function G(r) over every
     lattice vector, and its cosine series on the 2n-periodic grid is
       K~[p,q] = sum_{m in Z^2} G(cell |m|) cos(pi p m_x / n) cos(pi q m_y / n).

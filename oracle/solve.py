@@ -4,16 +4,16 @@ transient superposition.
 Test infrastructure only (see the package docstring). FP64 throughout.
 
 Model of the self-consistent temperature (this project's reading of
-Eqs. 4-8 and 12-14, generalised from a unit impulse to a power map):
+Eqs. 4-5, 9-12 and 13-16, generalised from a unit impulse to a power map):
 
-* power P = P_dyn + P_leak0 (1 + beta theta)       (Eq. 12, Eq. 5)
-* u = L[P], L = convolution with the imaged kernel (Eq. 2, Sec. III-G)
+* power P = P_dyn + P_leak0 (1 + beta theta)       (Eq. 13, Eq. 5)
+* u = L[P], L = convolution with the imaged kernel (Eq. 2, Sec. IV-F)
 * the Green's function is scaled at the field point by s (1 + alpha theta)
-  (Eqs. 7-8; s carries the conductivity variation), so theta = s u (1 + alpha
+  (Eqs. 11-12; s carries the conductivity variation), so theta = s u (1 + alpha
   theta), i.e. theta = phi(u) = s u / (1 - alpha s u)
 * the fixed point u = L[P_dyn + P_leak0 (1 + beta phi(u))] is what the
   paper's validation loop reaches by iterating power -> temperature ->
-  leakage/conductivity until convergence (Sec. V-B).
+  leakage/conductivity until convergence (Sec. V-C).
 """
 from __future__ import annotations
 
@@ -30,7 +30,7 @@ def mirror_operator(kper: np.ndarray) -> np.ndarray:
     """Dense matrix of the mirror-image convolution on an n x n grid (n <= 64).
 
     The power map is extended to twice its size with even mirror images at the
-    die edges (Sec. III-G) and convolved circularly with the 2n-periodic kernel
+    die edges (Sec. IV-F) and convolved circularly with the 2n-periodic kernel
     K_per; restricted to the die this is, for target i and source j,
       L_ij = sum over (ex, ey) in {i-j, i+j+1} of K_per(ey mod 2n, ex mod 2n)
     (four terms per pair). Row/column index = y*n + x.
@@ -89,7 +89,7 @@ class SolveError(RuntimeError):
 
 
 def phi(u, s, alpha):
-    """theta = s u / (1 - alpha s u) (field-point factor, Eq. 8)."""
+    """theta = s u / (1 - alpha s u) (field-point factor, Eq. 12)."""
     return s * u / (1.0 - alpha * s * u)
 
 
@@ -98,7 +98,7 @@ def picard(apply_L, p_dyn, p_leak0, s, beta, alpha, tol=1e-8, max_iter=400,
     """Plain Picard iteration on the unsplit fixed point from u = 0:
     u_{n+1} = L[P_dyn + P_leak0 (1 + beta phi(u_n))], stop when
     max |phi(u_{n+1}) - phi(u_n)| <= tol (the update-norm reading of the
-    paper's 'iterate until the temperature values converge', Sec. V-B).
+    validation loop of Sec. V-C, which iterates until the temperatures settle).
     Raises if 1 - alpha s u <= guard (conductivity runaway) or max_iter is hit.
     Returns (theta, u, iterations)."""
     u = np.zeros_like(p_dyn)
@@ -119,10 +119,10 @@ def picard(apply_L, p_dyn, p_leak0, s, beta, alpha, tol=1e-8, max_iter=400,
 
 
 def picard_split(Kt, p_dyn, p_leak0, s, beta, alpha, tol=1e-8, max_iter=400):
-    """The mean/variation split of Sec. III-C used as a preconditioner.
+    """The mean/variation split of Sec. IV-C used as a preconditioner.
 
     mu = mean(P_leak0), P_leak0 = mu + P_var. The shift-invariant part has the
-    modified kernel K_det = K~ / (1 - beta mu K~) (Eq. 20 with alpha = 0); the
+    modified kernel K_det = K~ / (1 - beta mu K~) (Eq. 21 with alpha = 0); the
     remaining shift-variant source is iterated:
       u_det = L_det[P_dyn + mu],
       c_{n+1} = L_det[P_var + beta (P_leak0 phi(u_det + c_n) - mu (u_det + c_n))].
@@ -146,20 +146,20 @@ def picard_split(Kt, p_dyn, p_leak0, s, beta, alpha, tol=1e-8, max_iter=400):
 
 def shift_invariant(Kt, p_dyn, p_leak0, beta):
     """Closed form for a uniform leakage map (no variation, alpha = 0):
-    u = IDCT(DCT(P_dyn + mu) K~ / (1 - beta mu K~)) (Eq. 20 with alpha = 0)."""
+    u = IDCT(DCT(P_dyn + mu) K~ / (1 - beta mu K~)) (Eq. 21 with alpha = 0)."""
     mu = float(np.mean(p_leak0))
     return spectral_convolve(Kt / (1.0 - beta * mu * Kt), p_dyn + mu)
 
 
 # --------------------------------------------------------------------------- #
-# Transient (Eqs. 23-31)                                                        #
+# Transient (Eqs. 27-37)                                                        #
 # --------------------------------------------------------------------------- #
 
 def step_spectrum(n, die_m, t, kappa, h, heat_cap, t_s, rel=1e-18):
     """Spectrum of the step-response Green's function at time t_s:
-    single pole per spatial frequency with tau(k) = C g^(k) (Eq. 23 with the
+    single pole per spatial frequency with tau(k) = C g^(k) (Eq. 35 with the
     alpha term of tau dropped; C = areal heat capacity), so the response to a
-    unit power step is g^(k) (1 - exp(-t / (C g^(k)))) (Eq. 29).
+    unit power step is g^(k) (1 - exp(-t / (C g^(k)))) (Eq. 35).
 
     Same real/spectral split as physics.spectrum: the top-layer part is static
     (the exp factor of the aliases with large k vanishes), the spectral part
@@ -195,7 +195,7 @@ def step_spectrum(n, die_m, t, kappa, h, heat_cap, t_s, rel=1e-18):
 
 
 def duhamel(step_spectra, p_dyn_trace, p_leak0, s, beta, alpha):
-    """Untruncated superposition of power differences (Eq. 30):
+    """Untruncated superposition of power differences (Eq. 36):
       u_n = sum_{j=1..n} S_j * (P_{n-j+1} - P_{n-j}),  P_0 = 0,
     with leakage lagged one step, P_m = P_dyn,m + P_leak0 (1 + beta theta_{m-1}),
     theta_0 = 0, and theta_n = phi(u_n). step_spectra[j-1] is S_j in the

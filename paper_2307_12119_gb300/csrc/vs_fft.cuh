@@ -1,6 +1,6 @@
 // Shared-memory FFT building blocks for the cosine-basis convolution.
 //
-// The mirror-image convolution of Sec. III-G is diagonal in the DCT-II basis
+// The mirror-image convolution of Sec. IV-F is diagonal in the DCT-II basis
 // (the even extension of the map is what a DCT-II encodes). A length-n DCT-II
 // of a real sequence is computed from a length-n complex FFT of the reordered
 // sequence v[i] = x[2i], v[n-1-i] = x[2i+1] (Makhoul's reordering), two real

@@ -1,10 +1,10 @@
 // Green's-function build: stack spectrum, Hankel quadrature of the top-layer
 // radial Green's function, fold of the image lattice, cosine transform and
-// spectral sum of the spreader part (Sec. II-B Eq. 2, Sec. II-F Eq. 10,
-// Appendix Theorem I, Sec. III-G images).
+// spectral sum of the spreader part (Sec. II-B Eq. 2, Sec. II-F Eq. 8,
+// Appendix Theorem I, Sec. IV-F images).
 //
-// Split used (Sec. II-B: "a rapidly decaying part f_silic plus the heat
-// redistributed by the spreader"):
+// Split used (Sec. II-B decomposes the Green's function into a part that decays
+// fast with r and a part carried by the heat spreader):
 //   g(k)  = g1(k) + R(k),  g1(k) = tanh(k t0) / (kappa0 k)
 // g1 is the source layer on an isothermal base; its radial function G1(r)
 // decays like K0(pi r / 2 t0) and is summed over the image lattice in real

@@ -1,17 +1,17 @@
 // Persistent batched solver of the leakage/conductivity fixed point
-// (Eqs. 12-22 with the convergence loop of Sec. V-B) and of the transient
-// superposition (Eqs. 23-31).
+// (Eqs. 13-26 with the convergence loop of Sec. V-C) and of the transient
+// superposition (Eqs. 27-37).
 //
 // One cooperative launch per solve. Every map is a set of tasks:
 //   row task  : RB consecutive rows of one map
 //     - inverse DCT along x of the column-phase output (transposed layout),
 //     - fused update: u -> theta = s u / (1 - alpha s u), residual
 //       max |theta - theta_prev|, source q = P_dyn + P_leak0
-//       + beta (P_leak0 theta - mu u) (mean/variation split, Sec. III-C),
+//       + beta (P_leak0 theta - mu u) (mean/variation split, Sec. IV-C),
 //     - forward DCT along x, stored transposed (x-frequency major);
 //   col task  : CB consecutive x-frequencies of one map
 //     - forward DCT along y, multiply by the shift-invariant modified kernel
-//       K / (1 - beta mu K) (Eq. 20 with alpha = 0), inverse DCT along y.
+//       K / (1 - beta mu K) (Eq. 21 with alpha = 0), inverse DCT along y.
 // Phases are separated by a grid barrier; after each row phase one thread
 // per map decides convergence. Maps converge independently; the launch ends
 // when no map is active.
@@ -547,7 +547,7 @@ __global__ void __launch_bounds__(kThreads, 3) k_solve_transient(PlanDev P) {
 // the CTA that produces them, so each exchange stores finished FFT inputs
 // straight into the consumer's shared memory (st.shared::cluster) and one
 // cluster barrier per exchange orders them. An iteration is: column phase
-// (forward DCT along y, multiply by K / (1 - beta mu K) (Eq. 20 with
+// (forward DCT along y, multiply by K / (1 - beta mu K) (Eq. 21 with
 // alpha = 0), inverse DCT along y, push to the row owners), barrier, row
 // phase (inverse DCT along x, the fused update of the streamed engine,
 // forward DCT along x, push to the column owners together with the residual
@@ -974,7 +974,7 @@ __global__ void __launch_bounds__(ClShape<N>::THREADS, ClShape<N>::MIN_BLOCKS)
   bool stop = false;
   cl_arrive_relaxed();  // peers store into this CTA only after every CTA started
 
-  // initial source (Eq. 17 at theta_0) and the mean leakage mu (Sec. III-C)
+  // initial source (Eq. 13 at theta_0) and the mean leakage mu (Sec. IV-C)
   if (d.theta_init) {
     double acc = 0.0;
     for (int i = t; i < kClRows * N; i += kClThreads)

@@ -6,14 +6,14 @@ the solver's arithmetic: it only draws the inputs the method consumes.
 
 * Power maps: rectangular blocks with uniform power density on a floor, plus
   small high-density hotspots painted last (the stress-test floorplans of the
-  paper's evaluation, Sec. V-B test cases 2/4/5; block sizes and overlap order
+  paper's evaluation, Sec. V-C test cases 2/4/5; block sizes and overlap order
   are unstated there, so later blocks simply overwrite earlier ones).
 * Variation field z: white Gaussian noise smoothed by a Gaussian filter of std
   l/2 with mirror boundaries, then standardised per sample, so that neighbouring
   points within about l are strongly correlated (systematic within-die
   variation modelled as a correlated multivariate Gaussian, Sec. II-C).
 * Baseline leakage P_leak0 = p_l * A_cell * exp(sigma * z) (the exponential
-  variation factor of Eq. 3) and conductivity multiplier s = 1 - gamma*sigma*z
+  variation factor of Eq. 4) and conductivity multiplier s = 1 - gamma*sigma*z
   (Sec. II-E): both come from the same field z.
 * Power traces for the transient: every block follows its own 3-state Markov
   chain {floor, half power, full power}.
@@ -51,7 +51,7 @@ class Stack:
 
 @dataclass
 class Physics:
-    """Leakage / conductivity coefficients (Eqs. 4, 6-8)."""
+    """Leakage / conductivity coefficients (Eqs. 4-5, 9-12)."""
     beta_per_K: float = 0.0275          # paper's chip parameter table
     gamma: float = 0.3                  # c' * k0' (unstated in the paper)
     eta: float = 1.3                    # exponent of kappa(T) for Si (unstated)

@@ -184,7 +184,7 @@ def test_direct_mirror_convolution_equals_dct_form_and_is_symmetric():
 
 
 def test_uniform_power_gives_uniform_rise_close_to_1d_resistance():
-    # TC4-like uniform map (Sec. V-B): theta = q K~[0,0] everywhere, and
+    # TC4-like uniform map (Sec. V-C): theta = q K~[0,0] everywhere, and
     # K~[0,0] cell^2 = g^(0) up to the sub-cell alias terms (<1e-3)
     t, kap, h = STACK3
     n, L = 32, 10e-3
@@ -235,7 +235,7 @@ def test_linearity_without_feedback():
 
 
 def test_uniform_variation_reduces_to_shift_invariant_solution():
-    # P7: no variation, alpha = 0: the converged fixed point is Eq. 20's
+    # P7: no variation, alpha = 0: the converged fixed point is Eq. 21's
     # shift-invariant modified Green's function applied to P_dyn + mu
     w, pd, pl, s = _c1_inputs(32, sigma=0.0, gamma=0.0)
     st = w.stack
@@ -295,7 +295,7 @@ def test_step_spectrum_limits_and_single_pole_law():
     assert all(b > a for a, b in zip(s, s[1:]))
     g0 = ph.ghat(np.array([0.0]), t, kap, h)[0]
     tau = C * g0
-    # the uniform mode decays with the single pole tau = C g^(0) (Eq. 29); the
+    # the uniform mode decays with the single pole tau = C g^(0) (Eq. 35); the
     # sub-cell alias modes have tau < 1 ms and are settled after a few ms
     for tt, val in zip((5e-3, 20e-3, 50e-3), s[2:]):
         assert (Kt[0, 0] - val) * (L / n) ** 2 == pytest.approx(g0 * math.exp(-tt / tau), rel=1e-5)
