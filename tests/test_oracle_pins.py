@@ -366,3 +366,36 @@ def test_cnn_oracle_gradient_matches_finite_differences():
         fd = (lp - lm) / (2 * h)
         assert abs(fd - g[i]) <= 1e-6 * max(1.0, abs(fd)), (i, fd, g[i])
     assert loss == pytest.approx(np.mean((cnn.forward(p, C, x) - t) ** 2), rel=1e-14)
+
+
+# ------------------------------------------- transient uniform mode (1024^2 fixture)
+
+def test_uniform_mode_depends_on_cell_size_not_on_die_size():
+    # The (0,0) cosine mode of the mirror-imaged kernel is the sum of the kernel
+    # over the whole image lattice, so for a fixed cell it is the same for any
+    # number of cells; this lets the 1024^2 transient be checked at any step
+    # from uniform-mode values computed on a small die with the same cell.
+    st = synth.workload("c4_1024").stack
+    cell = 20e-3 / 1024
+    args = (st.thickness_m, st.kappa_W_mK, st.h_conv_W_m2K)
+    assert ph.spectrum(32, 32 * cell, *args)[0, 0] == pytest.approx(
+        ph.spectrum(16, 16 * cell, *args)[0, 0], rel=1e-12)
+    for t_s in (1e-3, 40e-3):
+        a = so.step_spectrum(16, 16 * cell, *args, st.heat_cap_J_m2K, t_s)[0, 0]
+        b = so.step_spectrum(32, 32 * cell, *args, st.heat_cap_J_m2K, t_s)[0, 0]
+        assert a == pytest.approx(b, rel=1e-12)
+
+
+def test_transient_uniform_mode_fixture_is_current():
+    import importlib.util
+    spec = importlib.util.spec_from_file_location(
+        "make_transient_mode00", os.path.join(HERE, "golden", "make_transient_mode00.py"))
+    mk = importlib.util.module_from_spec(spec)
+    spec.loader.exec_module(mk)
+    d = json.load(open(os.path.join(HERE, "golden", "transient_mode00_c4_1024.json")))
+    assert len(d["S00"]) == mk.STEPS and d["dt_s"] == mk.DT_S
+    for j in (1, 137):
+        assert d["S00"][j - 1] == pytest.approx(mk.mode00(j), rel=1e-12)
+    # the step response rises monotonically towards the steady uniform mode
+    s = np.array(d["S00"])
+    assert np.all(np.diff(s) > 0)
