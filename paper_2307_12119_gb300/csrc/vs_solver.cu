@@ -742,21 +742,26 @@ __global__ void __launch_bounds__(ClShape<N>::THREADS, ClShape<N>::MIN_BLOCKS)
   // the spectra of the column phase, pre-twiddled, at digit-reversed places).
   auto row_phase = [&](int mode, float mu, float& resid, int& flags, double& pl_sum) {
     if (mode == 2) {
-      float2* p = base2(brow);
+      // brow holds the spectra in natural frequency order: the radix-R2 pass
+      // takes frequencies blk + 16 r and leaves its outputs in place
+      float2* p = brow + f2 * NP;
       float2 w[R2];
 #pragma unroll
-      for (int r = 0; r < R2; ++r) w[r] = p[r];
+      for (int r = 0; r < R2; ++r) w[r] = p[pad(blk + 16 * r)];
       dftR<R2, false>(w);
 #pragma unroll
-      for (int r = 0; r < R2; ++r) p[r] = w[r];
+      for (int r = 0; r < R2; ++r) p[pad(blk + 16 * r)] = w[r];
       __syncthreads();
     }
+    float2 v[16];
+    if (p16 && mode == 2) {
+      // radix-16 inputs of this thread: block j16 of the pass above
+#pragma unroll
+      for (int r = 0; r < 16; ++r) v[r] = brow[f16 * NP + pad(16 * j16 + r)];
+    }
+    if (mode == 2) __syncthreads();   // the forward pass below rewrites brow in another order
     if (p16) {
-      float2 v[16];
-      if (mode == 2) {
-        load16(brow, v);
-        inv16(v);       // v[r] = u at Makhoul position j + M1 r of rows ya, ya + 1
-      }
+      if (mode == 2) inv16(v);   // v[r] = u at Makhoul position j + M1 r of rows ya, ya + 1
       // Positions m (< N/2, x = 2m) of this lane and N - 1 - m (x + 1) of the
       // mirror lane are updated together, so every input is read as a
       // coalesced float2 (x, x + 1); u and q of x + 1 travel by shuffle.
@@ -844,28 +849,44 @@ __global__ void __launch_bounds__(ClShape<N>::THREADS, ClShape<N>::MIN_BLOCKS)
       for (int r = 0; r < R2; ++r) z[r] = p[r];
     }
     dftR<R2, true>(z);
-    const int ya = y0 + 2 * f2;
-    const unsigned oa = (unsigned)pad(makhoul_pos(ya, N)) * 8u;
-    const unsigned ob = (unsigned)pad(makhoul_pos(ya + 1, N)) * 8u;
+    float2 ea[R2 / 2], eb[R2 / 2];
 #pragma unroll
     for (int r = 0; r < R2 / 2; ++r) {
       // what the partner needs at its index r: Z[N - k'] for its k' = 16 r + (16 - blk)
       const float2 give = blk == 0 ? z[r == 0 ? R2 / 2 : R2 - r] : z[R2 - 1 - r];
       const float2 zn = shfl2(give, partner2);
       const int k = 16 * r + blk;
-      float2 ea, eb;
       if (k == 0) {
         const float2 x0 = dct_post(z[0], z[0], tw[0]), xh = dct_post(zn, zn, tw[half]);
-        ea = make_float2(x0.x, xh.x);
-        eb = make_float2(x0.y, xh.y);
+        ea[r] = make_float2(x0.x, xh.x);
+        eb[r] = make_float2(x0.y, xh.y);
       } else {
         const float2 xk = dct_post(z[r], zn, tw[k]), xn = dct_post(zn, z[r], tw[N - k]);
-        ea = make_float2(xk.x, xn.x);
-        eb = make_float2(xk.y, xn.y);
+        ea[r] = make_float2(xk.x, xn.x);
+        eb[r] = make_float2(xk.y, xn.y);
       }
-      const unsigned dst = cl_map(bcol, (unsigned)(k / kClF)) + (unsigned)((k % kClF) * NP) * 8u;
-      cl_put(dst + oa, ea);
-      cl_put(dst + ob, eb);
+    }
+    // Stage the outgoing values in brow in the order of their destinations:
+    // run (owner o, pair jj, even/odd rows) = 16 values that land on 16
+    // consecutive Makhoul positions of the owner's column buffer, so each
+    // half-warp then stores one contiguous 128-byte run remotely. Slots are
+    // rotated by jj to keep the staging writes free of bank conflicts.
+    __syncthreads();                  // every radix-R2 load of brow is done
+#pragma unroll
+    for (int r = 0; r < R2 / 2; ++r) {
+      const int run = (r * 16 + blk) * 2;           // owner k / 16 = r, pair k % 16 = blk
+      brow[run * 16 + ((f2 + blk) & 15)] = ea[r];
+      brow[(run + 1) * 16 + ((15 - f2 + blk) & 15)] = eb[r];
+    }
+    __syncthreads();
+    {
+      const int e = t & 15;
+      for (int R = t >> 4; R < 32 * ranks; R += kClThreads / 16) {
+        const int o = R >> 5, jj = (R >> 1) & 15;
+        const int m = (R & 1) ? N - y0 / 2 - 16 + e : y0 / 2 + e;
+        cl_put(cl_map(bcol, (unsigned)o) + (unsigned)(jj * NP + pad(m)) * 8u,
+               brow[R * 16 + ((e + jj) & 15)]);
+      }
     }
   };
 
@@ -913,31 +934,49 @@ __global__ void __launch_bounds__(ClShape<N>::THREADS, ClShape<N>::MIN_BLOCKS)
       for (int r = 0; r < R2; ++r) p[r] = e[r];
     }
     __syncthreads();
+    float2 ea[8], eb[8];
     if (p16) {
       float2 v[16];
       load16(bcol, v);
       inv16(v);         // v[r] = column data at Makhoul position j + M1 r of y
       const int j = j0 + f16;
-      const int pa = j == 0 ? 0 : j, pb = j == 0 ? half : N - j;
-      const float2 twa = tw[pa], twb = tw[pb];
-      const unsigned ra = (unsigned)pad(cl_dr<N>(pa)) * 8u, rb = (unsigned)pad(cl_dr<N>(pb)) * 8u;
+      const float2 twa = tw[j == 0 ? 0 : j], twb = tw[j == 0 ? half : N - j];
 #pragma unroll
       for (int r = 0; r < 8; ++r) {
         const float2 vb = shfl2(v[15 - r], partner16);   // the row ya + 1
         const float2 va = v[r];
-        const int ya = 2 * (j16 + r * M1);
-        float2 ea, eb;
         if (j == 0) {
-          ea = dct_pre(va.x, 0.f, vb.x, 0.f, twa);
-          eb = dct_pre(va.y, va.y, vb.y, vb.y, twb);
+          ea[r] = dct_pre(va.x, 0.f, vb.x, 0.f, twa);
+          eb[r] = dct_pre(va.y, va.y, vb.y, vb.y, twb);
         } else {
-          ea = dct_pre(va.x, va.y, vb.x, vb.y, twa);
-          eb = dct_pre(va.y, va.x, vb.y, vb.x, twb);
+          ea[r] = dct_pre(va.x, va.y, vb.x, vb.y, twa);
+          eb[r] = dct_pre(va.y, va.x, vb.y, vb.x, twb);
         }
-        const unsigned dst = cl_map(brow, (unsigned)(ya / kClRows)) +
-                             (unsigned)(((ya % kClRows) >> 1) * NP) * 8u;
-        cl_put(dst + ra, ea);
-        cl_put(dst + rb, eb);
+      }
+    }
+    // Stage in bcol in destination order: run (owner o, row-pair FFT fd,
+    // first/second frequency of the pair) = this CTA's 16 pairs, which land on
+    // consecutive natural-order frequencies of the owner's row buffer.
+    __syncthreads();                  // every radix-16 load of bcol is done
+    if (p16) {
+      const int jj = f16;
+#pragma unroll
+      for (int r = 0; r < 8; ++r) {
+        const int ya = 2 * (j16 + r * M1);
+        const int fd = (ya % kClRows) >> 1;
+        const int run = ((ya / kClRows) * 16 + fd) * 2;
+        bcol[run * 16 + ((jj + fd) & 15)] = ea[r];
+        bcol[(run + 1) * 16 + ((jj + fd) & 15)] = eb[r];
+      }
+    }
+    __syncthreads();
+    {
+      const int e = t & 15, j = j0 + e;
+      const int pos0 = j, pos1 = j == 0 ? half : N - j;
+      for (int R = t >> 4; R < 32 * ranks; R += kClThreads / 16) {
+        const int o = R >> 5, fd = (R >> 1) & 15;
+        cl_put(cl_map(brow, (unsigned)o) + (unsigned)(fd * NP + pad((R & 1) ? pos1 : pos0)) * 8u,
+               bcol[R * 16 + ((e + fd) & 15)]);
       }
     }
   };
