@@ -695,11 +695,24 @@ __global__ void __launch_bounds__(ClShape<N>::THREADS, ClShape<N>::MIN_BLOCKS)
   float2* tw = cl_smem + Lay::kTdct;
   ClSlots* slots = reinterpret_cast<ClSlots*>(cl_smem + Lay::kSlots);
   const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
+  // radix-16 role of the row phase: lanes run along x (coalesced inputs);
+  // the mirror position N - 1 - m sits in lane M1 - 1 - j16 of the group
   const bool p16 = t < kP16;
   const int f16 = t / M1, j16 = t % M1;
-  const int f2 = t >> 4, blk = t & 15;
-  const int partner2 = (lane & 16) | ((16 - blk) & 15);
   const int partner16 = (lane & ~(M1 - 1)) | (M1 - 1 - j16);
+  // radix-R2 role: warp w holds the frequency digits blk = w and 16 - w
+  // (w = 0: 0 and 8) for all 16 FFTs, one FFT per lane of each half-warp, so
+  // frequency k and N - k are in lanes l and l ^ 16 and the stores to a peer
+  // run along the FFTs (consecutive rows or pairs) in every half-warp
+  const int f2 = lane & 15;
+  const int blk = lane < 16 ? warp : (warp == 0 ? 8 : 16 - warp);
+  const int partner2 = (blk == 0 || blk == 8) ? lane : (lane ^ 16);
+  // radix-16 role of the column phase: warp w < M1/2 holds positions j = w
+  // and M1 - 1 - w for all 16 frequency pairs (lanes), so the two rows of a
+  // row pair are in lanes l and l ^ 16 and the stores run along the pairs
+  const bool c16 = warp < M1 / 2;
+  const int jc = lane & 15;
+  const int j16c = lane < 16 ? warp : M1 - 1 - warp;
   const int y0 = (int)rank * kClRows;
   const int j0 = (int)rank * kClF;
   const float beta = P.beta, alpha = P.alpha;
@@ -710,26 +723,26 @@ __global__ void __launch_bounds__(ClShape<N>::THREADS, ClShape<N>::MIN_BLOCKS)
   }
   __syncthreads();
 
-  auto load16 = [&](const float2* buf, float2* v) {
+  auto load16 = [&](const float2* buf, float2* v, int f, int j) {
 #pragma unroll
-    for (int r = 0; r < 16; ++r) v[r] = buf[f16 * NP + pad(j16 + r * M1)];
+    for (int r = 0; r < 16; ++r) v[r] = buf[f * NP + pad(j + r * M1)];
   };
-  auto store16 = [&](float2* buf, const float2* v) {
+  auto store16 = [&](float2* buf, const float2* v, int f, int j) {
 #pragma unroll
-    for (int r = 0; r < 16; ++r) buf[f16 * NP + pad(j16 + r * M1)] = v[r];
+    for (int r = 0; r < 16; ++r) buf[f * NP + pad(j + r * M1)] = v[r];
   };
   auto base2 = [&](float2* buf) { return buf + f2 * NP + blk * R2 + ((blk * R2) >> 4); };
-  auto fwd16 = [&](float2* v) {
+  auto fwd16 = [&](float2* v, int j) {
     dft16<true>(v);
     if (M1 > 1) {
 #pragma unroll
-      for (int r = 1; r < 16; ++r) v[r] = cmul(v[r], twp[r * M1 + j16]);
+      for (int r = 1; r < 16; ++r) v[r] = cmul(v[r], twp[r * M1 + j]);
     }
   };
-  auto inv16 = [&](float2* v) {
+  auto inv16 = [&](float2* v, int j) {
     if (M1 > 1) {
 #pragma unroll
-      for (int r = 1; r < 16; ++r) v[r] = cmulc(v[r], twp[r * M1 + j16]);
+      for (int r = 1; r < 16; ++r) v[r] = cmulc(v[r], twp[r * M1 + j]);
     }
     dft16<false>(v);
   };
@@ -761,7 +774,7 @@ __global__ void __launch_bounds__(ClShape<N>::THREADS, ClShape<N>::MIN_BLOCKS)
     }
     if (mode == 2) __syncthreads();   // the forward pass below rewrites brow in another order
     if (p16) {
-      if (mode == 2) inv16(v);   // v[r] = u at Makhoul position j + M1 r of rows ya, ya + 1
+      if (mode == 2) inv16(v, j16);   // v[r] = u at Makhoul position j16 + M1 r of rows ya, ya + 1
       // Positions m (< N/2, x = 2m) of this lane and N - 1 - m (x + 1) of the
       // mirror lane are updated together, so every input is read as a
       // coalesced float2 (x, x + 1); u and q of x + 1 travel by shuffle.
@@ -824,8 +837,8 @@ __global__ void __launch_bounds__(ClShape<N>::THREADS, ClShape<N>::MIN_BLOCKS)
           v[15 - r] = shfl2(make_float2(qo[0], qo[1]), partner16);
         }
       }
-      fwd16(v);
-      store16(brow, v);
+      fwd16(v, j16);
+      store16(brow, v, f16, j16);
     }
     // per-warp partials of the residual, flags and leakage sum
 #pragma unroll
@@ -849,55 +862,39 @@ __global__ void __launch_bounds__(ClShape<N>::THREADS, ClShape<N>::MIN_BLOCKS)
       for (int r = 0; r < R2; ++r) z[r] = p[r];
     }
     dftR<R2, true>(z);
-    float2 ea[R2 / 2], eb[R2 / 2];
+    // lanes 0-15 of a half-warp hold 16 consecutive row pairs of one pair k:
+    // each store below is one contiguous run in the owner's column buffer
+    const unsigned oe = (unsigned)pad(y0 / 2 + f2) * 8u, oo = (unsigned)pad(N - 1 - y0 / 2 - f2) * 8u;
 #pragma unroll
     for (int r = 0; r < R2 / 2; ++r) {
       // what the partner needs at its index r: Z[N - k'] for its k' = 16 r + (16 - blk)
       const float2 give = blk == 0 ? z[r == 0 ? R2 / 2 : R2 - r] : z[R2 - 1 - r];
       const float2 zn = shfl2(give, partner2);
       const int k = 16 * r + blk;
+      float2 ea, eb;
       if (k == 0) {
         const float2 x0 = dct_post(z[0], z[0], tw[0]), xh = dct_post(zn, zn, tw[half]);
-        ea[r] = make_float2(x0.x, xh.x);
-        eb[r] = make_float2(x0.y, xh.y);
+        ea = make_float2(x0.x, xh.x);
+        eb = make_float2(x0.y, xh.y);
       } else {
         const float2 xk = dct_post(z[r], zn, tw[k]), xn = dct_post(zn, z[r], tw[N - k]);
-        ea[r] = make_float2(xk.x, xn.x);
-        eb[r] = make_float2(xk.y, xn.y);
+        ea = make_float2(xk.x, xn.x);
+        eb = make_float2(xk.y, xn.y);
       }
-    }
-    // Stage the outgoing values in brow in the order of their destinations:
-    // run (owner o, pair jj, even/odd rows) = 16 values that land on 16
-    // consecutive Makhoul positions of the owner's column buffer, so each
-    // half-warp then stores one contiguous 128-byte run remotely. Slots are
-    // rotated by jj to keep the staging writes free of bank conflicts.
-    __syncthreads();                  // every radix-R2 load of brow is done
-#pragma unroll
-    for (int r = 0; r < R2 / 2; ++r) {
-      const int run = (r * 16 + blk) * 2;           // owner k / 16 = r, pair k % 16 = blk
-      brow[run * 16 + ((f2 + blk) & 15)] = ea[r];
-      brow[(run + 1) * 16 + ((15 - f2 + blk) & 15)] = eb[r];
-    }
-    __syncthreads();
-    {
-      const int e = t & 15;
-      for (int R = t >> 4; R < 32 * ranks; R += kClThreads / 16) {
-        const int o = R >> 5, jj = (R >> 1) & 15;
-        const int m = (R & 1) ? N - y0 / 2 - 16 + e : y0 / 2 + e;
-        cl_put(cl_map(bcol, (unsigned)o) + (unsigned)(jj * NP + pad(m)) * 8u,
-               brow[R * 16 + ((e + jj) & 15)]);
-      }
+      const unsigned dst = cl_map(bcol, (unsigned)r) + (unsigned)(blk * NP) * 8u;   // owner k / 16 = r
+      cl_put(dst + oe, ea);
+      cl_put(dst + oo, eb);
     }
   };
 
   // Column phase: bcol holds, for this CTA's frequency pairs, the x-spectra
   // of all rows at the Makhoul positions of y.
   auto col_phase = [&]() {
-    if (p16) {
+    if (c16) {
       float2 v[16];
-      load16(bcol, v);
-      fwd16(v);
-      store16(bcol, v);
+      load16(bcol, v, jc, j16c);
+      fwd16(v, j16c);
+      store16(bcol, v, jc, j16c);
     }
     __syncthreads();
     {
@@ -934,49 +931,34 @@ __global__ void __launch_bounds__(ClShape<N>::THREADS, ClShape<N>::MIN_BLOCKS)
       for (int r = 0; r < R2; ++r) p[r] = e[r];
     }
     __syncthreads();
-    float2 ea[8], eb[8];
-    if (p16) {
+    if (c16) {
       float2 v[16];
-      load16(bcol, v);
-      inv16(v);         // v[r] = column data at Makhoul position j + M1 r of y
-      const int j = j0 + f16;
-      const float2 twa = tw[j == 0 ? 0 : j], twb = tw[j == 0 ? half : N - j];
+      load16(bcol, v, jc, j16c);
+      inv16(v, j16c);   // v[r] = column data at Makhoul position j16c + M1 r of y
+      const int j = j0 + jc;
+      const int pa = j, pb = j == 0 ? half : N - j;
+      const float2 twa = tw[pa], twb = tw[pb];
+      const unsigned ra = (unsigned)pad(pa) * 8u, rb = (unsigned)pad(pb) * 8u;
+      // the rows ya = 2 m (m = j16c + M1 r < N/2) and ya + 1 (position
+      // N - 1 - m, lane ^ 16); lanes 0-15 hold 16 consecutive pairs, whose
+      // values land on consecutive natural-order frequencies of the owner
 #pragma unroll
       for (int r = 0; r < 8; ++r) {
-        const float2 vb = shfl2(v[15 - r], partner16);   // the row ya + 1
+        const float2 vb = shfl2(v[15 - r], lane ^ 16);
         const float2 va = v[r];
+        float2 ea, eb;
         if (j == 0) {
-          ea[r] = dct_pre(va.x, 0.f, vb.x, 0.f, twa);
-          eb[r] = dct_pre(va.y, va.y, vb.y, vb.y, twb);
+          ea = dct_pre(va.x, 0.f, vb.x, 0.f, twa);
+          eb = dct_pre(va.y, va.y, vb.y, vb.y, twb);
         } else {
-          ea[r] = dct_pre(va.x, va.y, vb.x, vb.y, twa);
-          eb[r] = dct_pre(va.y, va.x, vb.y, vb.x, twb);
+          ea = dct_pre(va.x, va.y, vb.x, vb.y, twa);
+          eb = dct_pre(va.y, va.x, vb.y, vb.x, twb);
         }
-      }
-    }
-    // Stage in bcol in destination order: run (owner o, row-pair FFT fd,
-    // first/second frequency of the pair) = this CTA's 16 pairs, which land on
-    // consecutive natural-order frequencies of the owner's row buffer.
-    __syncthreads();                  // every radix-16 load of bcol is done
-    if (p16) {
-      const int jj = f16;
-#pragma unroll
-      for (int r = 0; r < 8; ++r) {
-        const int ya = 2 * (j16 + r * M1);
-        const int fd = (ya % kClRows) >> 1;
-        const int run = ((ya / kClRows) * 16 + fd) * 2;
-        bcol[run * 16 + ((jj + fd) & 15)] = ea[r];
-        bcol[(run + 1) * 16 + ((jj + fd) & 15)] = eb[r];
-      }
-    }
-    __syncthreads();
-    {
-      const int e = t & 15, j = j0 + e;
-      const int pos0 = j, pos1 = j == 0 ? half : N - j;
-      for (int R = t >> 4; R < 32 * ranks; R += kClThreads / 16) {
-        const int o = R >> 5, fd = (R >> 1) & 15;
-        cl_put(cl_map(brow, (unsigned)o) + (unsigned)(fd * NP + pad((R & 1) ? pos1 : pos0)) * 8u,
-               bcol[R * 16 + ((e + fd) & 15)]);
+        const int ya = 2 * (j16c + r * M1);
+        const unsigned dst = cl_map(brow, (unsigned)(ya / kClRows)) +
+                             (unsigned)(((ya % kClRows) >> 1) * NP) * 8u;
+        cl_put(dst + ra, ea);
+        cl_put(dst + rb, eb);
       }
     }
   };
