@@ -97,10 +97,13 @@ def _peaks():
 
 # Source files that define each timed kernel: a traffic record taken with ncu
 # is used only while none of them has changed since.
-_SOLVER_SOURCES = ["paper_2307_12119_gb300/csrc/vs_solver.cu", "paper_2307_12119_gb300/csrc/vs_fft.cuh",
-                   "paper_2307_12119_gb300/csrc/vs_internal.cuh", "include/varsim.h"]
-KERNEL_SOURCES = {"k_solve_cluster": _SOLVER_SOURCES, "k_solve_steady": _SOLVER_SOURCES,
-                  "k_solve_steady_tc": _SOLVER_SOURCES + ["paper_2307_12119_gb300/csrc/vs_tc.cuh"]}
+_CSRC = "paper_2307_12119_gb300/csrc/"
+_COMMON = [_CSRC + "vs_fft.cuh", _CSRC + "vs_solve_common.cuh", "include/varsim.h"]
+KERNEL_SOURCES = {
+    "k_solve_cluster": [_CSRC + "vs_cluster.cu"] + _COMMON,
+    "k_solve_steady": [_CSRC + "vs_solver.cu", _CSRC + "vs_internal.cuh"] + _COMMON,
+    "k_solve_steady_tc": [_CSRC + "vs_solver.cu", _CSRC + "vs_internal.cuh", _CSRC + "vs_tc.cuh"] + _COMMON,
+}
 TRAFFIC_JSON = os.path.join(ROOT, "profiles", "traffic.json")
 
 

@@ -29,39 +29,19 @@
 
 #include "vs_fft.cuh"
 #include "vs_internal.cuh"
+#include "vs_solve_common.cuh"
 #include "vs_tc.cuh"
 
 using namespace vsfft;
+using namespace vsk;
 
 namespace {
 
 constexpr int kThreads = 256;
 constexpr int kU = 4;          // items per thread with loads issued together
 constexpr int kMaxIter = 1000;
-constexpr int kFlagRunaway = 1;
-constexpr int kFlagNonfinite = 2;
 constexpr long long kSpinLimit = 20000000LL;  // ~ seconds at ~100 ns per spin
 
-struct MapDesc {
-  const float* p_dyn;
-  const float* p_leak0;
-  const float* s;
-  float* theta;
-  const float* theta_init;  // warm start (nullable)
-  float* work;           // n*n, transposed spectral scratch
-  const float* Kt;       // n*n cosine-basis kernel
-  const float2* tw4n;
-  const int* digrev;
-  const float* trA;      // transient only
-  const float* trRho;
-  float* state;          // transient per-mode state, n*n
-  float* work2;          // second scratch map (tensor-core path)
-  const uint8_t* tcf;    // pre-tiled forward DCT matrix, BF16 hi/lo (tensor-core path)
-  const uint8_t* tci;    // pre-tiled inverse DCT matrix
-  float kmax;
-  int n, rb, cb;
-  int row_off, col_off, part_off;
-};
 
 struct MapState {
   double mu;
@@ -136,17 +116,6 @@ __device__ bool grid_barrier(Ctrl* c) {
 
 // ------------------------------------------------------------ reductions
 
-__device__ __forceinline__ double block_sum(double v, double* red) {
-  for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
-  int w = threadIdx.x >> 5, l = threadIdx.x & 31;
-  if (l == 0) red[w] = v;
-  __syncthreads();
-  double r = 0.0;
-  if (threadIdx.x == 0)
-    for (int i = 0; i < (int)(blockDim.x >> 5); ++i) r += red[i];
-  __syncthreads();
-  return r;  // valid in thread 0
-}
 
 __device__ __forceinline__ float block_max(float v, float* red) {
   for (int o = 16; o > 0; o >>= 1) v = fmaxf(v, __shfl_down_sync(0xffffffffu, v, o));
@@ -533,564 +502,6 @@ __global__ void __launch_bounds__(kThreads, 3) k_solve_transient(PlanDev P) {
       P.st[b] = s;
       write_info(P, b, s);
     }
-  }
-}
-
-// ------------------------------------------------------------ cluster engine
-// The same fixed point for grids up to 256 x 256, with each map held by one
-// thread-block cluster for the whole solve, so the map never leaves on-chip
-// memory between iterations. CTA c of a cluster of n / 32 CTAs owns
-//   - rows y in [32c, 32c + 32): 16 row FFTs, two rows packed per FFT;
-//   - the x-frequency pairs (j, n - j), j in [16c, 16c + 16), pair 0 being
-//     (0, n/2): 16 column FFTs, the two frequencies of a pair packed per FFT.
-// Pairing k with n - k puts both operands of every DCT pre/post-twiddle in
-// the CTA that produces them, so each exchange stores finished FFT inputs
-// straight into the consumer's shared memory (st.shared::cluster) and one
-// cluster barrier per exchange orders them. An iteration is: column phase
-// (forward DCT along y, multiply by K / (1 - beta mu K) (Eq. 21 with
-// alpha = 0), inverse DCT along y, push to the row owners), barrier, row
-// phase (inverse DCT along x, the fused update of the streamed engine,
-// forward DCT along x, push to the column owners together with the residual
-// partials), barrier; then every CTA takes the same convergence decision from
-// the same partials, so control flow stays uniform across the cluster. Global
-// memory sees only the inputs (read) and theta (written). There are no spin
-// waits: the cluster barriers are hardware barriers.
-
-// Rows (and x-frequencies) a CTA owns at most; the cluster holds N / rows CTAs.
-#ifndef VS_CL_ROWS
-#define VS_CL_ROWS 32
-#endif
-constexpr int kClMaxN = 256;
-constexpr int kClMaxRanks = 8;
-constexpr int kClBatch = 2;            // positions whose inputs are loaded together
-
-template <int N>
-struct ClShape {
-  static constexpr int ROWS = N < VS_CL_ROWS ? N : VS_CL_ROWS;
-  static constexpr int F = ROWS / 2;         // FFTs per CTA in each phase
-  static constexpr int THREADS = 16 * F;     // one radix-16 butterfly per thread
-  static constexpr int RANKS = N / ROWS;
-  static constexpr int MIN_BLOCKS = THREADS <= 256 ? 2 : 1;
-};
-
-struct ClSlots {
-  double part[kClMaxRanks];
-  float resid[kClMaxRanks];
-  int flags[kClMaxRanks];
-};
-
-struct ClusterDev {
-  const MapDesc* maps;
-  const int* order;      // cluster index -> map index
-  vs_solve_info* info;
-  int max_iter;
-  float beta, alpha, tol;
-};
-
-// Shared memory of one CTA for grid size N, in float2 units: row buffer
-// [F][NP], column buffer [F][NP], spectral multiplier of the CTA's frequency
-// pairs [N][F] (column index XOR-swizzled by the row), the first-pass FFT
-// twiddles W_N^{j r} stored [r][j] (r < 16, j < N/16), the DCT twiddles
-// W_4N^k (k < N), then the partials slots.
-template <int N>
-struct ClLayout {
-  static constexpr int F = ClShape<N>::F;
-  static constexpr int NP = N + N / 16 + 1;
-  static constexpr int kBcol = F * NP;
-  static constexpr int kLs = 2 * F * NP;
-  static constexpr int kTwp = kLs + N * F;
-  static constexpr int kTdct = kTwp + N;
-  static constexpr int kSlots = kTdct + N;
-  static constexpr size_t kBytes = (size_t)kSlots * sizeof(float2) + sizeof(ClSlots);
-};
-
-inline size_t cl_smem_bytes(int n) {
-  switch (n) {
-    case 32: return ClLayout<32>::kBytes;
-    case 64: return ClLayout<64>::kBytes;
-    case 128: return ClLayout<128>::kBytes;
-    default: return ClLayout<256>::kBytes;
-  }
-}
-
-__device__ __forceinline__ unsigned cl_rank() {
-  unsigned r;
-  asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
-  return r;
-}
-__device__ __forceinline__ unsigned cl_index() {
-  unsigned r;
-  asm volatile("mov.u32 %0, %%clusterid.x;" : "=r"(r));
-  return r;
-}
-__device__ __forceinline__ void cl_arrive_relaxed() {
-  asm volatile("barrier.cluster.arrive.relaxed.aligned;" ::: "memory");
-}
-__device__ __forceinline__ void cl_wait() {
-  asm volatile("barrier.cluster.wait.acquire.aligned;" ::: "memory");
-}
-__device__ __forceinline__ void cl_sync() {
-  asm volatile(
-      "barrier.cluster.arrive.release.aligned;\n\t"
-      "barrier.cluster.wait.acquire.aligned;" ::: "memory");
-}
-// Address of the same shared-memory location in the CTA of cluster rank `rank`.
-__device__ __forceinline__ unsigned cl_map(const void* p, unsigned rank) {
-  unsigned a = (unsigned)__cvta_generic_to_shared(p), r;
-  asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(r) : "r"(a), "r"(rank));
-  return r;
-}
-__device__ __forceinline__ void cl_put(unsigned a, float2 v) {
-  asm volatile("st.shared::cluster.v2.f32 [%0], {%1, %2};" ::"r"(a), "f"(v.x), "f"(v.y) : "memory");
-}
-__device__ __forceinline__ void cl_put(unsigned a, float v) {
-  asm volatile("st.shared::cluster.f32 [%0], %1;" ::"r"(a), "f"(v) : "memory");
-}
-__device__ __forceinline__ void cl_put(unsigned a, int v) {
-  asm volatile("st.shared::cluster.s32 [%0], %1;" ::"r"(a), "r"(v) : "memory");
-}
-__device__ __forceinline__ void cl_put(unsigned a, double v) {
-  asm volatile("st.shared::cluster.f64 [%0], %1;" ::"r"(a), "d"(v) : "memory");
-}
-
-// Digit-reversed position of frequency k in the output of the radix-16 x
-// (N/16) forward FFT below (the same order as the streamed engine's tables).
-template <int N>
-__device__ __forceinline__ int cl_dr(int k) {
-  return (k & 15) * (N / 16) + (k >> 4);
-}
-
-// Thread roles of the transforms (16 FFTs of length N = 16 R2 per buffer):
-//   radix-16 role (the first 16 M1 threads, M1 = N/16): FFT f = t / M1 and
-//     its positions j + M1 r, r < 16, j = t % M1;
-//   radix-R2 role (all 256 threads): FFT f = t / 16 and its positions
-//     16 b + r... stored as b R2 + r, r < R2, b = t % 16 (after the forward
-//     pass these hold the frequencies k = 16 r + b).
-// Forward transform = radix-16 pass (decimation in frequency, twiddled by
-// W_N^{j r}) then radix-R2 pass; the inverse undoes them in reverse order.
-// The radix-16 role keeps its 16 values in registers between the inverse and
-// the forward transform along x, so the fixed-point update runs on them
-// in place; the frequency k and its mirror N - k sit in lanes b and 16 - b of
-// one half-warp and are paired with shuffles.
-template <int N>
-__global__ void __launch_bounds__(ClShape<N>::THREADS, ClShape<N>::MIN_BLOCKS)
-    k_solve_cluster(ClusterDev P) {
-  using Lay = ClLayout<N>;
-  constexpr int kClRows = ClShape<N>::ROWS, kClF = ClShape<N>::F;
-  constexpr int kClThreads = ClShape<N>::THREADS, ranks = ClShape<N>::RANKS;
-  constexpr int NP = Lay::NP, half = N / 2;
-  constexpr int M1 = N / 16, R2 = N / 16;
-  constexpr int kP16 = kClF * M1;
-  extern __shared__ __align__(16) float2 cl_smem[];
-  __shared__ double red_d[kClThreads / 32];
-  __shared__ float red_f[kClThreads / 32];
-  __shared__ int red_i[kClThreads / 32];
-  const unsigned rank = cl_rank();
-  const int b = __ldg(&P.order[cl_index()]);
-  const MapDesc& d = P.maps[b];   // fields are read where used
-  float2* brow = cl_smem;
-  float2* bcol = cl_smem + Lay::kBcol;
-  float2* Ls = cl_smem + Lay::kLs;
-  float2* twp = cl_smem + Lay::kTwp;
-  float2* tw = cl_smem + Lay::kTdct;
-  ClSlots* slots = reinterpret_cast<ClSlots*>(cl_smem + Lay::kSlots);
-  const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
-  // radix-16 role of the row phase: lanes run along x (coalesced inputs);
-  // the mirror position N - 1 - m sits in lane M1 - 1 - j16 of the group
-  const bool p16 = t < kP16;
-  const int f16 = t / M1, j16 = t % M1;
-  const int partner16 = (lane & ~(M1 - 1)) | (M1 - 1 - j16);
-  // radix-R2 role: warp w holds the frequency digits blk = w and 16 - w
-  // (w = 0: 0 and 8) for all 16 FFTs, one FFT per lane of each half-warp, so
-  // frequency k and N - k are in lanes l and l ^ 16 and the stores to a peer
-  // run along the FFTs (consecutive rows or pairs) in every half-warp
-  const int f2 = lane & 15;
-  const int blk = lane < 16 ? warp : (warp == 0 ? 8 : 16 - warp);
-  const int partner2 = (blk == 0 || blk == 8) ? lane : (lane ^ 16);
-  // radix-16 role of the column phase: warp w < M1/2 holds positions j = w
-  // and M1 - 1 - w for all 16 frequency pairs (lanes), so the two rows of a
-  // row pair are in lanes l and l ^ 16 and the stores run along the pairs
-  const bool c16 = warp < M1 / 2;
-  const int jc = lane & 15;
-  const int j16c = lane < 16 ? warp : M1 - 1 - warp;
-  const int y0 = (int)rank * kClRows;
-  const int j0 = (int)rank * kClF;
-  const float beta = P.beta, alpha = P.alpha;
-  for (int i = t; i < N; i += kClThreads) {
-    const int r = i / M1, j = i % M1;
-    twp[i] = __ldg(&d.tw4n[4 * j * r]);
-    tw[i] = __ldg(&d.tw4n[i]);
-  }
-  __syncthreads();
-
-  auto load16 = [&](const float2* buf, float2* v, int f, int j) {
-#pragma unroll
-    for (int r = 0; r < 16; ++r) v[r] = buf[f * NP + pad(j + r * M1)];
-  };
-  auto store16 = [&](float2* buf, const float2* v, int f, int j) {
-#pragma unroll
-    for (int r = 0; r < 16; ++r) buf[f * NP + pad(j + r * M1)] = v[r];
-  };
-  auto base2 = [&](float2* buf) { return buf + f2 * NP + blk * R2 + ((blk * R2) >> 4); };
-  auto fwd16 = [&](float2* v, int j) {
-    dft16<true>(v);
-    if (M1 > 1) {
-#pragma unroll
-      for (int r = 1; r < 16; ++r) v[r] = cmul(v[r], twp[r * M1 + j]);
-    }
-  };
-  auto inv16 = [&](float2* v, int j) {
-    if (M1 > 1) {
-#pragma unroll
-      for (int r = 1; r < 16; ++r) v[r] = cmulc(v[r], twp[r * M1 + j]);
-    }
-    dft16<false>(v);
-  };
-  auto shfl2 = [&](float2 v, int src) {
-    return make_float2(__shfl_sync(0xffffffffu, v.x, src), __shfl_sync(0xffffffffu, v.y, src));
-  };
-
-  // Row phase. mode 0: initial source from theta_0 = 0 (leakage sum into
-  // pl_sum); 1: initial source from the warm start; 2: iteration (brow holds
-  // the spectra of the column phase, pre-twiddled, at digit-reversed places).
-  auto row_phase = [&](int mode, float mu, float& resid, int& flags, double& pl_sum) {
-    if (mode == 2) {
-      // brow holds the spectra in natural frequency order: the radix-R2 pass
-      // takes frequencies blk + 16 r and leaves its outputs in place
-      float2* p = brow + f2 * NP;
-      float2 w[R2];
-#pragma unroll
-      for (int r = 0; r < R2; ++r) w[r] = p[pad(blk + 16 * r)];
-      dftR<R2, false>(w);
-#pragma unroll
-      for (int r = 0; r < R2; ++r) p[pad(blk + 16 * r)] = w[r];
-      __syncthreads();
-    }
-    float2 v[16];
-    if (p16 && mode == 2) {
-      // radix-16 inputs of this thread: block j16 of the pass above
-#pragma unroll
-      for (int r = 0; r < 16; ++r) v[r] = brow[f16 * NP + pad(16 * j16 + r)];
-    }
-    if (mode == 2) __syncthreads();   // the forward pass below rewrites brow in another order
-    if (p16) {
-      if (mode == 2) inv16(v, j16);   // v[r] = u at Makhoul position j16 + M1 r of rows ya, ya + 1
-      // Positions m (< N/2, x = 2m) of this lane and N - 1 - m (x + 1) of the
-      // mirror lane are updated together, so every input is read as a
-      // coalesced float2 (x, x + 1); u and q of x + 1 travel by shuffle.
-      const size_t row_a = (size_t)(y0 + 2 * f16) * N;
-      auto ld2 = [&](const float* p, size_t idx) { return __ldg(reinterpret_cast<const float2*>(p + idx)); };
-#pragma unroll
-      for (int r0 = 0; r0 < 8; r0 += kClBatch) {
-        float2 pl[kClBatch][2], pd[kClBatch][2], sk[kClBatch][2], old[kClBatch][2];
-#pragma unroll
-        for (int u = 0; u < kClBatch; ++u) {
-          const int x = 2 * (j16 + (r0 + u) * M1);
-#pragma unroll
-          for (int h = 0; h < 2; ++h) {
-            const size_t idx = row_a + (size_t)h * N + x;
-            pl[u][h] = ld2(d.p_leak0, idx);
-            pd[u][h] = ld2(d.p_dyn, idx);
-            sk[u][h] = d.s ? ld2(d.s, idx) : make_float2(1.f, 1.f);
-            old[u][h] = mode == 2 ? *reinterpret_cast<const float2*>(d.theta + idx)
-                        : mode == 1 ? ld2(d.theta_init, idx) : make_float2(0.f, 0.f);
-          }
-        }
-#pragma unroll
-        for (int u = 0; u < kClBatch; ++u) {
-          const int r = r0 + u;
-          const int x = 2 * (j16 + r * M1);
-          const float2 um = shfl2(v[15 - r], partner16);   // u at x + 1 (mirror lane)
-          float qe[2], qo[2];
-#pragma unroll
-          for (int h = 0; h < 2; ++h) {
-            const size_t idx = row_a + (size_t)h * N + x;
-            float th[2];
-#pragma unroll
-            for (int e = 0; e < 2; ++e) {
-              const float PL = e ? pl[u][h].y : pl[u][h].x, PD = e ? pd[u][h].y : pd[u][h].x;
-              const float S = e ? sk[u][h].y : sk[u][h].x, O = e ? old[u][h].y : old[u][h].x;
-              float q;
-              if (mode == 0) {
-                th[e] = 0.f;
-                q = PD + PL;
-                pl_sum += (double)PL;
-              } else if (mode == 1) {
-                // u_0 = theta_0 / (s (1 + alpha theta_0))
-                const float u0 = O / (S * fmaf(alpha, O, 1.f));
-                th[e] = O;
-                q = PD + PL + beta * fmaf(PL, O, -mu * u0);
-              } else {
-                const float uu = e ? (h ? um.y : um.x) : (h ? v[r].y : v[r].x);
-                const float den = fmaf(-alpha * S, uu, 1.f);
-                if (!(den > 0.05f)) flags |= kFlagRunaway;
-                th[e] = S * uu / den;
-                if (!isfinite(th[e])) flags |= kFlagNonfinite;
-                else resid = fmaxf(resid, fabsf(th[e] - O));
-                q = PD + PL + beta * fmaf(PL, th[e], -mu * uu);
-              }
-              (e ? qo : qe)[h] = q;
-            }
-            *reinterpret_cast<float2*>(d.theta + idx) = make_float2(th[0], th[1]);
-          }
-          v[r] = make_float2(qe[0], qe[1]);
-          v[15 - r] = shfl2(make_float2(qo[0], qo[1]), partner16);
-        }
-      }
-      fwd16(v, j16);
-      store16(brow, v, f16, j16);
-    }
-    // per-warp partials of the residual, flags and leakage sum
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-      resid = fmaxf(resid, __shfl_down_sync(0xffffffffu, resid, o));
-      flags |= __shfl_down_sync(0xffffffffu, flags, o);
-      pl_sum += __shfl_down_sync(0xffffffffu, pl_sum, o);
-    }
-    if (lane == 0) {
-      red_f[warp] = resid;
-      red_i[warp] = flags;
-      red_d[warp] = pl_sum;
-    }
-    __syncthreads();
-    // radix-R2 pass: Z[k], k = 16 r + blk; pair with N - k from the partner
-    // lane, DCT-II post-twiddle, store into the column owner
-    float2 z[R2];
-    {
-      const float2* p = base2(brow);
-#pragma unroll
-      for (int r = 0; r < R2; ++r) z[r] = p[r];
-    }
-    dftR<R2, true>(z);
-    // lanes 0-15 of a half-warp hold 16 consecutive row pairs of one pair k:
-    // each store below is one contiguous run in the owner's column buffer
-    const unsigned oe = (unsigned)pad(y0 / 2 + f2) * 8u, oo = (unsigned)pad(N - 1 - y0 / 2 - f2) * 8u;
-#pragma unroll
-    for (int r = 0; r < R2 / 2; ++r) {
-      // what the partner needs at its index r: Z[N - k'] for its k' = 16 r + (16 - blk)
-      const float2 give = blk == 0 ? z[r == 0 ? R2 / 2 : R2 - r] : z[R2 - 1 - r];
-      const float2 zn = shfl2(give, partner2);
-      const int k = 16 * r + blk;
-      float2 ea, eb;
-      if (k == 0) {
-        const float2 x0 = dct_post(z[0], z[0], tw[0]), xh = dct_post(zn, zn, tw[half]);
-        ea = make_float2(x0.x, xh.x);
-        eb = make_float2(x0.y, xh.y);
-      } else {
-        const float2 xk = dct_post(z[r], zn, tw[k]), xn = dct_post(zn, z[r], tw[N - k]);
-        ea = make_float2(xk.x, xn.x);
-        eb = make_float2(xk.y, xn.y);
-      }
-      const unsigned dst = cl_map(bcol, (unsigned)r) + (unsigned)(blk * NP) * 8u;   // owner k / 16 = r
-      cl_put(dst + oe, ea);
-      cl_put(dst + oo, eb);
-    }
-  };
-
-  // Column phase: bcol holds, for this CTA's frequency pairs, the x-spectra
-  // of all rows at the Makhoul positions of y.
-  auto col_phase = [&]() {
-    if (c16) {
-      float2 v[16];
-      load16(bcol, v, jc, j16c);
-      fwd16(v, j16c);
-      store16(bcol, v, jc, j16c);
-    }
-    __syncthreads();
-    {
-      float2* p = base2(bcol);
-      float2 z[R2], e[R2];
-#pragma unroll
-      for (int r = 0; r < R2; ++r) z[r] = p[r];
-      dftR<R2, true>(z);
-      const int jj = f2;
-#pragma unroll
-      for (int r = 0; r < R2; ++r) {
-        const float2 give = blk == 0 ? z[(R2 - r) % R2] : z[R2 - 1 - r];
-        const float2 zn = shfl2(give, partner2);   // Z[N - q]
-        const int q = 16 * r + blk, qn = N - q;
-        const float2 L = Ls[q * kClF + (jj ^ (q & (kClF - 1)))];
-        float2 y = dct_post(z[r], zn, tw[q]);
-        y.x *= L.x;
-        y.y *= L.y;
-        float2 yn;
-        if (q == 0) {
-          yn = make_float2(0.f, 0.f);
-        } else if (q == half) {
-          yn = y;
-        } else {
-          const float2 Ln = Ls[qn * kClF + (jj ^ (qn & (kClF - 1)))];
-          yn = dct_post(zn, z[r], tw[qn]);
-          yn.x *= Ln.x;
-          yn.y *= Ln.y;
-        }
-        e[r] = dct_pre(y.x, yn.x, y.y, yn.y, tw[q]);
-      }
-      dftR<R2, false>(e);
-#pragma unroll
-      for (int r = 0; r < R2; ++r) p[r] = e[r];
-    }
-    __syncthreads();
-    if (c16) {
-      float2 v[16];
-      load16(bcol, v, jc, j16c);
-      inv16(v, j16c);   // v[r] = column data at Makhoul position j16c + M1 r of y
-      const int j = j0 + jc;
-      const int pa = j, pb = j == 0 ? half : N - j;
-      const float2 twa = tw[pa], twb = tw[pb];
-      const unsigned ra = (unsigned)pad(pa) * 8u, rb = (unsigned)pad(pb) * 8u;
-      // the rows ya = 2 m (m = j16c + M1 r < N/2) and ya + 1 (position
-      // N - 1 - m, lane ^ 16); lanes 0-15 hold 16 consecutive pairs, whose
-      // values land on consecutive natural-order frequencies of the owner
-#pragma unroll
-      for (int r = 0; r < 8; ++r) {
-        const float2 vb = shfl2(v[15 - r], lane ^ 16);
-        const float2 va = v[r];
-        float2 ea, eb;
-        if (j == 0) {
-          ea = dct_pre(va.x, 0.f, vb.x, 0.f, twa);
-          eb = dct_pre(va.y, va.y, vb.y, vb.y, twb);
-        } else {
-          ea = dct_pre(va.x, va.y, vb.x, vb.y, twa);
-          eb = dct_pre(va.y, va.x, vb.y, vb.x, twb);
-        }
-        const int ya = 2 * (j16c + r * M1);
-        const unsigned dst = cl_map(brow, (unsigned)(ya / kClRows)) +
-                             (unsigned)(((ya % kClRows) >> 1) * NP) * 8u;
-        cl_put(dst + ra, ea);
-        cl_put(dst + rb, eb);
-      }
-    }
-  };
-
-  auto put_slots = [&](bool part) {
-    if (t == 0) {
-      float rm = 0.f;
-      int fo = 0;
-      double ps = 0.0;
-      for (int w = 0; w < kClThreads / 32; ++w) {
-        rm = fmaxf(rm, red_f[w]);
-        fo |= red_i[w];
-        ps += red_d[w];
-      }
-      for (int r = 0; r < ranks; ++r) {
-        if (part) {
-          cl_put(cl_map(&slots->part[rank], (unsigned)r), ps);
-        } else {
-          cl_put(cl_map(&slots->resid[rank], (unsigned)r), rm);
-          cl_put(cl_map(&slots->flags[rank], (unsigned)r), fo);
-        }
-      }
-    }
-  };
-  auto cluster_mu = [&]() {
-    double sum = 0.0;
-    for (int r = 0; r < ranks; ++r) sum += slots->part[r];
-    return sum / ((double)N * N);
-  };
-
-  int status = VS_OK, iters = 0, growth = 0;
-  float prev = INFINITY;
-  double mu = 0.0;
-  bool stop = false;
-  cl_arrive_relaxed();  // peers store into this CTA only after every CTA started
-
-  // initial source (Eq. 13 at theta_0) and the mean leakage mu (Sec. IV-C)
-  if (d.theta_init) {
-    double acc = 0.0;
-    for (int i = t; i < kClRows * N; i += kClThreads)
-      acc += (double)__ldg(&d.p_leak0[(size_t)y0 * N + i]);
-    const double tot = block_sum(acc, red_d);
-    cl_wait();
-    if (t == 0)
-      for (int r = 0; r < ranks; ++r) cl_put(cl_map(&slots->part[rank], (unsigned)r), tot);
-    cl_sync();
-    mu = cluster_mu();
-    if ((double)beta * mu * (double)d.kmax >= 0.999) {
-      status = VS_ERR_RUNAWAY;
-      stop = true;
-    } else {
-      float r0 = 0.f;
-      int f0 = 0;
-      double unused = 0.0;
-      // the peers' start is already established by the barrier above
-      row_phase(1, (float)mu, r0, f0, unused);
-      cl_sync();
-    }
-  } else {
-    float r0 = 0.f;
-    int f0 = 0;
-    double acc = 0.0;
-    cl_wait();
-    row_phase(0, 0.f, r0, f0, acc);
-    put_slots(true);
-    cl_sync();
-    mu = cluster_mu();
-    if ((double)beta * mu * (double)d.kmax >= 0.999) {
-      status = VS_ERR_RUNAWAY;
-      stop = true;
-    }
-  }
-
-  if (!stop) {
-    const float mu_f = (float)mu;
-    {
-      // spectral multiplier of this CTA's frequency pairs, with the 1 / N^2
-      // of the two unnormalised inverse transforms folded in
-      const float bm = beta * mu_f;
-      const float inv_n2 = 1.f / ((float)N * (float)N);
-      for (int it = t; it < kClF * N; it += kClThreads) {
-        const int q = it % N, jj = it / N, j = j0 + jj;
-        const int pa = j == 0 ? 0 : j, pb = j == 0 ? half : N - j;
-        const float ka = __ldg(&d.Kt[(size_t)pa * N + q]), kb = __ldg(&d.Kt[(size_t)pb * N + q]);
-        Ls[q * kClF + (jj ^ (q & (kClF - 1)))] =
-            make_float2(ka / (1.f - bm * ka) * inv_n2, kb / (1.f - bm * kb) * inv_n2);
-      }
-      __syncthreads();
-    }
-    for (int it = 1; it <= P.max_iter; ++it) {
-      col_phase();
-      cl_sync();
-      float resid = 0.f;
-      int flags = 0;
-      double unused = 0.0;
-      row_phase(2, mu_f, resid, flags, unused);
-      put_slots(false);
-      cl_sync();
-      // the same decision in every thread of every CTA of the cluster
-      float rr = 0.f;
-      int ff = 0;
-      for (int r = 0; r < ranks; ++r) {
-        rr = fmaxf(rr, slots->resid[r]);
-        ff |= slots->flags[r];
-      }
-      iters = it;
-      if (ff & kFlagNonfinite) {
-        status = VS_ERR_NONFINITE;
-        stop = true;
-      } else if (ff & kFlagRunaway) {
-        status = VS_ERR_RUNAWAY;
-        stop = true;
-      } else if (rr <= P.tol) {
-        status = VS_OK;
-        stop = true;
-      } else {
-        growth = (it > 2 && rr > prev) ? growth + 1 : 0;
-        if (it >= P.max_iter || growth >= 5) {
-          status = VS_ERR_NO_CONVERGENCE;
-          stop = true;
-        }
-      }
-      prev = rr;
-      if (stop) break;
-    }
-  }
-  if (rank == 0 && t == 0) {
-    vs_solve_info* inf = P.info + b;
-    inf->status = status;
-    inf->iterations = iters;
-    inf->residual_K = (double)prev;
-    inf->mu_W = mu;
   }
 }
 
@@ -1837,31 +1248,6 @@ int plan_layout(vs_plan_t* p, int elems, cudaStream_t s, bool transient, int n_s
   return VS_OK;
 }
 
-bool cluster_size_ok(int n) { return n >= 32 && n <= kClMaxN; }
-
-struct ClHost {
-  int ranks, threads;
-  size_t smem;
-};
-ClHost cluster_shape(int n) {
-  switch (n) {
-    case 32: return {ClShape<32>::RANKS, ClShape<32>::THREADS, ClLayout<32>::kBytes};
-    case 64: return {ClShape<64>::RANKS, ClShape<64>::THREADS, ClLayout<64>::kBytes};
-    case 128: return {ClShape<128>::RANKS, ClShape<128>::THREADS, ClLayout<128>::kBytes};
-    default: return {ClShape<256>::RANKS, ClShape<256>::THREADS, ClLayout<256>::kBytes};
-  }
-}
-
-using ClusterFn = void (*)(ClusterDev);
-ClusterFn cluster_kernel(int n) {
-  switch (n) {
-    case 32: return k_solve_cluster<32>;
-    case 64: return k_solve_cluster<64>;
-    case 128: return k_solve_cluster<128>;
-    default: return k_solve_cluster<256>;
-  }
-}
-
 size_t g_smem_attr_cluster[4] = {0, 0, 0, 0};  // per instantiation, n = 32 .. 256
 
 cudaLaunchConfig_t cluster_config(int n, int count, cudaStream_t s, cudaLaunchAttribute* attr) {
@@ -1893,7 +1279,7 @@ int plan_layout_cluster(vs_plan_t* p, cudaStream_t s) {
   for (auto& g : by_n) {
     p->cl_groups.push_back({g.first, (int)g.second.size()});
     order.insert(order.end(), g.second.begin(), g.second.end());
-    smem = std::max(smem, cl_smem_bytes(g.first));
+    smem = std::max(smem, cluster_shape(g.first).smem);
   }
   std::vector<MapDesc> maps(n_items);
   for (int i = 0; i < n_items; ++i) {
@@ -1930,9 +1316,9 @@ int plan_layout_cluster(vs_plan_t* p, cudaStream_t s) {
       size_t& cur = g_smem_attr_cluster[__builtin_ctz((unsigned)g.first) - 5];
       if (cur == 0) {
         VS_CUDA_TRY(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)cl_smem_bytes(g.first)));
+                                         (int)cluster_shape(g.first).smem));
         VS_CUDA_TRY(cudaFuncSetAttribute(fn, cudaFuncAttributePreferredSharedMemoryCarveout, 100));
-        cur = cl_smem_bytes(g.first);
+        cur = cluster_shape(g.first).smem;
       }
     }
     cudaLaunchAttribute attr[1];
@@ -1946,7 +1332,7 @@ int plan_layout_cluster(vs_plan_t* p, cudaStream_t s) {
       cudaFuncAttributes fa;
       cudaFuncGetAttributes(&fa, fn);
       fprintf(stderr, "varsim plan: cluster n=%d maps=%d ranks=%d smem=%zu regs=%d local=%zu "
-              "active_clusters=%d\n", g.first, g.second, cluster_shape(g.first).ranks, cl_smem_bytes(g.first),
+              "active_clusters=%d\n", g.first, g.second, cluster_shape(g.first).ranks, cluster_shape(g.first).smem,
               fa.numRegs, fa.localSizeBytes, clusters);
     }
   }
