@@ -94,7 +94,8 @@ typedef struct {
 #define VS_PREC_BF16_SPLIT 1  /* cosine transforms as tcgen05 tensor-core GEMMs in
                                  BF16 hi/lo split precision with FP32 accumulation
                                  (x = hi + lo, products hi*hi + hi*lo + lo*hi);
-                                 batched plans with n = 128 or 256 */
+                                 n = 128 .. 1024 (power of two); outputs are
+                                 produced in chunks of 256 columns */
 
 /* Execution engines of the FP32 steady solve (identical arithmetic, different
  * data movement).
@@ -345,7 +346,8 @@ int vs_warm_apply(const float* theta1, const float* y, int count, int n, int res
  * (forward DCT-II of Sec. IV-F's mirror-imaged rows) or, with inverse != 0,
  *   out[r][j] = sum_k in[r][k] w_k cos(pi k (2j+1) / 2n) / n, w_0 = 1, w_k = 2
  * (its exact inverse). in/out: device float32 [rows][n], rows a multiple of
- * 128, n = 128 or 256, 16-byte aligned. Asynchronous on `stream`. */
+ * 128, n a power of two in [128, 1024], 16-byte aligned. Asynchronous on
+ * `stream`. */
 int vs_tc_transform(const float* in, float* out, int rows, int n, int inverse, void* stream);
 
 /* ------------------------------------------------------------------------ */

@@ -515,9 +515,11 @@ __global__ void k_twiddles(int n, float2* tw) {
 
 // ------------------------------------------------------------ tensor-core path
 // Split-precision cosine transforms on tcgen05 (BF16 hi/lo, FP32 accumulate).
-// One 1-D transform of 128 rows of a map is a GEMM D[128][N] = A[128][K] B^T
-// with K = N = n: A = map data (split x = hi + lo on the fly), B = the DCT
-// matrix (hi/lo pre-split, pre-tiled in core-matrix order). Three MMAs per
+// One 1-D transform of 128 rows of a map is a GEMM D[128][n] = A[128][n] B^T:
+// A = map data (split x = hi + lo on the fly), B = the DCT matrix (hi/lo
+// pre-split, pre-tiled in core-matrix order). The output columns are produced
+// in chunks of N = min(n, 256) (one TMEM accumulator of 128 lanes x N FP32
+// columns), each with the full K = n loop. Three MMAs per
 // K-step: A_hi B_hi + A_hi B_lo + A_lo B_hi (the lo*lo term, ~2^-16 relative,
 // is dropped). Per iteration four passes (rows fwd, columns fwd, columns inv,
 // rows inv) with the spectral multiply and the leakage/conductivity update in
@@ -608,10 +610,11 @@ __device__ __forceinline__ void tc_store(uint8_t* st, const float4* v) {
   }
 }
 
-// One 128-row GEMM into TMEM columns [0, N). Returns false on a wait timeout.
-__device__ bool tc_gemm(TcCtx& c, int N, const uint8_t* Bg, const float* G, int ld, int row0,
-                        const float* G2) {
-  const int nk = N / kTcChunkK;
+// One 128-row GEMM over K = `K` into TMEM columns [0, N) (N <= 256); Bg is the
+// pre-tiled B of this output chunk. Returns false on a wait timeout.
+__device__ bool tc_gemm(TcCtx& c, int K, int N, const uint8_t* Bg, const float* G, int ld,
+                        int row0, const float* G2) {
+  const int nk = K / kTcChunkK;
   const uint32_t idesc = vstc::idesc_bf16(128, N);
   const uint32_t bbytes = (uint32_t)N * kTcChunkK * 2;     // one of hi / lo
   float4 vnext[kTcPer];
@@ -758,53 +761,64 @@ __device__ bool tc_task(const PlanDev& P, TcCtx& c, int pass, int task) {
     __syncthreads();
     return true;
   }
-  if (pass == kTcRowFwdFirst || pass == kTcRowFwd) {
-    // rows forward: A[y][x] = q (first: P_dyn + P_leak0), B = C -> R[y][p], stored as RT[p][y]
-    if (first) ok = tc_gemm(c, n, d.tcf, d.p_dyn, n, r0, d.p_leak0);
-    else ok = tc_gemm(c, n, d.tcf, d.work2, n, r0, nullptr);
-    tc_epilogue(c, n, [&](int m, int c0, float* v) { store32_t(d.work, n, c0, r0 + m, v); });
-    if (first) {
-      // theta_0 = 0 and the partial sum of P_leak0 over the tile (coalesced)
-      for (int i = threadIdx.x; i < 128 * n / 4; i += blockDim.x) {
-        size_t idx = (size_t)r0 * n + 4 * (size_t)i;
-        *reinterpret_cast<float4*>(d.theta + idx) = make_float4(0.f, 0.f, 0.f, 0.f);
-        float4 w4 = __ldg(reinterpret_cast<const float4*>(d.p_leak0 + idx));
-        mu_acc += (double)w4.x + (double)w4.y + (double)w4.z + (double)w4.w;
-      }
+  // output chunks of NB columns; B of chunk nc starts nc * bstride bytes in
+  const int NB = n < 256 ? n : 256;
+  const size_t bstride = (size_t)(n / kTcChunkK) * 2 * NB * kTcChunkK * 2;
+  float* scratch = reinterpret_cast<float*>(c.sm->stage[0]);
+  for (int nc = 0; nc < n / NB && ok; ++nc) {
+    const int n0 = nc * NB;
+    if (nc > 0) {
+      // TMEM and the stage-0 epilogue scratch are reused by the next chunk
+      vstc::fence_proxy_async_smem();
+      vstc::tc_fence_before();
+      __syncthreads();
     }
-  } else if (pass == kTcColFwd) {
-    // columns forward: A[p][y] = RT, B = C -> X[p][q]; x K/(1-beta mu K) -> Y[p][q]
-    ok = tc_gemm(c, n, d.tcf, d.work, n, r0, nullptr);
-    const float bm = P.beta * ms->mu_f;
-    float* scratch = reinterpret_cast<float*>(c.sm->stage[0]);
-    tc_epilogue_rows(c, n, scratch, [&](int m, int col, float val) {
-      size_t idx = (size_t)(r0 + m) * n + col;
-      float k = __ldg(&d.Kt[idx]);
-      d.work2[idx] = val * k / (1.f - bm * k);
-    });
-  } else if (pass == kTcColInv) {
-    // columns inverse: A[p][q] = Y, B = Ci -> ZT[p][y], stored as Z[y][p]
-    ok = tc_gemm(c, n, d.tci, d.work2, n, r0, nullptr);
-    tc_epilogue(c, n, [&](int m, int c0, float* v) { store32_t(d.work, n, c0, r0 + m, v); });
-  } else {
-    // rows inverse: A[y][p] = Z, B = Ci -> u[y][x]; fused update -> q[y][x]
-    ok = tc_gemm(c, n, d.tci, d.work, n, r0, nullptr);
-    const float beta = P.beta, alpha = P.alpha, mu = ms->mu_f;
-    float* scratch = reinterpret_cast<float*>(c.sm->stage[0]);
-    tc_epilogue_rows(c, n, scratch, [&](int m, int col, float u) {
-      size_t idx = (size_t)(r0 + m) * n + col;
-      float pd = __ldg(&d.p_dyn[idx]);
-      float pl = __ldg(&d.p_leak0[idx]);
-      float sk = d.s ? __ldg(&d.s[idx]) : 1.f;
-      float old = d.theta[idx];
-      float den = fmaf(-alpha * sk, u, 1.f);
-      if (!(den > 0.05f)) flags |= kFlagRunaway;
-      float th = sk * u / den;
-      if (!isfinite(th)) flags |= kFlagNonfinite;
-      else resid = fmaxf(resid, fabsf(th - old));
-      d.theta[idx] = th;
-      d.work2[idx] = pd + pl + beta * fmaf(pl, th, -mu * u);
-    });
+    if (pass == kTcRowFwdFirst || pass == kTcRowFwd) {
+      // rows forward: A[y][x] = q (first: P_dyn + P_leak0), B = C -> R[y][p], stored as RT[p][y]
+      if (first) ok = tc_gemm(c, n, NB, d.tcf + nc * bstride, d.p_dyn, n, r0, d.p_leak0);
+      else ok = tc_gemm(c, n, NB, d.tcf + nc * bstride, d.work2, n, r0, nullptr);
+      tc_epilogue(c, NB, [&](int m, int c0, float* v) { store32_t(d.work, n, n0 + c0, r0 + m, v); });
+    } else if (pass == kTcColFwd) {
+      // columns forward: A[p][y] = RT, B = C -> X[p][q]; x K/(1-beta mu K) -> Y[p][q]
+      ok = tc_gemm(c, n, NB, d.tcf + nc * bstride, d.work, n, r0, nullptr);
+      const float bm = P.beta * ms->mu_f;
+      tc_epilogue_rows(c, NB, scratch, [&](int m, int col, float val) {
+        size_t idx = (size_t)(r0 + m) * n + n0 + col;
+        float k = __ldg(&d.Kt[idx]);
+        d.work2[idx] = val * k / (1.f - bm * k);
+      });
+    } else if (pass == kTcColInv) {
+      // columns inverse: A[p][q] = Y, B = Ci -> ZT[p][y], stored as Z[y][p]
+      ok = tc_gemm(c, n, NB, d.tci + nc * bstride, d.work2, n, r0, nullptr);
+      tc_epilogue(c, NB, [&](int m, int c0, float* v) { store32_t(d.work, n, n0 + c0, r0 + m, v); });
+    } else {
+      // rows inverse: A[y][p] = Z, B = Ci -> u[y][x]; fused update -> q[y][x]
+      ok = tc_gemm(c, n, NB, d.tci + nc * bstride, d.work, n, r0, nullptr);
+      const float beta = P.beta, alpha = P.alpha, mu = ms->mu_f;
+      tc_epilogue_rows(c, NB, scratch, [&](int m, int col, float u) {
+        size_t idx = (size_t)(r0 + m) * n + n0 + col;
+        float pd = __ldg(&d.p_dyn[idx]);
+        float pl = __ldg(&d.p_leak0[idx]);
+        float sk = d.s ? __ldg(&d.s[idx]) : 1.f;
+        float old = d.theta[idx];
+        float den = fmaf(-alpha * sk, u, 1.f);
+        if (!(den > 0.05f)) flags |= kFlagRunaway;
+        float th = sk * u / den;
+        if (!isfinite(th)) flags |= kFlagNonfinite;
+        else resid = fmaxf(resid, fabsf(th - old));
+        d.theta[idx] = th;
+        d.work2[idx] = pd + pl + beta * fmaf(pl, th, -mu * u);
+      });
+    }
+  }
+  if (first) {
+    // theta_0 = 0 and the partial sum of P_leak0 over the tile (coalesced)
+    for (int i = threadIdx.x; i < 128 * n / 4; i += blockDim.x) {
+      size_t idx = (size_t)r0 * n + 4 * (size_t)i;
+      *reinterpret_cast<float4*>(d.theta + idx) = make_float4(0.f, 0.f, 0.f, 0.f);
+      float4 w4 = __ldg(reinterpret_cast<const float4*>(d.p_leak0 + idx));
+      mu_acc += (double)w4.x + (double)w4.y + (double)w4.z + (double)w4.w;
+    }
   }
   // the epilogue scratch (stage 0) is refilled by the async proxy next
   vstc::fence_proxy_async_smem();
@@ -922,11 +936,19 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_tc_transform(const float* in,
   c.uses[0] = c.uses[1] = 0;
   c.chunk = 0;
   c.fin_uses = 0;
-  for (int t = blockIdx.x; t < rows / 128; t += gridDim.x) {
-    if (!tc_gemm(c, n, Bg, in, n, t * 128, nullptr)) break;
-    tc_epilogue(c, n, [&](int m, int c0, float* v) { store32(out + (size_t)(t * 128 + m) * n + c0, v); });
-    vstc::tc_fence_before();
-    __syncthreads();
+  const int NB = n < 256 ? n : 256;
+  const size_t bstride = (size_t)(n / kTcChunkK) * 2 * NB * kTcChunkK * 2;
+  bool ok = true;
+  for (int t = blockIdx.x; t < rows / 128 && ok; t += gridDim.x) {
+    for (int nc = 0; nc < n / NB && ok; ++nc) {
+      ok = tc_gemm(c, n, NB, Bg + nc * bstride, in, n, t * 128, nullptr);
+      if (!ok) break;
+      tc_epilogue(c, NB, [&](int m, int c0, float* v) {
+        store32(out + (size_t)(t * 128 + m) * n + nc * NB + c0, v);
+      });
+      vstc::tc_fence_before();
+      __syncthreads();
+    }
   }
   tc_finish(c);
 }
@@ -979,20 +1001,22 @@ struct TcMats {
 std::mutex g_tc_mutex;
 std::map<std::pair<int, int>, TcMats> g_tc;
 
-// Layout per K-chunk of 64: [hi: n x 64 core-matrix order][lo: same].
+// Layout: for each output chunk of NB = min(n, 256) rows j and each K-chunk of
+// 64 columns k: [hi: NB x 64 in core-matrix order][lo: same].
 std::vector<uint8_t> tile_matrix(int n, bool inverse) {
   const double pi = 3.141592653589793238462643383279502884;
   const int nk = n / kTcChunkK;
-  const size_t half = (size_t)n * kTcChunkK * 2;
-  std::vector<uint8_t> out((size_t)nk * 2 * half, 0);
+  const int NB = n < 256 ? n : 256;
+  const size_t half = (size_t)NB * kTcChunkK * 2;
+  std::vector<uint8_t> out((size_t)(n / NB) * nk * 2 * half, 0);
   for (int j = 0; j < n; ++j)
     for (int k = 0; k < n; ++k) {
       double v = inverse ? (k == 0 ? 1.0 : 2.0) * cos(pi * k * (2.0 * j + 1.0) / (2.0 * n)) / n
                          : cos(pi * j * (2.0 * k + 1.0) / (2.0 * n));
       uint16_t hi = host_bf16(v);
       uint16_t lo = host_bf16(v - host_bf16_val(hi));
-      int kc = k / kTcChunkK;
-      size_t off = (size_t)kc * 2 * half + vstc::core_off(j, k % kTcChunkK, kTcChunkK);
+      int kc = k / kTcChunkK, nc = j / NB;
+      size_t off = ((size_t)nc * nk + kc) * 2 * half + vstc::core_off(j % NB, k % kTcChunkK, kTcChunkK);
       memcpy(&out[off], &hi, 2);
       memcpy(&out[off + half], &lo, 2);
     }
@@ -1023,7 +1047,7 @@ const TcMats* get_tc_mats(int n, int* status) {
   return &g_tc[key];
 }
 
-bool tc_size_ok(int n) { return n == 128 || n == 256; }
+bool tc_size_ok(int n) { return n >= 128 && n <= 1024; }   // n is a power of two
 constexpr size_t kTcSmemBytes = sizeof(TcSmem) + 1024;
 
 struct TaskShape {
@@ -1447,7 +1471,7 @@ extern "C" int vs_plan_create(const vs_batch_item* items_host, int n_items,
     if (al & 15u) return vs_set_error(VS_ERR_INVALID_ARG, "item %d: maps must be 16-byte aligned", i);
     if (params->precision == VS_PREC_BF16_SPLIT && !tc_size_ok(it.k->n))
       return vs_set_error(VS_ERR_INVALID_ARG,
-                          "item %d: the BF16 split tensor-core path supports n = 128 or 256 (got %d)",
+                          "item %d: the BF16 split tensor-core path supports n = 128 .. 1024 (got %d)",
                           i, it.k->n);
   }
   bool cluster_ok = params->precision == VS_PREC_FP32;
@@ -1786,7 +1810,8 @@ extern "C" int vs_solve_steady_noalloc(vs_kernel k, const float* p_dyn, const fl
 extern "C" int vs_tc_transform(const float* in, float* out, int rows, int n, int inverse,
                                void* stream) {
   if (!in || !out) return vs_set_error(VS_ERR_INVALID_ARG, "NULL array");
-  if (!tc_size_ok(n)) return vs_set_error(VS_ERR_INVALID_ARG, "n must be 128 or 256 (got %d)", n);
+  if (!tc_size_ok(n) || (n & (n - 1)))
+    return vs_set_error(VS_ERR_INVALID_ARG, "n must be a power of two in [128, 1024] (got %d)", n);
   if (rows <= 0 || rows % 128) return vs_set_error(VS_ERR_INVALID_ARG, "rows must be a positive multiple of 128");
   if (((uintptr_t)in | (uintptr_t)out) & 15u) return vs_set_error(VS_ERR_INVALID_ARG, "arrays must be 16-byte aligned");
   int st = VS_OK;

@@ -32,7 +32,7 @@ def _dct(n, inverse):
     return w[None, :] * torch.cos(math.pi * k[None, :] * (2 * j[:, None] + 1) / (2 * n)) / n
 
 
-@pytest.mark.parametrize("n,rows", [(256, 256), (128, 384), (256, 1024)])
+@pytest.mark.parametrize("n,rows", [(256, 256), (128, 384), (256, 1024), (512, 256), (1024, 128)])
 @pytest.mark.parametrize("inverse", [False, True])
 def test_tc_transform_matches_fp64_matmul(n, rows, inverse):
     import paper_2307_12119_gb300 as vs
@@ -53,18 +53,21 @@ def test_tc_round_trip():
     assert float((back - x).abs().max()) <= 2e-4
 
 
-@pytest.mark.parametrize("name", ["c2_256", "c3_128"])
-def test_tc_solve_matches_oracle(name):
+@pytest.mark.parametrize("name,count", [("c2_256", 3), ("c3_128", 3), ("c3_512", 2),
+                                        ("c4_1024", 1)])
+def test_tc_solve_matches_oracle(name, count):
+    # the 1024^2 case is the split-precision steady solve of the 1024^2
+    # workload (its transient runs on the FP32 engine, tests/test_gpu_configs.py)
     import paper_2307_12119_gb300 as vs
     w = synth.workload(name)
     k = vs.Kernel(vs_stack(w), vs.Grid(w.n, w.die_m))
-    pd, pl, s = inputs(w, count=3)
+    pd, pl, s = inputs(w, count=count)
     th = torch.empty_like(pd)
     prm = vs_params(w, tol_K=TC_TOL_K, precision=vs.VS_PREC_BF16_SPLIT)
-    infos = vs.solve_batch([(k, pd[i], pl[i], s[i], th[i]) for i in range(3)], prm)
+    infos = vs.solve_batch([(k, pd[i], pl[i], s[i], th[i]) for i in range(count)], prm)
     assert all(i["status"] == vs.VS_OK for i in infos), infos
     Kt = oracle_spectrum(w)
-    for i in range(3):
+    for i in range(count):
         ref, _ = oracle_steady(w, Kt, pd[i], pl[i], s[i])
         emax, rel = errors(th[i], ref)
         assert emax <= REQ_MAX_K, (i, emax)
@@ -87,7 +90,7 @@ def test_tc_batch_agrees_with_fp32_path():
 
 def test_tc_rejects_unsupported_sizes():
     import paper_2307_12119_gb300 as vs
-    w = synth.workload("c3_512")
+    w = synth.workload("c1_64")                   # below the 128-row tile
     k = vs.Kernel(vs_stack(w), vs.Grid(w.n, w.die_m))
     pd, pl, s = inputs(w)
     th = torch.empty_like(pd[0])
@@ -95,3 +98,5 @@ def test_tc_rejects_unsupported_sizes():
         vs.solve_batch([(k, pd[0], pl[0], s[0], th)],
                        vs_params(w, precision=vs.VS_PREC_BF16_SPLIT))
     assert e.value.status == vs.VS_ERR_INVALID_ARG
+    with pytest.raises(vs.VarsimError):
+        vs.tc_transform(torch.zeros(128, 64, device="cuda"))
