@@ -273,6 +273,24 @@ int vs_solve_batch(const vs_batch_item* items_host, int n_items,
                    const vs_solve_params* params, vs_solve_info* info_host,
                    void* stream);
 
+/* Batched steady solve from and to HOST memory (the paper has no counterpart;
+ * the solve itself is that of vs_solve_batch, Eqs. 13-26). count maps of
+ * grid k->n: p_dyn, p_leak0, s_kappa (NULL => 1) and theta are host arrays
+ * [count][n][n]. The maps go through the GPU in chunks of chunk_maps maps
+ * (0 => a sixteenth of the batch, at most about 1 GiB of device buffers per
+ * chunk): the host-to-device copies of
+ * the next chunk and the device-to-host copy of the previous one overlap the
+ * solve of the current one (internal streams and events, two device buffer
+ * slots). The overlap needs page-locked host memory (cudaHostAlloc, or
+ * torch's pin_memory); pageable arrays work but serialise the copies. Every
+ * map gets exactly the result vs_solve_batch gives it. Ordered after work
+ * already queued on `stream`; returns when theta (and info_host, count entries,
+ * if not NULL) are complete in host memory. Allocates its device buffers per
+ * call. Returns the worst per-map status. */
+int vs_solve_batch_host(vs_kernel k, int count, const float* p_dyn, const float* p_leak0,
+                        const float* s_kappa, float* theta, const vs_solve_params* params,
+                        vs_solve_info* info_host, int chunk_maps, void* stream);
+
 /* ------------------------------------------------------------------------ */
 /* Transient (Sec. IV-D/E, Eqs. 27-37).                                     */
 /* ------------------------------------------------------------------------ */

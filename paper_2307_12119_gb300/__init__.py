@@ -20,7 +20,8 @@ __all__ = [
     "VS_OK", "VS_ERR_INVALID_ARG", "VS_ERR_CUDA", "VS_ERR_OOM", "VS_ERR_NO_CONVERGENCE",
     "VS_ERR_RUNAWAY", "VS_ERR_NONFINITE", "VS_ERR_TIMEOUT", "VarsimError", "Stack", "Grid",
     "KernelOpts", "SolveParams", "Kernel", "Plan", "lib", "lib_path", "solve_steady",
-    "solve_batch", "solve_transient", "hankel_radial", "EXPORTS", "solve_steady_noalloc",
+    "solve_batch", "solve_batch_host", "solve_transient", "hankel_radial", "EXPORTS",
+    "solve_steady_noalloc",
     "tc_transform", "VS_PREC_FP32", "VS_PREC_BF16_SPLIT", "VS_ENGINE_AUTO",
     "VS_ENGINE_STREAMED", "VS_ENGINE_CLUSTER", "Model", "WarmPlan",
     "warm_features", "warm_target", "warm_apply",
@@ -40,7 +41,7 @@ EXPORTS = [
     "vs_tc_transform", "vs_model_create", "vs_free_model", "vs_model_nparams",
     "vs_model_get_params", "vs_model_set_params", "vs_model_forward", "vs_model_loss_grad",
     "vs_model_train", "vs_model_save", "vs_model_load", "vs_warm_features", "vs_warm_target",
-    "vs_warm_apply",
+    "vs_warm_apply", "vs_solve_batch_host",
 ]
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
@@ -119,6 +120,8 @@ def lib():
         "vs_plan_free": (None, [vp]),
         "vs_solve_batch": (ip, [C.POINTER(_BatchItem), ip, C.POINTER(_SolveParams),
                                 C.POINTER(_SolveInfo), vp]),
+        "vs_solve_batch_host": (ip, [vp, ip, vp, vp, vp, vp, C.POINTER(_SolveParams),
+                                     C.POINTER(_SolveInfo), ip, vp]),
         "vs_solve_transient": (ip, [vp, ip, vp, vp, vp, C.POINTER(_SolveParams), vp,
                                     C.POINTER(_SolveInfo), vp]),
         "vs_tc_transform": (ip, [vp, vp, ip, ip, ip, vp]),
@@ -400,6 +403,40 @@ def solve_batch(items, params: Optional[SolveParams] = None, stream=None):
         return p.info(stream)
     finally:
         p.close()
+
+
+def _host_ptr(t, n: int, count: int, name: str, allow_none=False):
+    import torch
+    if t is None:
+        if allow_none:
+            return None
+        raise ValueError("%s is required" % name)
+    if not isinstance(t, torch.Tensor) or t.is_cuda or t.dtype != torch.float32:
+        raise TypeError("%s must be a float32 CPU tensor" % name)
+    if not t.is_contiguous() or tuple(t.shape) != (count, n, n):
+        raise ValueError("%s must be contiguous [%d, %d, %d], got %s"
+                         % (name, count, n, n, tuple(t.shape)))
+    return t.data_ptr()
+
+
+def solve_batch_host(kernel: Kernel, p_dyn, p_leak0, s_kappa=None, theta=None,
+                     params: Optional[SolveParams] = None, chunk_maps: int = 0, stream=None):
+    """vs_solve_batch_host: host (CPU) tensors [count, n, n] in and out; the
+    copies overlap the solve chunk by chunk (use pinned tensors for overlap).
+    Returns (theta, info list)."""
+    import torch
+    n, count = kernel.n, p_dyn.shape[0]
+    prm = params or SolveParams()
+    if theta is None:
+        theta = torch.empty((count, n, n), dtype=torch.float32, pin_memory=p_dyn.is_pinned())
+    info = (_SolveInfo * count)()
+    _check(lib().vs_solve_batch_host(kernel.handle, count, _host_ptr(p_dyn, n, count, "p_dyn"),
+                                     _host_ptr(p_leak0, n, count, "p_leak0"),
+                                     _host_ptr(s_kappa, n, count, "s_kappa", allow_none=True),
+                                     _host_ptr(theta, n, count, "theta"), C.byref(prm._c()), info,
+                                     int(chunk_maps), _stream(stream)),
+           "vs_solve_batch_host", ok=_SOLVE_OK)
+    return theta, [_info(i) for i in info]
 
 
 def solve_transient(kernel: Kernel, p_dyn_trace, p_leak0, s_kappa=None,

@@ -71,3 +71,9 @@ void vs_stack_to_dev(const vs_stack* s, vs_stack_dev* d);
 // radii (device arrays), see vs_kernel_build.cu.
 int vs_hankel_eval(const vs_stack_dev& st, double cell_m, int quad_nodes,
                    const double* r_dev, double* out_dev, int count, cudaStream_t s);
+
+// ---------------------------------------------------------------- plans
+// Asynchronous copy of a plan's per-map outcome to (pinned) host memory.
+int vs_plan_info_async(vs_plan p, vs_solve_info* info_host, cudaStream_t s);
+// VS_ERR_TIMEOUT if the plan's last run aborted on a barrier timeout (syncs s).
+int vs_plan_check_timeout(vs_plan p, cudaStream_t s);

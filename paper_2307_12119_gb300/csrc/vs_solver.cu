@@ -1569,6 +1569,19 @@ extern "C" int vs_plan_info(vs_plan p, vs_solve_info* info_host, void* stream) {
   return worst;
 }
 
+// Asynchronous copy of a plan's per-map outcome (no synchronisation, no
+// timeout check), for the pipelined host-memory solve.
+int vs_plan_info_async(vs_plan p, vs_solve_info* info_host, cudaStream_t s) {
+  VS_CUDA_TRY(cudaMemcpyAsync(info_host, p->d_info, sizeof(vs_solve_info) * p->n_items,
+                              cudaMemcpyDeviceToHost, s));
+  return VS_OK;
+}
+
+// VS_ERR_TIMEOUT if the last run of the plan aborted on a barrier timeout.
+int vs_plan_check_timeout(vs_plan p, cudaStream_t s) {
+  return p->cluster ? VS_OK : timeout_status(p, s);
+}
+
 extern "C" void vs_plan_free(vs_plan p) {
   if (!p) return;
   plan_release(p);
