@@ -508,8 +508,9 @@ def run_ours(a):
                    "d2h_bytes_per_step": d2h,
                    "not_ok": sum(1 for i in infos_e2e if i["status"] != vs.VS_OK),
                    "how": "vs_solve_batch_host (the C-ABI call with host buffers) on pinned host "
-                          "arrays, %s parameters: default chunks (a sixteenth of the batch), the copies of the next and "
-                          "previous chunk overlapping the solve of the current one" % best,
+                          "arrays, %s parameters: default chunks (a sixteenth of the batch), the "
+                          "copies of the next and previous chunk overlapping the solve of the "
+                          "current one" % best,
                    "serial": serial}
         else:
             e2e = dict(serial, h2d_bytes_per_step=h2d, d2h_bytes_per_step=d2h)

@@ -233,7 +233,9 @@ __global__ void __launch_bounds__(ClShape<N>::THREADS, ClShape<N>::MIN_BLOCKS)
       // mirror lane are updated together, so every input is read as a
       // coalesced float2 (x, x + 1); u and q of x + 1 travel by shuffle.
       const size_t row_a = (size_t)(y0 + 2 * f16) * N;
-      auto ld2 = [&](const float* p, size_t idx) { return __ldg(reinterpret_cast<const float2*>(p + idx)); };
+      auto ld2 = [&](const float* p, size_t idx) {
+        return __ldg(reinterpret_cast<const float2*>(p + idx));
+      };
 #pragma unroll
       for (int r0 = 0; r0 < 8; r0 += kClBatch) {
         float2 pl[kClBatch][2], pd[kClBatch][2], sk[kClBatch][2], old[kClBatch][2];
@@ -318,7 +320,8 @@ __global__ void __launch_bounds__(ClShape<N>::THREADS, ClShape<N>::MIN_BLOCKS)
     dftR<R2, true>(z);
     // lanes 0-15 of a half-warp hold 16 consecutive row pairs of one pair k:
     // each store below is one contiguous run in the owner's column buffer
-    const unsigned oe = (unsigned)pad(y0 / 2 + f2) * 8u, oo = (unsigned)pad(N - 1 - y0 / 2 - f2) * 8u;
+    const unsigned oe = (unsigned)pad(y0 / 2 + f2) * 8u;
+    const unsigned oo = (unsigned)pad(N - 1 - y0 / 2 - f2) * 8u;
 #pragma unroll
     for (int r = 0; r < R2 / 2; ++r) {
       // what the partner needs at its index r: Z[N - k'] for its k' = 16 r + (16 - blk)
