@@ -315,12 +315,36 @@ def _time_plan(plan, steps, warmup, ws, local, stream):
 
 
 def _max_over_ranks(x, ws, dev):
+    """The largest of every rank's x (the job's time is its slowest rank's)."""
     import torch
     import torch.distributed as dist
     t = torch.tensor([x], device=dev, dtype=torch.float64)
     if ws > 1:
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
     return float(t.item())
+
+
+def rank_seed(rank: int) -> int:
+    """Seed of a rank's shard: every rank solves its own maps (weak scaling,
+    no data exchange between ranks)."""
+    import synth
+    return synth.SEED + 7919 * rank
+
+
+def agree_on(names, local_best, ws, dev):
+    """Every rank reports rank 0's choice among `names`."""
+    if ws <= 1:
+        return local_best
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([list(names).index(local_best)], device=dev)
+    dist.broadcast(t, 0)
+    return list(names)[int(t.item())]
+
+
+def whole_job_rate(ws, maps_per_rank, seconds_max):
+    """Maps per second of the whole job: all ranks' maps over the slowest time."""
+    return ws * maps_per_rank / seconds_max
 
 
 def _train_warm_model(vs, synth, k, w, dev, n_train, epochs, seed_base, stream):
@@ -375,7 +399,7 @@ def run_ours(a):
         if v not in ALL_VARIANTS:
             raise SystemExit("unknown variant %r (known: %s)" % (v, ", ".join(ALL_VARIANTS)))
     # every rank solves its own shard of the sample space (weak scaling)
-    w, pd, pl, s = synth.batch_inputs(a.n, a.batch, device=dev, seed=synth.SEED + 7919 * rank)
+    w, pd, pl, s = synth.batch_inputs(a.n, a.batch, device=dev, seed=rank_seed(rank))
     st, phy = w.stack, w.physics
     stack = vs.Stack(st.thickness_m, st.kappa_W_mK, st.h_conv_W_m2K, st.heat_cap_J_m2K)
     k = vs.Kernel(stack, vs.Grid(w.n, w.die_m))
@@ -396,7 +420,7 @@ def run_ours(a):
         infos = runner.info()
         msx = _max_over_ranks(ms, ws, dev)
         its = [i["iterations"] for i in infos]
-        results[name] = {"value": ws * B / (msx * 1e-3), "unit": UNIT, "ms_per_step": msx,
+        results[name] = {"value": whole_job_rate(ws, B, msx * 1e-3), "unit": UNIT, "ms_per_step": msx,
                          "iterations_mean": sum(its) / len(its),
                          "not_ok": sum(1 for i in infos if i["status"] != vs.VS_OK),
                          "fell_back": sum(1 for i in infos if i.get("fell_back")),
@@ -439,10 +463,7 @@ def run_ours(a):
     if not batched:
         raise SystemExit("no batched variant at the headline tolerance was selected")
     best = max(batched, key=lambda name: results[name]["value"])
-    if ws > 1:                      # every rank reports the same headline path
-        t = torch.tensor([batched.index(best)], device=dev)
-        dist.broadcast(t, 0)
-        best = batched[int(t.item())]
+    best = agree_on(batched, best, ws, dev)        # every rank reports the same headline path
     th_best = thetas[best]
 
     # plain: FP32, one map per vs_solve_steady call
@@ -491,7 +512,7 @@ def run_ours(a):
             hth.copy_(th_best, non_blocking=True)
 
         dt_serial = timed(serial_step)
-        serial = {"value": ws * B / dt_serial, "unit": UNIT,
+        serial = {"value": whole_job_rate(ws, B, dt_serial), "unit": UNIT,
                   "how": "%s: pinned inputs copied in, one plan run, theta copied out, in "
                          "sequence on one stream" % best}
         h2d, d2h = 3 * pd.numel() * 4, th_best.numel() * 4
@@ -504,7 +525,7 @@ def run_ours(a):
                 infos_e2e[:] = inf
 
             dt = timed(host_step)
-            e2e = {"value": ws * B / dt, "unit": UNIT, "h2d_bytes_per_step": h2d,
+            e2e = {"value": whole_job_rate(ws, B, dt), "unit": UNIT, "h2d_bytes_per_step": h2d,
                    "d2h_bytes_per_step": d2h,
                    "not_ok": sum(1 for i in infos_e2e if i["status"] != vs.VS_OK),
                    "how": "vs_solve_batch_host (the C-ABI call with host buffers) on pinned host "
