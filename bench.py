@@ -283,8 +283,9 @@ def run_reference(a):
         "steps": a.steps, "warmup": a.warmup, "ms_per_step": 1e3 * dt / a.steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
         "data": "synthetic",
-        "config": {"workload": w.name, "n": w.n, "global_batch": a.batch,
-                   "note": "FP64 CPU oracle; each step solves %d maps of the batch" % per_step},
+        "config": dict(workload_config(w.n, a.batch, ws, 1e-2),
+                       note="FP64 CPU oracle (Picard to 1e-8 K); each step solves %d maps of "
+                            "the batch" % per_step),
         "cpu_baseline": {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle",
                          "sample": "%d maps per step x %d steps" % (per_step, a.steps)},
         "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
@@ -322,6 +323,14 @@ def _max_over_ranks(x, ws, dev):
     if ws > 1:
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
     return float(t.item())
+
+
+def workload_config(n: int, maps_per_rank: int, ws: int, tol: float) -> dict:
+    """The `config` both arms report: the workload, its size and tolerance."""
+    return {"workload": "steady %dx%d, 20x20 mm die, batch of %d maps per GPU "
+                        "(64 floorplans x per-map variation fields)" % (n, n, maps_per_rank),
+            "n": n, "global_batch": ws * maps_per_rank, "tol_K": tol,
+            "parallelism": "replicas x%d" % ws}
 
 
 def rank_seed(rank: int) -> int:
@@ -592,13 +601,10 @@ def run_ours(a):
             "warmup": a.warmup, "ms_per_step": bv["ms_per_step"], "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None,
             "dtype": "f32" if best.startswith("fp32") else "bf16", "data": "synthetic",
-            "config": {"workload": "steady %dx%d, 20x20 mm die, batch of %d maps per GPU "
-                                   "(64 floorplans x per-map variation fields)" % (w.n, w.n, B),
-                       "n": w.n, "global_batch": ws * B, "tol_K": tol,
-                       "path": "chosen by measurement = %s (fastest batched variant at the "
-                               "tolerance; all variants in 'variants')" % best,
-                       "l2": "inputs %.1f GiB per GPU > L2, no flush" % (3 * pd.numel() * 4 / 2**30),
-                       "parallelism": "replicas x%d" % ws},
+            "config": dict(workload_config(w.n, B, ws, tol),
+                           path="chosen by measurement = %s (fastest batched variant at the "
+                                "tolerance; all variants in 'variants')" % best,
+                           l2="inputs %.1f GiB per GPU > L2, no flush" % (3 * pd.numel() * 4 / 2**30)),
             "variants": results,
             "plain": {"value": plain_value, "unit": UNIT,
                       "how": "FP32, one map per vs_solve_steady call, tol %g K, %d maps"
