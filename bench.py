@@ -489,6 +489,49 @@ def run_ours(a):
     torch.cuda.synchronize()
     plain_value = plain_maps / (e0.elapsed_time(e1) * 1e-3)
 
+    # The transient (1024^2, 200 steps of 1 ms, Markov power trace) and the
+    # Green's-function build, timed once each on the full run.
+    extras = {}
+    if not a.variants:
+        wt = synth.workload("c4_1024")
+        stt = wt.stack
+        kt = vs.Kernel(vs.Stack(stt.thickness_m, stt.kappa_W_mK, stt.h_conv_W_m2K,
+                                stt.heat_cap_J_m2K), vs.Grid(wt.n, wt.die_m), vs.KernelOpts(dt_s=1e-3))
+        steps_t = 200
+        trace = synth.markov_trace(wt, steps_t, device=dev)
+        _, pl_t, s_t = synth.steady_inputs(wt, 1, device=dev)
+        prm_t = vs.SolveParams(wt.physics.beta_per_K, wt.physics.alpha_per_K, 1e-4, 50)
+        out_t = torch.empty_like(trace)
+        vs.solve_transient(kt, trace[:4].contiguous(), pl_t[0], s_t[0], prm_t)   # warm-up
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        _, tinfo = vs.solve_transient(kt, trace, pl_t[0], s_t[0], prm_t, out_t)
+        torch.cuda.synchronize()
+        dt_t = time.perf_counter() - t0
+        # per step the path must read P_dyn,n and write theta_n (P_leak0 and s stay in L2)
+        tbytes = steps_t * wt.n * wt.n * 8
+        extras["transient"] = {
+            "workload": "transient 1024x1024, 20x20 mm die, %d steps of 1 ms, Markov power "
+                        "trace, leakage and conductivity on" % steps_t,
+            "steps_per_s": steps_t / dt_t, "ms_per_step": 1e3 * dt_t / steps_t,
+            "status": tinfo["status"],
+            "how": "one vs_solve_transient call (plan set-up included), wall time",
+            "roofline": {"bound": "hbm", "achieved": tbytes / dt_t / 1e9, "peak": _peaks()[0],
+                         "unit": "GB/s", "frac": tbytes / dt_t / 1e9 / _peaks()[0], "traffic": None,
+                         "kernel": "k_solve_transient",
+                         "note": "8 B/pixel per step algorithmic (read P_dyn,n, write theta_n)"}}
+        del trace, out_t
+        builds = {}
+        for nb in (256, 1024):
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            kb = vs.Kernel(stack, vs.Grid(nb, 20e-3))
+            torch.cuda.synchronize()
+            builds["%dx%d" % (nb, nb)] = round((time.perf_counter() - t0) * 1e3, 2)
+            del kb
+        extras["kernel_build_ms"] = dict(builds, how="vs_make_kernel wall time (Hankel quadrature, "
+                                         "fold, cosine sums, spectral part), FP64 on the GPU")
+
     # e2e: pinned host inputs -> device -> headline path -> host theta, every step
     e2e = None
     if not a.no_e2e:
@@ -610,6 +653,7 @@ def run_ours(a):
                       "how": "FP32, one map per vs_solve_steady call, tol %g K, %d maps"
                              % (tol, plain_maps)},
             "warm_start_model": train_info,
+            **extras,
             "roofline": roofs[best],
             "rooflines": roofs,
             "cpu_baseline": cpu,
