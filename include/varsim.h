@@ -239,7 +239,7 @@ typedef struct {
   const float* s_kappa;    /* device, [n][n], or NULL => 1 */
   float* theta;            /* device output, [n][n] */
   const float* theta_init; /* device [n][n] initial temperature (warm start of the
-                              fixed point, e.g. from vs_model_predict), or NULL => 0 */
+                              fixed point, e.g. from vs_warm_apply), or NULL => 0 */
 } vs_batch_item;
 
 /* Creates a plan for n_items maps: uploads the item table and picks the
@@ -345,6 +345,9 @@ int vs_model_train(vs_model m, const float* x, const float* t, int n_samples, in
 /* Checkpoint (base channels, resolution, parameters) to / from a file. */
 int vs_model_save(vs_model m, const char* path);
 int vs_model_load(const char* path, vs_model* out);
+/* Base channel count C and input resolution R of a model (e.g. one loaded
+ * from a checkpoint). */
+int vs_model_shape(vs_model m, int* base_channels, int* resolution);
 
 /* Features of `count` maps [count][n][n] for the warm start, averaged over
  * (n/R)^2 blocks: x[b] = {theta1/100, 10 (P_leak0/mean - 1), 30 (s - 1)}
@@ -357,6 +360,41 @@ int vs_warm_target(const float* theta_star, const float* theta1, int count, int 
 /* theta_init = theta1 + 10 * bilinear upsampling of y to n x n. */
 int vs_warm_apply(const float* theta1, const float* y, int count, int n, int resolution,
                   float* theta_init, void* stream);
+
+/* Warm-started batched solve of `count` maps of one kernel's grid, in three
+ * stages that a run can take together or apart (bit mask `stages`):
+ *   VS_WARM_FIRST   one fixed-point iteration from theta_0 = 0 -> theta1;
+ *   VS_WARM_PREDICT features of theta1, network, theta_init = theta1 +
+ *                   predicted correction (vs_warm_features, vs_model_forward,
+ *                   vs_warm_apply);
+ *   VS_WARM_SOLVE   the batched solve (vs_plan_run) from theta_init -> theta.
+ * p_dyn, p_leak0, s_kappa (NULL => 1), theta, theta1, theta_init: device
+ * float32 [count][n][n], caller-owned, retained until vs_warm_plan_free;
+ * theta1 and theta_init may be written by the caller between stages (e.g. to
+ * run the solve from another start). The model's resolution must divide n.
+ * The plan owns the network's input and output buffers and both solve plans.
+ * A run is asynchronous and allocation-free (graph-capturable). Synchronises
+ * `stream` on create. */
+#define VS_WARM_FIRST 1
+#define VS_WARM_PREDICT 2
+#define VS_WARM_SOLVE 4
+#define VS_WARM_ALL 7
+typedef struct vs_warm_plan_t* vs_warm_plan;
+int vs_warm_plan_create(vs_kernel k, int count, const float* p_dyn, const float* p_leak0,
+                        const float* s_kappa, float* theta, float* theta1, float* theta_init,
+                        vs_model model, const vs_solve_params* params, vs_warm_plan* out,
+                        void* stream);
+int vs_warm_plan_run(vs_warm_plan plan, int stages, void* stream);
+/* Kernel launches of one full run (VS_WARM_ALL). */
+int vs_warm_plan_launches(vs_warm_plan plan);
+/* Per-map outcome of the last solve stage into info_host[count] (blocking).
+ * With `fallback` != 0, the maps whose status is not VS_OK are solved again
+ * from theta_0 = 0 (vs_solve_batch) and their entries replaced; fell_back_host
+ * (may be NULL) gets 1 for those maps, else 0. Returns the worst per-map
+ * status, or the launch-level error. */
+int vs_warm_plan_info(vs_warm_plan plan, vs_solve_info* info_host, int fallback,
+                      int* fell_back_host, void* stream);
+void vs_warm_plan_free(vs_warm_plan plan);
 
 /* Split-precision tensor-core transform (the building block of
  * VS_PREC_BF16_SPLIT), exposed for testing: for each of `rows` rows,

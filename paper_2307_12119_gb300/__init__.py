@@ -24,13 +24,15 @@ __all__ = [
     "solve_steady_noalloc",
     "tc_transform", "VS_PREC_FP32", "VS_PREC_BF16_SPLIT", "VS_ENGINE_AUTO",
     "VS_ENGINE_STREAMED", "VS_ENGINE_CLUSTER", "Model", "WarmPlan",
-    "warm_features", "warm_target", "warm_apply",
+    "warm_features", "warm_target", "warm_apply", "VS_WARM_FIRST", "VS_WARM_PREDICT",
+    "VS_WARM_SOLVE", "VS_WARM_ALL",
 ]
 
 VS_OK, VS_ERR_INVALID_ARG, VS_ERR_CUDA, VS_ERR_OOM = 0, 1, 2, 3
 VS_ERR_NO_CONVERGENCE, VS_ERR_RUNAWAY, VS_ERR_NONFINITE, VS_ERR_TIMEOUT = 4, 5, 6, 7
 VS_PREC_FP32, VS_PREC_BF16_SPLIT = 0, 1
 VS_ENGINE_AUTO, VS_ENGINE_STREAMED, VS_ENGINE_CLUSTER = 0, 1, 2
+VS_WARM_FIRST, VS_WARM_PREDICT, VS_WARM_SOLVE, VS_WARM_ALL = 1, 2, 4, 7
 VS_MAX_LAYERS = 8
 
 EXPORTS = [
@@ -41,7 +43,8 @@ EXPORTS = [
     "vs_tc_transform", "vs_model_create", "vs_free_model", "vs_model_nparams",
     "vs_model_get_params", "vs_model_set_params", "vs_model_forward", "vs_model_loss_grad",
     "vs_model_train", "vs_model_save", "vs_model_load", "vs_warm_features", "vs_warm_target",
-    "vs_warm_apply", "vs_solve_batch_host",
+    "vs_warm_apply", "vs_solve_batch_host", "vs_model_shape", "vs_warm_plan_create",
+    "vs_warm_plan_run", "vs_warm_plan_launches", "vs_warm_plan_info", "vs_warm_plan_free",
 ]
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
@@ -139,6 +142,13 @@ def lib():
         "vs_warm_features": (ip, [vp, vp, vp, ip, ip, ip, vp, vp]),
         "vs_warm_target": (ip, [vp, vp, ip, ip, ip, vp, vp]),
         "vs_warm_apply": (ip, [vp, vp, ip, ip, ip, vp, vp]),
+        "vs_model_shape": (ip, [vp, C.POINTER(ip), C.POINTER(ip)]),
+        "vs_warm_plan_create": (ip, [vp, ip, vp, vp, vp, vp, vp, vp, vp, C.POINTER(_SolveParams),
+                                     C.POINTER(vp), vp]),
+        "vs_warm_plan_run": (ip, [vp, ip, vp]),
+        "vs_warm_plan_launches": (ip, [vp]),
+        "vs_warm_plan_info": (ip, [vp, C.POINTER(_SolveInfo), ip, C.POINTER(ip), vp]),
+        "vs_warm_plan_free": (None, [vp]),
         "vs_status_string": (C.c_char_p, [ip]),
         "vs_last_error": (C.c_char_p, []),
         "vs_version": (C.c_char_p, []),
@@ -478,10 +488,12 @@ class Model:
         self.resolution = resolution
 
     @classmethod
-    def load(cls, path: str, base_channels: int, resolution: int):
+    def load(cls, path: str):
         h = C.c_void_p()
         _check(lib().vs_model_load(path.encode(), C.byref(h)), "vs_model_load")
-        return cls(base_channels, resolution, _handle=h.value)
+        c, r = C.c_int(), C.c_int()
+        _check(lib().vs_model_shape(h, C.byref(c), C.byref(r)), "vs_model_shape")
+        return cls(c.value, r.value, _handle=h.value)
 
     def save(self, path: str):
         _check(lib().vs_model_save(self.handle, path.encode()), "vs_model_save")
@@ -569,54 +581,59 @@ def warm_apply(theta1, y, out=None, stream=None):
 
 
 class WarmPlan:
-    """Warm-started batched solve of maps [B, n, n] with one kernel:
-    a one-iteration plan gives the first iterate theta_1; the network predicts
-    the remaining correction at reduced resolution; the main plan starts from
-    theta_init = theta_1 + correction. Maps that do not converge from the warm
-    start are re-solved from theta_0 = 0 (`fallback`)."""
+    """Warm-started batched solve of maps [B, n, n] with one kernel
+    (vs_warm_plan_*): a one-iteration solve gives the first iterate theta1;
+    the network predicts the remaining correction at reduced resolution; the
+    batched solve starts from theta_init = theta1 + correction. Maps that do
+    not converge from the warm start are solved again from theta_0 = 0 when
+    `info(fallback=True)` is read."""
 
     def __init__(self, kernel: Kernel, p_dyn, p_leak0, s_kappa, theta, model: Model,
                  params: Optional[SolveParams] = None, stream=None):
-        import copy
         import torch
         prm = params or SolveParams()
-        one = copy.copy(prm)
-        one.max_iter = 1
-        B = p_dyn.shape[0]
-        self.B, self.model, self.stream = B, model, stream
-        self.kernel, self.p_dyn, self.p_leak0, self.s, self.theta = kernel, p_dyn, p_leak0, s_kappa, theta
+        n = kernel.n
+        self.B, self.stream = p_dyn.shape[0], stream
         self.theta1 = torch.empty_like(p_dyn)
         self.theta_init = torch.empty_like(p_dyn)
-        sk = (lambda i: s_kappa[i]) if s_kappa is not None else (lambda i: None)
-        self.first = Plan([(kernel, p_dyn[i], p_leak0[i], sk(i), self.theta1[i]) for i in range(B)],
-                          one, stream)
-        self.warm = Plan([(kernel, p_dyn[i], p_leak0[i], sk(i), theta[i], self.theta_init[i])
-                          for i in range(B)], prm, stream)
-        self.params = prm
+        self._keep = (kernel, p_dyn, p_leak0, s_kappa, theta, model)
+        h = C.c_void_p()
+        _check(lib().vs_warm_plan_create(
+            kernel.handle, self.B, _ptr(p_dyn, n, "p_dyn"), _ptr(p_leak0, n, "p_leak0"),
+            _ptr(s_kappa, n, "s_kappa", allow_none=True), _ptr(theta, n, "theta"),
+            _ptr(self.theta1, n, "theta1"), _ptr(self.theta_init, n, "theta_init"),
+            model.handle, C.byref(prm._c()), C.byref(h), _stream(stream)), "vs_warm_plan_create")
+        self.handle = h.value
         self.fallbacks = 0
 
     @property
     def launches(self) -> int:
-        # first plan, features, network (8 convs, 2 pools, 2 upsamplings), apply, warm plan
-        return self.first.launches + 1 + 12 + 1 + self.warm.launches
+        return lib().vs_warm_plan_launches(self.handle)
 
-    def run(self, stream=None):
+    def run(self, stream=None, stages: int = VS_WARM_ALL):
         st = stream if stream is not None else self.stream
-        self.first.run(st)
-        x = warm_features(self.theta1, self.p_leak0, self.s, self.model.resolution, st)
-        y = self.model.forward(x, st)
-        warm_apply(self.theta1, y, self.theta_init, st)
-        self.warm.run(st)
+        _check(lib().vs_warm_plan_run(self.handle, stages, _stream(st)), "vs_warm_plan_run")
 
     def info(self, fallback: bool = True):
-        infos = self.warm.info(self.stream)
-        bad = [i for i, inf in enumerate(infos) if inf["status"] != VS_OK]
-        self.fallbacks = len(bad)
-        if fallback and bad:
-            sk = (lambda i: self.s[i]) if self.s is not None else (lambda i: None)
-            items = [(self.kernel, self.p_dyn[i], self.p_leak0[i], sk(i), self.theta[i]) for i in bad]
-            redo = solve_batch(items, self.params, self.stream)
-            for j, i in enumerate(bad):
-                redo[j]["fell_back"] = True
-                infos[i] = redo[j]
+        arr = (_SolveInfo * self.B)()
+        fell = (C.c_int * self.B)()
+        rc = lib().vs_warm_plan_info(self.handle, arr, int(fallback), fell, _stream(self.stream))
+        _check(rc, "vs_warm_plan_info", ok=_SOLVE_OK)
+        infos = [_info(a) for a in arr]
+        self.fallbacks = 0
+        for i in range(self.B):
+            if fell[i]:
+                infos[i]["fell_back"] = True
+                self.fallbacks += 1
         return infos
+
+    def close(self):
+        if getattr(self, "handle", None):
+            lib().vs_warm_plan_free(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

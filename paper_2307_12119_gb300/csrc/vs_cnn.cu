@@ -778,3 +778,162 @@ extern "C" int vs_warm_apply(const float* theta1, const float* y, int count, int
   VS_CUDA_TRY(cudaGetLastError());
   return VS_OK;
 }
+
+extern "C" int vs_model_shape(vs_model m, int* base_channels, int* resolution) {
+  if (!m || !base_channels || !resolution) return vs_set_error(VS_ERR_INVALID_ARG, "NULL model or output");
+  *base_channels = m->C;
+  *resolution = m->R;
+  return VS_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Warm-started batched solve: first iterate -> network -> warm solve, with a
+// cold re-solve of the maps the warm start did not bring to convergence.
+// ---------------------------------------------------------------------------
+
+struct vs_warm_plan_t {
+  vs_kernel k = nullptr;
+  vs_model model = nullptr;
+  int count = 0, n = 0, R = 0;
+  const float *pd = nullptr, *pl = nullptr, *sk = nullptr;
+  float *theta = nullptr, *theta1 = nullptr, *theta_init = nullptr;
+  float *x = nullptr, *y = nullptr;      // network input / output, owned
+  vs_plan first = nullptr, warm = nullptr;
+  vs_solve_params params;
+};
+
+namespace {
+
+// Outcomes that belong to single maps (the rest fail the whole launch).
+bool per_map_status(int rc) {
+  return rc == VS_OK || rc == VS_ERR_NO_CONVERGENCE || rc == VS_ERR_RUNAWAY || rc == VS_ERR_NONFINITE;
+}
+
+void warm_release(vs_warm_plan_t* p) {
+  vs_plan_free(p->first);
+  vs_plan_free(p->warm);
+  cudaFree(p->x);
+  cudaFree(p->y);
+  delete p;
+}
+
+int warm_items(const vs_warm_plan_t* p, float* out, const float* init, const std::vector<int>& idx,
+               std::vector<vs_batch_item>& items) {
+  const size_t nn = (size_t)p->n * p->n;
+  items.resize(idx.size());
+  for (size_t j = 0; j < idx.size(); ++j) {
+    const size_t o = (size_t)idx[j] * nn;
+    items[j] = vs_batch_item{p->k, p->pd + o, p->pl + o, p->sk ? p->sk + o : nullptr, out + o,
+                             init ? init + o : nullptr};
+  }
+  return VS_OK;
+}
+
+}  // namespace
+
+extern "C" int vs_warm_plan_create(vs_kernel k, int count, const float* p_dyn, const float* p_leak0,
+                                   const float* s_kappa, float* theta, float* theta1,
+                                   float* theta_init, vs_model model,
+                                   const vs_solve_params* params, vs_warm_plan* out,
+                                   void* stream) {
+  if (!out) return vs_set_error(VS_ERR_INVALID_ARG, "out is NULL");
+  *out = nullptr;
+  if (!k || !model || count < 1 || !p_dyn || !p_leak0 || !theta || !theta1 || !theta_init)
+    return vs_set_error(VS_ERR_INVALID_ARG, "bad warm-plan arguments");
+  const int n = k->n, R = model->R;
+  if (R < 4 || n % R) return vs_set_error(VS_ERR_INVALID_ARG, "model resolution %d does not divide n %d", R, n);
+  int rc = vs_validate_params(params);
+  if (rc) return rc;
+  vs_warm_plan_t* p = new vs_warm_plan_t();
+  p->k = k;
+  p->model = model;
+  p->count = count;
+  p->n = n;
+  p->R = R;
+  p->pd = p_dyn;
+  p->pl = p_leak0;
+  p->sk = s_kappa;
+  p->theta = theta;
+  p->theta1 = theta1;
+  p->theta_init = theta_init;
+  p->params = *params;
+  rc = ensure_acts(model, std::min(count, 256));     // no allocation inside a run
+  if (rc) {
+    delete p;
+    return rc;
+  }
+  cudaError_t e = cudaMalloc(&p->x, sizeof(float) * 3 * (size_t)R * R * count);
+  if (e == cudaSuccess) e = cudaMalloc(&p->y, sizeof(float) * (size_t)R * R * count);
+  if (e != cudaSuccess) {
+    warm_release(p);
+    return vs_set_error(e == cudaErrorMemoryAllocation ? VS_ERR_OOM : VS_ERR_CUDA,
+                        "warm-plan buffers: %s", cudaGetErrorString(e));
+  }
+  std::vector<int> all(count);
+  for (int i = 0; i < count; ++i) all[i] = i;
+  std::vector<vs_batch_item> items;
+  vs_solve_params one = *params;
+  one.max_iter = 1;                                   // the first iterate only
+  warm_items(p, theta1, nullptr, all, items);
+  rc = vs_plan_create(items.data(), count, &one, &p->first, stream);
+  if (rc == VS_OK) {
+    warm_items(p, theta, theta_init, all, items);
+    rc = vs_plan_create(items.data(), count, params, &p->warm, stream);
+  }
+  if (rc != VS_OK) {
+    warm_release(p);
+    return rc;
+  }
+  *out = p;
+  return VS_OK;
+}
+
+extern "C" int vs_warm_plan_run(vs_warm_plan p, int stages, void* stream) {
+  if (!p) return vs_set_error(VS_ERR_INVALID_ARG, "NULL warm plan");
+  if (stages < 1 || stages > VS_WARM_ALL) return vs_set_error(VS_ERR_INVALID_ARG, "stages %d not in 1..7", stages);
+  int rc = VS_OK;
+  if (stages & VS_WARM_FIRST) rc = vs_plan_run(p->first, stream);
+  if (rc == VS_OK && (stages & VS_WARM_PREDICT)) {
+    rc = vs_warm_features(p->theta1, p->pl, p->sk, p->count, p->n, p->R, p->x, stream);
+    if (rc == VS_OK) rc = vs_model_forward(p->model, p->x, p->y, p->count, stream);
+    if (rc == VS_OK)
+      rc = vs_warm_apply(p->theta1, p->y, p->count, p->n, p->R, p->theta_init, stream);
+  }
+  if (rc == VS_OK && (stages & VS_WARM_SOLVE)) rc = vs_plan_run(p->warm, stream);
+  return rc;
+}
+
+extern "C" int vs_warm_plan_launches(vs_warm_plan p) {
+  if (!p) return 0;
+  const int chunks = (p->count + 255) / 256;          // the network runs 256 maps at a time
+  return vs_plan_launches(p->first) + 1 + 12 * chunks + 1 + vs_plan_launches(p->warm);
+}
+
+extern "C" int vs_warm_plan_info(vs_warm_plan p, vs_solve_info* info_host, int fallback,
+                                 int* fell_back_host, void* stream) {
+  if (!p || !info_host) return vs_set_error(VS_ERR_INVALID_ARG, "NULL warm plan or output");
+  int rc = vs_plan_info(p->warm, info_host, stream);
+  if (!per_map_status(rc)) return rc;                 // a launch-level error
+  if (fell_back_host) memset(fell_back_host, 0, sizeof(int) * p->count);
+  std::vector<int> bad;
+  for (int i = 0; i < p->count; ++i)
+    if (info_host[i].status != VS_OK) bad.push_back(i);
+  if (!fallback || bad.empty()) return rc;
+  // solve those maps again from theta_0 = 0
+  std::vector<vs_batch_item> items;
+  warm_items(p, p->theta, nullptr, bad, items);
+  std::vector<vs_solve_info> redo(bad.size());
+  int rc2 = vs_solve_batch(items.data(), (int)bad.size(), &p->params, redo.data(), stream);
+  if (!per_map_status(rc2)) return rc2;
+  int worst = VS_OK;
+  for (size_t j = 0; j < bad.size(); ++j) {
+    info_host[bad[j]] = redo[j];
+    if (fell_back_host) fell_back_host[bad[j]] = 1;
+  }
+  for (int i = 0; i < p->count; ++i) worst = std::max(worst, info_host[i].status);
+  return worst;
+}
+
+extern "C" void vs_warm_plan_free(vs_warm_plan p) {
+  if (p) warm_release(p);
+}

@@ -54,6 +54,16 @@ def test_argument_errors_need_no_gpu(libpath):
     rc = L.vs_make_kernel(ctypes.byref(st), ctypes.byref(vs.Grid(64, 0.01)._c()), None,
                           ctypes.byref(h), None)
     assert rc == vs.VS_ERR_INVALID_ARG and h.value is None
+    # the warm-start plan rejects a missing kernel or model before touching the device
+    prm = vs.SolveParams()._c()
+    rc = L.vs_warm_plan_create(None, 4, None, None, None, None, None, None, None,
+                               ctypes.byref(prm), ctypes.byref(h), None)
+    assert rc == vs.VS_ERR_INVALID_ARG and h.value is None
+    assert L.vs_warm_plan_run(None, vs.VS_WARM_ALL, None) == vs.VS_ERR_INVALID_ARG
+    assert L.vs_warm_plan_launches(None) == 0
+    L.vs_warm_plan_free(None)
+    c, r = ctypes.c_int(), ctypes.c_int()
+    assert L.vs_model_shape(None, ctypes.byref(c), ctypes.byref(r)) == vs.VS_ERR_INVALID_ARG
 
 
 def test_missing_library_fails_loudly(monkeypatch, tmp_path):

@@ -61,7 +61,8 @@ def test_training_reduces_loss_and_checkpoint_round_trip(tmp_path):
     assert l1 < 0.3 * l0
     path = str(tmp_path / "m.bin")
     m.save(path)
-    m2 = vs.Model.load(path, C, R)
+    m2 = vs.Model.load(path)
+    assert (m2.base_channels, m2.resolution) == (C, R)
     assert np.array_equal(m2.get_params(), m.get_params())
     assert torch.equal(m2.forward(x[:8].contiguous()), m.forward(x[:8].contiguous()))
 
@@ -132,7 +133,7 @@ def test_bad_warm_start_falls_back_to_cold_solve():
     wp = vs.WarmPlan(k, pd, pl, s, th, m, vs_params(w))
     wp.run()
     wp.theta_init.fill_(5000.0)                         # poison the prediction
-    wp.warm.run()
+    wp.run(stages=vs.VS_WARM_SOLVE)
     infos = wp.info(fallback=True)
     assert all(i["status"] == vs.VS_OK for i in infos)
     assert wp.fallbacks == 2
