@@ -214,3 +214,69 @@ def duhamel(step_spectra, p_dyn_trace, p_leak0, s, beta, alpha):
         th_prev = phi(u, s, alpha)
         theta[k] = th_prev
     return theta
+
+
+def transient_variants(step_spectra, steady_spectrum, p_dyn_trace, p_leak0, s, beta, alpha,
+                       window=0, implicit=False, tol=1e-10, max_iter=200):
+    """The two variants of the superposition of Sec. IV-E, in the paper's terms.
+
+    * window K >= 1: beyond K steps the step response is taken as saturated,
+      S_j = S_inf for every j >= K (Sec. IV-E: five 1 ms steps), and the sum
+      of Eq. 36 is taken with those responses; K = 0 keeps every S_j.
+    * implicit: the leakage of step n is taken at the temperature of step n
+      itself (the leakage-aware step responses the paper substitutes in
+      Sec. IV-E make the leakage of a step follow that step's own
+      temperature). Each step iterates
+          P_n = P_dyn,n + P_leak0 (1 + beta theta),  u_n = Eq. 36 sum,
+          theta <- phi(u_n),
+      from theta = theta_{n-1} (0 for the first step) until the largest
+      change is <= tol. The history keeps the P_n of the last iteration, so
+      u_n is exactly the Eq. 36 sum of the stored powers and theta_n = phi(u_n).
+      Otherwise the leakage is lagged: P_n = P_dyn,n + P_leak0 (1 + beta
+      theta_{n-1}).
+
+    step_spectra[j-1] = S_j in the cosine basis (needed for j < K, or for
+    every j when K = 0); steady_spectrum = S_inf = K~. Returns
+    (theta[n_steps, n, n], iterations per step)."""
+    n_steps = p_dyn_trace.shape[0]
+    theta = np.zeros_like(p_dyn_trace)
+    iters = np.zeros(n_steps, dtype=np.int64)
+    P = []
+
+    def response(j):
+        if window and j >= window:
+            return steady_spectrum
+        return step_spectra[j - 1]
+
+    def u_of(k, Pk):
+        # Eq. 36 at step k + 1 (0-based k) with P_{k+1} = Pk
+        u = np.zeros_like(p_leak0)
+        for j in range(1, k + 2):
+            m = k + 1 - j                        # 0-based index of P_{n-j+1}
+            cur = Pk if m == k else P[m]
+            prev = P[m - 1] if m >= 1 else 0.0
+            u = u + spectral_convolve(response(j), cur - prev)
+        return u
+
+    th_prev = np.zeros_like(p_leak0)
+    for k in range(n_steps):
+        if not implicit:
+            Pk = p_dyn_trace[k] + p_leak0 * (1.0 + beta * th_prev)
+            th = phi(u_of(k, Pk), s, alpha)
+            iters[k] = 1
+        else:
+            th = th_prev
+            for it in range(1, max_iter + 1):
+                Pk = p_dyn_trace[k] + p_leak0 * (1.0 + beta * th)
+                new = phi(u_of(k, Pk), s, alpha)
+                d = float(np.max(np.abs(new - th)))
+                th = new
+                if d <= tol:
+                    break
+            else:
+                raise SolveError("transient step %d did not converge" % k)
+            iters[k] = it
+        P.append(Pk)
+        theta[k] = th
+        th_prev = th
+    return theta, iters

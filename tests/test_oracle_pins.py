@@ -1,5 +1,6 @@
 """Pins of the FP64 oracle against facts fixed by the paper and by mathematics
 (not against the oracle itself). CPU only."""
+import functools
 import json
 import math
 import os
@@ -332,6 +333,130 @@ def test_duhamel_superposition_without_feedback():
     c = np.repeat(a[:1], 6, axis=0)
     tc = so.duhamel(spectra, c, z, one, 0.0, 0.0)
     assert np.allclose(tc[4], so.spectral_convolve(spectra[4], a[0]), rtol=1e-12)
+
+
+# ------------------------------------ P10b: windowed / implicit transient
+
+@functools.lru_cache(maxsize=None)
+def _tr_spectra(n, steps, C, dt):
+    t, kap, h = STACK3
+    L = 10e-3
+    spectra = [so.step_spectrum(n, L, t, kap, h, C, j * dt) for j in range(1, steps + 1)]
+    return spectra, ph.spectrum(n, L, t, kap, h)
+
+
+def _tr_setup(n=8, steps=12, C=1.63e6 * 0.5e-3, dt=1e-3, seed=3):
+    spectra, Kt = _tr_spectra(n, steps, C, dt)
+    rng = np.random.default_rng(seed)
+    trace = rng.random((steps, n, n)) * 0.01
+    return n, 10e-3, spectra, Kt, trace
+
+
+def test_window_zero_or_longer_than_trace_is_the_untruncated_sum():
+    n, L, spectra, Kt, trace = _tr_setup()
+    rng = np.random.default_rng(4)
+    pl, s = rng.random((n, n)) * 2e-3, 1.0 - 0.05 * rng.random((n, n))
+    ref = so.duhamel(spectra, trace, pl, s, 0.0275, 1e-3)
+    for K in (0, trace.shape[0] + 1):
+        th, it = so.transient_variants(spectra, Kt, trace, pl, s, 0.0275, 1e-3, window=K)
+        assert np.allclose(th, ref, rtol=1e-13, atol=0.0)
+        assert np.all(it == 1)
+
+
+def test_window_one_is_the_quasi_static_image_convolution():
+    # every response settled: theta_n = mirror-image convolution of P_n (no
+    # feedback), checked against the dense image operator
+    t, kap, h = STACK3
+    n, L, spectra, Kt, trace = _tr_setup()
+    z, one = np.zeros((n, n)), np.ones((n, n))
+    th, _ = so.transient_variants(spectra, Kt, trace, z, one, 0.0, 0.0, window=1)
+    Lm = so.mirror_operator(ph.kernel_periodic(n, L, t, kap, h))
+    for k in range(trace.shape[0]):
+        assert np.allclose(th[k], so.direct_convolve(Lm, trace[k]), rtol=1e-10)
+
+
+@pytest.mark.parametrize("K", [2, 3, 5])
+def test_window_constant_power_jumps_to_steady_at_age_K(K):
+    n, L, spectra, Kt, trace = _tr_setup()
+    c = np.repeat(trace[:1], trace.shape[0], axis=0)
+    z, one = np.zeros((n, n)), np.ones((n, n))
+    th, _ = so.transient_variants(spectra, Kt, c, z, one, 0.0, 0.0, window=K)
+    for k in range(trace.shape[0]):
+        S = spectra[k] if k + 1 < K else Kt          # step n = k + 1 sees S_n, or S_inf
+        assert np.allclose(th[k], so.spectral_convolve(S, c[0]), rtol=1e-12)
+
+
+@pytest.mark.parametrize("K", [2, 5])
+def test_window_telescopes_to_the_last_K_differences_plus_settled_power(K):
+    # Sec. IV-E: with S_j = S_inf for j >= K the old differences sum to one power,
+    # u_n = sum_{j<K} S_j * (P_{n-j+1} - P_{n-j}) + S_inf * P_{n-K+1}
+    n, L, spectra, Kt, trace = _tr_setup()
+    z, one = np.zeros((n, n)), np.ones((n, n))
+    th, _ = so.transient_variants(spectra, Kt, trace, z, one, 0.0, 0.0, window=K)
+    P = lambda m: trace[m - 1] if m >= 1 else np.zeros((n, n))    # 1-based, P_0 = 0
+    for nn_ in range(1, trace.shape[0] + 1):
+        u = sum(so.spectral_convolve(spectra[j - 1], P(nn_ - j + 1) - P(nn_ - j))
+                for j in range(1, min(K, nn_ + 1)))
+        if nn_ - K + 1 >= 1:
+            u = u + so.spectral_convolve(Kt, P(nn_ - K + 1))
+        assert np.allclose(th[nn_ - 1], u, rtol=1e-11, atol=1e-15)
+
+
+def test_window_error_shrinks_with_the_window():
+    n, L, spectra, Kt, trace = _tr_setup(steps=16)
+    z, one = np.zeros((n, n)), np.ones((n, n))
+    ref, _ = so.transient_variants(spectra, Kt, trace, z, one, 0.0, 0.0)
+    errs = [np.max(np.abs(so.transient_variants(spectra, Kt, trace, z, one, 0.0, 0.0,
+                                                window=K)[0] - ref)) for K in (2, 4, 8, 16)]
+    assert all(b < a for a, b in zip(errs, errs[1:]))
+    assert errs[0] > 0.0
+
+
+def test_implicit_without_leakage_feedback_equals_lagged():
+    n, L, spectra, Kt, trace = _tr_setup()
+    rng = np.random.default_rng(6)
+    pl, s = rng.random((n, n)) * 2e-3, 1.0 - 0.05 * rng.random((n, n))
+    for K in (0, 3):
+        a, _ = so.transient_variants(spectra, Kt, trace, pl, s, 0.0, 1e-3, window=K)
+        b, it = so.transient_variants(spectra, Kt, trace, pl, s, 0.0, 1e-3, window=K,
+                                      implicit=True, tol=1e-13)
+        assert np.allclose(a, b, rtol=1e-12, atol=1e-15)
+        assert np.all(it <= 2)
+
+
+def test_implicit_steps_are_leakage_fixed_points():
+    # each step's theta_n reproduces itself through P_n(theta_n) and the
+    # superposition of the stored powers, within the iteration tolerance
+    n, L, spectra, Kt, trace = _tr_setup()
+    rng = np.random.default_rng(7)
+    pl, s = 0.02 + rng.random((n, n)) * 0.02, 1.0 - 0.05 * rng.random((n, n))
+    beta, alpha, tol = 0.0275, 1.2e-3, 1e-11
+    th, it = so.transient_variants(spectra, Kt, trace, pl, s, beta, alpha, implicit=True, tol=tol)
+    assert np.all(it >= 3)
+    Ps = [trace[k] + pl * (1.0 + beta * th[k]) for k in range(trace.shape[0])]
+    for k in range(trace.shape[0]):
+        u = sum(so.spectral_convolve(spectra[j - 1], Ps[k - j + 1] - (Ps[k - j] if k - j >= 0 else 0.0))
+                for j in range(1, k + 2))
+        assert np.max(np.abs(so.phi(u, s, alpha) - th[k])) <= 100 * tol
+    # lagged leakage trails the implicit one while the temperature rises
+    lag, _ = so.transient_variants(spectra, Kt, trace, pl, s, beta, alpha)
+    assert np.all(th[1:] >= lag[1:] - 1e-12) and np.max(th - lag) > 0.0
+
+
+@pytest.mark.parametrize("K", [0, 4])
+def test_implicit_constant_power_reaches_steady_fixed_point(K):
+    w, pd, pl, s = _c1_inputs(8, sigma=0.08)
+    st, phy = w.stack, w.physics
+    C, dt, steps = 20.0, 1e-3, 40          # tau ~ 1 ms: settled well within 40 steps
+    spectra = [so.step_spectrum(w.n, w.die_m, st.thickness_m, st.kappa_W_mK, st.h_conv_W_m2K,
+                                C, j * dt) for j in range(1, (K or steps + 1))]
+    Kt = ph.spectrum(w.n, w.die_m, st.thickness_m, st.kappa_W_mK, st.h_conv_W_m2K)
+    trace = np.repeat(pd[None], steps, axis=0)
+    th, _ = so.transient_variants(spectra, Kt, trace, pl, s, phy.beta_per_K, phy.alpha_per_K,
+                                  window=K, implicit=True, tol=1e-13)
+    ss, _, _ = so.picard(lambda x: so.spectral_convolve(Kt, x), pd, pl, s,
+                         phy.beta_per_K, phy.alpha_per_K, tol=1e-12)
+    assert np.max(np.abs(th[-1] - ss)) <= 1e-6
 
 
 # -------------------------------------------------- golden chip parameters
