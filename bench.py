@@ -502,12 +502,16 @@ def run_ours(a):
         _, pl_t, s_t = synth.steady_inputs(wt, 1, device=dev)
         prm_t = vs.SolveParams(wt.physics.beta_per_K, wt.physics.alpha_per_K, 1e-4, 50)
         out_t = torch.empty_like(trace)
-        vs.solve_transient(kt, trace[:4].contiguous(), pl_t[0], s_t[0], prm_t)   # warm-up
-        torch.cuda.synchronize()
-        t0 = time.perf_counter()
-        _, tinfo = vs.solve_transient(kt, trace, pl_t[0], s_t[0], prm_t, out_t)
-        torch.cuda.synchronize()
-        dt_t = time.perf_counter() - t0
+
+        def run_transient(out, **opts):
+            vs.solve_transient(kt, trace[:4].contiguous(), pl_t[0], s_t[0], prm_t, **opts)  # warm-up
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            _, info = vs.solve_transient(kt, trace, pl_t[0], s_t[0], prm_t, out, **opts)
+            torch.cuda.synchronize()
+            return time.perf_counter() - t0, info
+
+        dt_t, tinfo = run_transient(out_t)
         # per step the path must read P_dyn,n and write theta_n (P_leak0 and s stay in L2)
         tbytes = steps_t * wt.n * wt.n * 8
         extras["transient"] = {
@@ -520,6 +524,24 @@ def run_ours(a):
                          "unit": "GB/s", "frac": tbytes / dt_t / 1e9 / _peaks()[0], "traffic": None,
                          "kernel": "k_solve_transient",
                          "note": "8 B/pixel per step algorithmic (read P_dyn,n, write theta_n)"}}
+        # Sec. IV-E variants on the same trace: the paper's 5-step window, and the
+        # leakage of each step taken at its own temperature (per-step fixed point)
+        rise = float(out_t.abs().max())
+        variants_t = {}
+        for name, opts, against in (
+                ("window5_lagged", {"window": 5}, "untruncated, lagged leakage"),
+                ("untruncated_implicit", {"leakage": vs.VS_LEAK_IMPLICIT},
+                 "untruncated, lagged leakage")):
+            out_v = torch.empty_like(trace)
+            dt_v, info_v = run_transient(out_v, **opts)
+            dev_v = float((out_v - out_t).abs().max())
+            variants_t[name] = {"ms_per_step": 1e3 * dt_v / steps_t, "status": info_v["status"],
+                                "fixed_point_iterations_per_step": info_v["iterations"] / steps_t,
+                                "max_abs_dev_K": dev_v, "dev_pct_of_max_rise": 100 * dev_v / rise,
+                                "against": against}
+            del out_v
+        extras["transient"]["variants"] = variants_t
+        extras["transient"]["max_rise_K"] = rise
         del trace, out_t
         builds = {}
         for nb in (256, 1024):

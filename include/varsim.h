@@ -309,6 +309,35 @@ int vs_solve_transient(vs_kernel k, int n_steps, const float* p_dyn_trace,
                        const vs_solve_params* params, float* theta_trace,
                        vs_solve_info* info_host, void* stream);
 
+/* Variants of the transient (Sec. IV-E).
+ *   window : 0 => untruncated superposition (as vs_solve_transient). K >= 1 =>
+ *            the step response of every power difference of age >= K steps is
+ *            taken as settled, S_j = S_inf = K~ for j >= K, which telescopes to
+ *            u_n = sum_{j<K} S_j * (P_{n-j+1} - P_{n-j}) + K~ * P_{n-K+1}
+ *            (the paper uses K = 5 steps of 1 ms); at most VS_MAX_WINDOW.
+ *   leakage: VS_LEAK_LAGGED (P_n uses theta_{n-1}) or VS_LEAK_IMPLICIT: every
+ *            step iterates theta_n <- phi(u_n(P_dyn,n + P_leak0 (1 + beta
+ *            theta_n))) from theta_{n-1} until max |change| <= tol_K or
+ *            max_iter iterations (the history then holds the source of the
+ *            last iteration). */
+#define VS_LEAK_LAGGED 0
+#define VS_LEAK_IMPLICIT 1
+#define VS_MAX_WINDOW 256
+typedef struct {
+  int window;
+  int leakage;
+} vs_transient_opts;
+
+/* vs_solve_transient with options (opts NULL => window 0, lagged leakage).
+ * Device state: (max(1, window - 1) + implicit) * n * n floats. info_host:
+ * lagged, iterations = steps; implicit, iterations = fixed-point iterations
+ * summed over the steps, residual_K = the largest final change of a step, and
+ * status VS_ERR_NO_CONVERGENCE if a step ended above tol_K. */
+int vs_solve_transient_ex(vs_kernel k, int n_steps, const float* p_dyn_trace,
+                          const float* p_leak0, const float* s_kappa,
+                          const vs_solve_params* params, const vs_transient_opts* opts,
+                          float* theta_trace, vs_solve_info* info_host, void* stream);
+
 /* ------------------------------------------------------------------------ */
 /* Learned warm start of the fixed point. The paper iterates power ->       */
 /* temperature -> leakage until convergence (Sec. V-C); these calls predict */

@@ -25,7 +25,7 @@ __all__ = [
     "tc_transform", "VS_PREC_FP32", "VS_PREC_BF16_SPLIT", "VS_ENGINE_AUTO",
     "VS_ENGINE_STREAMED", "VS_ENGINE_CLUSTER", "Model", "WarmPlan",
     "warm_features", "warm_target", "warm_apply", "VS_WARM_FIRST", "VS_WARM_PREDICT",
-    "VS_WARM_SOLVE", "VS_WARM_ALL",
+    "VS_WARM_SOLVE", "VS_WARM_ALL", "VS_LEAK_LAGGED", "VS_LEAK_IMPLICIT", "VS_MAX_WINDOW",
 ]
 
 VS_OK, VS_ERR_INVALID_ARG, VS_ERR_CUDA, VS_ERR_OOM = 0, 1, 2, 3
@@ -33,6 +33,7 @@ VS_ERR_NO_CONVERGENCE, VS_ERR_RUNAWAY, VS_ERR_NONFINITE, VS_ERR_TIMEOUT = 4, 5, 
 VS_PREC_FP32, VS_PREC_BF16_SPLIT = 0, 1
 VS_ENGINE_AUTO, VS_ENGINE_STREAMED, VS_ENGINE_CLUSTER = 0, 1, 2
 VS_WARM_FIRST, VS_WARM_PREDICT, VS_WARM_SOLVE, VS_WARM_ALL = 1, 2, 4, 7
+VS_LEAK_LAGGED, VS_LEAK_IMPLICIT, VS_MAX_WINDOW = 0, 1, 256
 VS_MAX_LAYERS = 8
 
 EXPORTS = [
@@ -45,6 +46,7 @@ EXPORTS = [
     "vs_model_train", "vs_model_save", "vs_model_load", "vs_warm_features", "vs_warm_target",
     "vs_warm_apply", "vs_solve_batch_host", "vs_model_shape", "vs_warm_plan_create",
     "vs_warm_plan_run", "vs_warm_plan_launches", "vs_warm_plan_info", "vs_warm_plan_free",
+    "vs_solve_transient_ex",
 ]
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
@@ -82,6 +84,10 @@ class _SolveParams(C.Structure):
 class _SolveInfo(C.Structure):
     _fields_ = [("status", C.c_int), ("iterations", C.c_int), ("residual_K", C.c_double),
                 ("mu_W", C.c_double)]
+
+
+class _TransientOpts(C.Structure):
+    _fields_ = [("window", C.c_int), ("leakage", C.c_int)]
 
 
 class _BatchItem(C.Structure):
@@ -127,6 +133,8 @@ def lib():
                                      C.POINTER(_SolveInfo), ip, vp]),
         "vs_solve_transient": (ip, [vp, ip, vp, vp, vp, C.POINTER(_SolveParams), vp,
                                     C.POINTER(_SolveInfo), vp]),
+        "vs_solve_transient_ex": (ip, [vp, ip, vp, vp, vp, C.POINTER(_SolveParams),
+                                       C.POINTER(_TransientOpts), vp, C.POINTER(_SolveInfo), vp]),
         "vs_tc_transform": (ip, [vp, vp, ip, ip, ip, vp]),
         "vs_model_create": (ip, [ip, ip, C.c_ulonglong, C.POINTER(vp)]),
         "vs_free_model": (None, [vp]),
@@ -450,8 +458,11 @@ def solve_batch_host(kernel: Kernel, p_dyn, p_leak0, s_kappa=None, theta=None,
 
 
 def solve_transient(kernel: Kernel, p_dyn_trace, p_leak0, s_kappa=None,
-                    params: Optional[SolveParams] = None, theta_trace=None, stream=None):
-    """Transient over the trace [n_steps, n, n]; returns (theta_trace, info)."""
+                    params: Optional[SolveParams] = None, theta_trace=None, stream=None,
+                    window: int = 0, leakage: int = VS_LEAK_LAGGED):
+    """Transient over the trace [n_steps, n, n]; returns (theta_trace, info).
+    window: 0 untruncated, K >= 1 step responses settled from age K on;
+    leakage: VS_LEAK_LAGGED or VS_LEAK_IMPLICIT (vs_solve_transient_ex)."""
     import torch
     n = kernel.n
     prm = params or SolveParams()
@@ -459,12 +470,14 @@ def solve_transient(kernel: Kernel, p_dyn_trace, p_leak0, s_kappa=None,
     if theta_trace is None:
         theta_trace = torch.empty_like(p_dyn_trace)
     info = _SolveInfo()
-    _check(lib().vs_solve_transient(kernel.handle, steps, _ptr(p_dyn_trace, n, "p_dyn_trace"),
-                                    _ptr(p_leak0, n, "p_leak0"),
-                                    _ptr(s_kappa, n, "s_kappa", allow_none=True),
-                                    C.byref(prm._c()), _ptr(theta_trace, n, "theta_trace"),
-                                    C.byref(info), _stream(stream)),
-           "vs_solve_transient", ok=_SOLVE_OK)
+    opts = _TransientOpts(window, leakage)
+    _check(lib().vs_solve_transient_ex(kernel.handle, steps, _ptr(p_dyn_trace, n, "p_dyn_trace"),
+                                       _ptr(p_leak0, n, "p_leak0"),
+                                       _ptr(s_kappa, n, "s_kappa", allow_none=True),
+                                       C.byref(prm._c()), C.byref(opts),
+                                       _ptr(theta_trace, n, "theta_trace"),
+                                       C.byref(info), _stream(stream)),
+           "vs_solve_transient_ex", ok=_SOLVE_OK)
     return theta_trace, _info(info)
 
 

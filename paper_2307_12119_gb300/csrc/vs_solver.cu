@@ -76,6 +76,9 @@ struct PlanDev {
   float beta, alpha, tol;
   int n_steps;           // transient
   int warm;              // some map has a warm start
+  int window;            // transient: 0 untruncated, K >= 1 step responses settled from age K on
+  int implicit;          // transient: per-step leakage fixed point
+  float* xs;             // transient, implicit: the last source spectrum of the current step
 };
 
 // ------------------------------------------------------------ grid barrier
@@ -145,6 +148,65 @@ __device__ __forceinline__ int find_map(const PlanDev& P, int task, bool row) {
   return __ldg(row ? &P.row_map[task] : &P.col_map[task]);
 }
 
+// ------------------------------------------------------------ row transforms
+// Rows y0 .. y0 + rb - 1 of a map are held in buf as rb/2 interleaved pairs
+// (float2 = two rows), in the digit-reversed order of the radix FFT.
+
+// Inverse DCT along x of the rows from the transposed spectral work map.
+__device__ __forceinline__ void row_inverse(const MapDesc& d, int y0, float2* buf) {
+  const int n = d.n, F = d.rb >> 1, NP = padded_len(n), half = n >> 1;
+  const int lgF = __ffs(F) - 1;
+  const float* WT = d.work;
+  const float2* tw = d.tw4n;
+  const int* dr = d.digrev;
+  const int total = F * (half + 1);
+  for (int base = threadIdx.x; base < total; base += kU * blockDim.x) {
+    float2 xk[kU], xnk[kU];
+#pragma unroll
+    for (int u = 0; u < kU; ++u) {
+      int it = base + u * blockDim.x;
+      xk[u] = xnk[u] = make_float2(0.f, 0.f);
+      if (it < total) {
+        int f = it & (F - 1), k = it >> lgF;
+        xk[u] = *reinterpret_cast<const float2*>(WT + (size_t)k * n + y0 + 2 * f);
+        if (k != 0) xnk[u] = *reinterpret_cast<const float2*>(WT + (size_t)(n - k) * n + y0 + 2 * f);
+      }
+    }
+#pragma unroll
+    for (int u = 0; u < kU; ++u) {
+      int it = base + u * blockDim.x;
+      if (it < total) {
+        int f = it & (F - 1), k = it >> lgF, nk = n - k;
+        buf[f * NP + pad(__ldg(&dr[k]))] = dct_pre(xk[u].x, xnk[u].x, xk[u].y, xnk[u].y, __ldg(&tw[k]));
+        if (k != 0 && k != half)
+          buf[f * NP + pad(__ldg(&dr[nk]))] = dct_pre(xnk[u].x, xk[u].x, xnk[u].y, xk[u].y, __ldg(&tw[nk]));
+      }
+    }
+  }
+  __syncthreads();
+  fft_inverse(buf, n, F, NP, tw);
+}
+
+// Forward DCT along x of the rows in buf (natural Makhoul order), stored
+// transposed (x-frequency major) into the spectral work map.
+__device__ __forceinline__ void row_forward(const MapDesc& d, int y0, float2* buf) {
+  const int n = d.n, F = d.rb >> 1, NP = padded_len(n), half = n >> 1;
+  const int lgF = __ffs(F) - 1;
+  float* WT = d.work;
+  const float2* tw = d.tw4n;
+  const int* dr = d.digrev;
+  fft_forward(buf, n, F, NP, tw);
+  for (int it = threadIdx.x; it < F * (half + 1); it += blockDim.x) {
+    int f = it & (F - 1), k = it >> lgF, nk = n - k;
+    float2 zk = buf[f * NP + pad(__ldg(&dr[k]))];
+    float2 znk = buf[f * NP + pad(__ldg(&dr[k == 0 ? 0 : nk]))];
+    *reinterpret_cast<float2*>(WT + (size_t)k * n + y0 + 2 * f) = dct_post(zk, znk, __ldg(&tw[k]));
+    if (k != 0 && k != half)
+      *reinterpret_cast<float2*>(WT + (size_t)nk * n + y0 + 2 * f) = dct_post(znk, zk, __ldg(&tw[nk]));
+  }
+  __syncthreads();
+}
+
 // ------------------------------------------------------------ row task
 // MODE 0: steady iteration `step` (0 = initial source from theta_0 = 0,
 // -1 = initial source from a warm start theta_0, -2 = mean leakage only).
@@ -158,13 +220,10 @@ __device__ void row_task(const PlanDev& P, int task, int step, float2* buf) {
   const MapDesc d = P.maps[b];
   MapState* ms = P.st + b;
   if (MODE == 0 && (step > 0 || step == -1) && !ms->active) return;
-  const int n = d.n, F = d.rb >> 1, NP = padded_len(n), half = n >> 1;
-  const int lgF = __ffs(F) - 1, lgn = __ffs(n) - 1;
+  const int n = d.n, F = d.rb >> 1, NP = padded_len(n);
+  const int lgn = __ffs(n) - 1;
   const int chunk = task - d.row_off;
   const int y0 = chunk * d.rb;
-  float* WT = d.work;
-  const float2* tw = d.tw4n;
-  const int* dr = d.digrev;
   const bool first = (step <= 0);
   const bool warm = (MODE == 0) && (step == -1);
   const bool muonly = (MODE == 0) && (step == -2);
@@ -179,34 +238,7 @@ __device__ void row_task(const PlanDev& P, int task, int step, float2* buf) {
     return;
   }
 
-  if (!first) {
-    const int total = F * (half + 1);
-    for (int base = threadIdx.x; base < total; base += kU * blockDim.x) {
-      float2 xk[kU], xnk[kU];
-#pragma unroll
-      for (int u = 0; u < kU; ++u) {
-        int it = base + u * blockDim.x;
-        xk[u] = xnk[u] = make_float2(0.f, 0.f);
-        if (it < total) {
-          int f = it & (F - 1), k = it >> lgF;
-          xk[u] = *reinterpret_cast<const float2*>(WT + (size_t)k * n + y0 + 2 * f);
-          if (k != 0) xnk[u] = *reinterpret_cast<const float2*>(WT + (size_t)(n - k) * n + y0 + 2 * f);
-        }
-      }
-#pragma unroll
-      for (int u = 0; u < kU; ++u) {
-        int it = base + u * blockDim.x;
-        if (it < total) {
-          int f = it & (F - 1), k = it >> lgF, nk = n - k;
-          buf[f * NP + pad(__ldg(&dr[k]))] = dct_pre(xk[u].x, xnk[u].x, xk[u].y, xnk[u].y, __ldg(&tw[k]));
-          if (k != 0 && k != half)
-            buf[f * NP + pad(__ldg(&dr[nk]))] = dct_pre(xnk[u].x, xk[u].x, xnk[u].y, xk[u].y, __ldg(&tw[nk]));
-        }
-      }
-    }
-    __syncthreads();
-    fft_inverse(buf, n, F, NP, tw);
-  }
+  if (!first) row_inverse(d, y0, buf);
 
   // fused elementwise update
   const float beta = P.beta, alpha = P.alpha;
@@ -302,22 +334,15 @@ __device__ void row_task(const PlanDev& P, int task, int step, float2* buf) {
   }
   __syncthreads();
   if (last) return;
-
-  fft_forward(buf, n, F, NP, tw);
-  for (int it = threadIdx.x; it < F * (half + 1); it += blockDim.x) {
-    int f = it & (F - 1), k = it >> lgF, nk = n - k;
-    float2 zk = buf[f * NP + pad(__ldg(&dr[k]))];
-    float2 znk = buf[f * NP + pad(__ldg(&dr[k == 0 ? 0 : nk]))];
-    *reinterpret_cast<float2*>(WT + (size_t)k * n + y0 + 2 * f) = dct_post(zk, znk, __ldg(&tw[k]));
-    if (k != 0 && k != half)
-      *reinterpret_cast<float2*>(WT + (size_t)nk * n + y0 + 2 * f) = dct_post(znk, zk, __ldg(&tw[nk]));
-  }
-  __syncthreads();
+  row_forward(d, y0, buf);
 }
 
 // ------------------------------------------------------------ column task
+// MODE 1: `step` is the 1-based transient step n of the source in the work
+// map; `commit` (implicit leakage, first iteration of a step) first folds the
+// previous step's final source spectrum into the history.
 template <int MODE>
-__device__ void col_task(const PlanDev& P, int task, float2* buf) {
+__device__ void col_task(const PlanDev& P, int task, float2* buf, int step = 0, bool commit = false) {
   const int b = find_map(P, task, false);
   const MapDesc d = P.maps[b];
   MapState* ms = P.st + b;
@@ -375,12 +400,44 @@ __device__ void col_task(const PlanDev& P, int task, float2* buf) {
         ynk = make_float2(0.f, 0.f);
       }
     } else {
-      // per-mode recursion: W = (1 - rho) X + rho W_prev;  Y = (K - A) X + A W
+      // Step response of a mode: S_j = (K - A) + A (1 - rho^j) (the primary
+      // alias relaxes with rho = exp(-dt / tau), the finer aliases settle in one step).
       auto mode = [&](size_t idx, float x) {
-        float rho = __ldg(&d.trRho[idx]), A = __ldg(&d.trA[idx]), K = __ldg(&d.Kt[idx]);
-        float w = fmaf(rho, d.state[idx] - x, x);
-        d.state[idx] = w;
-        return fmaf(K - A, x, A * w) * inv_n2;
+        const float A = __ldg(&d.trA[idx]), K = __ldg(&d.Kt[idx]);
+        if (P.window == 1) return K * x * inv_n2;               // every response settled
+        const float rho = __ldg(&d.trRho[idx]);
+        if (P.window == 0) {
+          // untruncated: W_n = (1 - rho) X_n + rho W_{n-1};  Y = (K - A) X_n + A W_n
+          float w = d.state[idx];
+          if (P.implicit) {
+            if (commit) {
+              w = fmaf(rho, w - P.xs[idx], P.xs[idx]);
+              d.state[idx] = w;
+            }
+            P.xs[idx] = x;
+            return fmaf(K - A, x, A * fmaf(rho, w - x, x)) * inv_n2;
+          }
+          w = fmaf(rho, w - x, x);
+          d.state[idx] = w;
+          return fmaf(K - A, x, A * w) * inv_n2;
+        }
+        // window K: S_j = K for j >= K, so
+        //   Y_n = K X_n - A sum_{j=1}^{K-1} rho^j (X_{n-j+1} - X_{n-j})
+        // from a ring of the last K - 1 sources (X_m in slot m mod (K - 1)).
+        const int R = P.window - 1;
+        const size_t nn = (size_t)d.n * d.n;
+        auto slot = [&](int m) { return (size_t)(((m % R) + R) % R) * nn + idx; };
+        if (P.implicit && commit) d.state[slot(step - 1)] = P.xs[idx];
+        float acc = 0.f, r = rho, prev = x;
+        for (int j = 1; j <= R; ++j) {
+          const float older = d.state[slot(step - j)];
+          acc = fmaf(r, prev - older, acc);
+          prev = older;
+          r *= rho;
+        }
+        if (P.implicit) P.xs[idx] = x;
+        else d.state[slot(step)] = x;
+        return fmaf(K, x, -A * acc) * inv_n2;
       };
       yk = make_float2(mode(ra + k, xk.x), mode(rb + k, xk.y));
       if (k != 0 && k != half) ynk = make_float2(mode(ra + nk, xnk.x), mode(rb + nk, xnk.y));
@@ -481,23 +538,147 @@ __global__ void __launch_bounds__(kThreads, 3) k_solve_steady(PlanDev P) {
   }
 }
 
+// ------------------------------------------------------------ transient, implicit leakage
+// Step s (0-based), iteration `it`: theta = phi(u) of the column phase's output
+// into theta[s]; max |theta - previous iterate| into *slot (the first
+// iterate of step s starts from theta_{s-1}, or 0).
+__device__ __noinline__ void row_tr_update(const PlanDev& P, int task, int s, int it, unsigned* slot,
+                              float2* buf) {
+  __shared__ float red_f[kThreads / 32];
+  __shared__ int red_i[kThreads / 32];
+  const int b = find_map(P, task, true);
+  const MapDesc d = P.maps[b];
+  const int n = d.n, F = d.rb >> 1, NP = padded_len(n), lgn = __ffs(n) - 1;
+  const int y0 = (task - d.row_off) * d.rb;
+  const size_t nn = (size_t)n * n;
+  row_inverse(d, y0, buf);
+  float* th_cur = d.theta + (size_t)s * nn;
+  const float* th_prev = (it > 1) ? th_cur : (s > 0 ? th_cur - nn : nullptr);
+  const float alpha = P.alpha;
+  float resid = 0.f;
+  int flags = 0;
+  for (int i = threadIdx.x; i < F * n; i += blockDim.x) {
+    const int f = i >> lgn, x = i & (n - 1);
+    const float2 uv = buf[f * NP + pad(makhoul_pos(x, n))];
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      const size_t idx = (size_t)(y0 + 2 * f + h) * n + x;
+      const float uu = h ? uv.y : uv.x;
+      const float sk = d.s ? __ldg(&d.s[idx]) : 1.f;
+      const float den = fmaf(-alpha * sk, uu, 1.f);
+      if (!(den > 0.05f)) flags |= kFlagRunaway;
+      const float th = sk * uu / den;
+      const float old = th_prev ? th_prev[idx] : 0.f;
+      if (!isfinite(th)) flags |= kFlagNonfinite;
+      else resid = fmaxf(resid, fabsf(th - old));
+      th_cur[idx] = th;
+    }
+  }
+  const float r = block_max(resid, red_f);
+  const int fl = block_or(flags, red_i);
+  if (threadIdx.x == 0) {
+    if (r > 0.f) atomicMax(slot, __float_as_uint(r));
+    if (fl) atomicOr(&P.st[b].flags, fl);
+  }
+  __syncthreads();
+}
+
+// Source q = P_dyn[src] + P_leak0 (1 + beta theta[s]) (theta = 0 for s < 0),
+// forward DCT along x into the work map.
+__device__ __noinline__ void row_tr_source(const PlanDev& P, int task, int src, int s, float2* buf) {
+  const int b = find_map(P, task, true);
+  const MapDesc d = P.maps[b];
+  const int n = d.n, F = d.rb >> 1, NP = padded_len(n), lgn = __ffs(n) - 1;
+  const int y0 = (task - d.row_off) * d.rb;
+  const size_t nn = (size_t)n * n;
+  const float* th = s >= 0 ? d.theta + (size_t)s * nn : nullptr;
+  const float* pd = d.p_dyn + (size_t)src * nn;
+  for (int i = threadIdx.x; i < F * n; i += blockDim.x) {
+    const int f = i >> lgn, x = i & (n - 1);
+    float q[2];
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      const size_t idx = (size_t)(y0 + 2 * f + h) * n + x;
+      const float t = th ? th[idx] : 0.f;
+      q[h] = __ldg(&pd[idx]) + __ldg(&d.p_leak0[idx]) * fmaf(P.beta, t, 1.f);
+    }
+    buf[f * NP + pad(makhoul_pos(x, n))] = make_float2(q[0], q[1]);
+  }
+  __syncthreads();
+  row_forward(d, y0, buf);
+}
+
+// Lagged leakage: P_n = P_dyn,n + P_leak0 (1 + beta theta_{n-1}), one column
+// and one row phase per step.
+__device__ bool transient_lagged(const PlanDev& P, float2* smem) {
+  for (int t = blockIdx.x; t < P.row_tasks; t += gridDim.x) row_task<1>(P, t, 0, smem);
+  if (!grid_barrier(P.ctrl)) return false;
+  for (int step = 1; step <= P.n_steps; ++step) {
+    for (int t = blockIdx.x; t < P.col_tasks; t += gridDim.x) col_task<1>(P, t, smem, step);
+    if (!grid_barrier(P.ctrl)) return false;
+    for (int t = blockIdx.x; t < P.row_tasks; t += gridDim.x) row_task<1>(P, t, step, smem);
+    if (!grid_barrier(P.ctrl)) return false;
+  }
+  return true;
+}
+
+// Implicit leakage: P_n = P_dyn,n + P_leak0 (1 + beta theta_n); every step
+// iterates theta <- phi(u_n(P_n(theta))) from theta_{n-1} until the change is
+// <= tol or max_iter iterations. The history takes the source of the last
+// iteration. Every block reads the same residual word after the barrier, so
+// all take the same decision. The plan holds one map.
+__device__ __noinline__ bool transient_implicit(const PlanDev& P, float2* smem) {
+  unsigned* slot = P.ctrl->active;          // two residual words, used alternately
+  MapState* ms = P.st;
+  for (int t = blockIdx.x; t < P.row_tasks; t += gridDim.x) row_tr_source(P, t, 0, -1, smem);
+  if (!grid_barrier(P.ctrl)) return false;
+  int g = 0;
+  for (int s = 0; s < P.n_steps; ++s) {
+    for (int it = 1; it <= P.max_iter; ++it) {
+      const int cur = g & 1;
+      ++g;
+      for (int t = blockIdx.x; t < P.col_tasks; t += gridDim.x)
+        col_task<1>(P, t, smem, s + 1, it == 1 && s > 0);
+      if (!grid_barrier(P.ctrl)) return false;
+      for (int t = blockIdx.x; t < P.row_tasks; t += gridDim.x)
+        row_tr_update(P, t, s, it, slot + cur, smem);
+      if (!grid_barrier(P.ctrl)) return false;
+      const float r = __uint_as_float(ld_acquire(slot + cur));
+      const bool bad = ld_acquire(reinterpret_cast<const unsigned*>(&ms->flags)) & kFlagNonfinite;
+      const bool done = r <= P.tol || it == P.max_iter || bad;
+      if (blockIdx.x == 0 && threadIdx.x == 0) {
+        // every block read the other word one iteration ago, before this
+        // iteration's barriers
+        slot[cur ^ 1] = 0u;
+        if (done) {
+          ms->iters += it;
+          ms->prev_resid = fmaxf(ms->prev_resid, r);
+          if (r > P.tol) ms->growth = 1;     // a step ended unconverged
+        }
+      }
+      if (done && s == P.n_steps - 1) break;
+      for (int t = blockIdx.x; t < P.row_tasks; t += gridDim.x)
+        row_tr_source(P, t, done ? s + 1 : s, s, smem);
+      if (!grid_barrier(P.ctrl)) return false;
+      if (done) break;
+    }
+  }
+  return true;
+}
+
 __global__ void __launch_bounds__(kThreads, 3) k_solve_transient(PlanDev P) {
   extern __shared__ float2 smem[];
-  for (int t = blockIdx.x; t < P.row_tasks; t += gridDim.x) row_task<1>(P, t, 0, smem);
-  if (!grid_barrier(P.ctrl)) return;
-  for (int step = 1; step <= P.n_steps; ++step) {
-    for (int t = blockIdx.x; t < P.col_tasks; t += gridDim.x) col_task<1>(P, t, smem);
-    if (!grid_barrier(P.ctrl)) return;
-    for (int t = blockIdx.x; t < P.row_tasks; t += gridDim.x) row_task<1>(P, t, step, smem);
-    if (!grid_barrier(P.ctrl)) return;
-  }
+  if (!(P.implicit ? transient_implicit(P, smem) : transient_lagged(P, smem))) return;
   if (blockIdx.x == 0 && threadIdx.x == 0) {
     for (int b = 0; b < P.n_maps; ++b) {
       MapState s = P.st[b];
-      s.iters = P.n_steps;
       s.status = (s.flags & kFlagNonfinite) ? VS_ERR_NONFINITE
-                 : (s.flags & kFlagRunaway) ? VS_ERR_RUNAWAY : VS_OK;
-      s.prev_resid = 0.f;
+                 : (s.flags & kFlagRunaway) ? VS_ERR_RUNAWAY
+                 : (P.implicit && s.growth) ? VS_ERR_NO_CONVERGENCE : VS_OK;
+      if (!P.implicit) {
+        s.iters = P.n_steps;
+        s.prev_resid = 0.f;
+      }
       s.mu = 0.0;
       P.st[b] = s;
       write_info(P, b, s);
@@ -1109,6 +1290,9 @@ struct vs_plan_t {
   float* d_work = nullptr;
   float* d_trstate = nullptr;
   int transient_steps = 0;
+  int tr_window = 0;                          // transient options (vs_transient_opts)
+  int tr_implicit = 0;
+  int tr_slices = 1;                          // n*n slices of per-mode state per map
   int warm = 0;
   bool cluster = false;                       // cluster engine
   std::vector<std::pair<int, int>> cl_groups; // (n, maps) per launch, in order
@@ -1197,11 +1381,12 @@ int plan_layout(vs_plan_t* p, int elems, cudaStream_t s, bool transient, int n_s
   p->part_total = part_off;
   p->smem = smem;
   VS_CUDA_TRY(cudaMalloc(&p->d_work, work_total * sizeof(float)));
-  if (transient) VS_CUDA_TRY(cudaMalloc(&p->d_trstate, work_total * sizeof(float)));
+  if (transient)
+    VS_CUDA_TRY(cudaMalloc(&p->d_trstate, work_total * (size_t)p->tr_slices * sizeof(float)));
   size_t off = 0;
   for (int i = 0; i < n_items; ++i) {
     maps[i].work = p->d_work + off;
-    maps[i].state = transient ? p->d_trstate + off : nullptr;
+    maps[i].state = transient ? p->d_trstate + off * p->tr_slices : nullptr;
     off += (size_t)maps[i].n * maps[i].n;
     if (tc) {
       maps[i].work2 = p->d_work + off;
@@ -1408,6 +1593,13 @@ int plan_launch(vs_plan_t* p, cudaStream_t s, bool transient) {
   P.tol = (float)p->params.tol_K;
   P.n_steps = p->transient_steps;
   P.warm = p->warm;
+  P.window = transient ? p->tr_window : 0;
+  P.implicit = transient ? p->tr_implicit : 0;
+  // the implicit transient keeps the current step's source spectrum in the
+  // last state slice (one map per transient plan)
+  P.xs = (transient && p->tr_implicit)
+             ? p->d_trstate + (size_t)(p->tr_slices - 1) * p->items[0].k->n * p->items[0].k->n
+             : nullptr;
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3(p->grid);
   cfg.blockDim = dim3(p->params.precision == VS_PREC_BF16_SPLIT && !transient ? kTcThreads : kThreads);
@@ -1615,16 +1807,21 @@ extern "C" int vs_solve_steady(vs_kernel k, const float* p_dyn, const float* p_l
   return rc;
 }
 
-extern "C" int vs_solve_transient(vs_kernel k, int n_steps, const float* p_dyn_trace,
-                                  const float* p_leak0, const float* s_kappa,
-                                  const vs_solve_params* params, float* theta_trace,
-                                  vs_solve_info* info_host, void* stream) {
+extern "C" int vs_solve_transient_ex(vs_kernel k, int n_steps, const float* p_dyn_trace,
+                                     const float* p_leak0, const float* s_kappa,
+                                     const vs_solve_params* params, const vs_transient_opts* opts,
+                                     float* theta_trace, vs_solve_info* info_host, void* stream) {
   if (!k) return vs_set_error(VS_ERR_INVALID_ARG, "NULL kernel");
   if (!(k->dt > 0.0) || !k->trA)
     return vs_set_error(VS_ERR_INVALID_ARG, "kernel was built without a time step (dt_s = 0)");
   if (n_steps < 1 || n_steps > 1000000) return vs_set_error(VS_ERR_INVALID_ARG, "n_steps %d", n_steps);
   int rc = vs_validate_params(params);
   if (rc) return rc;
+  const vs_transient_opts o = opts ? *opts : vs_transient_opts{0, VS_LEAK_LAGGED};
+  if (o.window < 0 || o.window > VS_MAX_WINDOW)
+    return vs_set_error(VS_ERR_INVALID_ARG, "window %d not in 0..%d", o.window, VS_MAX_WINDOW);
+  if (o.leakage != VS_LEAK_LAGGED && o.leakage != VS_LEAK_IMPLICIT)
+    return vs_set_error(VS_ERR_INVALID_ARG, "leakage mode %d", o.leakage);
   if (!p_dyn_trace || !p_leak0 || !theta_trace)
     return vs_set_error(VS_ERR_INVALID_ARG, "NULL map");
   uintptr_t al = (uintptr_t)p_dyn_trace | (uintptr_t)p_leak0 | (uintptr_t)theta_trace |
@@ -1635,11 +1832,17 @@ extern "C" int vs_solve_transient(vs_kernel k, int n_steps, const float* p_dyn_t
   p->n_items = 1;
   p->items.push_back(vs_batch_item{k, p_dyn_trace, p_leak0, s_kappa, theta_trace, nullptr});
   p->params = *params;
+  p->tr_window = o.window;
+  p->tr_implicit = o.leakage == VS_LEAK_IMPLICIT;
+  // per-mode history: the recursion state W (untruncated) or a ring of the
+  // last window - 1 source spectra; plus the current source (implicit)
+  p->tr_slices = std::max(1, o.window == 0 ? 1 : o.window - 1) + p->tr_implicit;
   // a single map: tasks of 4096 elements (4 rows at 1024^2) spread it over more
   // CTAs than the 8192 of batched plans (measured 46 vs 57 us per 1024^2 step)
   rc = plan_layout(p, 4096, s, true, n_steps);
   if (rc == VS_OK) {
-    cudaError_t e = cudaMemsetAsync(p->d_trstate, 0, sizeof(float) * (size_t)k->n * k->n, s);
+    cudaError_t e = cudaMemsetAsync(p->d_trstate, 0,
+                                    sizeof(float) * (size_t)k->n * k->n * p->tr_slices, s);
     if (e != cudaSuccess) rc = vs_set_error(VS_ERR_CUDA, "memset: %s", cudaGetErrorString(e));
   }
   if (rc == VS_OK) rc = plan_launch(p, s, true);
@@ -1652,6 +1855,14 @@ extern "C" int vs_solve_transient(vs_kernel k, int n_steps, const float* p_dyn_t
   plan_release(p);
   delete p;
   return rc;
+}
+
+extern "C" int vs_solve_transient(vs_kernel k, int n_steps, const float* p_dyn_trace,
+                                  const float* p_leak0, const float* s_kappa,
+                                  const vs_solve_params* params, float* theta_trace,
+                                  vs_solve_info* info_host, void* stream) {
+  return vs_solve_transient_ex(k, n_steps, p_dyn_trace, p_leak0, s_kappa, params, nullptr,
+                               theta_trace, info_host, stream);
 }
 
 // ---------------------------------------------------------------------------

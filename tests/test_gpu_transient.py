@@ -68,3 +68,91 @@ def test_transient_first_step_is_single_pole_response():
         S = so.step_spectrum(w.n, w.die_m, st.thickness_m, st.kappa_W_mK, st.h_conv_W_m2K,
                              st.heat_cap_J_m2K, (j + 1) * dt)
         assert float(th[j].double().mean()) == pytest.approx(1e-3 * S[0, 0], rel=1e-4)
+
+
+# ---------------------------------------------------------------- variants
+
+def _tr_case(steps, dt=1e-3, config="c1_64"):
+    vs = _vs()
+    w = synth.workload(config)
+    trace = synth.markov_trace(w, steps, device="cuda")
+    _, pl, s = synth.steady_inputs(w, 1, device="cuda")
+    k = vs.Kernel(vs_stack(w), vs.Grid(w.n, w.die_m), vs.KernelOpts(dt_s=dt))
+    return vs, w, k, trace, pl[0], s[0]
+
+
+def _oracle_variant(w, trace, pl, s, dt, window, implicit):
+    st = w.stack
+    need = trace.shape[0] if window == 0 else min(window - 1, trace.shape[0])
+    spectra = [so.step_spectrum(w.n, w.die_m, st.thickness_m, st.kappa_W_mK, st.h_conv_W_m2K,
+                                st.heat_cap_J_m2K, j * dt) for j in range(1, need + 1)]
+    Kt = ph.spectrum(w.n, w.die_m, st.thickness_m, st.kappa_W_mK, st.h_conv_W_m2K)
+    f64 = lambda t: t.double().cpu().numpy()
+    return so.transient_variants(spectra, Kt, f64(trace), f64(pl), f64(s), w.physics.beta_per_K,
+                                 w.physics.alpha_per_K, window=window, implicit=implicit,
+                                 tol=1e-10)
+
+
+@pytest.mark.parametrize("window", [1, 2, 5, 12])
+def test_windowed_superposition_matches_oracle(window):
+    dt, steps = 1e-3, 24
+    vs, w, k, trace, pl, s = _tr_case(steps, dt)
+    th, info = vs.solve_transient(k, trace, pl, s, vs_params(w), window=window)
+    assert info["status"] == vs.VS_OK and info["iterations"] == steps
+    ref, _ = _oracle_variant(w, trace, pl, s, dt, window, False)
+    emax, rel = errors(th, ref)
+    assert emax <= 5e-3 and rel <= 2e-4
+
+
+@pytest.mark.parametrize("window", [0, 5])
+def test_implicit_leakage_matches_oracle(window):
+    dt, steps = 1e-3, 16
+    vs, w, k, trace, pl, s = _tr_case(steps, dt)
+    th, info = vs.solve_transient(k, trace, pl, s, vs_params(w, tol_K=1e-4), window=window,
+                                  leakage=vs.VS_LEAK_IMPLICIT)
+    assert info["status"] == vs.VS_OK
+    assert info["residual_K"] <= 1e-4
+    ref, its = _oracle_variant(w, trace, pl, s, dt, window, True)
+    emax, rel = errors(th, ref)
+    assert emax <= 5e-3 and rel <= 2e-4
+    # the GPU stops at 1e-4 K, the oracle at 1e-10 K: it takes fewer iterations
+    assert steps <= info["iterations"] <= int(its.sum())
+    # the implicit solution differs from the lagged one by more than the tolerance
+    lag, _ = vs.solve_transient(k, trace, pl, s, vs_params(w), window=window)
+    assert float((th - lag).abs().max()) > 1e-3
+
+
+def test_implicit_reports_unconverged_steps():
+    vs, w, k, trace, pl, s = _tr_case(6)
+    th, info = vs.solve_transient(k, trace, pl, s, vs_params(w, tol_K=1e-9, max_iter=2),
+                                  leakage=vs.VS_LEAK_IMPLICIT)
+    assert info["status"] == vs.VS_ERR_NO_CONVERGENCE
+    assert info["iterations"] == 12 and info["residual_K"] > 1e-9
+    assert bool(torch.isfinite(th).all())
+
+
+@pytest.mark.parametrize("config,steps", [("c2_256", 40), ("c4_1024", 200)])
+def test_variants_reduce_to_the_untruncated_lagged_solve(config, steps):
+    # properties that hold at any size, checked at the bench's 1024^2 x 200:
+    # a window longer than the trace is the untruncated sum, and without
+    # leakage feedback the implicit steps equal the lagged ones
+    vs, w, k, trace, pl, s = _tr_case(steps, 1e-3, config)
+    prm = vs_params(w)
+    ref, _ = vs.solve_transient(k, trace, pl, s, prm)
+    long_, info = vs.solve_transient(k, trace, pl, s, prm, window=min(steps + 1, vs.VS_MAX_WINDOW))
+    assert info["status"] == vs.VS_OK
+    scale = float(ref.abs().max())
+    assert float((long_ - ref).abs().max()) <= 2e-5 * scale
+    nofb = vs_params(w, beta_per_K=0.0)
+    a, _ = vs.solve_transient(k, trace, pl, s, nofb)
+    b, info = vs.solve_transient(k, trace, pl, s, nofb, leakage=vs.VS_LEAK_IMPLICIT)
+    assert info["status"] == vs.VS_OK and info["iterations"] <= 2 * steps
+    assert float((a - b).abs().max()) <= 2e-5 * scale
+
+
+def test_transient_options_are_validated():
+    vs, w, k, trace, pl, s = _tr_case(2)
+    for kw in ({"window": -1}, {"window": vs.VS_MAX_WINDOW + 1}, {"leakage": 7}):
+        with pytest.raises(vs.VarsimError) as e:
+            vs.solve_transient(k, trace, pl, s, vs_params(w), **kw)
+        assert e.value.status == vs.VS_ERR_INVALID_ARG
