@@ -152,6 +152,43 @@ def shift_invariant(Kt, p_dyn, p_leak0, beta):
 
 
 # --------------------------------------------------------------------------- #
+# One-shot closed form (Sec. IV-C, Eqs. 21, 25, 26)                             #
+# --------------------------------------------------------------------------- #
+
+def closed_form(Kt, p_dyn, p_leak0, s, beta, alpha, mode="conv"):
+    """The paper's one-shot modified Green's functions combined by convolution
+    and Hadamard product, instead of the iterated fixed point.
+
+    Readings (the paper's Lemma I and F(mu) terms are not computable as printed):
+    * deterministic part, Eq. 21 without its alpha term (F(mu) of a constant is
+      a delta; alpha acts through phi at the field point as in the fixed point):
+      L_det = K~ / (1 - beta mu K~), applied to the whole source P_dyn + P_leak0
+      (a convolution, exact for the mean and for the variation's own heat);
+    * random part, Eq. 25 to first order in the variation (the Q term of its
+      denominator dropped, as the paper drops term V): per unit of variation
+      the response is beta L_det^2 applied to the source;
+    * Eq. 26: that response times the local variation P_leak0 - mu (Hadamard
+      product). mode "conv" applies it to the actual power map; mode "impulse"
+      takes the paper's form literally: the response to a unit impulse at the
+      die's centre cell (n/2, n/2), scaled by the total power of the map.
+    theta = phi(u_det + (P_leak0 - mu) * r, s, alpha)."""
+    n = p_dyn.shape[-1]
+    mu = float(np.mean(p_leak0))
+    Ld = Kt / (1.0 - beta * mu * Kt)
+    q = p_dyn + p_leak0
+    u_det = spectral_convolve(Ld, q)
+    if mode == "conv":
+        r = spectral_convolve(beta * Ld * Ld, q)
+    elif mode == "impulse":
+        e = np.zeros((n, n))
+        e[n // 2, n // 2] = 1.0
+        r = spectral_convolve(beta * Ld * Ld, e) * float(np.sum(q))
+    else:
+        raise ValueError(mode)
+    return phi(u_det + (p_leak0 - mu) * r, s, alpha)
+
+
+# --------------------------------------------------------------------------- #
 # Transient (Eqs. 27-37)                                                        #
 # --------------------------------------------------------------------------- #
 

@@ -335,6 +335,84 @@ def test_duhamel_superposition_without_feedback():
     assert np.allclose(tc[4], so.spectral_convolve(spectra[4], a[0]), rtol=1e-12)
 
 
+# ------------------------------------------ P9b: one-shot closed form
+
+def _cf_case(n=8, sigma=0.3, seed=9):
+    t, kap, h = STACK3
+    L = 10e-3
+    rng = np.random.default_rng(seed)
+    pd = rng.random((n, n)) * 0.05
+    pl = 0.02 * np.exp(sigma * rng.standard_normal((n, n)))
+    return n, L, t, kap, h, pd, pl
+
+
+def test_closed_form_is_exact_without_variation():
+    # uniform leakage, alpha = 0: Eq. 21 is the exact fixed point
+    n, L, t, kap, h, pd, _ = _cf_case()
+    Kt = ph.spectrum(n, L, t, kap, h)
+    pl = np.full((n, n), 0.03)
+    one = np.ones((n, n))
+    ex, _, _ = so.picard(lambda x: so.spectral_convolve(Kt, x), pd, pl, one, 0.0275, 0.0, tol=1e-13)
+    for mode in ("conv", "impulse"):
+        assert np.allclose(so.closed_form(Kt, pd, pl, one, 0.0275, 0.0, mode), ex, rtol=1e-10)
+
+
+def test_closed_form_without_feedback_is_the_image_convolution():
+    n, L, t, kap, h, pd, pl = _cf_case()
+    Kt = ph.spectrum(n, L, t, kap, h)
+    Lm = so.mirror_operator(ph.kernel_periodic(n, L, t, kap, h))
+    s = 1.0 - 0.05 * np.random.default_rng(2).random((n, n))
+    alpha = 1.2e-3
+    u = so.direct_convolve(Lm, pd + pl)
+    assert np.allclose(so.closed_form(Kt, pd, pl, s, 0.0, alpha), s * u / (1 - alpha * s * u),
+                       rtol=1e-10)
+
+
+def test_closed_form_random_part_by_dense_image_operators():
+    # u = L_det (P_dyn + P_leak0) + P_var * (beta L_det L_det (P_dyn + P_leak0)) with
+    # L_det = (I - beta mu L)^-1 L built from the dense mirror-image matrix
+    n, L, t, kap, h, pd, pl = _cf_case()
+    Kt = ph.spectrum(n, L, t, kap, h)
+    Lm = so.mirror_operator(ph.kernel_periodic(n, L, t, kap, h))
+    beta, mu = 0.0275, float(np.mean(pl))
+    Ld = np.linalg.solve(np.eye(n * n) - beta * mu * Lm, Lm)
+    q = (pd + pl).ravel()
+    u = Ld @ q + (pl - mu).ravel() * (beta * (Ld @ (Ld @ q)))
+    one = np.ones((n, n))
+    assert np.allclose(so.closed_form(Kt, pd, pl, one, beta, 0.0), u.reshape(n, n), rtol=1e-9)
+
+
+def test_closed_form_impulse_mode_is_exact_for_a_centred_impulse():
+    # the paper's scaling by the total power is exact when the source is one
+    # impulse at the centre
+    n, L, t, kap, h, _, pl = _cf_case()
+    Kt = ph.spectrum(n, L, t, kap, h)
+    src = np.zeros((n, n))
+    src[n // 2, n // 2] = 0.7
+    pd = src - pl
+    one = np.ones((n, n))
+    a = so.closed_form(Kt, pd, pl, one, 0.0275, 1e-3, "conv")
+    b = so.closed_form(Kt, pd, pl, one, 0.0275, 1e-3, "impulse")
+    assert np.allclose(a, b, rtol=1e-12)
+
+
+def test_closed_form_error_is_first_order_in_the_variation():
+    # the Hadamard step is exact at zero variation and its error grows
+    # linearly with the variation's amplitude
+    n, L, t, kap, h, pd, _ = _cf_case()
+    Kt = ph.spectrum(n, L, t, kap, h)
+    v = np.random.default_rng(4).standard_normal((n, n))
+    v -= v.mean()
+    one = np.ones((n, n))
+    errs = []
+    for eps in (4e-3, 2e-3, 1e-3):
+        pl = 0.03 + eps * v
+        ex, _, _ = so.picard(lambda x: so.spectral_convolve(Kt, x), pd, pl, one, 0.0275, 0.0,
+                             tol=1e-14)
+        errs.append(np.max(np.abs(so.closed_form(Kt, pd, pl, one, 0.0275, 0.0) - ex)))
+    assert 1.6 < errs[0] / errs[1] < 2.4 and 1.6 < errs[1] / errs[2] < 2.4
+
+
 # ------------------------------------ P10b: windowed / implicit transient
 
 @functools.lru_cache(maxsize=None)
