@@ -554,6 +554,41 @@ def run_ours(a):
         extras["kernel_build_ms"] = dict(builds, how="vs_make_kernel wall time (Hankel quadrature, "
                                          "fold, cosine sums, spectral part), FP64 on the GPU")
 
+        # The paper's one-shot closed form (Eqs. 21, 25, 26) on the headline batch:
+        # throughput, and its error against the converged maps of the headline path
+        cf = {}
+        th_cf = torch.empty_like(pd)
+        for mode, name in ((vs.VS_CF_CONV, "conv"), (vs.VS_CF_IMPULSE, "impulse")):
+            for _ in range(max(3, a.warmup)):
+                vs.solve_closed_form(k, pd, pl, s, mk(vs.VS_PREC_FP32), mode, th_cf, stream, info=False)
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            for _ in range(a.steps):
+                vs.solve_closed_form(k, pd, pl, s, mk(vs.VS_PREC_FP32), mode, th_cf, stream, info=False)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            ms_cf = e0.elapsed_time(e1) / a.steps
+            _, infos_cf = vs.solve_closed_form(k, pd, pl, s, mk(vs.VS_PREC_FP32), mode, th_cf, stream)
+            rise_b = th_best.amax(dim=(1, 2))
+            rel_err = ((th_cf - th_best).abs().amax(dim=(1, 2)) / rise_b)
+            algo = B * w.n * w.n * 16                 # read P_dyn, P_leak0, s; write theta
+            cf[name] = {"value": whole_job_rate(1, B, ms_cf * 1e-3), "unit": UNIT, "ms_per_step": ms_cf,
+                        "not_ok": sum(1 for i in infos_cf if i["status"] != vs.VS_OK),
+                        "err_pct_of_max_rise": {"max": 100 * float(rel_err.max()),
+                                                "mean": 100 * float(rel_err.mean())},
+                        "roofline": {"bound": "hbm", "achieved": algo / (ms_cf * 1e-3) / 1e9,
+                                     "peak": _peaks()[0], "unit": "GB/s",
+                                     "frac": algo / (ms_cf * 1e-3) / 1e9 / _peaks()[0],
+                                     "traffic": None, "kernel": "k_cf_rows_fwd + k_cf_cols + "
+                                     "k_cf_rows_inv",
+                                     "note": "16 B/pixel algorithmic (3 maps in, theta out); the "
+                                             "three passes also move 24 B/pixel of spectra"}}
+        del th_cf
+        extras["closed_form"] = dict(cf, how="vs_solve_closed_form over the %d-map batch (4 launches, "
+                                     "CUDA events, inputs > L2); error against the headline path's "
+                                     "converged maps (tolerance %.0e K)" % (B, tol))
+
     # e2e: pinned host inputs -> device -> headline path -> host theta, every step
     e2e = None
     if not a.no_e2e:

@@ -339,6 +339,33 @@ int vs_solve_transient_ex(vs_kernel k, int n_steps, const float* p_dyn_trace,
                           float* theta_trace, vs_solve_info* info_host, void* stream);
 
 /* ------------------------------------------------------------------------ */
+/* One-shot closed form (Sec. IV-C: Eqs. 21, 25, 26), the paper's own       */
+/* alternative to iterating the fixed point.                                */
+/* ------------------------------------------------------------------------ */
+
+/* For `count` maps of one kernel ([count][n][n] device float32, 16-byte
+ * aligned; s_kappa may be NULL => 1):
+ *   u = L_det * (P_dyn + P_leak0) + (P_leak0 - mu) . r,  theta = phi(u),
+ *   L_det = K~ / (1 - beta mu K~)  (Eq. 21 without its alpha term, which the
+ *   paper derives through Lemma I; alpha acts through phi as in the solve),
+ *   r = beta L_det^2 * (P_dyn + P_leak0)            (VS_CF_CONV: Eq. 25 to
+ *       first order in the variation, applied to the power map), or
+ *   r = (beta L_det^2 * impulse at cell (n/2, n/2)) sum(P_dyn + P_leak0)
+ *                                                   (VS_CF_IMPULSE: Eq. 26's
+ *       total-power scaling of the impulse response, literally),
+ * with * the mirror-image convolution and . the Hadamard product. No
+ * iteration: the result differs from the fixed point of vs_solve_steady by
+ * the approximation. Four kernel launches; scratch 8 bytes per cell from the
+ * stream-ordered allocator. info_host (may be NULL => no synchronisation)
+ * gets status VS_OK, VS_ERR_RUNAWAY or VS_ERR_NONFINITE per map,
+ * iterations 0, residual_K 0 and mu_W. */
+#define VS_CF_CONV 0
+#define VS_CF_IMPULSE 1
+int vs_solve_closed_form(vs_kernel k, int count, const float* p_dyn, const float* p_leak0,
+                         const float* s_kappa, const vs_solve_params* params, int mode,
+                         float* theta, vs_solve_info* info_host, void* stream);
+
+/* ------------------------------------------------------------------------ */
 /* Learned warm start of the fixed point. The paper iterates power ->       */
 /* temperature -> leakage until convergence (Sec. V-C); these calls predict */
 /* most of the remaining correction after the first iterate so that the     */

@@ -26,6 +26,7 @@ __all__ = [
     "VS_ENGINE_STREAMED", "VS_ENGINE_CLUSTER", "Model", "WarmPlan",
     "warm_features", "warm_target", "warm_apply", "VS_WARM_FIRST", "VS_WARM_PREDICT",
     "VS_WARM_SOLVE", "VS_WARM_ALL", "VS_LEAK_LAGGED", "VS_LEAK_IMPLICIT", "VS_MAX_WINDOW",
+    "VS_CF_CONV", "VS_CF_IMPULSE", "solve_closed_form",
 ]
 
 VS_OK, VS_ERR_INVALID_ARG, VS_ERR_CUDA, VS_ERR_OOM = 0, 1, 2, 3
@@ -34,6 +35,7 @@ VS_PREC_FP32, VS_PREC_BF16_SPLIT = 0, 1
 VS_ENGINE_AUTO, VS_ENGINE_STREAMED, VS_ENGINE_CLUSTER = 0, 1, 2
 VS_WARM_FIRST, VS_WARM_PREDICT, VS_WARM_SOLVE, VS_WARM_ALL = 1, 2, 4, 7
 VS_LEAK_LAGGED, VS_LEAK_IMPLICIT, VS_MAX_WINDOW = 0, 1, 256
+VS_CF_CONV, VS_CF_IMPULSE = 0, 1
 VS_MAX_LAYERS = 8
 
 EXPORTS = [
@@ -46,7 +48,7 @@ EXPORTS = [
     "vs_model_train", "vs_model_save", "vs_model_load", "vs_warm_features", "vs_warm_target",
     "vs_warm_apply", "vs_solve_batch_host", "vs_model_shape", "vs_warm_plan_create",
     "vs_warm_plan_run", "vs_warm_plan_launches", "vs_warm_plan_info", "vs_warm_plan_free",
-    "vs_solve_transient_ex",
+    "vs_solve_transient_ex", "vs_solve_closed_form",
 ]
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
@@ -135,6 +137,8 @@ def lib():
                                     C.POINTER(_SolveInfo), vp]),
         "vs_solve_transient_ex": (ip, [vp, ip, vp, vp, vp, C.POINTER(_SolveParams),
                                        C.POINTER(_TransientOpts), vp, C.POINTER(_SolveInfo), vp]),
+        "vs_solve_closed_form": (ip, [vp, ip, vp, vp, vp, C.POINTER(_SolveParams), ip, vp,
+                                      vp, vp]),
         "vs_tc_transform": (ip, [vp, vp, ip, ip, ip, vp]),
         "vs_model_create": (ip, [ip, ip, C.c_ulonglong, C.POINTER(vp)]),
         "vs_free_model": (None, [vp]),
@@ -479,6 +483,27 @@ def solve_transient(kernel: Kernel, p_dyn_trace, p_leak0, s_kappa=None,
                                        C.byref(info), _stream(stream)),
            "vs_solve_transient_ex", ok=_SOLVE_OK)
     return theta_trace, _info(info)
+
+
+def solve_closed_form(kernel: Kernel, p_dyn, p_leak0, s_kappa=None,
+                      params: Optional[SolveParams] = None, mode: int = VS_CF_CONV,
+                      theta=None, stream=None, info: bool = True):
+    """One-shot closed form (vs_solve_closed_form) of maps [B, n, n]; returns
+    (theta, infos) -- infos is None with info=False (no synchronisation)."""
+    import torch
+    n = kernel.n
+    prm = params or SolveParams()
+    B = p_dyn.shape[0]
+    if theta is None:
+        theta = torch.empty_like(p_dyn)
+    arr = (_SolveInfo * B)() if info else None
+    _check(lib().vs_solve_closed_form(kernel.handle, B, _ptr(p_dyn, n, "p_dyn"),
+                                      _ptr(p_leak0, n, "p_leak0"),
+                                      _ptr(s_kappa, n, "s_kappa", allow_none=True),
+                                      C.byref(prm._c()), mode, _ptr(theta, n, "theta"),
+                                      C.cast(arr, C.c_void_p) if info else None, _stream(stream)),
+           "vs_solve_closed_form", ok=_SOLVE_OK)
+    return theta, ([_info(a) for a in arr] if info else None)
 
 
 # --------------------------------------------------------------------------
