@@ -535,10 +535,11 @@ def run_ours(a):
             out_v = torch.empty_like(trace)
             dt_v, info_v = run_transient(out_v, **opts)
             dev_v = float((out_v - out_t).abs().max())
+            dev_late = float((out_v[steps_t // 2:] - out_t[steps_t // 2:]).abs().max())
             variants_t[name] = {"ms_per_step": 1e3 * dt_v / steps_t, "status": info_v["status"],
                                 "fixed_point_iterations_per_step": info_v["iterations"] / steps_t,
                                 "max_abs_dev_K": dev_v, "dev_pct_of_max_rise": 100 * dev_v / rise,
-                                "against": against}
+                                "max_abs_dev_K_second_half": dev_late, "against": against}
             del out_v
         extras["transient"]["variants"] = variants_t
         extras["transient"]["max_rise_K"] = rise

@@ -339,9 +339,10 @@ __device__ void row_task(const PlanDev& P, int task, int step, float2* buf) {
 
 // ------------------------------------------------------------ column task
 // MODE 1: `step` is the 1-based transient step n of the source in the work
-// map; `commit` (implicit leakage, first iteration of a step) first folds the
+// map. VAR: the variants (window, implicit leakage) are compiled in; then
+// `commit` (implicit leakage, first iteration of a step) first folds the
 // previous step's final source spectrum into the history.
-template <int MODE>
+template <int MODE, bool VAR = false>
 __device__ void col_task(const PlanDev& P, int task, float2* buf, int step = 0, bool commit = false) {
   const int b = find_map(P, task, false);
   const MapDesc d = P.maps[b];
@@ -404,6 +405,12 @@ __device__ void col_task(const PlanDev& P, int task, float2* buf, int step = 0, 
       // alias relaxes with rho = exp(-dt / tau), the finer aliases settle in one step).
       auto mode = [&](size_t idx, float x) {
         const float A = __ldg(&d.trA[idx]), K = __ldg(&d.Kt[idx]);
+        if (!VAR) {
+          const float rho = __ldg(&d.trRho[idx]);
+          const float w = fmaf(rho, d.state[idx] - x, x);
+          d.state[idx] = w;
+          return fmaf(K - A, x, A * w) * inv_n2;
+        }
         if (P.window == 1) return K * x * inv_n2;               // every response settled
         const float rho = __ldg(&d.trRho[idx]);
         if (P.window == 0) {
@@ -610,11 +617,12 @@ __device__ __noinline__ void row_tr_source(const PlanDev& P, int task, int src, 
 
 // Lagged leakage: P_n = P_dyn,n + P_leak0 (1 + beta theta_{n-1}), one column
 // and one row phase per step.
-__device__ bool transient_lagged(const PlanDev& P, float2* smem) {
+template <bool VAR>
+__device__ __forceinline__ bool transient_lagged(const PlanDev& P, float2* smem) {
   for (int t = blockIdx.x; t < P.row_tasks; t += gridDim.x) row_task<1>(P, t, 0, smem);
   if (!grid_barrier(P.ctrl)) return false;
   for (int step = 1; step <= P.n_steps; ++step) {
-    for (int t = blockIdx.x; t < P.col_tasks; t += gridDim.x) col_task<1>(P, t, smem, step);
+    for (int t = blockIdx.x; t < P.col_tasks; t += gridDim.x) col_task<1, VAR>(P, t, smem, step);
     if (!grid_barrier(P.ctrl)) return false;
     for (int t = blockIdx.x; t < P.row_tasks; t += gridDim.x) row_task<1>(P, t, step, smem);
     if (!grid_barrier(P.ctrl)) return false;
@@ -638,7 +646,7 @@ __device__ __noinline__ bool transient_implicit(const PlanDev& P, float2* smem) 
       const int cur = g & 1;
       ++g;
       for (int t = blockIdx.x; t < P.col_tasks; t += gridDim.x)
-        col_task<1>(P, t, smem, s + 1, it == 1 && s > 0);
+        col_task<1, true>(P, t, smem, s + 1, it == 1 && s > 0);
       if (!grid_barrier(P.ctrl)) return false;
       for (int t = blockIdx.x; t < P.row_tasks; t += gridDim.x)
         row_tr_update(P, t, s, it, slot + cur, smem);
@@ -666,9 +674,7 @@ __device__ __noinline__ bool transient_implicit(const PlanDev& P, float2* smem) 
   return true;
 }
 
-__global__ void __launch_bounds__(kThreads, 3) k_solve_transient(PlanDev P) {
-  extern __shared__ float2 smem[];
-  if (!(P.implicit ? transient_implicit(P, smem) : transient_lagged(P, smem))) return;
+__device__ __forceinline__ void transient_info(const PlanDev& P) {
   if (blockIdx.x == 0 && threadIdx.x == 0) {
     for (int b = 0; b < P.n_maps; ++b) {
       MapState s = P.st[b];
@@ -684,6 +690,18 @@ __global__ void __launch_bounds__(kThreads, 3) k_solve_transient(PlanDev P) {
       write_info(P, b, s);
     }
   }
+}
+
+// Untruncated superposition with lagged leakage.
+__global__ void __launch_bounds__(kThreads, 3) k_solve_transient(PlanDev P) {
+  extern __shared__ float2 smem[];
+  if (transient_lagged<false>(P, smem)) transient_info(P);
+}
+
+// The variants: a window of settled responses and/or implicit leakage.
+__global__ void __launch_bounds__(kThreads, 3) k_solve_transient_var(PlanDev P) {
+  extern __shared__ float2 smem[];
+  if (P.implicit ? transient_implicit(P, smem) : transient_lagged<true>(P, smem)) transient_info(P);
 }
 
 __global__ void k_twiddles(int n, float2* tw) {
@@ -1303,7 +1321,7 @@ namespace {
 
 std::mutex g_tune_mutex;
 std::mutex g_attr_mutex;
-size_t g_smem_attr_steady = 0, g_smem_attr_transient = 0;
+size_t g_smem_attr_steady = 0, g_smem_attr_transient = 0, g_smem_attr_transient_var = 0;
 std::map<std::vector<int>, int> g_tuned;  // key: sorted n list + batch bucket
 
 void plan_release(vs_plan_t* p) {
@@ -1413,7 +1431,9 @@ int plan_layout(vs_plan_t* p, int elems, cudaStream_t s, bool transient, int n_s
                               cudaMemcpyHostToDevice, s));
   VS_CUDA_TRY(cudaMemsetAsync(p->d_info, 0, sizeof(vs_solve_info) * n_items, s));
 
-  auto fn = transient ? (const void*)k_solve_transient
+  const bool tr_var = transient && (p->tr_window || p->tr_implicit);
+  auto fn = tr_var    ? (const void*)k_solve_transient_var
+            : transient ? (const void*)k_solve_transient
             : tc      ? (const void*)k_solve_steady_tc
                       : (const void*)k_solve_steady;
   if (tc) {
@@ -1423,7 +1443,8 @@ int plan_layout(vs_plan_t* p, int elems, cudaStream_t s, bool transient, int n_s
     // Function attributes are process-wide: only ever raise the limit, so a
     // plan with a smaller footprint never invalidates a larger one.
     std::lock_guard<std::mutex> lk(g_attr_mutex);
-    size_t& cur = transient ? g_smem_attr_transient : g_smem_attr_steady;
+    size_t& cur = tr_var ? g_smem_attr_transient_var
+                  : transient ? g_smem_attr_transient : g_smem_attr_steady;
     if (smem > cur) {
       VS_CUDA_TRY(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
       VS_CUDA_TRY(cudaFuncSetAttribute(fn, cudaFuncAttributePreferredSharedMemoryCarveout, 100));
@@ -1610,7 +1631,8 @@ int plan_launch(vs_plan_t* p, cudaStream_t s, bool transient) {
   attr[0].val.cooperative = 1;
   cfg.attrs = attr;
   cfg.numAttrs = 1;
-  cudaError_t e = transient ? cudaLaunchKernelEx(&cfg, k_solve_transient, P)
+  cudaError_t e = transient ? ((P.window || P.implicit) ? cudaLaunchKernelEx(&cfg, k_solve_transient_var, P)
+                                                       : cudaLaunchKernelEx(&cfg, k_solve_transient, P))
                   : p->params.precision == VS_PREC_BF16_SPLIT
                       ? cudaLaunchKernelEx(&cfg, k_solve_steady_tc, P)
                       : cudaLaunchKernelEx(&cfg, k_solve_steady, P);
