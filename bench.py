@@ -150,6 +150,67 @@ def record_traffic(csv_path: str, kernel: str, maps: int, how: str):
     raise SystemExit("no launch of %s in %s" % (kernel, csv_path))
 
 
+# Effect ablation in the layout of the paper's table of errors (Sec. V): the
+# effects are random conductivity (s), temperature-dependent conductivity
+# (alpha), leakage variability (P_leak0 - mu) and temperature-dependent leakage
+# (beta); every scenario switches some off and is compared with all of them on.
+ABLATION_SCENARIOS = [
+    # name, s varies, alpha on, leakage varies, beta on
+    ("no effects", False, False, False, False),
+    ("rand-cond, cond(T)", True, True, False, False),
+    ("leakage-var", False, False, True, False),
+    ("leakage(T)", False, False, False, True),
+    ("rand-cond, cond(T), leakage(T)", True, True, False, True),
+    ("leakage-var, leakage(T)", False, False, True, True),
+    ("cond(T), leakage-var, leakage(T)", False, True, True, True),
+]
+ABLATION_MAPS = 256
+
+
+def ablation_inputs(pl, s, s_var, l_var):
+    """Inputs of one scenario: s -> None (= 1) and P_leak0 -> its per-map mean
+    when the variation is switched off."""
+    pl_x = pl if l_var else pl.mean(dim=(1, 2), keepdim=True).expand_as(pl).contiguous()
+    return pl_x, (s if s_var else None)
+
+
+def effect_ablation(vs, k, w, pd, pl, s, mk):
+    """Max deviation of each scenario from the all-effects solve, per map, as
+    K and as % of the all-effects maximum rise (the paper's percent deviation),
+    plus the one-shot closed form in the last row as the paper has its method."""
+    import torch
+    phy = w.physics
+    B = pd.shape[0]
+
+    def solve(pl_x, s_x, beta, alpha):
+        th = torch.empty_like(pd)
+        prm = vs.SolveParams(beta, alpha, 1e-4, 50)
+        infos = vs.solve_batch([(k, pd[i], pl_x[i], None if s_x is None else s_x[i], th[i])
+                                for i in range(B)], prm)
+        return th, sum(1 for i in infos if i["status"] != vs.VS_OK)
+
+    full, bad = solve(pl, s, phy.beta_per_K, phy.alpha_per_K)
+    rise = full.amax(dim=(1, 2))
+    rows = []
+
+    def row(name, th, nb):
+        dev = (th - full).abs().amax(dim=(1, 2))
+        rows.append({"effects": name, "max_rise_K_mean": float(th.amax(dim=(1, 2)).mean()),
+                     "max_dev_K_mean": float(dev.mean()), "max_dev_K_max": float(dev.max()),
+                     "pct_of_rise_mean": 100 * float((dev / rise).mean()),
+                     "pct_of_rise_max": 100 * float((dev / rise).max()), "not_ok": nb})
+
+    for name, s_var, a_on, l_var, b_on in ABLATION_SCENARIOS:
+        pl_x, s_x = ablation_inputs(pl, s, s_var, l_var)
+        th, nb = solve(pl_x, s_x, phy.beta_per_K if b_on else 0.0, phy.alpha_per_K if a_on else 0.0)
+        row(name, th, nb)
+    th_cf, infos_cf = vs.solve_closed_form(k, pd, pl, s, mk(vs.VS_PREC_FP32))
+    row("closed form (Eqs. 21, 25, 26)", th_cf, sum(1 for i in infos_cf if i["status"] != vs.VS_OK))
+    return {"maps": B, "all_effects_max_rise_K_mean": float(rise.mean()), "all_effects_not_ok": bad,
+            "rows": rows, "how": "each scenario solved to 1e-4 K on the headline workload's first "
+                                 "%d maps; deviation = max |theta - theta_all| per map" % B}
+
+
 class Clocks:
     """Samples SM clocks and throttle reasons with nvidia-smi during a region."""
 
@@ -589,6 +650,8 @@ def run_ours(a):
         extras["closed_form"] = dict(cf, how="vs_solve_closed_form over the %d-map batch (4 launches, "
                                      "CUDA events, inputs > L2); error against the headline path's "
                                      "converged maps (tolerance %.0e K)" % (B, tol))
+        extras["effect_ablation"] = effect_ablation(vs, k, w, pd[:ABLATION_MAPS], pl[:ABLATION_MAPS],
+                                                    s[:ABLATION_MAPS], mk)
 
     # e2e: pinned host inputs -> device -> headline path -> host theta, every step
     e2e = None
