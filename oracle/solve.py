@@ -152,6 +152,54 @@ def shift_invariant(Kt, p_dyn, p_leak0, beta):
 
 
 # --------------------------------------------------------------------------- #
+# Richer physics: piecewise-linear leakage (Sec. II-E), kappa(T) (Eq. 10)         #
+# --------------------------------------------------------------------------- #
+
+def leak_pwl(theta, pts_theta, pts_g):
+    """Piecewise-linear leakage factor g(theta), P_leak = P_leak0 g(theta)
+    (the piecewise-linear leakage model Sec. II-E names for accuracy): linear
+    interpolation through (pts_theta[i], pts_g[i]), pts_theta increasing, and
+    the first / last segment extended beyond the table."""
+    x = np.asarray(pts_theta, dtype=np.float64)
+    y = np.asarray(pts_g, dtype=np.float64)
+    i = np.clip(np.searchsorted(x, theta, side="right") - 1, 0, len(x) - 2)
+    return y[i] + (y[i + 1] - y[i]) / (x[i + 1] - x[i]) * (theta - x[i])
+
+
+def kirchhoff_theta(U, eta, t_amb, guard=0.05):
+    """Temperature rise from the Kirchhoff variable U when the conductivity
+    follows Eq. 10 with the reference at ambient, kappa = kappa_amb (T/T_amb)^-eta:
+      U = int_{T_amb}^{T} (T'/T_amb)^-eta dT' = T_amb ((T/T_amb)^(1-eta) - 1) / (1 - eta),
+    inverted: theta = T - T_amb = T_amb ((1 + (1 - eta) U / T_amb)^(1/(1-eta)) - 1).
+    Raises where the base 1 + (1 - eta) U / T_amb is <= guard (the
+    conductivity model breaks down)."""
+    base = 1.0 + (1.0 - eta) * U / t_amb
+    if np.min(base) <= guard:
+        raise SolveError("conductivity runaway: Kirchhoff base <= %g" % guard)
+    return t_amb * (base ** (1.0 / (1.0 - eta)) - 1.0)
+
+
+def picard_physics(apply_L, p_dyn, p_leak0, s, leak, field, tol=1e-8, max_iter=400):
+    """Plain Picard on the fixed point with a general leakage factor and
+    field-point map, from u = 0:
+      u_{n+1} = L[P_dyn + P_leak0 leak(theta_n)],  theta = field(s u)
+    (leak(theta) = 1 + beta theta and field(v) = v / (1 - alpha v) give
+    `picard`). Stops when max |theta_{n+1} - theta_n| <= tol.
+    Returns (theta, u, iterations)."""
+    theta = np.zeros_like(p_dyn)
+    for it in range(1, max_iter + 1):
+        u = apply_L(p_dyn + p_leak0 * leak(theta))
+        new = field(s * u)
+        if not np.all(np.isfinite(new)):
+            raise SolveError("non-finite temperature")
+        d = np.max(np.abs(new - theta))
+        theta = new
+        if d <= tol:
+            return theta, u, it
+    raise SolveError("no convergence in %d iterations" % max_iter)
+
+
+# --------------------------------------------------------------------------- #
 # One-shot closed form (Sec. IV-C, Eqs. 21, 25, 26)                             #
 # --------------------------------------------------------------------------- #
 

@@ -335,6 +335,64 @@ def test_duhamel_superposition_without_feedback():
     assert np.allclose(tc[4], so.spectral_convolve(spectra[4], a[0]), rtol=1e-12)
 
 
+# -------------------------------- P9c: piecewise-linear leakage, kappa(T)
+
+def test_pwl_leakage_through_a_line_is_the_linear_model():
+    n, L, t, kap, h, pd, pl = _cf_case(sigma=0.2)
+    Kt = ph.spectrum(n, L, t, kap, h)
+    s = 1.0 - 0.05 * np.random.default_rng(3).random((n, n))
+    beta, alpha = 0.0275, 1.2e-3
+    apply_L = lambda x: so.spectral_convolve(Kt, x)
+    ref, _, _ = so.picard(apply_L, pd, pl, s, beta, alpha, tol=1e-12)
+    for pts in ((0.0, 50.0), (-10.0, 3.0, 20.0, 200.0)):       # extrapolation and interior knots
+        g = [1.0 + beta * x for x in pts]
+        th, _, _ = so.picard_physics(apply_L, pd, pl, s, lambda x: so.leak_pwl(x, pts, g),
+                                     lambda v: v / (1.0 - alpha * v), tol=1e-12)
+        assert np.allclose(th, ref, rtol=1e-10, atol=1e-12)
+    # interpolation on a known polyline
+    assert so.leak_pwl(np.array([0.0, 5.0, 10.0, 15.0, 30.0]), (0.0, 10.0, 20.0),
+                       (1.0, 2.0, 4.0)).tolist() == [1.0, 1.5, 2.0, 3.0, 6.0]
+
+
+@pytest.mark.parametrize("eta", [1.3, 0.7, 2.0])
+def test_kirchhoff_map_inverts_the_conductivity_integral(eta):
+    t_amb = 318.15
+    for theta in (0.5, 12.0, 60.0):
+        U, _ = integrate.quad(lambda T: (T / t_amb) ** (-eta), t_amb, t_amb + theta,
+                              epsabs=1e-13, epsrel=1e-13)
+        assert so.kirchhoff_theta(np.array([U]), eta, t_amb)[0] == pytest.approx(theta, rel=1e-11)
+    # second order: theta = U + eta U^2 / (2 T_amb) + O(U^3)
+    U = 1e-3
+    th = so.kirchhoff_theta(np.array([U]), eta, t_amb)[0]
+    assert (th - U) / U ** 2 == pytest.approx(eta / (2 * t_amb), rel=1e-4)
+
+
+def test_kirchhoff_uniform_power_without_leakage_is_the_uniform_mode():
+    t, kap, h = STACK3
+    n, L = 8, 10e-3
+    Kt = ph.spectrum(n, L, t, kap, h)
+    q = np.full((n, n), 2e-3)
+    z, one = np.zeros((n, n)), np.ones((n, n))
+    th, _, _ = so.picard_physics(lambda x: so.spectral_convolve(Kt, x), q, z, one,
+                                 lambda x: 1.0, lambda v: so.kirchhoff_theta(v, 1.3, 318.15),
+                                 tol=1e-13)
+    U = Kt[0, 0] * 2e-3                        # the uniform mode of the imaged kernel
+    assert np.allclose(th, 318.15 * ((1 - 0.3 * U / 318.15) ** (-1 / 0.3) - 1), rtol=1e-12)
+
+
+def test_kirchhoff_fixed_point_residual():
+    n, L, t, kap, h, pd, pl = _cf_case(sigma=0.2)
+    Kt = ph.spectrum(n, L, t, kap, h)
+    s = 1.0 - 0.05 * np.random.default_rng(5).random((n, n))
+    pts, g = (0.0, 20.0, 40.0, 80.0), (1.0, 1.5, 2.3, 4.5)
+    leak = lambda x: so.leak_pwl(x, pts, g)
+    field = lambda v: so.kirchhoff_theta(v, 1.3, 318.15)
+    th, u, _ = so.picard_physics(lambda x: so.spectral_convolve(Kt, x), pd, pl, s, leak, field,
+                                 tol=1e-13)
+    u2 = so.spectral_convolve(Kt, pd + pl * leak(th))
+    assert np.max(np.abs(field(s * u2) - th)) <= 1e-11
+
+
 # ------------------------------------------ P9b: one-shot closed form
 
 def _cf_case(n=8, sigma=0.3, seed=9):
