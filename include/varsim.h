@@ -114,6 +114,12 @@ typedef struct {
 #define VS_ENGINE_STREAMED 1
 #define VS_ENGINE_CLUSTER 2
 
+#define VS_COND_LINEAR 0      /* theta = s u / (1 - alpha s u) (Eqs. 11-12) */
+#define VS_COND_KIRCHHOFF 1   /* kappa = kappa_amb (T / T_amb)^-eta (Eq. 10) through the
+                                 Kirchhoff transform: theta = T_amb ((1 + (1 - eta) s u /
+                                 T_amb)^(1 / (1 - eta)) - 1) */
+#define VS_MAX_LEAK_POINTS 16
+
 /* Parameters of a solve.
  *   beta_per_K : temperature coefficient of leakage (Eq. 5), >= 0
  *   alpha_per_K: temperature coefficient of the Green's function (Eq. 12), >= 0
@@ -122,7 +128,19 @@ typedef struct {
  *   precision  : VS_PREC_FP32 or VS_PREC_BF16_SPLIT
  *   engine     : VS_ENGINE_AUTO (0, what a zero-initialised struct selects),
  *                VS_ENGINE_STREAMED or VS_ENGINE_CLUSTER; asking for the
- *                cluster engine where it does not apply is VS_ERR_INVALID_ARG */
+ *                cluster engine where it does not apply is VS_ERR_INVALID_ARG
+ * Physics variants (zero-initialised = the linear models above):
+ *   conductivity: VS_COND_LINEAR, or VS_COND_KIRCHHOFF with eta (> 0, != 1)
+ *                 and t_amb_K (> 0); alpha_per_K is then unused
+ *   leak_points : 0 => P_leak = P_leak0 (1 + beta theta); 2 .. 16 =>
+ *                 P_leak = P_leak0 g(theta), g piecewise linear through
+ *                 (leak_theta_K[i], leak_g[i]) (theta strictly increasing, g
+ *                 finite), the end segments extended (Sec. II-E). The
+ *                 iteration then preconditions with the secant slope of the
+ *                 table instead of beta_per_K; the fixed point is the same.
+ * A variant needs the streamed FP32 engine (VS_ENGINE_AUTO selects it) and a
+ * steady solve; the cluster and tensor-core engines, the transient and
+ * vs_solve_steady_noalloc return VS_ERR_INVALID_ARG for it. */
 typedef struct {
   double beta_per_K;
   double alpha_per_K;
@@ -130,6 +148,12 @@ typedef struct {
   int max_iter;
   int precision;
   int engine;
+  int conductivity;
+  double eta;
+  double t_amb_K;
+  int leak_points;
+  double leak_theta_K[VS_MAX_LEAK_POINTS];
+  double leak_g[VS_MAX_LEAK_POINTS];
 } vs_solve_params;
 
 /* Per-map outcome. status is a vs_status; iterations counts applications of

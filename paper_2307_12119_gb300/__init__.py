@@ -26,7 +26,7 @@ __all__ = [
     "VS_ENGINE_STREAMED", "VS_ENGINE_CLUSTER", "Model", "WarmPlan",
     "warm_features", "warm_target", "warm_apply", "VS_WARM_FIRST", "VS_WARM_PREDICT",
     "VS_WARM_SOLVE", "VS_WARM_ALL", "VS_LEAK_LAGGED", "VS_LEAK_IMPLICIT", "VS_MAX_WINDOW",
-    "VS_CF_CONV", "VS_CF_IMPULSE", "solve_closed_form",
+    "VS_CF_CONV", "VS_CF_IMPULSE", "solve_closed_form", "VS_COND_LINEAR", "VS_COND_KIRCHHOFF",
 ]
 
 VS_OK, VS_ERR_INVALID_ARG, VS_ERR_CUDA, VS_ERR_OOM = 0, 1, 2, 3
@@ -36,6 +36,7 @@ VS_ENGINE_AUTO, VS_ENGINE_STREAMED, VS_ENGINE_CLUSTER = 0, 1, 2
 VS_WARM_FIRST, VS_WARM_PREDICT, VS_WARM_SOLVE, VS_WARM_ALL = 1, 2, 4, 7
 VS_LEAK_LAGGED, VS_LEAK_IMPLICIT, VS_MAX_WINDOW = 0, 1, 256
 VS_CF_CONV, VS_CF_IMPULSE = 0, 1
+VS_COND_LINEAR, VS_COND_KIRCHHOFF = 0, 1
 VS_MAX_LAYERS = 8
 
 EXPORTS = [
@@ -78,9 +79,15 @@ class _KernelOpts(C.Structure):
     _fields_ = [("quad_nodes", C.c_int), ("rel_tol", C.c_double), ("dt_s", C.c_double)]
 
 
+VS_MAX_LEAK_POINTS = 16
+
+
 class _SolveParams(C.Structure):
     _fields_ = [("beta_per_K", C.c_double), ("alpha_per_K", C.c_double), ("tol_K", C.c_double),
-                ("max_iter", C.c_int), ("precision", C.c_int), ("engine", C.c_int)]
+                ("max_iter", C.c_int), ("precision", C.c_int), ("engine", C.c_int),
+                ("conductivity", C.c_int), ("eta", C.c_double), ("t_amb_K", C.c_double),
+                ("leak_points", C.c_int), ("leak_theta_K", C.c_double * VS_MAX_LEAK_POINTS),
+                ("leak_g", C.c_double * VS_MAX_LEAK_POINTS)]
 
 
 class _SolveInfo(C.Structure):
@@ -245,10 +252,21 @@ class SolveParams:
     max_iter: int = 50
     precision: int = 0
     engine: int = 0
+    conductivity: int = 0                 # VS_COND_LINEAR or VS_COND_KIRCHHOFF (eta, t_amb_K)
+    eta: float = 0.0
+    t_amb_K: float = 0.0
+    leak_table: Optional[Sequence] = None  # [(theta_K, g), ...]: piecewise-linear leakage
 
     def _c(self) -> _SolveParams:
-        return _SolveParams(self.beta_per_K, self.alpha_per_K, self.tol_K, self.max_iter,
-                            self.precision, self.engine)
+        c = _SolveParams(self.beta_per_K, self.alpha_per_K, self.tol_K, self.max_iter,
+                         self.precision, self.engine, self.conductivity, self.eta, self.t_amb_K,
+                         len(self.leak_table) if self.leak_table else 0)
+        for i, (x, g) in enumerate(self.leak_table or ()):
+            if i >= VS_MAX_LEAK_POINTS:
+                break
+            c.leak_theta_K[i] = x
+            c.leak_g[i] = g
+        return c
 
 
 def _info(i: _SolveInfo) -> dict:

@@ -75,7 +75,27 @@ int vs_validate_params(const vs_solve_params* p) {
   if (p->engine != VS_ENGINE_AUTO && p->engine != VS_ENGINE_STREAMED &&
       p->engine != VS_ENGINE_CLUSTER)
     return vs_set_error(VS_ERR_INVALID_ARG, "unknown engine %d", p->engine);
+  if (p->conductivity != VS_COND_LINEAR && p->conductivity != VS_COND_KIRCHHOFF)
+    return vs_set_error(VS_ERR_INVALID_ARG, "unknown conductivity model %d", p->conductivity);
+  if (p->conductivity == VS_COND_KIRCHHOFF &&
+      (!pos_finite(p->eta) || fabs(p->eta - 1.0) < 1e-6 || !pos_finite(p->t_amb_K)))
+    return vs_set_error(VS_ERR_INVALID_ARG, "Kirchhoff model needs eta > 0, eta != 1 and T_amb > 0");
+  if (p->leak_points != 0) {
+    if (p->leak_points < 2 || p->leak_points > VS_MAX_LEAK_POINTS)
+      return vs_set_error(VS_ERR_INVALID_ARG, "leak_points %d not 0 or in [2, %d]", p->leak_points,
+                          VS_MAX_LEAK_POINTS);
+    for (int i = 0; i < p->leak_points; ++i) {
+      if (!isfinite(p->leak_theta_K[i]) || !isfinite(p->leak_g[i]))
+        return vs_set_error(VS_ERR_INVALID_ARG, "leakage table entry %d is not finite", i);
+      if (i && !(p->leak_theta_K[i] > p->leak_theta_K[i - 1]))
+        return vs_set_error(VS_ERR_INVALID_ARG, "leakage table temperatures must increase");
+    }
+  }
   return VS_OK;
+}
+
+int vs_params_physics(const vs_solve_params* p) {
+  return p->conductivity != VS_COND_LINEAR || p->leak_points != 0;
 }
 
 void vs_stack_to_dev(const vs_stack* s, vs_stack_dev* d) {

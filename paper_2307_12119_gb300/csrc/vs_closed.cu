@@ -268,6 +268,8 @@ extern "C" int vs_solve_closed_form(vs_kernel k, int count, const float* p_dyn,
     return vs_set_error(VS_ERR_INVALID_ARG, "closed-form mode %d", mode);
   int rc = vs_validate_params(params);
   if (rc) return rc;
+  if (vs_params_physics(params))
+    return vs_set_error(VS_ERR_INVALID_ARG, "the closed form uses the linear models only");
   const uintptr_t al = (uintptr_t)p_dyn | (uintptr_t)p_leak0 | (uintptr_t)theta | (uintptr_t)s_kappa;
   if (al & 15u) return vs_set_error(VS_ERR_INVALID_ARG, "maps must be 16-byte aligned");
   const int n = k->n;

@@ -65,6 +65,9 @@ struct vs_kernel_t {
 int vs_validate_stack(const vs_stack* s);
 int vs_validate_grid(const vs_grid* g);
 int vs_validate_params(const vs_solve_params* p);
+// Non-zero if the parameters ask for a physics variant (Kirchhoff conductivity
+// or piecewise-linear leakage), which only the streamed engine runs.
+int vs_params_physics(const vs_solve_params* p);
 void vs_stack_to_dev(const vs_stack* s, vs_stack_dev* d);
 
 // Hankel quadrature of the top-layer radial Green's function at `count`

@@ -79,7 +79,48 @@ struct PlanDev {
   int window;            // transient: 0 untruncated, K >= 1 step responses settled from age K on
   int implicit;          // transient: per-step leakage fixed point
   float* xs;             // transient, implicit: the last source spectrum of the current step
+  // physics variants (the k_solve_steady<true> instantiation); beta above is
+  // then the preconditioner slope (the secant of a piecewise-linear table)
+  int cond;              // VS_COND_*
+  float one_me, t_amb;   // Kirchhoff: 1 - eta, T_amb
+  int leak_n;            // 0: linear leakage 1 + beta theta; else table points
+  float leak_x[VS_MAX_LEAK_POINTS], leak_y[VS_MAX_LEAK_POINTS];
 };
+
+// ------------------------------------------------------------ physics variants
+// Leakage factor g(theta): linear, or piecewise linear through the table with
+// the end segments extended (Sec. II-E).
+__device__ __forceinline__ float leak_factor(const PlanDev& P, float th) {
+  if (P.leak_n == 0) return fmaf(P.beta, th, 1.f);
+  int i = 0;
+  while (i < P.leak_n - 2 && th >= P.leak_x[i + 1]) ++i;
+  const float x0 = P.leak_x[i], y0 = P.leak_y[i];
+  return fmaf((P.leak_y[i + 1] - y0) / (P.leak_x[i + 1] - x0), th - x0, y0);
+}
+
+// theta from the linear solution u at the field point: Eqs. 11-12, or the
+// inverse Kirchhoff transform of s u for kappa ~ T^-eta (Eq. 10). Flags a base
+// (1 - alpha s u, or 1 + (1 - eta) s u / T_amb) <= 0.05 as runaway.
+__device__ __forceinline__ float field_theta(const PlanDev& P, float sk, float uu, int& flags) {
+  if (P.cond == VS_COND_KIRCHHOFF) {
+    float x = P.one_me * sk * uu / P.t_amb;
+    if (!(x > -0.95f)) {
+      flags |= kFlagRunaway;
+      x = -0.95f;                         // keep theta finite; the map stops on the flag
+    }
+    return P.t_amb * expm1f(log1pf(x) / P.one_me);
+  }
+  const float den = fmaf(-P.alpha * sk, uu, 1.f);
+  if (!(den > 0.05f)) flags |= kFlagRunaway;
+  return sk * uu / den;
+}
+
+// Its inverse: the u of a temperature (warm starts).
+__device__ __forceinline__ float field_u(const PlanDev& P, float sk, float t0) {
+  if (P.cond == VS_COND_KIRCHHOFF)
+    return P.t_amb * expm1f(P.one_me * log1pf(t0 / P.t_amb)) / (P.one_me * sk);
+  return t0 / (sk * fmaf(P.alpha, t0, 1.f));
+}
 
 // ------------------------------------------------------------ grid barrier
 
@@ -211,7 +252,8 @@ __device__ __forceinline__ void row_forward(const MapDesc& d, int y0, float2* bu
 // MODE 0: steady iteration `step` (0 = initial source from theta_0 = 0,
 // -1 = initial source from a warm start theta_0, -2 = mean leakage only).
 // MODE 1: transient step `step` (0 = first source, n_steps = last inverse only).
-template <int MODE>
+// PHYS (MODE 0): the leakage factor and field-point map of the physics variants.
+template <int MODE, bool PHYS = false>
 __device__ void row_task(const PlanDev& P, int task, int step, float2* buf) {
   __shared__ double red_d[kThreads / 32];
   __shared__ float red_f[kThreads / 32];
@@ -286,7 +328,23 @@ __device__ void row_task(const PlanDev& P, int task, int step, float2* buf) {
         size_t idx = (size_t)(y0 + 2 * f + h) * n + x;
         float uu = h ? uv[u].y : uv[u].x;
         if (MODE == 0) {
-          if (warm) {
+          if (PHYS) {
+            // P_dyn + P_leak0 g(theta) - beta mu u, beta the preconditioner slope
+            float th = 0.f, uq = 0.f;
+            if (warm) {
+              th = old[u][h];
+              uq = field_u(P, sk[u][h], th);
+            } else if (!first) {
+              th = field_theta(P, sk[u][h], uu, flags);
+              uq = uu;
+              if (!isfinite(th)) flags |= kFlagNonfinite;
+              else resid = fmaxf(resid, fabsf(th - old[u][h]));
+            } else {
+              mu_acc += (double)pl[u][h];
+            }
+            d.theta[idx] = th;
+            q[h] = fmaf(pl[u][h], leak_factor(P, th), pd[u][h]) - beta * mu * uq;
+          } else if (warm) {
             // theta_0 from the warm start; u_0 = theta_0 / (s (1 + alpha theta_0))
             float t0 = old[u][h];
             float u0 = t0 / (sk[u][h] * fmaf(alpha, t0, 1.f));
@@ -522,22 +580,23 @@ __device__ void decide(const PlanDev& P, int it) {
   }
 }
 
+template <bool PHYS>
 __global__ void __launch_bounds__(kThreads, 3) k_solve_steady(PlanDev P) {
   extern __shared__ float2 smem[];
   const int first = P.warm ? -2 : 0;
-  for (int t = blockIdx.x; t < P.row_tasks; t += gridDim.x) row_task<0>(P, t, first, smem);
+  for (int t = blockIdx.x; t < P.row_tasks; t += gridDim.x) row_task<0, PHYS>(P, t, first, smem);
   if (!grid_barrier(P.ctrl)) return;
   decide(P, 0);
   if (!grid_barrier(P.ctrl)) return;
   if (ld_acquire(&P.ctrl->active[0]) == 0u) return;
   if (P.warm) {
-    for (int t = blockIdx.x; t < P.row_tasks; t += gridDim.x) row_task<0>(P, t, -1, smem);
+    for (int t = blockIdx.x; t < P.row_tasks; t += gridDim.x) row_task<0, PHYS>(P, t, -1, smem);
     if (!grid_barrier(P.ctrl)) return;
   }
   for (int it = 1; it <= P.max_iter; ++it) {
     for (int t = blockIdx.x; t < P.col_tasks; t += gridDim.x) col_task<0>(P, t, smem);
     if (!grid_barrier(P.ctrl)) return;
-    for (int t = blockIdx.x; t < P.row_tasks; t += gridDim.x) row_task<0>(P, t, it, smem);
+    for (int t = blockIdx.x; t < P.row_tasks; t += gridDim.x) row_task<0, PHYS>(P, t, it, smem);
     if (!grid_barrier(P.ctrl)) return;
     decide(P, it);
     if (!grid_barrier(P.ctrl)) return;
@@ -1321,7 +1380,8 @@ namespace {
 
 std::mutex g_tune_mutex;
 std::mutex g_attr_mutex;
-size_t g_smem_attr_steady = 0, g_smem_attr_transient = 0, g_smem_attr_transient_var = 0;
+size_t g_smem_attr_steady = 0, g_smem_attr_steady_phys = 0, g_smem_attr_transient = 0,
+       g_smem_attr_transient_var = 0;
 std::map<std::vector<int>, int> g_tuned;  // key: sorted n list + batch bucket
 
 void plan_release(vs_plan_t* p) {
@@ -1435,7 +1495,8 @@ int plan_layout(vs_plan_t* p, int elems, cudaStream_t s, bool transient, int n_s
   auto fn = tr_var    ? (const void*)k_solve_transient_var
             : transient ? (const void*)k_solve_transient
             : tc      ? (const void*)k_solve_steady_tc
-                      : (const void*)k_solve_steady;
+                      : vs_params_physics(&p->params) ? (const void*)k_solve_steady<true>
+                                                      : (const void*)k_solve_steady<false>;
   if (tc) {
     VS_CUDA_TRY(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     VS_CUDA_TRY(cudaFuncSetAttribute(fn, cudaFuncAttributePreferredSharedMemoryCarveout, 100));
@@ -1444,7 +1505,8 @@ int plan_layout(vs_plan_t* p, int elems, cudaStream_t s, bool transient, int n_s
     // plan with a smaller footprint never invalidates a larger one.
     std::lock_guard<std::mutex> lk(g_attr_mutex);
     size_t& cur = tr_var ? g_smem_attr_transient_var
-                  : transient ? g_smem_attr_transient : g_smem_attr_steady;
+                  : transient ? g_smem_attr_transient
+                  : vs_params_physics(&p->params) ? g_smem_attr_steady_phys : g_smem_attr_steady;
     if (smem > cur) {
       VS_CUDA_TRY(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
       VS_CUDA_TRY(cudaFuncSetAttribute(fn, cudaFuncAttributePreferredSharedMemoryCarveout, 100));
@@ -1614,6 +1676,22 @@ int plan_launch(vs_plan_t* p, cudaStream_t s, bool transient) {
   P.tol = (float)p->params.tol_K;
   P.n_steps = p->transient_steps;
   P.warm = p->warm;
+  const vs_solve_params& pp = p->params;
+  P.cond = pp.conductivity;
+  P.one_me = (float)(1.0 - pp.eta);
+  P.t_amb = (float)pp.t_amb_K;
+  P.leak_n = pp.leak_points;
+  for (int i = 0; i < VS_MAX_LEAK_POINTS; ++i) {
+    P.leak_x[i] = i < pp.leak_points ? (float)pp.leak_theta_K[i] : 0.f;
+    P.leak_y[i] = i < pp.leak_points ? (float)pp.leak_g[i] : 0.f;
+  }
+  if (pp.leak_points >= 2) {
+    // precondition with the secant slope of the table (any slope gives the
+    // same fixed point; one close to g' converges fastest)
+    const int m = pp.leak_points - 1;
+    P.beta = (float)std::max(0.0, (pp.leak_g[m] - pp.leak_g[0]) /
+                                      (pp.leak_theta_K[m] - pp.leak_theta_K[0]));
+  }
   P.window = transient ? p->tr_window : 0;
   P.implicit = transient ? p->tr_implicit : 0;
   // the implicit transient keeps the current step's source spectrum in the
@@ -1635,7 +1713,8 @@ int plan_launch(vs_plan_t* p, cudaStream_t s, bool transient) {
                                                        : cudaLaunchKernelEx(&cfg, k_solve_transient, P))
                   : p->params.precision == VS_PREC_BF16_SPLIT
                       ? cudaLaunchKernelEx(&cfg, k_solve_steady_tc, P)
-                      : cudaLaunchKernelEx(&cfg, k_solve_steady, P);
+                  : vs_params_physics(&p->params) ? cudaLaunchKernelEx(&cfg, k_solve_steady<true>, P)
+                                                  : cudaLaunchKernelEx(&cfg, k_solve_steady<false>, P);
   if (e != cudaSuccess)
     return vs_set_error(VS_ERR_CUDA, "cooperative launch (grid %d, smem %zu): %s", p->grid,
                         p->smem, cudaGetErrorString(e));
@@ -1688,7 +1767,11 @@ extern "C" int vs_plan_create(const vs_batch_item* items_host, int n_items,
                           "item %d: the BF16 split tensor-core path supports n = 128 .. 1024 (got %d)",
                           i, it.k->n);
   }
-  bool cluster_ok = params->precision == VS_PREC_FP32;
+  if (vs_params_physics(params) && params->precision != VS_PREC_FP32)
+    return vs_set_error(VS_ERR_INVALID_ARG, "the physics variants need FP32 precision");
+  if (vs_params_physics(params) && params->engine == VS_ENGINE_CLUSTER)
+    return vs_set_error(VS_ERR_INVALID_ARG, "the physics variants run on the streamed engine");
+  bool cluster_ok = params->precision == VS_PREC_FP32 && !vs_params_physics(params);
   for (int i = 0; i < n_items && cluster_ok; ++i) cluster_ok = cluster_size_ok(items_host[i].k->n);
   if (params->engine == VS_ENGINE_CLUSTER && !cluster_ok)
     return vs_set_error(VS_ERR_INVALID_ARG,
@@ -1839,6 +1922,8 @@ extern "C" int vs_solve_transient_ex(vs_kernel k, int n_steps, const float* p_dy
   if (n_steps < 1 || n_steps > 1000000) return vs_set_error(VS_ERR_INVALID_ARG, "n_steps %d", n_steps);
   int rc = vs_validate_params(params);
   if (rc) return rc;
+  if (vs_params_physics(params))
+    return vs_set_error(VS_ERR_INVALID_ARG, "the transient runs the linear models only");
   const vs_transient_opts o = opts ? *opts : vs_transient_opts{0, VS_LEAK_LAGGED};
   if (o.window < 0 || o.window > VS_MAX_WINDOW)
     return vs_set_error(VS_ERR_INVALID_ARG, "window %d not in 0..%d", o.window, VS_MAX_WINDOW);
@@ -1948,6 +2033,8 @@ extern "C" int vs_solve_steady_noalloc(vs_kernel k, const float* p_dyn, const fl
   if (!k) return vs_set_error(VS_ERR_INVALID_ARG, "NULL kernel");
   int rc = vs_validate_params(params);
   if (rc) return rc;
+  if (vs_params_physics(params))
+    return vs_set_error(VS_ERR_INVALID_ARG, "vs_solve_steady_noalloc runs the linear models only");
   if (!p_dyn || !p_leak0 || !theta) return vs_set_error(VS_ERR_INVALID_ARG, "NULL map");
   uintptr_t al = (uintptr_t)p_dyn | (uintptr_t)p_leak0 | (uintptr_t)theta | (uintptr_t)s_kappa;
   if (al & 15u) return vs_set_error(VS_ERR_INVALID_ARG, "maps must be 16-byte aligned");
@@ -1997,15 +2084,16 @@ extern "C" int vs_solve_steady_noalloc(vs_kernel k, const float* p_dyn, const fl
   {
     std::lock_guard<std::mutex> lk(g_attr_mutex);
     if (smem > g_smem_attr_steady) {
-      VS_CUDA_TRY(cudaFuncSetAttribute((const void*)k_solve_steady,
+      VS_CUDA_TRY(cudaFuncSetAttribute((const void*)k_solve_steady<false>,
                                        cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-      VS_CUDA_TRY(cudaFuncSetAttribute((const void*)k_solve_steady,
+      VS_CUDA_TRY(cudaFuncSetAttribute((const void*)k_solve_steady<false>,
                                        cudaFuncAttributePreferredSharedMemoryCarveout, 100));
       g_smem_attr_steady = smem;
     }
   }
   int per_sm = 0, sms = 0;
-  VS_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_solve_steady, kThreads, smem));
+  VS_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_solve_steady<false>, kThreads,
+                                                            smem));
   VS_CUDA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
   if (per_sm < 1) return vs_set_error(VS_ERR_INVALID_ARG, "no block fits on an SM");
 
@@ -2040,7 +2128,7 @@ extern "C" int vs_solve_steady_noalloc(vs_kernel k, const float* p_dyn, const fl
   attr[0].val.cooperative = 1;
   cfg.attrs = attr;
   cfg.numAttrs = 1;
-  cudaError_t e = cudaLaunchKernelEx(&cfg, k_solve_steady, P);
+  cudaError_t e = cudaLaunchKernelEx(&cfg, k_solve_steady<false>, P);
   if (e != cudaSuccess)
     return vs_set_error(VS_ERR_CUDA, "cooperative launch: %s", cudaGetErrorString(e));
 

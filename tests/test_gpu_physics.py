@@ -1,0 +1,125 @@
+"""GPU parity of the physics variants (piecewise-linear leakage, Sec. II-E;
+kappa(T) through the Kirchhoff transform, Eq. 10) against the FP64 oracle."""
+import dataclasses
+
+import numpy as np
+import pytest
+import torch
+
+import synth
+from oracle import solve as so
+
+from _util import errors, oracle_spectrum, vs_params, vs_stack
+
+pytestmark = pytest.mark.gpu
+
+T_AMB, ETA = 318.15, 1.3
+# exp(0.0275 theta) sampled every 25 K: a leakage that grows faster than linear
+EXP_TABLE = [(x, float(np.exp(0.0275 * x))) for x in (0.0, 25.0, 50.0, 75.0, 100.0, 150.0, 250.0)]
+
+
+def _vs():
+    import paper_2307_12119_gb300 as vs
+    return vs
+
+
+def _case(config, count, n=None):
+    vs = _vs()
+    w = synth.workload(config)
+    if n is not None:
+        w = dataclasses.replace(w, name="%s_%d" % (config, n), n=n)
+    pd, pl, s = synth.steady_inputs(w, count, device="cuda")
+    k = vs.Kernel(vs_stack(w), vs.Grid(w.n, w.die_m))
+    return vs, w, k, pd, pl, s
+
+
+def _params(vs, w, kirchhoff, table, **kw):
+    p = vs_params(w, **kw)
+    if kirchhoff:
+        p.conductivity, p.eta, p.t_amb_K = vs.VS_COND_KIRCHHOFF, ETA, T_AMB
+    if table:
+        p.leak_table = table
+    return p
+
+
+def _oracle(w, pd, pl, s, kirchhoff, table):
+    Kt = oracle_spectrum(w)
+    beta, alpha = w.physics.beta_per_K, w.physics.alpha_per_K
+    leak = (lambda th: so.leak_pwl(th, [x for x, _ in table], [g for _, g in table])) if table \
+        else (lambda th: 1.0 + beta * th)
+    field = (lambda v: so.kirchhoff_theta(v, ETA, T_AMB)) if kirchhoff \
+        else (lambda v: v / (1.0 - alpha * v))
+    f64 = lambda t: t.double().cpu().numpy()
+    th, _, _ = so.picard_physics(lambda x: so.spectral_convolve(Kt, x), f64(pd), f64(pl), f64(s),
+                                 leak, field, tol=1e-10)
+    return th
+
+
+@pytest.mark.parametrize("kirchhoff,table", [(True, None), (False, EXP_TABLE), (True, EXP_TABLE)])
+@pytest.mark.parametrize("config,n", [("c1_64", None), ("c2_256", None), ("c1_64", 128)])
+def test_physics_variants_match_oracle(config, n, kirchhoff, table):
+    vs, w, k, pd, pl, s = _case(config, 2, n)
+    th = torch.empty_like(pd)
+    infos = vs.solve_batch([(k, pd[b], pl[b], s[b], th[b]) for b in range(2)],
+                           _params(vs, w, kirchhoff, table))
+    for b in range(2):
+        assert infos[b]["status"] == vs.VS_OK
+        emax, rel = errors(th[b], _oracle(w, pd[b], pl[b], s[b], kirchhoff, table))
+        assert emax <= 2e-3 and rel <= 1e-4, (b, emax, rel)
+
+
+def test_linear_table_equals_the_linear_model():
+    vs, w, k, pd, pl, s = _case("c2_256", 2)
+    beta = w.physics.beta_per_K
+    table = [(0.0, 1.0), (300.0, 1.0 + 300.0 * beta)]
+    a = torch.empty_like(pd)
+    b = torch.empty_like(pd)
+    vs.solve_batch([(k, pd[i], pl[i], s[i], a[i]) for i in range(2)],
+                   vs_params(w, tol=1e-6, engine=vs.VS_ENGINE_STREAMED))
+    infos = vs.solve_batch([(k, pd[i], pl[i], s[i], b[i]) for i in range(2)],
+                           _params(vs, w, False, table, tol=1e-6))
+    assert all(i["status"] == vs.VS_OK for i in infos)
+    assert float((a - b).abs().max()) <= 1e-4
+
+
+def test_physics_variant_full_batch_and_warm_start():
+    vs = _vs()
+    w, pd, pl, s = synth.batch_inputs(256, 4096, device="cuda")
+    k = vs.Kernel(vs_stack(w), vs.Grid(w.n, w.die_m))
+    prm = _params(vs, w, True, EXP_TABLE)
+    th = torch.empty_like(pd)
+    infos = vs.solve_batch([(k, pd[b], pl[b], s[b], th[b]) for b in range(4096)], prm)
+    assert all(i["status"] == vs.VS_OK for i in infos)
+    for b in (0, 2049, 4095):
+        emax, rel = errors(th[b], _oracle(w, pd[b], pl[b], s[b], True, EXP_TABLE))
+        assert emax <= 2e-3 and rel <= 1e-4, (b, emax, rel)
+    # a warm start from a perturbed solution reaches the same fixed point
+    th2 = torch.empty_like(pd[:4])
+    init = (th[:4] * 0.9).contiguous()
+    infos = vs.solve_batch([(k, pd[b], pl[b], s[b], th2[b], init[b]) for b in range(4)],
+                           _params(vs, w, True, EXP_TABLE, tol=1e-5))
+    assert all(i["status"] == vs.VS_OK for i in infos)
+    assert float((th2 - th[:4]).abs().max()) <= 2e-3
+
+
+def test_physics_variants_are_rejected_where_not_supported():
+    vs, w, k, pd, pl, s = _case("c1_64", 1)
+    prm = _params(vs, w, True, None)
+    with pytest.raises(vs.VarsimError) as e:
+        vs.solve_batch([(k, pd[0], pl[0], s[0], torch.empty_like(pd[0]))],
+                       _params(vs, w, True, None, engine=vs.VS_ENGINE_CLUSTER))
+    assert e.value.status == vs.VS_ERR_INVALID_ARG
+    with pytest.raises(vs.VarsimError):
+        vs.solve_steady_noalloc(k, pd[0], pl[0], s[0], prm)
+    with pytest.raises(vs.VarsimError):
+        vs.solve_closed_form(k, pd, pl, s, prm)
+    bad = _params(vs, w, False, [(10.0, 1.0), (5.0, 2.0)])       # temperatures not increasing
+    with pytest.raises(vs.VarsimError):
+        vs.solve_steady(k, pd[0], pl[0], s[0], bad)
+
+
+def test_kirchhoff_runaway_is_reported():
+    vs, w, k, pd, pl, s = _case("c1_64", 1)
+    hot = (pd[0] * 40).contiguous()       # s u beyond T_amb / (eta - 1)
+    th, info = vs.solve_steady(k, hot, pl[0], s[0], _params(vs, w, True, None, beta_per_K=0.0))
+    assert info["status"] == vs.VS_ERR_RUNAWAY
