@@ -211,6 +211,55 @@ def effect_ablation(vs, k, w, pd, pl, s, mk):
                                  "%d maps; deviation = max |theta - theta_all| per map" % B}
 
 
+def physics_variants(vs, k, w, pd, pl, s, th_lin, a, stream):
+    """The streamed engine with kappa(T) through the Kirchhoff transform (Eq. 10,
+    eta and T_amb of the workload) and with a convex leakage as a
+    piecewise-linear table: throughput on the batch and the deviation of the
+    result from the linear models (th_lin)."""
+    import torch
+    phy = w.physics
+    B = pd.shape[0]
+    # a convex leakage 1 + beta theta (1 + theta / 400); exp(beta theta) runs away
+    # on these maps (their linear-model rise is ~130 K)
+    table = [(x, 1.0 + phy.beta_per_K * x * (1.0 + x / 400.0))
+             for x in (0.0, 25.0, 50.0, 75.0, 100.0, 150.0, 200.0, 300.0)]
+    out = {}
+    for name, kw in (("linear (streamed)", {}),
+                     ("kirchhoff", {"conductivity": vs.VS_COND_KIRCHHOFF, "eta": phy.eta,
+                                    "t_amb_K": phy.t_amb_K}),
+                     ("pwl convex leakage", {"leak_table": table}),
+                     ("kirchhoff + pwl convex leakage", {"conductivity": vs.VS_COND_KIRCHHOFF,
+                                                      "eta": phy.eta, "t_amb_K": phy.t_amb_K,
+                                                      "leak_table": table})):
+        prm = vs.SolveParams(phy.beta_per_K, phy.alpha_per_K, 1e-2, 50, vs.VS_PREC_FP32,
+                             vs.VS_ENGINE_STREAMED, **kw)
+        th = torch.empty_like(pd)
+        plan = vs.Plan([(k, pd[i], pl[i], s[i], th[i]) for i in range(B)], prm, stream)
+        for _ in range(max(3, a.warmup)):
+            plan.run(stream)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(a.steps):
+            plan.run(stream)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / a.steps
+        infos = plan.info(stream)
+        plan.close()
+        rise = th_lin.amax(dim=(1, 2))
+        dev = (th - th_lin).abs().amax(dim=(1, 2))
+        out[name] = {"value": whole_job_rate(1, B, ms * 1e-3), "unit": UNIT, "ms_per_step": ms,
+                     "iterations_mean": sum(i["iterations"] for i in infos) / B,
+                     "not_ok": sum(1 for i in infos if i["status"] != vs.VS_OK),
+                     "max_rise_K_mean": float(th.amax(dim=(1, 2)).mean()),
+                     "dev_from_linear_K_mean": float(dev.mean()),
+                     "dev_from_linear_pct_of_rise_max": 100 * float((dev / rise).max())}
+        del th
+    return dict(out, how="streamed engine over the %d-map batch at 1e-2 K; deviation per map from "
+                         "the headline path's linear-model maps" % B)
+
+
 class Clocks:
     """Samples SM clocks and throttle reasons with nvidia-smi during a region."""
 
@@ -652,6 +701,7 @@ def run_ours(a):
                                      "converged maps (tolerance %.0e K)" % (B, tol))
         extras["effect_ablation"] = effect_ablation(vs, k, w, pd[:ABLATION_MAPS], pl[:ABLATION_MAPS],
                                                     s[:ABLATION_MAPS], mk)
+        extras["physics_variants"] = physics_variants(vs, k, w, pd, pl, s, th_best, a, stream)
 
     # e2e: pinned host inputs -> device -> headline path -> host theta, every step
     e2e = None

@@ -136,8 +136,9 @@ typedef struct {
  *                 P_leak = P_leak0 g(theta), g piecewise linear through
  *                 (leak_theta_K[i], leak_g[i]) (theta strictly increasing, g
  *                 finite), the end segments extended (Sec. II-E). The
- *                 iteration then preconditions with the secant slope of the
- *                 table instead of beta_per_K; the fixed point is the same.
+ *                 iteration then preconditions with the table's slope at
+ *                 theta = 0 instead of beta_per_K (the fixed point is the
+ *                 same); that slope also enters the runaway check.
  * A variant needs the streamed FP32 engine (VS_ENGINE_AUTO selects it) and a
  * steady solve; the cluster and tensor-core engines, the transient and
  * vs_solve_steady_noalloc return VS_ERR_INVALID_ARG for it. */

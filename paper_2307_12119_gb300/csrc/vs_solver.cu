@@ -1686,11 +1686,12 @@ int plan_launch(vs_plan_t* p, cudaStream_t s, bool transient) {
     P.leak_y[i] = i < pp.leak_points ? (float)pp.leak_g[i] : 0.f;
   }
   if (pp.leak_points >= 2) {
-    // precondition with the secant slope of the table (any slope gives the
-    // same fixed point; one close to g' converges fastest)
-    const int m = pp.leak_points - 1;
-    P.beta = (float)std::max(0.0, (pp.leak_g[m] - pp.leak_g[0]) /
-                                      (pp.leak_theta_K[m] - pp.leak_theta_K[0]));
+    // precondition with the slope of the table at theta = 0 (any slope gives
+    // the same fixed point; it also sets the runaway check beta mu max K < 1)
+    int i = 0;
+    while (i < pp.leak_points - 2 && pp.leak_theta_K[i + 1] <= 0.0) ++i;
+    P.beta = (float)std::max(0.0, (pp.leak_g[i + 1] - pp.leak_g[i]) /
+                                      (pp.leak_theta_K[i + 1] - pp.leak_theta_K[i]));
   }
   P.window = transient ? p->tr_window : 0;
   P.implicit = transient ? p->tr_implicit : 0;

@@ -14,8 +14,12 @@ from _util import errors, oracle_spectrum, vs_params, vs_stack
 pytestmark = pytest.mark.gpu
 
 T_AMB, ETA = 318.15, 1.3
-# exp(0.0275 theta) sampled every 25 K: a leakage that grows faster than linear
+# exp(0.0275 theta): a leakage that grows faster than linear (the 64^2 maps
+# converge with it; the hotter 256^2 maps run away, also in the oracle)
 EXP_TABLE = [(x, float(np.exp(0.0275 * x))) for x in (0.0, 25.0, 50.0, 75.0, 100.0, 150.0, 250.0)]
+# 1 + beta theta (1 + theta / 400): convex, converges on the 256^2 maps
+CONVEX_TABLE = [(x, 1.0 + 0.0275 * x * (1.0 + x / 400.0))
+                for x in (0.0, 25.0, 50.0, 75.0, 100.0, 150.0, 200.0, 300.0)]
 
 
 def _vs():
@@ -55,9 +59,12 @@ def _oracle(w, pd, pl, s, kirchhoff, table):
     return th
 
 
-@pytest.mark.parametrize("kirchhoff,table", [(True, None), (False, EXP_TABLE), (True, EXP_TABLE)])
+@pytest.mark.parametrize("kirchhoff,table", [(True, None), (False, EXP_TABLE), (True, EXP_TABLE),
+                                             (False, CONVEX_TABLE), (True, CONVEX_TABLE)])
 @pytest.mark.parametrize("config,n", [("c1_64", None), ("c2_256", None), ("c1_64", 128)])
 def test_physics_variants_match_oracle(config, n, kirchhoff, table):
+    if config == "c2_256" and table is EXP_TABLE:
+        pytest.skip("thermal runaway of the exponential leakage on these maps (oracle too)")
     vs, w, k, pd, pl, s = _case(config, 2, n)
     th = torch.empty_like(pd)
     infos = vs.solve_batch([(k, pd[b], pl[b], s[b], th[b]) for b in range(2)],
@@ -86,18 +93,18 @@ def test_physics_variant_full_batch_and_warm_start():
     vs = _vs()
     w, pd, pl, s = synth.batch_inputs(256, 4096, device="cuda")
     k = vs.Kernel(vs_stack(w), vs.Grid(w.n, w.die_m))
-    prm = _params(vs, w, True, EXP_TABLE)
+    prm = _params(vs, w, True, CONVEX_TABLE)
     th = torch.empty_like(pd)
     infos = vs.solve_batch([(k, pd[b], pl[b], s[b], th[b]) for b in range(4096)], prm)
     assert all(i["status"] == vs.VS_OK for i in infos)
     for b in (0, 2049, 4095):
-        emax, rel = errors(th[b], _oracle(w, pd[b], pl[b], s[b], True, EXP_TABLE))
+        emax, rel = errors(th[b], _oracle(w, pd[b], pl[b], s[b], True, CONVEX_TABLE))
         assert emax <= 2e-3 and rel <= 1e-4, (b, emax, rel)
     # a warm start from a perturbed solution reaches the same fixed point
     th2 = torch.empty_like(pd[:4])
     init = (th[:4] * 0.9).contiguous()
     infos = vs.solve_batch([(k, pd[b], pl[b], s[b], th2[b], init[b]) for b in range(4)],
-                           _params(vs, w, True, EXP_TABLE, tol=1e-5))
+                           _params(vs, w, True, CONVEX_TABLE, tol=1e-5))
     assert all(i["status"] == vs.VS_OK for i in infos)
     assert float((th2 - th[:4]).abs().max()) <= 2e-3
 
