@@ -227,11 +227,8 @@ def physics_variants(vs, k, w, pd, pl, s, th_lin, a, stream):
     for name, kw in (("linear (streamed)", {}),
                      ("kirchhoff", {"conductivity": vs.VS_COND_KIRCHHOFF, "eta": phy.eta,
                                     "t_amb_K": phy.t_amb_K}),
-                     ("pwl convex leakage", {"leak_table": table}),
-                     ("kirchhoff + pwl convex leakage", {"conductivity": vs.VS_COND_KIRCHHOFF,
-                                                      "eta": phy.eta, "t_amb_K": phy.t_amb_K,
-                                                      "leak_table": table})):
-        prm = vs.SolveParams(phy.beta_per_K, phy.alpha_per_K, 1e-2, 50, vs.VS_PREC_FP32,
+                     ("pwl convex leakage", {"leak_table": table})):
+        prm = vs.SolveParams(phy.beta_per_K, phy.alpha_per_K, 1e-2, 200, vs.VS_PREC_FP32,
                              vs.VS_ENGINE_STREAMED, **kw)
         th = torch.empty_like(pd)
         plan = vs.Plan([(k, pd[i], pl[i], s[i], th[i]) for i in range(B)], prm, stream)
