@@ -77,6 +77,7 @@ class Workload:
     hot_size_m: float = 0.5 * MM
     sigma: tuple = (0.05, 0.05)        # range of the variation std
     corr_len_m: tuple = (1 * MM, 1 * MM)
+    corr: str = "gaussian"             # "gaussian" or "spherical" (range = corr_len)
     stack: Stack = field(default_factory=Stack)
     physics: Physics = field(default_factory=Physics)
     config_id: int = 0
@@ -155,7 +156,12 @@ def variation_fields(w: Workload, count: int, seed: int = SEED, first: int = 0,
 
     Smoothing is done on the mirror-extended (2n x 2n) field in the Fourier
     domain with a Gaussian of std corr_len/2, i.e. a Gaussian filter with
-    reflecting boundaries.
+    reflecting boundaries. With w.corr == "spherical" the filter is instead the
+    square root of the spectrum of the spherical correlation
+    rho(r) = 1 - 1.5 r/phi + 0.5 (r/phi)^3 for r < phi, 0 beyond (phi =
+    corr_len), the correlation Sec. II-C gives the systematic variation, taken
+    on the periodic 2n x 2n grid (circulant embedding; negative spectral
+    values from the truncation are clipped to zero).
     """
     n = w.n
     zs = torch.empty(count, n, n, device=device, dtype=torch.float64)
@@ -173,13 +179,27 @@ def variation_fields(w: Workload, count: int, seed: int = SEED, first: int = 0,
             params[j, 1] = w.corr_len_m[0] + (w.corr_len_m[1] - w.corr_len_m[0]) * u[1]
         ext = torch.cat([white, white.flip(-1)], dim=-1)
         ext = torch.cat([ext, ext.flip(-2)], dim=-2)
-        sf = (params[c0:c1, 1] / 2).to(device)[:, None, None]
-        filt = torch.exp(-0.5 * sf ** 2 * k2[None])
+        if w.corr == "spherical":
+            filt = _spherical_filter(n, w.cell_m, params[c0:c1, 1].to(device))
+        else:
+            sf = (params[c0:c1, 1] / 2).to(device)[:, None, None]
+            filt = torch.exp(-0.5 * sf ** 2 * k2[None])
         sm = torch.fft.ifft2(torch.fft.fft2(ext) * filt).real[:, :n, :n]
         sm = sm - sm.mean(dim=(-1, -2), keepdim=True)
         sm = sm / sm.std(dim=(-1, -2), keepdim=True).clamp_min(1e-300)
         zs[c0:c1] = sm
     return zs.to(dtype), params
+
+
+def _spherical_filter(n: int, cell_m: float, phi: torch.Tensor) -> torch.Tensor:
+    """sqrt of the 2n x 2n periodic spectrum of the spherical correlation of
+    range phi (one filter per entry of phi)."""
+    d = torch.arange(2 * n, device=phi.device, dtype=torch.float64)
+    d = torch.minimum(d, 2 * n - d) * cell_m
+    r = torch.sqrt(d[:, None] ** 2 + d[None, :] ** 2)[None]
+    x = (r / phi[:, None, None]).clamp(max=1.0)
+    rho = 1.0 - 1.5 * x + 0.5 * x ** 3
+    return torch.fft.fft2(rho).real.clamp_min(0.0).sqrt()
 
 
 def leakage_and_conductivity(w: Workload, z: torch.Tensor, sigma: torch.Tensor,

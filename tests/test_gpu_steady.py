@@ -24,10 +24,12 @@ def _kernel(w):
     return vs.Kernel(vs_stack(w), vs.Grid(w.n, w.die_m))
 
 
-@pytest.mark.parametrize("name", ["c1_64", "tiny_8", "tiny_16", "tiny_32"])
+@pytest.mark.parametrize("name", ["c1_64", "tiny_8", "tiny_16", "tiny_32", "c1_64/spherical"])
 def test_single_map_matches_oracle(name):
     vs = _vs()
-    w = synth.workload(name)
+    w = synth.workload(name.split("/")[0])
+    if name.endswith("/spherical"):
+        w.corr = "spherical"                    # spherical correlation of the variation
     pd, pl, s = inputs(w)
     k = _kernel(w)
     th, info = vs.solve_steady(k, pd[0], pl[0], s[0], vs_params(w))

@@ -660,3 +660,25 @@ def test_transient_uniform_mode_fixture_is_current():
     # the step response rises monotonically towards the steady uniform mode
     s = np.array(d["S00"])
     assert np.all(np.diff(s) > 0)
+
+
+# ------------------------------------- input recipe: spherical correlation
+
+def test_spherical_variation_fields_follow_the_spherical_correlation():
+    # Sec. II-C: systematic variation with a spherical correlation of range phi.
+    # Empirical correlation along x over many fields against
+    # 1 - 1.5 r/phi + 0.5 (r/phi)^3 (0 beyond phi); standardised fields.
+    w = synth.workload("c1_64")
+    w.corr = "spherical"
+    phi = 2.5e-3
+    w.corr_len_m = (phi, phi)
+    z, _ = synth.variation_fields(w, 256, dtype=torch.float64)
+    z = z.numpy()
+    c = w.cell_m
+    for lag in (2, 6, 12, 20):
+        r = lag * c
+        a, b = z[:, 8:56, 8:56 - lag], z[:, 8:56, 8 + lag:56]
+        emp = float(np.mean(a * b) / np.sqrt(np.mean(a * a) * np.mean(b * b)))
+        x = min(r / phi, 1.0)
+        ref = 1 - 1.5 * x + 0.5 * x ** 3
+        assert emp == pytest.approx(ref, abs=0.06), (lag, emp, ref)
