@@ -46,6 +46,7 @@ constexpr long long kSpinLimit = 20000000LL;  // ~ seconds at ~100 ns per spin
 struct MapState {
   double mu;
   float mu_f;
+  float b_col, b_row;    // preconditioner coefficient of the next column / row phase
   unsigned resid_bits;
   float prev_resid;
   int growth;
@@ -78,6 +79,7 @@ struct PlanDev {
   int warm;              // some map has a warm start
   int window;            // transient: 0 untruncated, K >= 1 step responses settled from age K on
   int implicit;          // transient: per-step leakage fixed point
+  int adaptive;          // steady FP32: the preconditioner follows beta mu (1 + 2 alpha mean(u))
   float* xs;             // transient, implicit: the last source spectrum of the current step
   // physics variants (the k_solve_steady<true> instantiation); beta above is
   // then the preconditioner slope (the secant of a piecewise-linear table)
@@ -282,10 +284,12 @@ __device__ void row_task(const PlanDev& P, int task, int step, float2* buf) {
 
   if (!first) row_inverse(d, y0, buf);
 
-  // fused elementwise update
+  // fused elementwise update; bq is the preconditioner coefficient of the
+  // source term - bq u (the next column phase multiplies by K / (1 - bq K))
   const float beta = P.beta, alpha = P.alpha;
-  const float mu = (MODE == 0 && (!first || warm)) ? ms->mu_f : 0.f;
+  const float bq = (MODE == 0 && (!first || warm)) ? ms->b_row : 0.f;
   double mu_acc = 0.0;
+  float dsum = 0.f;      // sum of u (adaptive preconditioner)
   float resid = 0.f;
   int flags = 0;
   const size_t nn = (size_t)n * n;
@@ -343,13 +347,13 @@ __device__ void row_task(const PlanDev& P, int task, int step, float2* buf) {
               mu_acc += (double)pl[u][h];
             }
             d.theta[idx] = th;
-            q[h] = fmaf(pl[u][h], leak_factor(P, th), pd[u][h]) - beta * mu * uq;
+            q[h] = fmaf(pl[u][h], leak_factor(P, th), pd[u][h]) - bq * uq;
           } else if (warm) {
             // theta_0 from the warm start; u_0 = theta_0 / (s (1 + alpha theta_0))
             float t0 = old[u][h];
             float u0 = t0 / (sk[u][h] * fmaf(alpha, t0, 1.f));
             d.theta[idx] = t0;
-            q[h] = pd[u][h] + pl[u][h] + beta * fmaf(pl[u][h], t0, -mu * u0);
+            q[h] = fmaf(beta * pl[u][h], t0, pd[u][h] + pl[u][h]) - bq * u0;
           } else if (first) {
             d.theta[idx] = 0.f;
             q[h] = pd[u][h] + pl[u][h];
@@ -361,7 +365,8 @@ __device__ void row_task(const PlanDev& P, int task, int step, float2* buf) {
             if (!isfinite(th)) flags |= kFlagNonfinite;
             else resid = fmaxf(resid, fabsf(th - old[u][h]));
             d.theta[idx] = th;
-            q[h] = pd[u][h] + pl[u][h] + beta * fmaf(pl[u][h], th, -mu * uu);
+            q[h] = fmaf(beta * pl[u][h], th, pd[u][h] + pl[u][h]) - bq * uu;
+            dsum += uu;
           }
         } else {
           float th = 0.f;
@@ -380,6 +385,10 @@ __device__ void row_task(const PlanDev& P, int task, int step, float2* buf) {
   }
   if (MODE == 0 && first && !warm) {
     double tot = block_sum(mu_acc, red_d);
+    if (threadIdx.x == 0) P.part[d.part_off + chunk] = tot;
+  }
+  if (MODE == 0 && !first && !PHYS && P.adaptive) {
+    double tot = block_sum((double)dsum, red_d);
     if (threadIdx.x == 0) P.part[d.part_off + chunk] = tot;
   }
   if (!first || MODE == 1) {
@@ -439,7 +448,7 @@ __device__ void col_task(const PlanDev& P, int task, float2* buf, int step = 0, 
   fft_forward(buf, n, F, NP, tw);
 
   const float inv_n2 = 1.f / ((float)n * (float)n);
-  const float bm = P.beta * ((MODE == 0) ? ms->mu_f : 0.f);
+  const float bm = (MODE == 0) ? ms->b_col : 0.f;
   for (int it = threadIdx.x; it < F * (half + 1); it += blockDim.x) {
     int f = it & (F - 1), k = it >> lgF, nk = n - k;
     int ia = f * NP + pad(__ldg(&dr[k]));
@@ -543,6 +552,7 @@ __device__ void decide(const PlanDev& P, int it) {
       for (int i = 0; i < tasks; ++i) sum += P.part[d.part_off + i];
       s.mu = sum / ((double)d.n * d.n);
       s.mu_f = (float)s.mu;
+      s.b_col = s.b_row = P.beta * s.mu_f;
       s.active = 1;
       s.status = VS_OK;
       s.iters = 0;
@@ -555,6 +565,19 @@ __device__ void decide(const PlanDev& P, int it) {
       if (!s.active) continue;
       float r = __uint_as_float(s.resid_bits);
       s.iters = it;
+      if (P.adaptive) {
+        // the next column phase uses the coefficient of this row phase; the
+        // next row phase beta mu (1 + 2 alpha mean(u)) of this iterate, an
+        // estimate of the mean of beta P_leak0 dtheta/du
+        int tasks = d.n / d.rb;
+        double sum = 0.0;
+        for (int i = 0; i < tasks; ++i) sum += P.part[d.part_off + i];
+        const float b_next = P.beta * s.mu_f * fmaf(2.f * P.alpha, (float)(sum / ((double)d.n * d.n)), 1.f);
+        s.b_col = s.b_row;
+        // follow changes above 1e-3 only (the late iterations keep one b)
+        if (b_next >= 0.f && b_next < 0.95f / d.kmax && fabsf(b_next - s.b_row) > 1e-3f * s.b_row)
+          s.b_row = b_next;
+      }
       if (s.flags & kFlagNonfinite) {
         s.active = 0;
         s.status = VS_ERR_NONFINITE;
@@ -1659,7 +1682,7 @@ int plan_launch(vs_plan_t* p, cudaStream_t s, bool transient) {
   if (p->cluster && !transient) return plan_launch_cluster(p, s);
   VS_CUDA_TRY(cudaMemsetAsync(p->d_ctrl, 0, sizeof(Ctrl), s));
   VS_CUDA_TRY(cudaMemsetAsync(p->d_state, 0, sizeof(MapState) * p->n_items, s));
-  PlanDev P;
+  PlanDev P = {};
   P.maps = p->d_maps;
   P.row_map = p->d_row_map;
   P.col_map = p->d_col_map;
@@ -1693,6 +1716,7 @@ int plan_launch(vs_plan_t* p, cudaStream_t s, bool transient) {
     P.beta = (float)std::max(0.0, (pp.leak_g[i + 1] - pp.leak_g[i]) /
                                       (pp.leak_theta_K[i + 1] - pp.leak_theta_K[i]));
   }
+  P.adaptive = !transient && pp.precision == VS_PREC_FP32 && !vs_params_physics(&pp);
   P.window = transient ? p->tr_window : 0;
   P.implicit = transient ? p->tr_implicit : 0;
   // the implicit transient keeps the current step's source spectrum in the
@@ -2102,7 +2126,7 @@ extern "C" int vs_solve_steady_noalloc(vs_kernel k, const float* p_dyn, const fl
   k_noalloc_init<<<1, 256, 0, s>>>(m, base, l);
   VS_CUDA_TRY(cudaGetLastError());
 
-  PlanDev P;
+  PlanDev P = {};
   P.maps = reinterpret_cast<const MapDesc*>(base + l.desc);
   P.row_map = reinterpret_cast<const int*>(base + l.row_map);
   P.col_map = reinterpret_cast<const int*>(base + l.col_map);
@@ -2119,6 +2143,7 @@ extern "C" int vs_solve_steady_noalloc(vs_kernel k, const float* p_dyn, const fl
   P.tol = (float)params->tol_K;
   P.n_steps = 0;
   P.warm = 0;
+  P.adaptive = 1;
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3(std::max(1, std::min(per_sm * sms, std::max(row_tasks, col_tasks))));
   cfg.blockDim = dim3(kThreads);
