@@ -205,10 +205,13 @@ __global__ void __launch_bounds__(ClShape<N>::THREADS, ClShape<N>::MIN_BLOCKS)
   };
 
   // Row phase. mode 0: initial source from theta_0 = 0 (leakage sum into
-  // pl_sum); 1: initial source from the warm start; 2: iteration (brow holds
-  // the spectra of the column phase, pre-twiddled, at digit-reversed places).
+  // pl_sum; theta_0 is not stored); 1: initial source from the warm start;
+  // 2: iteration (brow holds the spectra of the column phase, pre-twiddled,
+  // at digit-reversed places); 3: the first iteration after mode 0 (the
+  // previous iterate is 0 and is not read).
   auto row_phase = [&](int mode, float mu, float& resid, int& flags, double& pl_sum) {
-    if (mode == 2) {
+    const bool iter = mode >= 2;
+    if (iter) {
       // brow holds the spectra in natural frequency order: the radix-R2 pass
       // takes frequencies blk + 16 r and leaves its outputs in place
       float2* p = brow + f2 * NP;
@@ -221,14 +224,14 @@ __global__ void __launch_bounds__(ClShape<N>::THREADS, ClShape<N>::MIN_BLOCKS)
       __syncthreads();
     }
     float2 v[16];
-    if (p16 && mode == 2) {
+    if (p16 && iter) {
       // radix-16 inputs of this thread: block j16 of the pass above
 #pragma unroll
       for (int r = 0; r < 16; ++r) v[r] = brow[f16 * NP + pad(16 * j16 + r)];
     }
-    if (mode == 2) __syncthreads();   // the forward pass below rewrites brow in another order
+    if (iter) __syncthreads();   // the forward pass below rewrites brow in another order
     if (p16) {
-      if (mode == 2) inv16(v, j16);   // v[r] = u at Makhoul position j16 + M1 r of rows ya, ya + 1
+      if (iter) inv16(v, j16);   // v[r] = u at Makhoul position j16 + M1 r of rows ya, ya + 1
       // Positions m (< N/2, x = 2m) of this lane and N - 1 - m (x + 1) of the
       // mirror lane are updated together, so every input is read as a
       // coalesced float2 (x, x + 1); u and q of x + 1 travel by shuffle.
@@ -287,7 +290,7 @@ __global__ void __launch_bounds__(ClShape<N>::THREADS, ClShape<N>::MIN_BLOCKS)
               }
               (e ? qo : qe)[h] = q;
             }
-            *reinterpret_cast<float2*>(d.theta + idx) = make_float2(th[0], th[1]);
+            if (mode != 0) *reinterpret_cast<float2*>(d.theta + idx) = make_float2(th[0], th[1]);
           }
           v[r] = make_float2(qe[0], qe[1]);
           v[15 - r] = shfl2(make_float2(qo[0], qo[1]), partner16);
@@ -450,6 +453,20 @@ __global__ void __launch_bounds__(ClShape<N>::THREADS, ClShape<N>::MIN_BLOCKS)
   float prev = INFINITY;
   double mu = 0.0;
   bool stop = false;
+  // this CTA's kernel values for the multiplier table (pairs a / b of frequency
+  // column j, N / 16 per thread), loaded while the cluster exchanges the
+  // leakage partial sums
+  constexpr int kKv = kClF * N / kClThreads;
+  float2 kv[kKv];
+  auto load_k = [&]() {
+#pragma unroll
+    for (int i = 0; i < kKv; ++i) {
+      const int it = t + i * kClThreads;
+      const int q = it % N, j = j0 + it / N;
+      const int pa = j == 0 ? 0 : j, pb = j == 0 ? half : N - j;
+      kv[i] = make_float2(__ldg(&d.Kt[(size_t)pa * N + q]), __ldg(&d.Kt[(size_t)pb * N + q]));
+    }
+  };
   cl_arrive_relaxed();  // peers store into this CTA only after every CTA started
 
   // initial source (Eq. 13 at theta_0) and the mean leakage mu (Sec. IV-C)
@@ -461,6 +478,7 @@ __global__ void __launch_bounds__(ClShape<N>::THREADS, ClShape<N>::MIN_BLOCKS)
     cl_wait();
     if (t == 0)
       for (int r = 0; r < ranks; ++r) cl_put(cl_map(&slots->part[rank], (unsigned)r), tot);
+    load_k();
     cl_sync();
     mu = cluster_mu();
     if ((double)beta * mu * (double)d.kmax >= 0.999) {
@@ -481,11 +499,15 @@ __global__ void __launch_bounds__(ClShape<N>::THREADS, ClShape<N>::MIN_BLOCKS)
     cl_wait();
     row_phase(0, 0.f, r0, f0, acc);
     put_slots(true);
+    load_k();
     cl_sync();
     mu = cluster_mu();
     if ((double)beta * mu * (double)d.kmax >= 0.999) {
       status = VS_ERR_RUNAWAY;
       stop = true;
+      // theta_0 = 0 is the result of a map stopped before its first iterate
+      for (int i = t; i < kClRows * N / 4; i += kClThreads)
+        *reinterpret_cast<float4*>(d.theta + (size_t)y0 * N + 4 * i) = make_float4(0.f, 0.f, 0.f, 0.f);
     }
   }
 
@@ -496,12 +518,13 @@ __global__ void __launch_bounds__(ClShape<N>::THREADS, ClShape<N>::MIN_BLOCKS)
       // of the two unnormalised inverse transforms folded in
       const float bm = beta * mu_f;
       const float inv_n2 = 1.f / ((float)N * (float)N);
-      for (int it = t; it < kClF * N; it += kClThreads) {
-        const int q = it % N, jj = it / N, j = j0 + jj;
-        const int pa = j == 0 ? 0 : j, pb = j == 0 ? half : N - j;
-        const float ka = __ldg(&d.Kt[(size_t)pa * N + q]), kb = __ldg(&d.Kt[(size_t)pb * N + q]);
+#pragma unroll
+      for (int i = 0; i < kKv; ++i) {
+        const int it = t + i * kClThreads;
+        const int q = it % N, jj = it / N;
+        const float ka = kv[i].x, kb = kv[i].y;
         Ls[q * kClF + (jj ^ (q & (kClF - 1)))] =
-            make_float2(ka / (1.f - bm * ka) * inv_n2, kb / (1.f - bm * kb) * inv_n2);
+            make_float2(__fdividef(ka, 1.f - bm * ka) * inv_n2, __fdividef(kb, 1.f - bm * kb) * inv_n2);
       }
       __syncthreads();
     }
@@ -511,7 +534,7 @@ __global__ void __launch_bounds__(ClShape<N>::THREADS, ClShape<N>::MIN_BLOCKS)
       float resid = 0.f;
       int flags = 0;
       double unused = 0.0;
-      row_phase(2, mu_f, resid, flags, unused);
+      row_phase(it == 1 && !d.theta_init ? 3 : 2, mu_f, resid, flags, unused);
       put_slots(false);
       cl_sync();
       // the same decision in every thread of every CTA of the cluster
