@@ -211,6 +211,9 @@ __global__ void __launch_bounds__(ClShape<N>::THREADS, ClShape<N>::MIN_BLOCKS)
   // previous iterate is 0 and is not read).
   auto row_phase = [&](int mode, float mu, float& resid, int& flags, double& pl_sum) {
     const bool iter = mode >= 2;
+    // mode 0: compensated FP32 sum of P_leak0 (s_hi + s_lo is the exact sum to
+    // ~1e-14 relative; FP64 adds run at a small fraction of the FP32 rate)
+    float s_hi = 0.f, s_lo = 0.f;
     if (iter) {
       // brow holds the spectra in natural frequency order: the radix-R2 pass
       // takes frequencies blk + 16 r and leaves its outputs in place
@@ -273,7 +276,9 @@ __global__ void __launch_bounds__(ClShape<N>::THREADS, ClShape<N>::MIN_BLOCKS)
               if (mode == 0) {
                 th[e] = 0.f;
                 q = PD + PL;
-                pl_sum += (double)PL;
+                const float tsum = s_hi + PL, bp = tsum - s_hi;
+                s_lo += (s_hi - (tsum - bp)) + (PL - bp);
+                s_hi = tsum;
               } else if (mode == 1) {
                 // u_0 = theta_0 / (s (1 + alpha theta_0))
                 const float u0 = O / (S * fmaf(alpha, O, 1.f));
@@ -299,12 +304,18 @@ __global__ void __launch_bounds__(ClShape<N>::THREADS, ClShape<N>::MIN_BLOCKS)
       fwd16(v, j16);
       store16(brow, v, f16, j16);
     }
-    // per-warp partials of the residual, flags and leakage sum
+    // per-warp partials of the residual and flags (iterations) or of the
+    // leakage sum (mode 0, the only FP64 work of the solve)
+    if (mode == 0) {
+      pl_sum = (double)s_hi + (double)s_lo;
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-      resid = fmaxf(resid, __shfl_down_sync(0xffffffffu, resid, o));
-      flags |= __shfl_down_sync(0xffffffffu, flags, o);
-      pl_sum += __shfl_down_sync(0xffffffffu, pl_sum, o);
+      for (int o = 16; o > 0; o >>= 1) pl_sum += __shfl_down_sync(0xffffffffu, pl_sum, o);
+    } else {
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) {
+        resid = fmaxf(resid, __shfl_down_sync(0xffffffffu, resid, o));
+        flags |= __shfl_down_sync(0xffffffffu, flags, o);
+      }
     }
     if (lane == 0) {
       red_f[warp] = resid;
