@@ -89,6 +89,20 @@ struct PlanDev {
   float leak_x[VS_MAX_LEAK_POINTS], leak_y[VS_MAX_LEAK_POINTS];
 };
 
+// ------------------------------------------------------------ sums
+// Compensated FP32 accumulation (Knuth's two-sum): hi + lo is the exact sum of
+// the added values to about 1e-14 relative. FP64 adds run at a small fraction
+// of the FP32 rate on this part, and the leakage sums touch every cell.
+struct Sum2 {
+  float hi = 0.f, lo = 0.f;
+  __device__ __forceinline__ void add(float x) {
+    const float t = hi + x, bp = t - hi;
+    lo += (hi - (t - bp)) + (x - bp);
+    hi = t;
+  }
+  __device__ __forceinline__ double value() const { return (double)hi + (double)lo; }
+};
+
 // ------------------------------------------------------------ physics variants
 // Leakage factor g(theta): linear, or piecewise linear through the table with
 // the end segments extended (Sec. II-E).
@@ -288,7 +302,7 @@ __device__ void row_task(const PlanDev& P, int task, int step, float2* buf) {
   // source term - bq u (the next column phase multiplies by K / (1 - bq K))
   const float beta = P.beta, alpha = P.alpha;
   const float bq = (MODE == 0 && (!first || warm)) ? ms->b_row : 0.f;
-  double mu_acc = 0.0;
+  Sum2 mu_acc;           // sum of P_leak0 (first pass)
   float dsum = 0.f;      // sum of u (adaptive preconditioner)
   float resid = 0.f;
   int flags = 0;
@@ -344,7 +358,7 @@ __device__ void row_task(const PlanDev& P, int task, int step, float2* buf) {
               if (!isfinite(th)) flags |= kFlagNonfinite;
               else resid = fmaxf(resid, fabsf(th - old[u][h]));
             } else {
-              mu_acc += (double)pl[u][h];
+              mu_acc.add(pl[u][h]);
             }
             d.theta[idx] = th;
             q[h] = fmaf(pl[u][h], leak_factor(P, th), pd[u][h]) - bq * uq;
@@ -357,7 +371,7 @@ __device__ void row_task(const PlanDev& P, int task, int step, float2* buf) {
           } else if (first) {
             d.theta[idx] = 0.f;
             q[h] = pd[u][h] + pl[u][h];
-            mu_acc += (double)pl[u][h];
+            mu_acc.add(pl[u][h]);
           } else {
             float den = fmaf(-alpha * sk[u][h], uu, 1.f);
             if (!(den > 0.05f)) flags |= kFlagRunaway;
@@ -384,7 +398,7 @@ __device__ void row_task(const PlanDev& P, int task, int step, float2* buf) {
     }
   }
   if (MODE == 0 && first && !warm) {
-    double tot = block_sum(mu_acc, red_d);
+    double tot = block_sum(mu_acc.value(), red_d);
     if (threadIdx.x == 0) P.part[d.part_off + chunk] = tot;
   }
   if (MODE == 0 && !first && !PHYS && P.adaptive) {
@@ -1016,7 +1030,7 @@ __device__ bool tc_task(const PlanDev& P, TcCtx& c, int pass, int task) {
   const int tile = task - d.row_off;
   const int r0 = tile * 128;
   bool ok = true;
-  double mu_acc = 0.0;
+  Sum2 mu_acc;
   float resid = 0.f;
   int flags = 0;
   if (pass == kTcMu || pass == kTcWarm) {
@@ -1026,7 +1040,7 @@ __device__ bool tc_task(const PlanDev& P, TcCtx& c, int pass, int task) {
       size_t idx = (size_t)r0 * n + i;
       float pl = __ldg(&d.p_leak0[idx]);
       if (pass == kTcMu) {
-        mu_acc += (double)pl;
+        mu_acc.add(pl);
       } else {
         float t0 = d.theta_init ? __ldg(&d.theta_init[idx]) : 0.f;
         float sk = d.s ? __ldg(&d.s[idx]) : 1.f;
@@ -1036,7 +1050,7 @@ __device__ bool tc_task(const PlanDev& P, TcCtx& c, int pass, int task) {
       }
     }
     if (pass == kTcMu) {
-      double tot = block_sum(mu_acc, red_d);
+      double tot = block_sum(mu_acc.value(), red_d);
       if (threadIdx.x == 0) P.part[d.part_off + tile] = tot;
     }
     __syncthreads();
@@ -1098,14 +1112,17 @@ __device__ bool tc_task(const PlanDev& P, TcCtx& c, int pass, int task) {
       size_t idx = (size_t)r0 * n + 4 * (size_t)i;
       *reinterpret_cast<float4*>(d.theta + idx) = make_float4(0.f, 0.f, 0.f, 0.f);
       float4 w4 = __ldg(reinterpret_cast<const float4*>(d.p_leak0 + idx));
-      mu_acc += (double)w4.x + (double)w4.y + (double)w4.z + (double)w4.w;
+      mu_acc.add(w4.x);
+      mu_acc.add(w4.y);
+      mu_acc.add(w4.z);
+      mu_acc.add(w4.w);
     }
   }
   // the epilogue scratch (stage 0) is refilled by the async proxy next
   vstc::fence_proxy_async_smem();
   vstc::tc_fence_before();
   if (first) {
-    double tot = block_sum(mu_acc, red_d);
+    double tot = block_sum(mu_acc.value(), red_d);
     if (threadIdx.x == 0) P.part[d.part_off + tile] = tot;
   } else if (pass == kTcRowInv) {
     float r = block_max(resid, red_f);
