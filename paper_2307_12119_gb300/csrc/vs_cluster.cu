@@ -288,7 +288,7 @@ __global__ void __launch_bounds__(ClShape<N>::THREADS, ClShape<N>::MIN_BLOCKS)
                 const float uu = e ? (h ? um.y : um.x) : (h ? v[r].y : v[r].x);
                 const float den = fmaf(-alpha * S, uu, 1.f);
                 if (!(den > 0.05f)) flags |= kFlagRunaway;
-                th[e] = S * uu / den;
+                th[e] = __fdividef(S * uu, den);   // 2 ulp, far below the FFT noise
                 if (!isfinite(th[e])) flags |= kFlagNonfinite;
                 else resid = fmaxf(resid, fabsf(th[e] - O));
                 q = PD + PL + beta * fmaf(PL, th[e], -mu * uu);
