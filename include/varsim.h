@@ -97,25 +97,24 @@ typedef struct {
                                  n = 128 .. 1024 (power of two); outputs are
                                  produced in chunks of 256 columns */
 
-/* Execution engines of the FP32 steady solve (the same fixed point and
- * update; they differ in data movement and in the preconditioner coefficient
- * b of the iteration u <- K/(1 - b K) * (P_dyn + P_leak0 (1 + beta theta) - b u),
- * which does not change the fixed point).
+/* Execution engines of the FP32 steady solve (identical arithmetic, different
+ * data movement). Both precondition the iteration
+ *   u <- K/(1 - b K) * (P_dyn + P_leak0 (1 + beta theta) - b u)
+ * (every scalar b has the same fixed point) with b = beta mu, and a cold start
+ * switches to b = beta mu (1 + 2 alpha mean(u_1)) after its first iterate (about
+ * the mean of beta P_leak0 dtheta/du), which saves about one iteration in ten
+ * at 1e-2 K and one in six at 1e-4 K.
  *   VS_ENGINE_STREAMED: one cooperative launch over all maps of a plan; the
  *     spectral work map streams through global memory between the row and
- *     column phases, phases separated by grid barriers; any n. b follows
- *     beta mu (1 + 2 alpha mean(u)) of the last iterate (the mean of
- *     beta P_leak0 dtheta/du), which saves about one iteration in ten at
- *     1e-2 K and one in six at 1e-4 K; b = beta mu with a physics variant.
+ *     column phases, phases separated by grid barriers; any n.
  *   VS_ENGINE_CLUSTER: one thread-block cluster of n/32 CTAs per map that
  *     keeps the map in shared memory for the whole solve (transposes through
  *     distributed shared memory, cluster barriers); n in [32, 256]; one launch
- *     per distinct n of a plan. b = beta mu (adapting it costs this engine
- *     more per iteration than the iterations it saves at 1e-2 K).
+ *     per distinct n of a plan.
  *   VS_ENGINE_AUTO: the cluster engine when precision is FP32 and every map
  *     has n in [32, 256], the streamed engine otherwise.
  * The transient solve and vs_solve_steady_noalloc always use the streamed
- * engine; VS_PREC_BF16_SPLIT has its own tensor-core engine. */
+ * engine; VS_PREC_BF16_SPLIT has its own tensor-core engine (b = beta mu). */
 #define VS_ENGINE_AUTO 0
 #define VS_ENGINE_STREAMED 1
 #define VS_ENGINE_CLUSTER 2

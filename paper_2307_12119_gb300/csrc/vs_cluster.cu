@@ -289,6 +289,7 @@ __global__ void __launch_bounds__(ClShape<N>::THREADS, ClShape<N>::MIN_BLOCKS)
                 const float den = fmaf(-alpha * S, uu, 1.f);
                 if (!(den > 0.05f)) flags |= kFlagRunaway;
                 th[e] = __fdividef(S * uu, den);   // 2 ulp, far below the FFT noise
+                if (mode == 3) s_hi += uu;          // mean(u) of the first iterate
                 if (!isfinite(th[e])) flags |= kFlagNonfinite;
                 else resid = fmaxf(resid, fabsf(th[e] - O));
                 q = PD + PL + beta * fmaf(PL, th[e], -mu * uu);
@@ -304,13 +305,15 @@ __global__ void __launch_bounds__(ClShape<N>::THREADS, ClShape<N>::MIN_BLOCKS)
       fwd16(v, j16);
       store16(brow, v, f16, j16);
     }
-    // per-warp partials of the residual and flags (iterations) or of the
-    // leakage sum (mode 0, the only FP64 work of the solve)
-    if (mode == 0) {
+    // per-warp partials: the leakage sum (mode 0) or the sum of u of the
+    // first iterate (mode 3), the only FP64 work of the solve; the residual
+    // and flags of an iterate
+    if (mode == 0 || mode == 3) {
       pl_sum = (double)s_hi + (double)s_lo;
 #pragma unroll
       for (int o = 16; o > 0; o >>= 1) pl_sum += __shfl_down_sync(0xffffffffu, pl_sum, o);
-    } else {
+    }
+    if (iter) {
 #pragma unroll
       for (int o = 16; o > 0; o >>= 1) {
         resid = fmaxf(resid, __shfl_down_sync(0xffffffffu, resid, o));
@@ -434,7 +437,8 @@ __global__ void __launch_bounds__(ClShape<N>::THREADS, ClShape<N>::MIN_BLOCKS)
     }
   };
 
-  auto put_slots = [&](bool part) {
+  // part: the FP64 partial sum; resid: the residual and flags
+  auto put_slots = [&](bool part, bool resid) {
     if (t == 0) {
       float rm = 0.f;
       int fo = 0;
@@ -445,9 +449,8 @@ __global__ void __launch_bounds__(ClShape<N>::THREADS, ClShape<N>::MIN_BLOCKS)
         ps += red_d[w];
       }
       for (int r = 0; r < ranks; ++r) {
-        if (part) {
-          cl_put(cl_map(&slots->part[rank], (unsigned)r), ps);
-        } else {
+        if (part) cl_put(cl_map(&slots->part[rank], (unsigned)r), ps);
+        if (resid) {
           cl_put(cl_map(&slots->resid[rank], (unsigned)r), rm);
           cl_put(cl_map(&slots->flags[rank], (unsigned)r), fo);
         }
@@ -509,7 +512,7 @@ __global__ void __launch_bounds__(ClShape<N>::THREADS, ClShape<N>::MIN_BLOCKS)
     double acc = 0.0;
     cl_wait();
     row_phase(0, 0.f, r0, f0, acc);
-    put_slots(true);
+    put_slots(true, false);
     load_k();
     cl_sync();
     mu = cluster_mu();
@@ -539,14 +542,35 @@ __global__ void __launch_bounds__(ClShape<N>::THREADS, ClShape<N>::MIN_BLOCKS)
       }
       __syncthreads();
     }
+    // Preconditioner: the source term - beta mu_p u and the multiplier
+    // K / (1 - beta mu_p K) have the same fixed point for every mu_p. A cold
+    // start begins with mu_p = mu and then takes mu_p = mu (1 + 2 alpha
+    // mean(u_1)) from its first iterate: beta P_leak0 dtheta/du, with dtheta/du
+    // = s / (1 - alpha s u)^2, averages about that over the die, so the
+    // remaining coupling is the variation alone. The row phase of iteration 2
+    // is the first to use it, so the table is rescaled just before it, after
+    // the column phase of iteration 2 has used the old one.
+    float mu_p = mu_f, mu_next = mu_f;
+    const bool cold = !d.theta_init;
     for (int it = 1; it <= P.max_iter; ++it) {
       col_phase();
       cl_sync();
+      if (mu_next != mu_p) {
+        // 1/L' = 1/L + beta (mu_p - mu_next) N^2 for L = K / (1 - beta mu_p K) / N^2
+        const float dbn = beta * (mu_p - mu_next) * (float)N * (float)N;
+        for (int i = t; i < kClF * N; i += kClThreads) {
+          float2 L = Ls[i];
+          L.x = __fdividef(L.x, fmaf(dbn, L.x, 1.f));
+          L.y = __fdividef(L.y, fmaf(dbn, L.y, 1.f));
+          Ls[i] = L;
+        }
+        mu_p = mu_next;
+      }
       float resid = 0.f;
       int flags = 0;
-      double unused = 0.0;
-      row_phase(it == 1 && !d.theta_init ? 3 : 2, mu_f, resid, flags, unused);
-      put_slots(false);
+      double usum = 0.0;
+      row_phase(it == 1 && cold ? 3 : 2, mu_p, resid, flags, usum);
+      put_slots(it == 1 && cold, true);
       cl_sync();
       // the same decision in every thread of every CTA of the cluster
       float rr = 0.f;
@@ -574,6 +598,12 @@ __global__ void __launch_bounds__(ClShape<N>::THREADS, ClShape<N>::MIN_BLOCKS)
       }
       prev = rr;
       if (stop) break;
+      if (it == 1 && cold) {
+        double us = 0.0;
+        for (int r = 0; r < ranks; ++r) us += slots->part[r];
+        const float m = mu_f * fmaf(2.f * alpha, (float)(us / ((double)N * N)), 1.f);
+        if (m > 0.f && beta * m * d.kmax < 0.95f) mu_next = m;
+      }
     }
   }
   if (rank == 0 && t == 0) {

@@ -79,7 +79,7 @@ struct PlanDev {
   int warm;              // some map has a warm start
   int window;            // transient: 0 untruncated, K >= 1 step responses settled from age K on
   int implicit;          // transient: per-step leakage fixed point
-  int adaptive;          // steady FP32: the preconditioner follows beta mu (1 + 2 alpha mean(u))
+  int adaptive;          // steady FP32: the preconditioner takes beta mu (1 + 2 alpha mean(u_1))
   float* xs;             // transient, implicit: the last source spectrum of the current step
   // physics variants (the k_solve_steady<true> instantiation); beta above is
   // then the preconditioner slope (the secant of a piecewise-linear table)
@@ -401,7 +401,7 @@ __device__ void row_task(const PlanDev& P, int task, int step, float2* buf) {
     double tot = block_sum(mu_acc.value(), red_d);
     if (threadIdx.x == 0) P.part[d.part_off + chunk] = tot;
   }
-  if (MODE == 0 && !first && !PHYS && P.adaptive) {
+  if (MODE == 0 && step == 1 && !d.theta_init && !PHYS && P.adaptive) {
     double tot = block_sum((double)dsum, red_d);
     if (threadIdx.x == 0) P.part[d.part_off + chunk] = tot;
   }
@@ -579,18 +579,17 @@ __device__ void decide(const PlanDev& P, int it) {
       if (!s.active) continue;
       float r = __uint_as_float(s.resid_bits);
       s.iters = it;
-      if (P.adaptive) {
-        // the next column phase uses the coefficient of this row phase; the
-        // next row phase beta mu (1 + 2 alpha mean(u)) of this iterate, an
-        // estimate of the mean of beta P_leak0 dtheta/du
+      // the next column phase uses the coefficient of this row phase; after
+      // the first iterate of a cold start the row phases take
+      // beta mu (1 + 2 alpha mean(u_1)), an estimate of the mean of
+      // beta P_leak0 dtheta/du
+      s.b_col = s.b_row;
+      if (P.adaptive && it == 1 && !d.theta_init) {
         int tasks = d.n / d.rb;
         double sum = 0.0;
         for (int i = 0; i < tasks; ++i) sum += P.part[d.part_off + i];
         const float b_next = P.beta * s.mu_f * fmaf(2.f * P.alpha, (float)(sum / ((double)d.n * d.n)), 1.f);
-        s.b_col = s.b_row;
-        // follow changes above 1e-3 only (the late iterations keep one b)
-        if (b_next >= 0.f && b_next < 0.95f / d.kmax && fabsf(b_next - s.b_row) > 1e-3f * s.b_row)
-          s.b_row = b_next;
+        if (b_next > 0.f && b_next * d.kmax < 0.95f) s.b_row = b_next;
       }
       if (s.flags & kFlagNonfinite) {
         s.active = 0;

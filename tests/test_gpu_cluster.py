@@ -51,10 +51,9 @@ def test_cluster_matches_oracle_and_streamed(name):
         assert emax <= REQ_MAX_K and rel <= REQ_REL_L2
         assert emax <= ENG_TOL_K, (i, emax)
         assert 1 <= ic[i]["iterations"] < it
-        # the same fixed point as the streamed engine; the streamed engine adapts
-        # its preconditioner, so the two stop at different iterates within tol
+        # same arithmetic as the streamed engine, only the data movement differs
         assert abs(ic[i]["iterations"] - is_[i]["iterations"]) <= 1
-        assert float((thc[i] - ths[i]).abs().max()) <= 1e-3
+        assert float((thc[i] - ths[i]).abs().max()) <= 2e-4
         assert ic[i]["mu_W"] == pytest.approx(float(pl[i].double().mean()), rel=1e-12)
         assert ic[i]["residual_K"] <= 1e-4
 
