@@ -46,6 +46,7 @@ struct ClShape {
 
 struct ClSlots {
   double part[kClMaxRanks];
+  double part2[kClMaxRanks];
   float resid[kClMaxRanks];
   int flags[kClMaxRanks];
 };
@@ -205,15 +206,12 @@ __global__ void __launch_bounds__(ClShape<N>::THREADS, ClShape<N>::MIN_BLOCKS)
   };
 
   // Row phase. mode 0: initial source from theta_0 = 0 (leakage sum into
-  // pl_sum; theta_0 is not stored); 1: initial source from the warm start;
-  // 2: iteration (brow holds the spectra of the column phase, pre-twiddled,
-  // at digit-reversed places); 3: the first iteration after mode 0 (the
-  // previous iterate is 0 and is not read).
-  auto row_phase = [&](int mode, float mu, float& resid, int& flags, double& pl_sum) {
+  // pl_sum; theta_0 is not stored); 1: initial source from theta_0, the warm
+  // start's map or the uniform th0 (not stored); 2: iteration (brow holds
+  // the spectra of the column phase, pre-twiddled, at digit-reversed places);
+  // 3: the first iteration after a uniform theta_0 = th0 (not read).
+  auto row_phase = [&](int mode, float mu, float th0, float& resid, int& flags) {
     const bool iter = mode >= 2;
-    // mode 0: compensated FP32 sum of P_leak0 (s_hi + s_lo is the exact sum to
-    // ~1e-14 relative; FP64 adds run at a small fraction of the FP32 rate)
-    float s_hi = 0.f, s_lo = 0.f;
     if (iter) {
       // brow holds the spectra in natural frequency order: the radix-R2 pass
       // takes frequencies blk + 16 r and leaves its outputs in place
@@ -255,7 +253,8 @@ __global__ void __launch_bounds__(ClShape<N>::THREADS, ClShape<N>::MIN_BLOCKS)
             pd[u][h] = ld2(d.p_dyn, idx);
             sk[u][h] = d.s ? ld2(d.s, idx) : make_float2(1.f, 1.f);
             old[u][h] = mode == 2 ? *reinterpret_cast<const float2*>(d.theta + idx)
-                        : mode == 1 ? ld2(d.theta_init, idx) : make_float2(0.f, 0.f);
+                        : (mode == 1 && d.theta_init) ? ld2(d.theta_init, idx)
+                        : make_float2(th0, th0);
           }
         }
 #pragma unroll
@@ -273,15 +272,9 @@ __global__ void __launch_bounds__(ClShape<N>::THREADS, ClShape<N>::MIN_BLOCKS)
               const float PL = e ? pl[u][h].y : pl[u][h].x, PD = e ? pd[u][h].y : pd[u][h].x;
               const float S = e ? sk[u][h].y : sk[u][h].x, O = e ? old[u][h].y : old[u][h].x;
               float q;
-              if (mode == 0) {
-                th[e] = 0.f;
-                q = PD + PL;
-                const float tsum = s_hi + PL, bp = tsum - s_hi;
-                s_lo += (s_hi - (tsum - bp)) + (PL - bp);
-                s_hi = tsum;
-              } else if (mode == 1) {
+              if (mode == 1) {
                 // u_0 = theta_0 / (s (1 + alpha theta_0))
-                const float u0 = O / (S * fmaf(alpha, O, 1.f));
+                const float u0 = __fdividef(O, S * fmaf(alpha, O, 1.f));
                 th[e] = O;
                 q = PD + PL + beta * fmaf(PL, O, -mu * u0);
               } else {
@@ -289,14 +282,15 @@ __global__ void __launch_bounds__(ClShape<N>::THREADS, ClShape<N>::MIN_BLOCKS)
                 const float den = fmaf(-alpha * S, uu, 1.f);
                 if (!(den > 0.05f)) flags |= kFlagRunaway;
                 th[e] = __fdividef(S * uu, den);   // 2 ulp, far below the FFT noise
-                if (mode == 3) s_hi += uu;          // mean(u) of the first iterate
                 if (!isfinite(th[e])) flags |= kFlagNonfinite;
                 else resid = fmaxf(resid, fabsf(th[e] - O));
                 q = PD + PL + beta * fmaf(PL, th[e], -mu * uu);
               }
               (e ? qo : qe)[h] = q;
             }
-            if (mode != 0) *reinterpret_cast<float2*>(d.theta + idx) = make_float2(th[0], th[1]);
+            // theta_0 is kept only for a warm start (a uniform one is th0)
+            if (mode == 2 || mode == 3 || d.theta_init)
+              *reinterpret_cast<float2*>(d.theta + idx) = make_float2(th[0], th[1]);
           }
           v[r] = make_float2(qe[0], qe[1]);
           v[15 - r] = shfl2(make_float2(qo[0], qo[1]), partner16);
@@ -305,14 +299,7 @@ __global__ void __launch_bounds__(ClShape<N>::THREADS, ClShape<N>::MIN_BLOCKS)
       fwd16(v, j16);
       store16(brow, v, f16, j16);
     }
-    // per-warp partials: the leakage sum (mode 0) or the sum of u of the
-    // first iterate (mode 3), the only FP64 work of the solve; the residual
-    // and flags of an iterate
-    if (mode == 0 || mode == 3) {
-      pl_sum = (double)s_hi + (double)s_lo;
-#pragma unroll
-      for (int o = 16; o > 0; o >>= 1) pl_sum += __shfl_down_sync(0xffffffffu, pl_sum, o);
-    }
+    // per-warp partials of the residual and flags of an iterate
     if (iter) {
 #pragma unroll
       for (int o = 16; o > 0; o >>= 1) {
@@ -323,7 +310,6 @@ __global__ void __launch_bounds__(ClShape<N>::THREADS, ClShape<N>::MIN_BLOCKS)
     if (lane == 0) {
       red_f[warp] = resid;
       red_i[warp] = flags;
-      red_d[warp] = pl_sum;
     }
     __syncthreads();
     // radix-R2 pass: Z[k], k = 16 r + blk; pair with N - k from the partner
@@ -437,23 +423,18 @@ __global__ void __launch_bounds__(ClShape<N>::THREADS, ClShape<N>::MIN_BLOCKS)
     }
   };
 
-  // part: the FP64 partial sum; resid: the residual and flags
-  auto put_slots = [&](bool part, bool resid) {
+  // the residual and flags of an iterate to every CTA of the cluster
+  auto put_slots = [&]() {
     if (t == 0) {
       float rm = 0.f;
       int fo = 0;
-      double ps = 0.0;
       for (int w = 0; w < kClThreads / 32; ++w) {
         rm = fmaxf(rm, red_f[w]);
         fo |= red_i[w];
-        ps += red_d[w];
       }
       for (int r = 0; r < ranks; ++r) {
-        if (part) cl_put(cl_map(&slots->part[rank], (unsigned)r), ps);
-        if (resid) {
-          cl_put(cl_map(&slots->resid[rank], (unsigned)r), rm);
-          cl_put(cl_map(&slots->flags[rank], (unsigned)r), fo);
-        }
+        cl_put(cl_map(&slots->resid[rank], (unsigned)r), rm);
+        cl_put(cl_map(&slots->flags[rank], (unsigned)r), fo);
       }
     }
   };
@@ -483,54 +464,96 @@ __global__ void __launch_bounds__(ClShape<N>::THREADS, ClShape<N>::MIN_BLOCKS)
   };
   cl_arrive_relaxed();  // peers store into this CTA only after every CTA started
 
-  // initial source (Eq. 13 at theta_0) and the mean leakage mu (Sec. IV-C)
-  if (d.theta_init) {
-    double acc = 0.0;
-    for (int i = t; i < kClRows * N; i += kClThreads)
-      acc += (double)__ldg(&d.p_leak0[(size_t)y0 * N + i]);
-    const double tot = block_sum(acc, red_d);
+  // The means of the inputs over the die: mu = mean(P_leak0) (Sec. IV-C) and,
+  // for a cold start, mean(P_dyn), as compensated FP32 sums.
+  const bool cold = !d.theta_init;
+  {
+    float lh = 0.f, ll = 0.f, dh = 0.f, dl = 0.f;
+    auto add2 = [](float& hi, float& lo, float x) {
+      const float tsum = hi + x, bp = tsum - hi;
+      lo += (hi - (tsum - bp)) + (x - bp);
+      hi = tsum;
+    };
+    // all loads of a thread are issued before the sums (first touch of the
+    // inputs: HBM latency)
+    constexpr int kM = kClRows * N / 4 / kClThreads;
+    float4 a[kM], c[kM];
+#pragma unroll
+    for (int k = 0; k < kM; ++k) {
+      const size_t idx = (size_t)y0 * N + 4 * (size_t)(t + k * kClThreads);
+      a[k] = __ldg(reinterpret_cast<const float4*>(d.p_leak0 + idx));
+      c[k] = cold ? __ldg(reinterpret_cast<const float4*>(d.p_dyn + idx)) : make_float4(0.f, 0.f, 0.f, 0.f);
+    }
+#pragma unroll
+    for (int k = 0; k < kM; ++k) {
+      add2(lh, ll, a[k].x);
+      add2(lh, ll, a[k].y);
+      add2(lh, ll, a[k].z);
+      add2(lh, ll, a[k].w);
+      add2(dh, dl, c[k].x);
+      add2(dh, dl, c[k].y);
+      add2(dh, dl, c[k].z);
+      add2(dh, dl, c[k].w);
+    }
+    const double tot_l = block_sum((double)lh + (double)ll, red_d);
+    const double tot_d = cold ? block_sum((double)dh + (double)dl, red_d) : 0.0;
     cl_wait();
     if (t == 0)
-      for (int r = 0; r < ranks; ++r) cl_put(cl_map(&slots->part[rank], (unsigned)r), tot);
-    load_k();
-    cl_sync();
-    mu = cluster_mu();
-    if ((double)beta * mu * (double)d.kmax >= 0.999) {
-      status = VS_ERR_RUNAWAY;
-      stop = true;
-    } else {
-      float r0 = 0.f;
-      int f0 = 0;
-      double unused = 0.0;
-      // the peers' start is already established by the barrier above
-      row_phase(1, (float)mu, r0, f0, unused);
-      cl_sync();
-    }
-  } else {
-    float r0 = 0.f;
-    int f0 = 0;
-    double acc = 0.0;
-    cl_wait();
-    row_phase(0, 0.f, r0, f0, acc);
-    put_slots(true, false);
-    load_k();
-    cl_sync();
-    mu = cluster_mu();
-    if ((double)beta * mu * (double)d.kmax >= 0.999) {
-      status = VS_ERR_RUNAWAY;
-      stop = true;
-      // theta_0 = 0 is the result of a map stopped before its first iterate
+      for (int r = 0; r < ranks; ++r) {
+        cl_put(cl_map(&slots->part[rank], (unsigned)r), tot_l);
+        cl_put(cl_map(&slots->part2[rank], (unsigned)r), tot_d);
+      }
+  }
+  load_k();
+  cl_sync();
+  mu = cluster_mu();
+  // Preconditioner and start. The source term - beta mu_p u and the
+  // multiplier K / (1 - beta mu_p K) have the same fixed point for every mu_p.
+  // A cold start solves the uniform mode of the die first (a scalar fixed
+  // point: u = K00 (mean P_dyn + mu (1 + beta theta)), theta = u / (1 - alpha u)),
+  // starts from that uniform temperature th0 instead of 0, and takes
+  // mu_p = mu (1 + 2 alpha u): beta P_leak0 dtheta/du, with dtheta/du =
+  // s / (1 - alpha s u)^2, averages about beta mu_p over the die, so the
+  // iteration is left with the variation alone.
+  float th0 = 0.f, mu_p = (float)mu;
+  if ((double)beta * mu * (double)d.kmax >= 0.999) {
+    status = VS_ERR_RUNAWAY;
+    stop = true;
+    if (cold)   // theta_0 = 0 is the result of a map stopped before its first iterate
       for (int i = t; i < kClRows * N / 4; i += kClThreads)
         *reinterpret_cast<float4*>(d.theta + (size_t)y0 * N + 4 * i) = make_float4(0.f, 0.f, 0.f, 0.f);
+  } else {
+    if (cold) {
+      double pd_sum = 0.0;
+      for (int r = 0; r < ranks; ++r) pd_sum += slots->part2[r];
+      const float pdm = (float)(pd_sum / ((double)N * N)), muf = (float)mu;
+      const float k00 = __ldg(d.Kt);
+      float ub = 0.f;
+      bool ok = true;
+      for (int k = 0; k < 16 && ok; ++k) {   // contracts by ~beta mu K00 per step
+        const float den = fmaf(-alpha, ub, 1.f);
+        ok = den > 0.05f;
+        ub = k00 * fmaf(muf, fmaf(beta, __fdividef(ub, den), 1.f), pdm);
+      }
+      const float den = fmaf(-alpha, ub, 1.f);
+      const float mp = muf * fmaf(2.f * alpha, ub, 1.f);
+      if (ok && den > 0.05f && isfinite(ub) && beta * mp * d.kmax < 0.95f) {
+        th0 = __fdividef(ub, den);
+        mu_p = mp;
+      }
     }
+    float r0 = 0.f;
+    int f0 = 0;
+    // the peers' start is already established by the barrier above
+    row_phase(1, mu_p, th0, r0, f0);
+    cl_sync();
   }
 
   if (!stop) {
-    const float mu_f = (float)mu;
     {
       // spectral multiplier of this CTA's frequency pairs, with the 1 / N^2
       // of the two unnormalised inverse transforms folded in
-      const float bm = beta * mu_f;
+      const float bm = beta * mu_p;
       const float inv_n2 = 1.f / ((float)N * (float)N);
 #pragma unroll
       for (int i = 0; i < kKv; ++i) {
@@ -542,35 +565,13 @@ __global__ void __launch_bounds__(ClShape<N>::THREADS, ClShape<N>::MIN_BLOCKS)
       }
       __syncthreads();
     }
-    // Preconditioner: the source term - beta mu_p u and the multiplier
-    // K / (1 - beta mu_p K) have the same fixed point for every mu_p. A cold
-    // start begins with mu_p = mu and then takes mu_p = mu (1 + 2 alpha
-    // mean(u_1)) from its first iterate: beta P_leak0 dtheta/du, with dtheta/du
-    // = s / (1 - alpha s u)^2, averages about that over the die, so the
-    // remaining coupling is the variation alone. The row phase of iteration 2
-    // is the first to use it, so the table is rescaled just before it, after
-    // the column phase of iteration 2 has used the old one.
-    float mu_p = mu_f, mu_next = mu_f;
-    const bool cold = !d.theta_init;
     for (int it = 1; it <= P.max_iter; ++it) {
       col_phase();
       cl_sync();
-      if (mu_next != mu_p) {
-        // 1/L' = 1/L + beta (mu_p - mu_next) N^2 for L = K / (1 - beta mu_p K) / N^2
-        const float dbn = beta * (mu_p - mu_next) * (float)N * (float)N;
-        for (int i = t; i < kClF * N; i += kClThreads) {
-          float2 L = Ls[i];
-          L.x = __fdividef(L.x, fmaf(dbn, L.x, 1.f));
-          L.y = __fdividef(L.y, fmaf(dbn, L.y, 1.f));
-          Ls[i] = L;
-        }
-        mu_p = mu_next;
-      }
       float resid = 0.f;
       int flags = 0;
-      double usum = 0.0;
-      row_phase(it == 1 && cold ? 3 : 2, mu_p, resid, flags, usum);
-      put_slots(it == 1 && cold, true);
+      row_phase(it == 1 && cold ? 3 : 2, mu_p, th0, resid, flags);
+      put_slots();
       cl_sync();
       // the same decision in every thread of every CTA of the cluster
       float rr = 0.f;
@@ -598,12 +599,6 @@ __global__ void __launch_bounds__(ClShape<N>::THREADS, ClShape<N>::MIN_BLOCKS)
       }
       prev = rr;
       if (stop) break;
-      if (it == 1 && cold) {
-        double us = 0.0;
-        for (int r = 0; r < ranks; ++r) us += slots->part[r];
-        const float m = mu_f * fmaf(2.f * alpha, (float)(us / ((double)N * N)), 1.f);
-        if (m > 0.f && beta * m * d.kmax < 0.95f) mu_next = m;
-      }
     }
   }
   if (rank == 0 && t == 0) {

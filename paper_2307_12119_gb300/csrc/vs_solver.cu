@@ -47,6 +47,7 @@ struct MapState {
   double mu;
   float mu_f;
   float b_col, b_row;    // preconditioner coefficient of the next column / row phase
+  float th0;             // uniform start of a cold map (adaptive plans)
   unsigned resid_bits;
   float prev_resid;
   int growth;
@@ -69,7 +70,8 @@ struct PlanDev {
   const int* row_map;    // task -> map index
   const int* col_map;
   MapState* st;
-  double* part;
+  double* part;          // per row task: sum of P_leak0 (then of the iteration's data)
+  double* part2;         // per row task: sum of P_dyn (adaptive plans)
   vs_solve_info* info;
   Ctrl* ctrl;
   int n_maps, row_tasks, col_tasks;
@@ -277,7 +279,14 @@ __device__ void row_task(const PlanDev& P, int task, int step, float2* buf) {
   const int b = find_map(P, task, true);
   const MapDesc d = P.maps[b];
   MapState* ms = P.st + b;
-  if (MODE == 0 && (step > 0 || step == -1) && !ms->active) return;
+  if (MODE == 0 && (step > 0 || step == -1) && !ms->active) {
+    if (step == -1 && !d.theta_init) {
+      // a cold map stopped before its first iterate (runaway): theta_0 = 0
+      const int n = d.n, y0 = (task - d.row_off) * d.rb;
+      for (int i = threadIdx.x; i < d.rb * n; i += blockDim.x) d.theta[(size_t)y0 * n + i] = 0.f;
+    }
+    return;
+  }
   const int n = d.n, F = d.rb >> 1, NP = padded_len(n);
   const int lgn = __ffs(n) - 1;
   const int chunk = task - d.row_off;
@@ -287,14 +296,35 @@ __device__ void row_task(const PlanDev& P, int task, int step, float2* buf) {
   const bool muonly = (MODE == 0) && (step == -2);
   const bool last = (MODE == 1) && (step == P.n_steps);
   if (muonly) {
-    double acc = 0.0;
-    for (int i = threadIdx.x; i < d.rb * n; i += blockDim.x)
-      acc += (double)__ldg(&d.p_leak0[(size_t)y0 * n + i]);
-    double tot = block_sum(acc, red_d);
-    if (threadIdx.x == 0) P.part[d.part_off + chunk] = tot;
+    // the means of the inputs: P_leak0, and P_dyn of a cold map of an adaptive plan
+    const bool with_pd = P.adaptive && !d.theta_init;
+    Sum2 acc, acc_d;
+    const float4* l4 = reinterpret_cast<const float4*>(d.p_leak0 + (size_t)y0 * n);
+    const float4* d4 = reinterpret_cast<const float4*>(d.p_dyn + (size_t)y0 * n);
+#pragma unroll 4
+    for (int i = threadIdx.x; i < d.rb * n / 4; i += blockDim.x) {
+      const float4 a = __ldg(l4 + i);
+      const float4 c = with_pd ? __ldg(d4 + i) : make_float4(0.f, 0.f, 0.f, 0.f);
+      acc.add(a.x);
+      acc.add(a.y);
+      acc.add(a.z);
+      acc.add(a.w);
+      acc_d.add(c.x);
+      acc_d.add(c.y);
+      acc_d.add(c.z);
+      acc_d.add(c.w);
+    }
+    double tot = block_sum(acc.value(), red_d);
+    double tot_d = with_pd ? block_sum(acc_d.value(), red_d) : 0.0;
+    if (threadIdx.x == 0) {
+      P.part[d.part_off + chunk] = tot;
+      P.part2[d.part_off + chunk] = tot_d;
+    }
     __syncthreads();
     return;
   }
+  // a cold map of an adaptive plan starts from the uniform temperature th0
+  const bool uni = MODE == 0 && !PHYS && P.adaptive && !d.theta_init;
 
   if (!first) row_inverse(d, y0, buf);
 
@@ -303,7 +333,6 @@ __device__ void row_task(const PlanDev& P, int task, int step, float2* buf) {
   const float beta = P.beta, alpha = P.alpha;
   const float bq = (MODE == 0 && (!first || warm)) ? ms->b_row : 0.f;
   Sum2 mu_acc;           // sum of P_leak0 (first pass)
-  float dsum = 0.f;      // sum of u (adaptive preconditioner)
   float resid = 0.f;
   int flags = 0;
   const size_t nn = (size_t)n * n;
@@ -327,7 +356,8 @@ __device__ void row_task(const PlanDev& P, int task, int step, float2* buf) {
           if (d.s) sk[u][h] = __ldg(&d.s[idx]);
           if (MODE == 0) {
             pd[u][h] = __ldg(&d.p_dyn[idx]);
-            if (!first) old[u][h] = d.theta[idx];
+            if (uni && (warm || step == 1)) old[u][h] = ms->th0;
+            else if (!first) old[u][h] = d.theta[idx];
             else if (warm && d.theta_init) old[u][h] = __ldg(&d.theta_init[idx]);
           } else if (!last) {
             pd[u][h] = __ldg(&d.p_dyn[(size_t)step * nn + idx]);
@@ -363,10 +393,11 @@ __device__ void row_task(const PlanDev& P, int task, int step, float2* buf) {
             d.theta[idx] = th;
             q[h] = fmaf(pl[u][h], leak_factor(P, th), pd[u][h]) - bq * uq;
           } else if (warm) {
-            // theta_0 from the warm start; u_0 = theta_0 / (s (1 + alpha theta_0))
+            // theta_0 from the warm start (or uniform, not stored);
+            // u_0 = theta_0 / (s (1 + alpha theta_0))
             float t0 = old[u][h];
-            float u0 = t0 / (sk[u][h] * fmaf(alpha, t0, 1.f));
-            d.theta[idx] = t0;
+            float u0 = __fdividef(t0, sk[u][h] * fmaf(alpha, t0, 1.f));
+            if (!uni) d.theta[idx] = t0;
             q[h] = fmaf(beta * pl[u][h], t0, pd[u][h] + pl[u][h]) - bq * u0;
           } else if (first) {
             d.theta[idx] = 0.f;
@@ -375,12 +406,11 @@ __device__ void row_task(const PlanDev& P, int task, int step, float2* buf) {
           } else {
             float den = fmaf(-alpha * sk[u][h], uu, 1.f);
             if (!(den > 0.05f)) flags |= kFlagRunaway;
-            float th = sk[u][h] * uu / den;
+            float th = __fdividef(sk[u][h] * uu, den);   // as the cluster engine
             if (!isfinite(th)) flags |= kFlagNonfinite;
             else resid = fmaxf(resid, fabsf(th - old[u][h]));
             d.theta[idx] = th;
             q[h] = fmaf(beta * pl[u][h], th, pd[u][h] + pl[u][h]) - bq * uu;
-            dsum += uu;
           }
         } else {
           float th = 0.f;
@@ -399,10 +429,6 @@ __device__ void row_task(const PlanDev& P, int task, int step, float2* buf) {
   }
   if (MODE == 0 && first && !warm) {
     double tot = block_sum(mu_acc.value(), red_d);
-    if (threadIdx.x == 0) P.part[d.part_off + chunk] = tot;
-  }
-  if (MODE == 0 && step == 1 && !d.theta_init && !PHYS && P.adaptive) {
-    double tot = block_sum((double)dsum, red_d);
     if (threadIdx.x == 0) P.part[d.part_off + chunk] = tot;
   }
   if (!first || MODE == 1) {
@@ -567,6 +593,7 @@ __device__ void decide(const PlanDev& P, int it) {
       s.mu = sum / ((double)d.n * d.n);
       s.mu_f = (float)s.mu;
       s.b_col = s.b_row = P.beta * s.mu_f;
+      s.th0 = 0.f;
       s.active = 1;
       s.status = VS_OK;
       s.iters = 0;
@@ -574,23 +601,33 @@ __device__ void decide(const PlanDev& P, int it) {
       if ((double)P.beta * s.mu * (double)d.kmax >= 0.999) {
         s.active = 0;
         s.status = VS_ERR_RUNAWAY;
+      } else if (P.adaptive && !d.theta_init) {
+        // Uniform mode of the die (a scalar fixed point: u = K00 (mean P_dyn +
+        // mu (1 + beta theta)), theta = u / (1 - alpha u)): the cold map starts
+        // from that uniform theta and preconditions with beta mu (1 + 2 alpha u),
+        // about the mean of beta P_leak0 dtheta/du (dtheta/du = s / (1 - alpha s u)^2).
+        double sd = 0.0;
+        for (int i = 0; i < tasks; ++i) sd += P.part2[d.part_off + i];
+        const float pdm = (float)(sd / ((double)d.n * d.n)), muf = s.mu_f;
+        const float k00 = __ldg(d.Kt), alpha = P.alpha, beta = P.beta;
+        float ub = 0.f;
+        bool ok = true;
+        for (int k = 0; k < 16 && ok; ++k) {   // contracts by ~beta mu K00 per step
+          const float den = fmaf(-alpha, ub, 1.f);
+          ok = den > 0.05f;
+          ub = k00 * fmaf(muf, fmaf(beta, __fdividef(ub, den), 1.f), pdm);
+        }
+        const float den = fmaf(-alpha, ub, 1.f);
+        const float mp = muf * fmaf(2.f * alpha, ub, 1.f);
+        if (ok && den > 0.05f && isfinite(ub) && beta * mp * d.kmax < 0.95f) {
+          s.th0 = __fdividef(ub, den);
+          s.b_col = s.b_row = beta * mp;
+        }
       }
     } else {
       if (!s.active) continue;
       float r = __uint_as_float(s.resid_bits);
       s.iters = it;
-      // the next column phase uses the coefficient of this row phase; after
-      // the first iterate of a cold start the row phases take
-      // beta mu (1 + 2 alpha mean(u_1)), an estimate of the mean of
-      // beta P_leak0 dtheta/du
-      s.b_col = s.b_row;
-      if (P.adaptive && it == 1 && !d.theta_init) {
-        int tasks = d.n / d.rb;
-        double sum = 0.0;
-        for (int i = 0; i < tasks; ++i) sum += P.part[d.part_off + i];
-        const float b_next = P.beta * s.mu_f * fmaf(2.f * P.alpha, (float)(sum / ((double)d.n * d.n)), 1.f);
-        if (b_next > 0.f && b_next * d.kmax < 0.95f) s.b_row = b_next;
-      }
       if (s.flags & kFlagNonfinite) {
         s.active = 0;
         s.status = VS_ERR_NONFINITE;
@@ -619,16 +656,18 @@ __device__ void decide(const PlanDev& P, int it) {
 template <bool PHYS>
 __global__ void __launch_bounds__(kThreads, 3) k_solve_steady(PlanDev P) {
   extern __shared__ float2 smem[];
-  const int first = P.warm ? -2 : 0;
-  for (int t = blockIdx.x; t < P.row_tasks; t += gridDim.x) row_task<0, PHYS>(P, t, first, smem);
+  // two passes before the iterations (the means, then the first source from
+  // theta_0) for warm starts and for the uniform start of adaptive plans
+  const bool two = P.warm || (P.adaptive && !PHYS);
+  for (int t = blockIdx.x; t < P.row_tasks; t += gridDim.x) row_task<0, PHYS>(P, t, two ? -2 : 0, smem);
   if (!grid_barrier(P.ctrl)) return;
   decide(P, 0);
   if (!grid_barrier(P.ctrl)) return;
-  if (ld_acquire(&P.ctrl->active[0]) == 0u) return;
-  if (P.warm) {
+  if (two) {
     for (int t = blockIdx.x; t < P.row_tasks; t += gridDim.x) row_task<0, PHYS>(P, t, -1, smem);
     if (!grid_barrier(P.ctrl)) return;
   }
+  if (ld_acquire(&P.ctrl->active[0]) == 0u) return;
   for (int it = 1; it <= P.max_iter; ++it) {
     for (int t = blockIdx.x; t < P.col_tasks; t += gridDim.x) col_task<0>(P, t, smem);
     if (!grid_barrier(P.ctrl)) return;
@@ -1512,7 +1551,7 @@ int plan_layout(vs_plan_t* p, int elems, cudaStream_t s, bool transient, int n_s
   }
   VS_CUDA_TRY(cudaMalloc(&p->d_maps, sizeof(MapDesc) * n_items));
   VS_CUDA_TRY(cudaMalloc(&p->d_state, sizeof(MapState) * n_items));
-  VS_CUDA_TRY(cudaMalloc(&p->d_part, sizeof(double) * std::max(1, part_off)));
+  VS_CUDA_TRY(cudaMalloc(&p->d_part, 2 * sizeof(double) * std::max(1, part_off)));   // part, part2
   VS_CUDA_TRY(cudaMalloc(&p->d_info, sizeof(vs_solve_info) * n_items));
   VS_CUDA_TRY(cudaMalloc(&p->d_ctrl, sizeof(Ctrl)));
   VS_CUDA_TRY(cudaMemcpyAsync(p->d_maps, maps.data(), sizeof(MapDesc) * n_items,
@@ -1704,6 +1743,7 @@ int plan_launch(vs_plan_t* p, cudaStream_t s, bool transient) {
   P.col_map = p->d_col_map;
   P.st = p->d_state;
   P.part = p->d_part;
+  P.part2 = p->d_part + std::max(1, p->part_total);
   P.info = p->d_info;
   P.ctrl = p->d_ctrl;
   P.n_maps = p->n_items;
@@ -2049,7 +2089,7 @@ NoAllocLayout noalloc_layout(int row_tasks, int col_tasks) {
   l.desc = kNoAllocWorkBytes;
   l.state = align256(l.desc + sizeof(MapDesc));
   l.part = align256(l.state + sizeof(MapState));
-  l.info = align256(l.part + sizeof(double) * row_tasks);
+  l.info = align256(l.part + 2 * sizeof(double) * row_tasks);   // part, part2
   l.ctrl = align256(l.info + sizeof(vs_solve_info));
   l.row_map = align256(l.ctrl + sizeof(Ctrl));
   l.col_map = align256(l.row_map + sizeof(int) * row_tasks);
@@ -2148,6 +2188,7 @@ extern "C" int vs_solve_steady_noalloc(vs_kernel k, const float* p_dyn, const fl
   P.col_map = reinterpret_cast<const int*>(base + l.col_map);
   P.st = reinterpret_cast<MapState*>(base + l.state);
   P.part = reinterpret_cast<double*>(base + l.part);
+  P.part2 = P.part + row_tasks;
   P.info = reinterpret_cast<vs_solve_info*>(base + l.info);
   P.ctrl = reinterpret_cast<Ctrl*>(base + l.ctrl);
   P.n_maps = 1;
