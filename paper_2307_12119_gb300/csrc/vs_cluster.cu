@@ -205,11 +205,11 @@ __global__ void __launch_bounds__(ClShape<N>::THREADS, ClShape<N>::MIN_BLOCKS)
     return make_float2(__shfl_sync(0xffffffffu, v.x, src), __shfl_sync(0xffffffffu, v.y, src));
   };
 
-  // Row phase. mode 0: initial source from theta_0 = 0 (leakage sum into
-  // pl_sum; theta_0 is not stored); 1: initial source from theta_0, the warm
-  // start's map or the uniform th0 (not stored); 2: iteration (brow holds
-  // the spectra of the column phase, pre-twiddled, at digit-reversed places);
-  // 3: the first iteration after a uniform theta_0 = th0 (not read).
+  // Row phase. mode 1: initial source from theta_0, the warm start's map or
+  // the uniform th0 (not stored); 2: iteration (brow holds the spectra of the
+  // column phase, pre-twiddled, at digit-reversed places); 3: the first
+  // iteration after a uniform theta_0 = th0 (not read). mu is the mean leakage
+  // of the preconditioner (source term - beta mu u).
   auto row_phase = [&](int mode, float mu, float th0, float& resid, int& flags) {
     const bool iter = mode >= 2;
     if (iter) {
