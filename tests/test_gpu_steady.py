@@ -205,3 +205,26 @@ def test_plans_with_different_footprints_coexist():
     plan.run()
     torch.cuda.synchronize()
     assert torch.equal(a, th)
+
+
+@pytest.mark.parametrize("engine", [1, 2])          # streamed, cluster
+def test_uniform_maps_converge_from_the_uniform_start(engine):
+    # Uniform P_dyn and P_leak0 (s = 1): the fixed point is the uniform mode
+    # u = K00 (P_dyn + P_leak0 (1 + beta phi(u))), which the cold start solves
+    # as a scalar before the first transform, so the first iterate is already
+    # the answer and the solve stops after one iteration.
+    vs = _vs()
+    w = synth.workload("c2_256")
+    k = _kernel(w)
+    Kt = oracle_spectrum(w)
+    beta, alpha = w.physics.beta_per_K, w.physics.alpha_per_K
+    c, m = 2.0e-3, 1.0e-3                                   # W per cell
+    u = 0.0
+    for _ in range(200):                                    # FP64 scalar fixed point
+        u = Kt[0, 0] * (c + m * (1.0 + beta * u / (1.0 - alpha * u)))
+    theta_star = u / (1.0 - alpha * u)
+    pd = torch.full((w.n, w.n), c, device="cuda")
+    pl = torch.full((w.n, w.n), m, device="cuda")
+    th, info = vs.solve_steady(k, pd, pl, None, vs_params(w, tol=1e-2, engine=engine))
+    assert info["status"] == vs.VS_OK and info["iterations"] == 1
+    assert float((th.double() - theta_star).abs().max()) <= 1e-3 * theta_star
