@@ -81,7 +81,8 @@ struct PlanDev {
   int warm;              // some map has a warm start
   int window;            // transient: 0 untruncated, K >= 1 step responses settled from age K on
   int implicit;          // transient: per-step leakage fixed point
-  int adaptive;          // steady FP32: the preconditioner takes beta mu (1 + 2 alpha mean(u_1))
+  int adaptive;          // steady FP32: a cold map starts from the die's uniform-mode
+                         // temperature, preconditioned with beta mu (1 + 2 alpha u)
   float* xs;             // transient, implicit: the last source spectrum of the current step
   // physics variants (the k_solve_steady<true> instantiation); beta above is
   // then the preconditioner slope (the secant of a piecewise-linear table)
