@@ -49,11 +49,18 @@ def fp32_flops_per_map(n: int, iterations: float) -> float:
     value) and the fused update (13 per value). The initial source costs one
     forward stage and the source sum. Radix-16 butterfly: 8 radix-4 DFTs
     (16 adds each) + 9 inner twiddle products (6 flops each) = 182 flops, plus
-    15 outer twiddle products (90) in the twiddled pass."""
-    lg = int(math.log2(n))
-    r2 = n >> 4 if lg >= 4 else 1
+    15 outer twiddle products (90) when another pass follows."""
+    # radix-16 passes first, then the remaining factor; twiddle products
+    # (R - 1 per butterfly, 6 flops each) after every pass but the last
     dft = {16: 182, 8: 72, 4: 16, 2: 4}
-    fft = (n // 16) * (dft[16] + (90 if n > 16 else 0)) + 16 * dft.get(r2, 0)
+    radices, m = [], n
+    while m >= 16:
+        radices.append(16)
+        m //= 16
+    if m > 1:
+        radices.append(m)
+    fft = sum((n // r) * dft[r] for r in radices)
+    fft += sum((n // r) * (r - 1) * 6 for r in radices[:-1])
     stage = (n // 2) * fft + 7 * n * n
     per_iter = 4 * stage + n * n * (1 + 13)
     return iterations * per_iter + stage + 2 * n * n
