@@ -72,3 +72,37 @@ def test_missing_library_fails_loudly(monkeypatch, tmp_path):
     monkeypatch.setattr(vs, "lib_path", lambda: str(tmp_path / "nope.so"))
     with pytest.raises(RuntimeError, match="libvarsim.so not found"):
         vs.lib()
+
+
+def test_solve_params_marshal_the_physics_variants():
+    import paper_2307_12119_gb300 as vs
+    p = vs.SolveParams(0.03, 1e-3, 1e-4, 40, vs.VS_PREC_FP32, vs.VS_ENGINE_STREAMED,
+                       conductivity=vs.VS_COND_KIRCHHOFF, eta=1.3, t_amb_K=318.15,
+                       leak_table=[(0.0, 1.0), (50.0, 2.5), (100.0, 5.0)])
+    c = p._c()
+    assert (c.beta_per_K, c.alpha_per_K, c.tol_K, c.max_iter) == (0.03, 1e-3, 1e-4, 40)
+    assert (c.precision, c.engine, c.conductivity) == (0, 1, 1)
+    assert (c.eta, c.t_amb_K, c.leak_points) == (1.3, 318.15, 3)
+    assert list(c.leak_theta_K[:3]) == [0.0, 50.0, 100.0]
+    assert list(c.leak_g[:3]) == [1.0, 2.5, 5.0]
+    # the default struct selects the linear models
+    d = vs.SolveParams()._c()
+    assert d.conductivity == vs.VS_COND_LINEAR and d.leak_points == 0
+
+
+def test_invalid_physics_parameters_need_no_gpu(libpath):
+    # parameter validation runs before any device work; vs_plan_create with no
+    # items reports the parameter error first
+    import paper_2307_12119_gb300 as vs
+    L = vs.lib()
+    h = ctypes.c_void_p()
+    cases = (({"conductivity": 3}, "conductivity model"),
+             ({"conductivity": vs.VS_COND_KIRCHHOFF, "eta": 1.0, "t_amb_K": 300.0}, "Kirchhoff"),
+             ({"leak_table": [(0.0, 1.0)]}, "leak_points"),
+             ({"leak_table": [(5.0, 1.0), (1.0, 2.0)]}, "must increase"))
+    for kw, msg in cases:
+        prm = vs.SolveParams(**kw)._c()
+        item = (vs._BatchItem * 1)()
+        rc = L.vs_plan_create(item, 1, ctypes.byref(prm), ctypes.byref(h), None)
+        assert rc == vs.VS_ERR_INVALID_ARG, kw
+        assert msg in L.vs_last_error().decode(), (kw, L.vs_last_error())
