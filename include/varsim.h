@@ -162,9 +162,12 @@ typedef struct {
   double leak_g[VS_MAX_LEAK_POINTS];
 } vs_solve_params;
 
-/* Per-map outcome. status is a vs_status; iterations counts applications of
- * the convolution after the initial one; residual_K is the last
- * max |theta_n - theta_{n-1}|; mu_W is the mean of P_leak0 (W per cell). */
+/* Per-map outcome. status is a vs_status; iterations counts the applications
+ * of the convolution, each followed by the update and the convergence check
+ * (0 for a map stopped before its first, e.g. a runaway at the start);
+ * residual_K is the last max |theta_n - theta_{n-1}| (theta_0 is the start:
+ * 0, the warm start's map, or the die's uniform-mode temperature); mu_W is the
+ * mean of P_leak0 (W per cell). */
 typedef struct {
   int status;
   int iterations;
@@ -269,7 +272,9 @@ typedef struct {
   const float* s_kappa;    /* device, [n][n], or NULL => 1 */
   float* theta;            /* device output, [n][n] */
   const float* theta_init; /* device [n][n] initial temperature (warm start of the
-                              fixed point, e.g. from vs_warm_apply), or NULL => 0 */
+                              fixed point, e.g. from vs_warm_apply), or NULL: the
+                              FP32 engines then start from the die's uniform-mode
+                              temperature, the tensor-core engine from 0 */
 } vs_batch_item;
 
 /* Creates a plan for n_items maps: uploads the item table and picks the
