@@ -12,8 +12,11 @@ physics : layer-stack spectrum g^(k), the fast-decaying top-layer
           half-space closed form, and the spectral kernel K~ of the imaged die.
 solve   : the mirror-image convolution (direct summation and dense-cosine
           spectral form), the leakage/conductivity fixed point (plain Picard on
-          the unsplit equation, and the mean/variation split), and the
-          transient Duhamel superposition.
+          the unsplit equation, and the mean/variation split), the fixed point
+          with a piecewise-linear leakage and kappa(T) through the Kirchhoff
+          transform, the paper's one-shot closed form, and the transient
+          Duhamel superposition with its windowed and implicit-leakage variants.
+cnn     : the warm-start network (forward and backward).
 
 Every function cites the passage of the paper it follows (section / equation).
 Where the paper is silent the reading used is stated in the docstring.
