@@ -422,7 +422,10 @@ long long vs_model_nparams(vs_model m);
  * them also resets the optimiser state. Blocking. */
 int vs_model_get_params(vs_model m, float* host);
 int vs_model_set_params(vs_model m, const float* host);
-/* y[b][0][R][R] = net(x[b][3][R][R]) for `batch` samples (device arrays). */
+/* y[b][0][R][R] = net(x[b][3][R][R]) for `batch` samples (device arrays).
+ * The model's forward, gradient and training calls (and the warm plans that
+ * hold it) share its activation buffers: calls on one model must be ordered,
+ * e.g. on one stream; different models are independent. */
 int vs_model_forward(vs_model m, const float* x, float* y, int batch, void* stream);
 /* Mean-squared-error loss against t[b][1][R][R] and its parameter gradient
  * (host arrays; grad_host may be NULL). No update. Blocking. */
