@@ -290,7 +290,9 @@ int vs_plan_create(const vs_batch_item* items_host, int n_items,
  * cluster engine: one per distinct grid size, a cluster per map) that
  * iterates every map to its own convergence. Asynchronous; makes no host
  * allocation or synchronisation, so it can be captured in a CUDA graph.
- * Per-map results go to the plan's device info array (vs_plan_info). */
+ * Per-map results go to the plan's device info array (vs_plan_info). A plan
+ * owns its scratch: runs of one plan must be ordered (e.g. on one stream);
+ * different plans, and kernels shared between them, may run concurrently. */
 int vs_plan_run(vs_plan plan, void* stream);
 
 /* Copies the per-map vs_solve_info of the last run to host memory
