@@ -100,10 +100,15 @@ typedef struct {
 /* Execution engines of the FP32 steady solve (identical arithmetic, different
  * data movement). Both precondition the iteration
  *   u <- K/(1 - b K) * (P_dyn + P_leak0 (1 + beta theta) - b u)
- * (every scalar b has the same fixed point) with b = beta mu, and a cold start
- * switches to b = beta mu (1 + 2 alpha mean(u_1)) after its first iterate (about
- * the mean of beta P_leak0 dtheta/du), which saves about one iteration in ten
- * at 1e-2 K and one in six at 1e-4 K.
+ * (every scalar b has the same fixed point). A cold map (no theta_init)
+ * first solves the uniform mode of its die, the scalar fixed point
+ *   u_bar = K[0][0] (mean P_dyn + mu (1 + beta theta_bar)),
+ *   theta_bar = u_bar / (1 - alpha u_bar),
+ * from the means of its inputs; every cell then starts at theta_bar and
+ * b = beta mu (1 + 2 alpha u_bar) (about the mean of beta P_leak0 dtheta/du,
+ * so the iteration is left with the variation alone). On the 256 x 256 bench
+ * maps this takes 3.0 instead of 4.4 iterations at 1e-2 K. A warm start
+ * (theta_init given) keeps b = beta mu.
  *   VS_ENGINE_STREAMED: one cooperative launch over all maps of a plan; the
  *     spectral work map streams through global memory between the row and
  *     column phases, phases separated by grid barriers; any n.
@@ -167,12 +172,15 @@ typedef struct {
  * (0 for a map stopped before its first, e.g. a runaway at the start);
  * residual_K is the last max |theta_n - theta_{n-1}| (theta_0 is the start:
  * 0, the warm start's map, or the die's uniform-mode temperature); mu_W is the
- * mean of P_leak0 (W per cell). */
+ * mean of P_leak0 (W per cell); fell_back is 1 for a map of a warm-started
+ * solve that did not converge from the network's start and was solved again
+ * cold (vs_warm_plan_info with fallback), else 0. */
 typedef struct {
   int status;
   int iterations;
   double residual_K;
   double mu_W;
+  int fell_back;
 } vs_solve_info;
 
 typedef struct vs_kernel_t* vs_kernel;
@@ -249,9 +257,15 @@ int vs_solve_steady(vs_kernel k, const float* p_dyn, const float* p_leak0,
  * process exits.
  *   Limit: n <= 512 (the work map of a 512 x 512 grid fills the array);
  *          larger grids return VS_ERR_INVALID_ARG with a message.
- *   Arguments, layout, outputs and statuses are those of vs_solve_steady.
+ *   Arguments, layout, outputs and statuses are those of vs_solve_steady,
+ *   except that it always runs the FP32 streamed engine: params->precision
+ *   other than VS_PREC_FP32, or params->engine = VS_ENGINE_CLUSTER, return
+ *   VS_ERR_INVALID_ARG.
  *   The first call on each device resolves the array's device address
- *   (cudaGetSymbolAddress); make that first call outside any stream capture.
+ *   (cudaGetSymbolAddress) and keeps it for the life of the process; make
+ *   that first call outside any stream capture. The address belongs to the
+ *   device's primary context: after cudaDeviceReset the module may load
+ *   elsewhere, so do not call this entry point again in that process.
  *   Every call re-initialises the parts of the array that must start at zero,
  *   but all calls share the one array: calls whose GPU work overlaps (different
  *   streams or host threads without ordering) race and corrupt each other.
@@ -485,9 +499,9 @@ int vs_warm_plan_run(vs_warm_plan plan, int stages, void* stream);
 int vs_warm_plan_launches(vs_warm_plan plan);
 /* Per-map outcome of the last solve stage into info_host[count] (blocking).
  * With `fallback` != 0, the maps whose status is not VS_OK are solved again
- * from theta_0 = 0 (vs_solve_batch) and their entries replaced; fell_back_host
- * (may be NULL) gets 1 for those maps, else 0. Returns the worst per-map
- * status, or the launch-level error. */
+ * from theta_0 = 0 (vs_solve_batch) and their entries replaced, with
+ * fell_back = 1; fell_back_host (may be NULL) gets the same flags. Returns the
+ * worst per-map status, or the launch-level error. */
 int vs_warm_plan_info(vs_warm_plan plan, vs_solve_info* info_host, int fallback,
                       int* fell_back_host, void* stream);
 void vs_warm_plan_free(vs_warm_plan plan);

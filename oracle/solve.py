@@ -301,6 +301,34 @@ def duhamel(step_spectra, p_dyn_trace, p_leak0, s, beta, alpha):
     return theta
 
 
+def duhamel_modes(step_spectra, p_dyn_trace, p_leak0, s, beta, alpha):
+    """The same untruncated superposition as `duhamel` (Eq. 36, lagged
+    leakage), with the sum over past power differences taken mode by mode in
+    the cosine basis: since L_S[q] = IDCT2(DCT2(q) S) is linear in q,
+      u_n = IDCT2( sum_{j=1..n} S_j * DCT2(P_{n-j+1} - P_{n-j}) ),
+    so every power difference is transformed once and every step needs one
+    inverse transform instead of n. Equal to `duhamel` up to rounding; used
+    for long traces. Returns theta[n_steps, n, n]."""
+    n_steps = p_dyn_trace.shape[0]
+    n = p_leak0.shape[-1]
+    C = dct_matrix(n)
+    Ci = idct_matrix(n)
+    theta = np.zeros_like(p_dyn_trace)
+    dP_hat = []                                  # DCT2 of P_m - P_{m-1}, m = 1..
+    P_prev = np.zeros_like(p_leak0)
+    th_prev = np.zeros_like(p_leak0)
+    for k in range(n_steps):
+        P_k = p_dyn_trace[k] + p_leak0 * (1.0 + beta * th_prev)
+        dP_hat.append(C @ (P_k - P_prev) @ C.T)
+        P_prev = P_k
+        U = np.zeros_like(p_leak0)
+        for j in range(1, k + 2):
+            U = U + step_spectra[j - 1] * dP_hat[k + 1 - j]
+        th_prev = phi(Ci @ U @ Ci.T, s, alpha)
+        theta[k] = th_prev
+    return theta
+
+
 def transient_variants(step_spectra, steady_spectrum, p_dyn_trace, p_leak0, s, beta, alpha,
                        window=0, implicit=False, tol=1e-10, max_iter=200):
     """The two variants of the superposition of Sec. IV-E, in the paper's terms.

@@ -92,7 +92,7 @@ class _SolveParams(C.Structure):
 
 class _SolveInfo(C.Structure):
     _fields_ = [("status", C.c_int), ("iterations", C.c_int), ("residual_K", C.c_double),
-                ("mu_W", C.c_double)]
+                ("mu_W", C.c_double), ("fell_back", C.c_int)]
 
 
 class _TransientOpts(C.Structure):
@@ -271,7 +271,7 @@ class SolveParams:
 
 def _info(i: _SolveInfo) -> dict:
     return {"status": i.status, "iterations": i.iterations, "residual_K": i.residual_K,
-            "mu_W": i.mu_W}
+            "mu_W": i.mu_W, "fell_back": i.fell_back}
 
 
 class Kernel:

@@ -250,6 +250,7 @@ __global__ void k_cf_info(CfArgs a) {
   inf.iterations = 0;
   inf.residual_K = 0.0;
   inf.mu_W = map_mu(a, b, nullptr);
+  inf.fell_back = 0;
   a.info[b] = inf;
 }
 

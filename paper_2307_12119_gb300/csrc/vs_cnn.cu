@@ -928,6 +928,7 @@ extern "C" int vs_warm_plan_info(vs_warm_plan p, vs_solve_info* info_host, int f
   int worst = VS_OK;
   for (size_t j = 0; j < bad.size(); ++j) {
     info_host[bad[j]] = redo[j];
+    info_host[bad[j]].fell_back = 1;
     if (fell_back_host) fell_back_host[bad[j]] = 1;
   }
   for (int i = 0; i < p->count; ++i) worst = std::max(worst, info_host[i].status);

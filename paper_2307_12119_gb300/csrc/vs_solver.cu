@@ -2117,6 +2117,10 @@ extern "C" int vs_solve_steady_noalloc(vs_kernel k, const float* p_dyn, const fl
   if (rc) return rc;
   if (vs_params_physics(params))
     return vs_set_error(VS_ERR_INVALID_ARG, "vs_solve_steady_noalloc runs the linear models only");
+  if (params->precision != VS_PREC_FP32 || params->engine == VS_ENGINE_CLUSTER)
+    return vs_set_error(VS_ERR_INVALID_ARG,
+                        "vs_solve_steady_noalloc runs the FP32 streamed engine only (precision "
+                        "VS_PREC_FP32, engine VS_ENGINE_AUTO or VS_ENGINE_STREAMED)");
   if (!p_dyn || !p_leak0 || !theta) return vs_set_error(VS_ERR_INVALID_ARG, "NULL map");
   uintptr_t al = (uintptr_t)p_dyn | (uintptr_t)p_leak0 | (uintptr_t)theta | (uintptr_t)s_kappa;
   if (al & 15u) return vs_set_error(VS_ERR_INVALID_ARG, "maps must be 16-byte aligned");

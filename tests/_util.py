@@ -58,3 +58,20 @@ def inputs(w, count=1, seed=synth.SEED, first=0, n_floorplans=None):
     pd, pl, s = synth.steady_inputs(w, count, seed=seed, first=first, n_floorplans=n_floorplans,
                                     device="cuda")
     return pd, pl, s
+
+
+def step_spectra(w, dt, steps, workers=None):
+    """The oracle's step-response spectra S_1 .. S_steps of workload w
+    (Eq. 35 per mode, oracle.solve.step_spectrum), computed in parallel in
+    spawned worker processes (a forked child of a process that has used CUDA
+    can hang; a spawned one starts clean)."""
+    import multiprocessing as mp
+    import os
+    from concurrent.futures import ProcessPoolExecutor
+    st = w.stack
+    args = [(w.n, w.die_m, tuple(st.thickness_m), tuple(st.kappa_W_mK), st.h_conv_W_m2K,
+             st.heat_cap_J_m2K, j * dt) for j in range(1, steps + 1)]
+    workers = workers or max(1, min(steps, len(os.sched_getaffinity(0))))
+    with ProcessPoolExecutor(workers, mp_context=mp.get_context("spawn")) as ex:
+        futs = [ex.submit(so.step_spectrum, *a) for a in args]
+        return [f.result() for f in futs]

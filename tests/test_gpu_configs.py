@@ -17,7 +17,7 @@ import synth
 from oracle import solve as so
 
 from _util import (ENG_TOL_K, REQ_MAX_K, REQ_REL_L2, errors, oracle_spectrum, oracle_steady,
-                   vs_params, vs_stack)
+                   step_spectra, vs_params, vs_stack)
 
 pytestmark = pytest.mark.gpu
 HERE = os.path.dirname(os.path.abspath(__file__))
@@ -113,17 +113,50 @@ def test_transient_1024_two_hundred_steps():
     del th
 
     # With leakage and temperature-dependent conductivity: statuses over all
-    # 200 steps, and the first two steps against the oracle's superposition.
+    # 200 steps, and the first 8 steps element by element against the
+    # oracle's superposition (Eq. 36 with the exact step spectra).
     _, pl, s = synth.steady_inputs(w, 1, device="cuda")
     th, info = vs.solve_transient(k, trace, pl[0], s[0], vs_params(w))
     assert info["status"] == vs.VS_OK and info["iterations"] == steps
     assert bool(torch.isfinite(th).all()) and float(th[-1].min()) > 0
-    st = w.stack
-    spectra = [so.step_spectrum(w.n, w.die_m, st.thickness_m, st.kappa_W_mK, st.h_conv_W_m2K,
-                                st.heat_cap_J_m2K, j * dt) for j in (1, 2)]
+    first = 8
+    spectra = step_spectra(w, dt, first)
     f64 = lambda t: t.double().cpu().numpy()
-    ref = so.duhamel(spectra, f64(trace[:2]), f64(pl[0]), f64(s[0]), w.physics.beta_per_K,
-                     w.physics.alpha_per_K)
-    emax, rel = errors(th[:2], ref)
-    assert emax <= REQ_MAX_K
-    assert emax <= 5e-3 and rel <= 2e-4
+    ref = so.duhamel_modes(spectra, f64(trace[:first]), f64(pl[0]), f64(s[0]),
+                           w.physics.beta_per_K, w.physics.alpha_per_K)
+    got = f64(th[:first])
+    for j in range(first):
+        d = got[j] - ref[j]
+        emax = float(np.max(np.abs(d)))
+        rel = float(np.linalg.norm(d) / np.linalg.norm(ref[j]))
+        print("1024^2 step %d: max|dT| %.2e K, rel-L2 %.2e" % (j + 1, emax, rel))
+        assert emax <= REQ_MAX_K, (j, emax)
+        assert emax <= 5e-3 and rel <= 2e-4, (j, emax, rel)
+
+
+def test_transient_256_every_step_of_two_hundred():
+    """The transient at 256^2 (20 x 20 mm die, Markov power trace, leakage and
+    conductivity on), 200 steps of 1 ms, every step element by element
+    against the oracle's untruncated superposition (Eq. 36, lagged leakage)."""
+    vs = _vs()
+    w = synth.workload("c2_256")
+    dt, steps = 1e-3, 200
+    trace = synth.markov_trace(w, steps, device="cuda")
+    k = vs.Kernel(vs_stack(w), vs.Grid(w.n, w.die_m), vs.KernelOpts(dt_s=dt))
+    _, pl, s = synth.steady_inputs(w, 1, device="cuda")
+    th, info = vs.solve_transient(k, trace, pl[0], s[0], vs_params(w))
+    assert info["status"] == vs.VS_OK and info["iterations"] == steps
+    spectra = step_spectra(w, dt, steps)
+    f64 = lambda t: t.double().cpu().numpy()
+    ref = so.duhamel_modes(spectra, f64(trace), f64(pl[0]), f64(s[0]), w.physics.beta_per_K,
+                           w.physics.alpha_per_K)
+    got = f64(th)
+    d = got - ref
+    emax_step = np.max(np.abs(d), axis=(1, 2))
+    rel_step = np.linalg.norm(d.reshape(steps, -1), axis=1) / np.linalg.norm(ref.reshape(steps, -1),
+                                                                             axis=1)
+    print("256^2 transient: worst max|dT| %.2e K (step %d), worst rel-L2 %.2e (step %d), "
+          "max rise %.1f K" % (emax_step.max(), emax_step.argmax() + 1, rel_step.max(),
+                               rel_step.argmax() + 1, float(np.max(ref))))
+    assert emax_step.max() <= REQ_MAX_K
+    assert emax_step.max() <= 5e-3 and rel_step.max() <= 2e-4

@@ -335,6 +335,22 @@ def test_duhamel_superposition_without_feedback():
     assert np.allclose(tc[4], so.spectral_convolve(spectra[4], a[0]), rtol=1e-12)
 
 
+def test_duhamel_in_the_cosine_basis_is_the_same_sum():
+    """duhamel_modes takes the sum of Eq. 36 mode by mode (the transform is
+    linear): it must reproduce the term-by-term `duhamel` with leakage
+    feedback and the conductivity factor on, up to rounding."""
+    w, pd, pl, s = _c1_inputs(16, sigma=0.08)
+    st, phy = w.stack, w.physics
+    dt = 1e-3
+    spectra = [so.step_spectrum(w.n, w.die_m, st.thickness_m, st.kappa_W_mK, st.h_conv_W_m2K,
+                                st.heat_cap_J_m2K, j * dt) for j in range(1, 13)]
+    rng = np.random.default_rng(5)
+    trace = pd[None] * (0.5 + rng.random((12, 1, 1)))
+    a = so.duhamel(spectra, trace, pl, s, phy.beta_per_K, phy.alpha_per_K)
+    b = so.duhamel_modes(spectra, trace, pl, s, phy.beta_per_K, phy.alpha_per_K)
+    assert np.max(np.abs(a - b)) <= 1e-11 * np.max(np.abs(a))
+
+
 # -------------------------------- P9c: piecewise-linear leakage, kappa(T)
 
 def test_pwl_leakage_through_a_line_is_the_linear_model():

@@ -25,7 +25,7 @@ def _call_noalloc(vs, k, pd, pl, s, params, out):
     return rc, info
 
 
-@pytest.mark.parametrize("name", ["c1_64", "c3_256"])
+@pytest.mark.parametrize("name", ["c1_64", "c3_256", "c3_512"])
 def test_noalloc_matches_allocating_entry_point_twice(name):
     import paper_2307_12119_gb300 as vs
     w = synth.workload(name)
@@ -38,7 +38,8 @@ def test_noalloc_matches_allocating_entry_point_twice(name):
         rc, info = _call_noalloc(vs, k, pd[i], pl[i], s[i], params, out[i])
         assert rc == vs.VS_OK and info.status == vs.VS_OK
         _, rinfo = vs.solve_steady(k, pd[i], pl[i], s[i], params, ref[i])
-        # streamed engine against the cluster engine (same arithmetic, other rounding)
+        # streamed engine against the automatic engine (the cluster engine for
+        # n <= 256: same arithmetic, other rounding)
         assert abs(info.iterations - rinfo["iterations"]) <= 1
         assert float((out[i] - ref[i]).abs().max()) <= ENG_TOL_K
 
@@ -51,3 +52,19 @@ def test_noalloc_rejects_grids_beyond_its_array():
     rc, _ = _call_noalloc(vs, k, z, z, None, vs_params(w), z.clone())
     assert rc == vs.VS_ERR_INVALID_ARG
     assert "n <= 512" in vs.lib().vs_last_error().decode()
+
+
+def test_noalloc_rejects_other_engines_and_precisions():
+    """It runs the FP32 streamed engine only; asking for the cluster engine or
+    for split precision is an argument error, not a silent substitution."""
+    import paper_2307_12119_gb300 as vs
+    w = synth.workload("c1_64")
+    k = vs.Kernel(vs_stack(w), vs.Grid(w.n, w.die_m))
+    pd, pl, s = inputs(w, count=1)
+    out = torch.empty_like(pd[0])
+    for kw in ({"engine": vs.VS_ENGINE_CLUSTER}, {"precision": vs.VS_PREC_BF16_SPLIT}):
+        rc, _ = _call_noalloc(vs, k, pd[0], pl[0], s[0], vs_params(w, **kw), out)
+        assert rc == vs.VS_ERR_INVALID_ARG, kw
+        assert "streamed engine only" in vs.lib().vs_last_error().decode()
+    rc, info = _call_noalloc(vs, k, pd[0], pl[0], s[0], vs_params(w, engine=vs.VS_ENGINE_STREAMED), out)
+    assert rc == vs.VS_OK and info.status == vs.VS_OK
