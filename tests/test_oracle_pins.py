@@ -151,11 +151,15 @@ def _image_road_kper(n, L, t, kap, h, Rmax, nodes=3000):
     return Kp
 
 
+@pytest.mark.parametrize("n", [8, 32])
 @pytest.mark.parametrize("stack", [((0.5e-3,), (130.0,), 1e5),
                                    ((0.3e-3, 0.5e-3), (130.0, 400.0), 2e5)])
-def test_kernel_split_equals_image_sum(stack):
+def test_kernel_split_equals_image_sum(stack, n):
+    """The real-space/spectral split of the kernel against the plain image
+    sum at 8^2 (cells wider than the silicon) and 32^2 (cells thinner than
+    it, many lattice radii inside the real-space cutoff)."""
     t, kap, h = stack
-    n, L = 8, 4e-3
+    L = 4e-3
     g0 = ph.ghat(np.array([0.0]), t, kap, h)[0]
     lam = math.sqrt(sum(a * b for a, b in zip(t, kap)) * g0)
     Ki = _image_road_kper(n, L, t, kap, h, 32 * lam)
