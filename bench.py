@@ -91,6 +91,12 @@ def _args():
     ap.add_argument("--how", default="")
     ap.add_argument("--variants", default="",
                     help="comma-separated subset of the variants to time (default: all)")
+    ap.add_argument("--unit", default="map", help="unit of --record-traffic's --batch count")
+    ap.add_argument("--case", default="", choices=["", "transient", "transient_window5",
+                                                   "closed_form", "network"],
+                    help="run one kernel's small case for a profiler capture (a warm-up "
+                         "call, then one timed call) and print its timing instead of the bench")
+    ap.add_argument("--tsteps", type=int, default=10, help="steps of --case transient*")
     return ap.parse_args()
 
 
@@ -117,6 +123,11 @@ KERNEL_SOURCES = {
     "k_solve_cluster": [_CSRC + "vs_cluster.cu"] + _COMMON,
     "k_solve_steady": [_CSRC + "vs_solver.cu", _CSRC + "vs_internal.cuh"] + _COMMON,
     "k_solve_steady_tc": [_CSRC + "vs_solver.cu", _CSRC + "vs_internal.cuh", _CSRC + "vs_tc.cuh"] + _COMMON,
+    "k_solve_transient": [_CSRC + "vs_solver.cu", _CSRC + "vs_internal.cuh"] + _COMMON,
+    "k_cf_rows_fwd": [_CSRC + "vs_closed.cu"] + _COMMON,
+    "k_cf_cols": [_CSRC + "vs_closed.cu"] + _COMMON,
+    "k_cf_rows_inv": [_CSRC + "vs_closed.cu"] + _COMMON,
+    "k_conv_fwd": [_CSRC + "vs_cnn.cu"] + _COMMON,
 }
 TRAFFIC_JSON = os.path.join(ROOT, "profiles", "traffic.json")
 
@@ -137,8 +148,9 @@ def _source_hash(files) -> str:
 
 
 def _traffic_record(kernel: str):
-    """DRAM bytes per map of `kernel` from a committed ncu capture, or None if
-    the kernel's sources changed since it was taken."""
+    """DRAM bytes per unit (map, or transient step) of `kernel` from a
+    committed ncu capture, or None if the kernel's sources changed since it
+    was taken."""
     if not os.path.exists(TRAFFIC_JSON) or kernel not in KERNEL_SOURCES:
         return None
     d = json.load(open(TRAFFIC_JSON)).get(kernel)
@@ -147,10 +159,11 @@ def _traffic_record(kernel: str):
     return d
 
 
-def record_traffic(csv_path: str, kernel: str, maps: int, how: str):
+def record_traffic(csv_path: str, kernel: str, maps: int, how: str, unit: str = "map"):
     """Writes the traffic record of `kernel` from `ncu -i <report> --page raw
     --csv` output: dram__bytes_read.sum + dram__bytes_write.sum of the first
-    captured launch of that kernel, divided by the maps the launch solved."""
+    captured launch of that kernel, divided by the units (maps, or transient
+    steps) the launch processed."""
     import csv
     rows = list(csv.reader(open(csv_path)))
     head, units = rows[0], rows[1]
@@ -162,12 +175,12 @@ def record_traffic(csv_path: str, kernel: str, maps: int, how: str):
         get = lambda m: float(r[col[m]].replace(",", "")) * scale.get(units[col[m]], 1.0)
         rd, wr = get("dram__bytes_read.sum"), get("dram__bytes_write.sum")
         d = json.load(open(TRAFFIC_JSON)) if os.path.exists(TRAFFIC_JSON) else {}
-        d[kernel] = {"source_hash": _source_hash(KERNEL_SOURCES[kernel]),
-                     "dram_bytes_per_map": (rd + wr) / maps, "captured_maps": maps,
+        d[kernel] = {"source_hash": _source_hash(KERNEL_SOURCES[kernel]), "unit": unit,
+                     "dram_bytes_per_unit": (rd + wr) / maps, "captured_units": maps,
                      "dram_read_bytes": rd, "dram_write_bytes": wr, "how": how}
         json.dump(d, open(TRAFFIC_JSON, "w"), indent=1)
-        print("%s: %.3f MB per map (read %.1f MB, write %.1f MB over %d maps)"
-              % (kernel, (rd + wr) / maps / 1e6, rd / 1e6, wr / 1e6, maps))
+        print("%s: %.3f MB per %s (read %.1f MB, write %.1f MB over %d)"
+              % (kernel, (rd + wr) / maps / 1e6, unit, rd / 1e6, wr / 1e6, maps))
         return
     raise SystemExit("no launch of %s in %s" % (kernel, csv_path))
 
@@ -670,9 +683,12 @@ def run_ours(a):
             "status": tinfo["status"],
             "how": "one vs_solve_transient call (plan set-up included), wall time",
             "roofline": {"bound": "hbm", "achieved": tbytes / dt_t / 1e9, "peak": _peaks()[0],
-                         "unit": "GB/s", "frac": tbytes / dt_t / 1e9 / _peaks()[0], "traffic": None,
+                         "unit": "GB/s", "frac": tbytes / dt_t / 1e9 / _peaks()[0],
+                         "traffic": (_traffic_record("k_solve_transient")["dram_bytes_per_unit"]
+                                     * steps_t) if _traffic_record("k_solve_transient") else None,
                          "kernel": "k_solve_transient",
-                         "note": "8 B/pixel per step algorithmic (read P_dyn,n, write theta_n)"}}
+                         "note": "8 B/pixel per step algorithmic (read P_dyn,n, write theta_n); "
+                                 "traffic per launch from the committed per-step capture"}}
         # Sec. IV-E variants on the same trace: the paper's 5-step window, and the
         # leakage of each step taken at its own temperature (per-step fixed point)
         rise = float(out_t.abs().max())
@@ -730,8 +746,10 @@ def run_ours(a):
                         "roofline": {"bound": "hbm", "achieved": algo / (ms_cf * 1e-3) / 1e9,
                                      "peak": _peaks()[0], "unit": "GB/s",
                                      "frac": algo / (ms_cf * 1e-3) / 1e9 / _peaks()[0],
-                                     "traffic": None, "kernel": "k_cf_rows_fwd + k_cf_cols + "
-                                     "k_cf_rows_inv",
+                                     "traffic": {kn: (_traffic_record(kn)["dram_bytes_per_unit"]
+                                                      * B) if _traffic_record(kn) else None
+                                                 for kn in ("k_cf_rows_fwd", "k_cf_cols")},
+                                     "kernel": "k_cf_rows_fwd + k_cf_cols + k_cf_rows_inv",
                                      "note": "16 B/pixel algorithmic (3 maps in, theta out); the "
                                              "three passes also move 24 B/pixel of spectra"}}
         del th_cf
@@ -814,7 +832,7 @@ def run_ours(a):
             hb = alg_bytes / sec / 1e9
             return {"bound": "alu", "achieved": ach, "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s",
                     "frac": ach / FP32_PEAK_TFLOPS,
-                    "traffic": (tr["dram_bytes_per_map"] * B) if tr else None, "kernel": kernel,
+                    "traffic": (tr["dram_bytes_per_unit"] * B) if tr else None, "kernel": kernel,
                     "kernel_count": {"achieved": ach_k, "frac": ach_k / FP32_PEAK_TFLOPS},
                     "hbm_view": {"achieved": hb, "peak": hbm, "unit": "GB/s", "frac": hb / hbm},
                     "note": "achieved = maps x iterations x 2 x 2.5 n^2 log2(n^2) (a fast 2-D "
@@ -829,8 +847,11 @@ def run_ours(a):
             r = results[name]
             it = r["iterations_mean"] + (1.0 if extra_iteration else 0.0)
             ach = B * it * 4 * 2 * w.n ** 3 * 3 / (r["ms_per_step"] * 1e-3) / 1e12
+            tr = _traffic_record("k_solve_steady_tc")
             return {"bound": "tensor", "achieved": ach, "peak": tc_peak, "unit": "TFLOP/s",
-                    "frac": ach / tc_peak, "traffic": None, "kernel": "k_solve_steady_tc",
+                    "frac": ach / tc_peak,
+                    "traffic": (tr["dram_bytes_per_unit"] * B) if tr else None,
+                    "kernel": "k_solve_steady_tc",
                     "note": "achieved = maps x iterations x 4 passes x 2n^3 x 3 split products "
                             "/ step time; peak = measured bf16 sustained"}
 
@@ -900,10 +921,64 @@ def run_ours(a):
         dist.destroy_process_group()
 
 
+def run_case(a):
+    """One kernel on a small case, for a profiler capture: a warm-up call and
+    one timed call (CUDA events on the current stream)."""
+    import torch
+    import paper_2307_12119_gb300 as vs
+    import synth
+    dev = torch.device("cuda", 0)
+    stream = torch.cuda.current_stream()
+    out = {"case": a.case}
+    if a.case.startswith("transient"):
+        w = synth.workload("c4_1024" if a.n == 1024 else "c2_256")
+        st = w.stack
+        k = vs.Kernel(vs.Stack(st.thickness_m, st.kappa_W_mK, st.h_conv_W_m2K, st.heat_cap_J_m2K),
+                      vs.Grid(w.n, w.die_m), vs.KernelOpts(dt_s=1e-3))
+        trace = synth.markov_trace(w, a.tsteps, device=dev)
+        _, pl, s = synth.steady_inputs(w, 1, device=dev)
+        prm = vs.SolveParams(w.physics.beta_per_K, w.physics.alpha_per_K, 1e-4, 50)
+        opts = {"window": 5} if a.case == "transient_window5" else {}
+        th = torch.empty_like(trace)
+        call = lambda: vs.solve_transient(k, trace, pl[0], s[0], prm, th, **opts)
+        units, unit = a.tsteps, "step"
+        out["workload"] = "transient %dx%d, %d steps of 1 ms" % (w.n, w.n, a.tsteps)
+    else:
+        w, pd, pl, s = synth.batch_inputs(a.n, a.batch, device=dev)
+        units, unit = a.batch, "map"
+        if a.case == "closed_form":
+            st = w.stack
+            k = vs.Kernel(vs.Stack(st.thickness_m, st.kappa_W_mK, st.h_conv_W_m2K,
+                                   st.heat_cap_J_m2K), vs.Grid(w.n, w.die_m))
+            prm = vs.SolveParams(w.physics.beta_per_K, w.physics.alpha_per_K, 1e-2, 50)
+            th = torch.empty_like(pd)
+            call = lambda: vs.solve_closed_form(k, pd, pl, s, prm, vs.VS_CF_CONV, th, stream,
+                                                info=False)
+            out["workload"] = "closed form (conv mode), %d maps of %dx%d" % (a.batch, w.n, w.n)
+        else:
+            R = 64
+            m = vs.Model(16, R, seed=11)
+            x = torch.rand(a.batch, 3, R, R, device=dev)
+            call = lambda: m.forward(x, stream)
+            out["workload"] = "warm-start network forward, %d inputs of 3x%dx%d" % (a.batch, R, R)
+    call()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    call()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1)
+    out.update(ms=ms, units=units, unit=unit, ms_per_unit=ms / units)
+    print(json.dumps(out))
+
+
 if __name__ == "__main__":
     args = _args()
     if args.record_traffic:
-        record_traffic(args.record_traffic, args.kernel, args.batch, args.how)
+        record_traffic(args.record_traffic, args.kernel, args.batch, args.how, args.unit)
+    elif args.case:
+        run_case(args)
     elif args.impl == "reference":
         run_reference(args)
     else:

@@ -119,7 +119,8 @@ def solve(n, die_m, t, kappa, h, r, sources, cells_per_layer=None, overhang_cell
 
     Returns (theta[len(sources), n, n] in K/W, info) where info holds the
     number of unknowns and, per source, the heat leaving through the bottom
-    (W; 1 by conservation)."""
+    (W; 1 by conservation) and the mean source-plane rise over the whole die
+    area (every finite volume, not only the cell centres)."""
     if r % 2 != 1:
         raise ValueError("r must be odd (a finite volume at every cell centre)")
     cpl = [2.0] * len(t) if cells_per_layer is None else cells_per_layer
@@ -129,7 +130,7 @@ def solve(n, die_m, t, kappa, h, r, sources, cells_per_layer=None, overhang_cell
     top = index[0]
     c = (r - 1) // 2
     out = np.zeros((len(sources), n, n))
-    bottom_heat = []
+    bottom_heat, die_mean = [], []
     for k, (sy, sx) in enumerate(sources):
         q = np.zeros((N, N))                      # flux (W/m^2) into the top volumes
         y0, x0 = off + sy * r, off + sx * r
@@ -141,9 +142,10 @@ def solve(n, die_m, t, kappa, h, r, sources, cells_per_layer=None, overhang_cell
         surf = Ttop + q * g["dz"][0] / (2 * g["kz"][0])
         die = surf[off:off + n * r, off:off + n * r]
         out[k] = die[c::r, c::r]
+        die_mean.append(float(die.mean()))
         bi = index[-1]
         bottom_heat.append(float(np.sum(T[bi[bi >= 0]]) * g["g_bottom"]))
-    return out, {"unknowns": A.shape[0], "bottom_heat_W": bottom_heat}
+    return out, {"unknowns": A.shape[0], "bottom_heat_W": bottom_heat, "die_mean": die_mean}
 
 
 def solve_extrapolated(n, die_m, t, kappa, h, refinements, sources, cells_per_layer=None,

@@ -178,6 +178,70 @@ def g_top_radial(r, t0: float, kappa0: float, a: float):
 
 
 # --------------------------------------------------------------------------- #
+# Spreader wider than the die (Sec. II-B)                                       #
+# --------------------------------------------------------------------------- #
+
+def spreader_mean_impedance(t, kappa, h, first: int, die_m: float, side_m: float,
+                            terms: int = 2000):
+    """Footprint-mean impedance [K m^2/W] of layers first..M-1 when they are
+    a square of side side_m (>= die_m, adiabatic side walls, convective
+    bottom) heated by a uniform flux over the centred die footprint of side
+    die_m: the mean temperature rise over the footprint per unit flux.
+
+    Cosine series of the wide layers (Neumann walls at 0 and side_m): with
+    d_m = (1/L) int_a^{a+L} cos(m pi x / L_s) dx (d_0 = 1, a = (L_s - L)/2)
+    the flux is q sum_{m,n} c_m c_n cos cos with c_m = eps_m (L/L_s) d_m
+    (eps_0 = 1, eps_m = 2), each mode answers with Z(k_mn), k_mn = pi
+    sqrt(m^2 + n^2) / L_s (the impedance recursion of `impedance_below`),
+    and its footprint mean is d_m d_n: so the mean is
+    sum_{m,n} w_m w_n Z(k_mn), w_m = eps_m (L/L_s) d_m^2. The terms fall like
+    1/(m^2 n^2 sqrt(m^2+n^2)); `terms` modes per axis. For side_m = die_m only
+    m = n = 0 survives and the result is Z(0), the die-sized stack."""
+    L, Ls = float(die_m), float(side_m)
+    a = 0.5 * (Ls - L)
+    m = np.arange(terms, dtype=np.float64)
+    d = np.ones(terms)
+    mm = m[1:]
+    d[1:] = Ls / (mm * math.pi * L) * (np.sin(mm * math.pi * (a + L) / Ls)
+                                       - np.sin(mm * math.pi * a / Ls))
+    w = (L / Ls) * np.where(m == 0, 1.0, 2.0) * d * d
+    keep = np.abs(w) > 0.0
+    w, mk = w[keep], m[keep]
+    k = math.pi * np.sqrt(mk[:, None] ** 2 + mk[None, :] ** 2) / Ls
+    Z = impedance_below(k, t, kappa, h, first)
+    return float(np.sum(w[:, None] * w[None, :] * Z))
+
+
+def ghat0_wide(t, kappa, h, first: int, die_m: float, side_m: float):
+    """g^ of the uniform mode when layers first.. are a spreader of side
+    side_m under a die of side die_m: the die layers in series (1-D, the die's
+    own walls are adiabatic) over the spreader's footprint-mean impedance.
+
+    This is the reading of Sec. II-B's decomposition of the Green's function
+    into a fast-decaying part and a CONSTANT carried by the spreader: a wider
+    spreader changes only that constant, i.e. only the uniform mode of the
+    imaged kernel; every other mode keeps the stack spectrum of
+    `impedance_below`. Equal to ghat(0) for side_m = die_m."""
+    if not 1 <= first < len(t):
+        raise ValueError("the spreader is layers first..M-1 with 1 <= first < M")
+    top = sum(float(t[i]) / float(kappa[i]) for i in range(first))
+    return top + spreader_mean_impedance(t, kappa, h, first, die_m, side_m)
+
+
+def _uniform_mode_shift(n, die_m, t, kappa, h, spreader):
+    """Change of K~[0, 0] for a spreader (first, side_m) wider than the die:
+    (g^0_wide - g^(0)) / cell^2 (the primary uniform term is g^(0) D(0) /
+    cell^2), i.e. a constant (g^0_wide - g^(0)) / L^2 added to the Green's
+    function. 0 without a spreader."""
+    if spreader is None:
+        return 0.0
+    first, side_m = spreader
+    g0 = float(ghat(np.array([0.0]), t, kappa, h)[0])
+    cell = die_m / n
+    return (ghat0_wide(t, kappa, h, first, die_m, side_m) - g0) / cell ** 2
+
+
+# --------------------------------------------------------------------------- #
 # Spectral kernel of the imaged die                                            #
 # --------------------------------------------------------------------------- #
 
@@ -198,7 +262,7 @@ def real_space_cutoff(t0: float, rel: float = 1e-18) -> float:
 
 
 def spectrum(n: int, die_m: float, t, kappa, h, n_modes: int | None = None,
-             rel: float = 1e-18):
+             rel: float = 1e-18, spreader=None):
     """K~[p, q] for p, q in [0, n_modes) (n_modes defaults to n).
 
     Definition (Sec. IV-F images + Eq. 2): with all mirror images the imaged
@@ -212,6 +276,8 @@ def spectrum(n: int, die_m: float, t, kappa, h, n_modes: int | None = None,
         sum_m G_R(cell|m|) e^{-i w.m cell} = cell^-2 sum_{s,t} R(|k|) D(|k|a),
         k = (pi (p + 2 n s) / L, pi (q + 2 n t) / L), truncated where
         exp(-2 k t0) is below `rel`.
+    spreader = (first, side_m): layers first.. are a spreader wider than the
+    die (`ghat0_wide`): the uniform mode K~[0, 0] takes its g^0_wide.
     Returns the FP64 array [n_modes, n_modes] (row index = y mode).
     """
     t = tuple(float(x) for x in t)
@@ -239,13 +305,15 @@ def spectrum(n: int, die_m: float, t, kappa, h, n_modes: int | None = None,
             kk = np.sqrt(ky[:, None] ** 2 + kx[None, :] ** 2)
             KR += ghat_rest(kk, t, kappa, h) * _disc_factor(kk * a)
     KR /= cell ** 2
-    return K1 + KR
+    K = K1 + KR
+    K[0, 0] += _uniform_mode_shift(n, die_m, t, kappa, h, spreader)
+    return K
 
 
-def kernel_periodic(n: int, die_m: float, t, kappa, h):
+def kernel_periodic(n: int, die_m: float, t, kappa, h, spreader=None):
     """Imaged kernel K_per(dy, dx) on the 2n x 2n periodic grid: the inverse
     2n-point DFT of the full spectrum K~[p, q], p, q in [0, 2n)."""
-    Kfull = spectrum(n, die_m, t, kappa, h, n_modes=2 * n)
+    Kfull = spectrum(n, die_m, t, kappa, h, n_modes=2 * n, spreader=spreader)
     return np.real(np.fft.ifft2(Kfull))
 
 

@@ -240,7 +240,7 @@ def closed_form(Kt, p_dyn, p_leak0, s, beta, alpha, mode="conv"):
 # Transient (Eqs. 27-37)                                                        #
 # --------------------------------------------------------------------------- #
 
-def step_spectrum(n, die_m, t, kappa, h, heat_cap, t_s, rel=1e-18):
+def step_spectrum(n, die_m, t, kappa, h, heat_cap, t_s, rel=1e-18, spreader=None):
     """Spectrum of the step-response Green's function at time t_s:
     single pole per spatial frequency with tau(k) = C g^(k) (Eq. 35 with the
     alpha term of tau dropped; C = areal heat capacity), so the response to a
@@ -249,6 +249,10 @@ def step_spectrum(n, die_m, t, kappa, h, heat_cap, t_s, rel=1e-18):
     Same real/spectral split as physics.spectrum: the top-layer part is static
     (the exp factor of the aliases with large k vanishes), the spectral part
     is R(k) - g^(k) exp(-t/(C g^(k))), which decays exponentially in k for t > 0.
+
+    spreader = (first, side_m): a spreader wider than the die changes the
+    uniform mode only (physics.ghat0_wide): its step response is
+    g^0_wide (1 - exp(-t / (C g^0_wide))).
     """
     import math
     t = tuple(float(x) for x in t)
@@ -276,7 +280,14 @@ def step_spectrum(n, die_m, t, kappa, h, heat_cap, t_s, rel=1e-18):
             g = physics.ghat(kk, t, kappa, h)
             KR += (physics.ghat_rest(kk, t, kappa, h)
                    - g * np.exp(-t_s / (heat_cap * g))) * physics._disc_factor(kk * a)
-    return K1 + KR / cell ** 2
+    S_ = K1 + KR / cell ** 2
+    if spreader is not None:
+        # primary uniform term g (1 - e^{-t/(C g)}) with g^0_wide for g^(0)
+        g0 = float(physics.ghat(np.array([0.0]), t, kappa, h)[0])
+        gw = physics.ghat0_wide(t, kappa, h, spreader[0], die_m, spreader[1])
+        S_[0, 0] += (gw * (1.0 - math.exp(-t_s / (heat_cap * gw)))
+                     - g0 * (1.0 - math.exp(-t_s / (heat_cap * g0)))) / cell ** 2
+    return S_
 
 
 def duhamel(step_spectra, p_dyn_trace, p_leak0, s, beta, alpha):

@@ -24,7 +24,7 @@ def test_traffic_records_resolve_only_for_their_sources():
     assert recs
     for kernel, rec in recs.items():
         assert kernel in bench.KERNEL_SOURCES, kernel
-        assert rec["dram_bytes_per_map"] > 0 and rec["captured_maps"] > 0
+        assert rec["dram_bytes_per_unit"] > 0 and rec["captured_units"] > 0
         cur = bench._source_hash(bench.KERNEL_SOURCES[kernel])
         got = bench._traffic_record(kernel)
         assert (got is not None) == (rec["source_hash"] == cur), kernel
