@@ -182,7 +182,7 @@ def g_top_radial(r, t0: float, kappa0: float, a: float):
 # --------------------------------------------------------------------------- #
 
 def spreader_mean_impedance(t, kappa, h, first: int, die_m: float, side_m: float,
-                            terms: int = 2000):
+                            terms: int = 2048):
     """Footprint-mean impedance [K m^2/W] of layers first..M-1 when they are
     a square of side side_m (>= die_m, adiabatic side walls, convective
     bottom) heated by a uniform flux over the centred die footprint of side
@@ -195,8 +195,19 @@ def spreader_mean_impedance(t, kappa, h, first: int, die_m: float, side_m: float
     sqrt(m^2 + n^2) / L_s (the impedance recursion of `impedance_below`),
     and its footprint mean is d_m d_n: so the mean is
     sum_{m,n} w_m w_n Z(k_mn), w_m = eps_m (L/L_s) d_m^2. The terms fall like
-    1/(m^2 n^2 sqrt(m^2+n^2)); `terms` modes per axis. For side_m = die_m only
+    1/(m^2 n^2 sqrt(m^2+n^2)), so the sum over m, n < M misses a tail that
+    falls like 1/M^2; it is removed by one Richardson step,
+    S = (4 S_M - S_{M/2}) / 3, with M = `terms`. For side_m = die_m only
     m = n = 0 survives and the result is Z(0), the die-sized stack."""
+    M = int(terms)
+    if M < 4 or M % 2:
+        raise ValueError("terms must be even and >= 4")
+    return (4.0 * _spreader_partial(t, kappa, h, first, die_m, side_m, M)
+            - _spreader_partial(t, kappa, h, first, die_m, side_m, M // 2)) / 3.0
+
+
+def _spreader_partial(t, kappa, h, first, die_m, side_m, terms):
+    """sum_{m, n < terms} w_m w_n Z(k_mn) of `spreader_mean_impedance`."""
     L, Ls = float(die_m), float(side_m)
     a = 0.5 * (Ls - L)
     m = np.arange(terms, dtype=np.float64)

@@ -68,7 +68,8 @@ class VarsimError(RuntimeError):
 class _Stack(C.Structure):
     _fields_ = [("n_layers", C.c_int), ("thickness_m", C.c_double * VS_MAX_LAYERS),
                 ("kappa_W_mK", C.c_double * VS_MAX_LAYERS), ("h_conv_W_m2K", C.c_double),
-                ("heat_cap_J_m2K", C.c_double)]
+                ("heat_cap_J_m2K", C.c_double), ("spreader_layer", C.c_int),
+                ("spreader_side_m", C.c_double)]
 
 
 class _Grid(C.Structure):
@@ -211,11 +212,15 @@ def _ptr(t, n: Optional[int] = None, name: str = "map", allow_none=False):
 
 @dataclass
 class Stack:
-    """Layer stack, top (source) layer first; SI units."""
+    """Layer stack, top (source) layer first; SI units. spreader_layer > 0
+    makes layers spreader_layer.. a spreader of side spreader_side_m wider
+    than the die (vs_stack)."""
     thickness_m: Sequence[float] = (0.5e-3, 0.02e-3, 3.5e-3)
     kappa_W_mK: Sequence[float] = (130.0, 4.0, 400.0)
     h_conv_W_m2K: float = 2.0e4
     heat_cap_J_m2K: float = 1.63e6 * 0.5e-3
+    spreader_layer: int = 0
+    spreader_side_m: float = 0.0
 
     def _c(self) -> _Stack:
         s = _Stack()
@@ -225,6 +230,8 @@ class Stack:
             s.kappa_W_mK[i] = k
         s.h_conv_W_m2K = self.h_conv_W_m2K
         s.heat_cap_J_m2K = self.heat_cap_J_m2K
+        s.spreader_layer = self.spreader_layer
+        s.spreader_side_m = self.spreader_side_m
         return s
 
 

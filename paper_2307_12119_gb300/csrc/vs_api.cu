@@ -49,6 +49,13 @@ int vs_validate_stack(const vs_stack* s) {
   if (!pos_finite(s->h_conv_W_m2K)) return vs_set_error(VS_ERR_INVALID_ARG, "h_conv must be > 0");
   if (!(s->heat_cap_J_m2K >= 0.0) || !isfinite(s->heat_cap_J_m2K))
     return vs_set_error(VS_ERR_INVALID_ARG, "heat_cap must be >= 0");
+  if (s->spreader_layer != 0) {
+    if (s->spreader_layer < 1 || s->spreader_layer >= s->n_layers)
+      return vs_set_error(VS_ERR_INVALID_ARG, "spreader_layer %d outside [1, %d)",
+                          s->spreader_layer, s->n_layers);
+    if (!pos_finite(s->spreader_side_m))
+      return vs_set_error(VS_ERR_INVALID_ARG, "spreader_side_m must be > 0");
+  }
   return VS_OK;
 }
 
@@ -107,4 +114,6 @@ void vs_stack_to_dev(const vs_stack* s, vs_stack_dev* d) {
   }
   d->h = s->h_conv_W_m2K;
   d->heat_cap = s->heat_cap_J_m2K;
+  d->spreader_layer = s->spreader_layer;
+  d->spreader_side = s->spreader_side_m;
 }

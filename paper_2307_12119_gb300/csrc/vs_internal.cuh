@@ -31,6 +31,8 @@ struct vs_stack_dev {
   double kappa[VS_MAX_LAYERS];
   double h;
   double heat_cap;
+  int spreader_layer;      // 0: die-sized stack
+  double spreader_side;    // metres, >= the die side when spreader_layer > 0
 };
 
 // ---------------------------------------------------------------- FFT tables

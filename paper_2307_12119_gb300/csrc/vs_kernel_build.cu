@@ -218,13 +218,87 @@ __global__ void k_cos_table(int n, double* __restrict__ c) {
   if (j < 2 * n) c[j] = cospi((double)j / (double)n);
 }
 
+// ------------------------------------------------------------ wider spreader
+// Footprint-mean impedance of the spreader layers (first .. M-1) when they are
+// a square of side Ls centred under the die of side L (Sec. II-B: the spreader
+// carries a constant part of the Green's function). Cosine series of the wide
+// layers: with d_m = (1/L) int_a^{a+L} cos(m pi x / Ls) dx (a = (Ls - L)/2,
+// d_0 = 1) and w_m = eps_m (L / Ls) d_m^2 (eps_0 = 1, else 2), the mean rise
+// over the footprint per unit flux is sum_{m,n} w_m w_n Z(pi sqrt(m^2+n^2)/Ls).
+// Partial sums over m, n < M and m, n < M/2 per block, in a fixed order.
+constexpr int kSprTerms = 2048;   // modes per axis (even)
+constexpr int kSprBlocks = 128;
+constexpr int kSprThreads = 256;
+
+__device__ double spr_w(int m, double L, double Ls) {
+  if (m == 0) return L / Ls;
+  const double a = 0.5 * (Ls - L);
+  const double d = Ls / ((double)m * kPi * L) *
+                   (sin((double)m * kPi * (a + L) / Ls) - sin((double)m * kPi * a / Ls));
+  return 2.0 * (L / Ls) * d * d;
+}
+
+__global__ void __launch_bounds__(kSprThreads) k_spreader_partial(vs_stack_dev st, double L,
+                                                                  double* __restrict__ part) {
+  __shared__ double red[2][kSprThreads];
+  __shared__ double w[kSprTerms];
+  const double Ls = st.spreader_side;
+  for (int m = threadIdx.x; m < kSprTerms; m += kSprThreads) w[m] = spr_w(m, L, Ls);
+  __syncthreads();
+  double full = 0.0, half = 0.0;
+  const long long total = (long long)kSprTerms * kSprTerms;
+  for (long long i = (long long)blockIdx.x * kSprThreads + threadIdx.x; i < total;
+       i += (long long)kSprBlocks * kSprThreads) {
+    const int m = (int)(i / kSprTerms), n = (int)(i % kSprTerms);
+    const double wm = w[m], wn = w[n];
+    if (wm == 0.0 || wn == 0.0) continue;
+    const double k = kPi * sqrt((double)m * m + (double)n * n) / Ls;
+    const double v = wm * wn * impedance_d(k, st, st.spreader_layer);
+    full += v;
+    if (m < kSprTerms / 2 && n < kSprTerms / 2) half += v;
+  }
+  red[0][threadIdx.x] = full;
+  red[1][threadIdx.x] = half;
+  __syncthreads();
+  for (int s = kSprThreads / 2; s > 0; s >>= 1) {
+    if (threadIdx.x < s) {
+      red[0][threadIdx.x] += red[0][threadIdx.x + s];
+      red[1][threadIdx.x] += red[1][threadIdx.x + s];
+    }
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    part[2 * blockIdx.x] = red[0][0];
+    part[2 * blockIdx.x + 1] = red[1][0];
+  }
+}
+
+// g^ of the uniform mode with the wide spreader: the die layers in series over
+// the footprint-mean impedance, its 1/M^2 series tail removed by one
+// Richardson step (4 S_M - S_{M/2}) / 3. Single thread, fixed order.
+__global__ void k_spreader_g0(vs_stack_dev st, const double* __restrict__ part,
+                              double* __restrict__ g0w) {
+  if (blockIdx.x != 0 || threadIdx.x != 0) return;
+  double full = 0.0, half = 0.0;
+  for (int b = 0; b < kSprBlocks; ++b) {
+    full += part[2 * b];
+    half += part[2 * b + 1];
+  }
+  double top = 0.0;
+  for (int i = 0; i < st.spreader_layer; ++i) top += st.t[i] / st.kappa[i];
+  *g0w = top + (4.0 * full - half) / 3.0;
+}
+
 // Spectral part: cell^-2 sum_{s,t in [-S,S]} R(|k|) D(|k| a),
 // k = pi (p + 2 n s, q + 2 n t) / L; added to K1 and converted to FP32.
-// Also the transient tables for the primary mode when dt > 0.
+// Also the transient tables for the primary mode when dt > 0. With a wider
+// spreader (g0w != NULL) the uniform mode's primary term g^(0) / cell^2 takes
+// g0w instead, in K and in the transient tables.
 __global__ void k_spectral(const double* __restrict__ K1, int n, double L, int S,
                            vs_stack_dev st, double a, double dt,
                            double* __restrict__ K64, float* __restrict__ K32,
-                           float* __restrict__ trA, float* __restrict__ trRho) {
+                           float* __restrict__ trA, float* __restrict__ trRho,
+                           const double* __restrict__ g0w) {
   int q = blockIdx.x * blockDim.x + threadIdx.x;
   int p = blockIdx.y;
   if (q >= n || p >= n) return;
@@ -243,11 +317,13 @@ __global__ void k_spectral(const double* __restrict__ K1, int n, double L, int S
   }
   size_t idx = (size_t)p * n + q;
   double v = K1[idx] + acc / (cell * cell);
+  const bool wide = g0w != nullptr && idx == 0;
+  if (wide) v += (*g0w - ghat_d(0.0, st)) / (cell * cell);
   K64[idx] = v;
   K32[idx] = (float)v;
   if (trA != nullptr) {
     double k0 = kPi * sqrt((double)p * p + (double)q * q) / L;
-    double g = ghat_d(k0, st);
+    double g = wide ? *g0w : ghat_d(k0, st);
     trA[idx] = (float)(g * disc_d(k0 * a) / (cell * cell));
     trRho[idx] = (float)exp(-dt / (st.heat_cap * g));
   }
@@ -399,6 +475,10 @@ extern "C" int vs_make_kernel(const vs_stack* stack, const vs_grid* grid,
   if (!(dt >= 0.0) || !isfinite(dt)) return vs_set_error(VS_ERR_INVALID_ARG, "dt_s must be >= 0");
   if (dt > 0.0 && !(stack->heat_cap_J_m2K > 0.0))
     return vs_set_error(VS_ERR_INVALID_ARG, "heat_cap_J_m2K must be > 0 for a transient kernel");
+  const bool wide = stack->spreader_layer > 0 && stack->spreader_side_m != grid->die_m;
+  if (stack->spreader_layer > 0 && !(stack->spreader_side_m >= grid->die_m))
+    return vs_set_error(VS_ERR_INVALID_ARG, "spreader_side_m %g is smaller than the die (%g)",
+                        stack->spreader_side_m, grid->die_m);
 
   cudaStream_t s = (cudaStream_t)stream;
   int n = grid->n;
@@ -446,7 +526,7 @@ extern "C" int vs_make_kernel(const vs_stack* stack, const vs_grid* grid,
 
   int* d_mlist = nullptr;
   double *d_r = nullptr, *d_g = nullptr, *d_kper = nullptr, *d_T = nullptr, *d_K1 = nullptr,
-         *d_cos = nullptr;
+         *d_cos = nullptr, *d_spr = nullptr;
   QuadRule q;
   auto fail = [&](int code) {
     cudaStreamSynchronize(s);
@@ -457,6 +537,7 @@ extern "C" int vs_make_kernel(const vs_stack* stack, const vs_grid* grid,
     cudaFree(d_T);
     cudaFree(d_K1);
     cudaFree(d_cos);
+    cudaFree(d_spr);
     free_quad_rule(&q, s);
     free_kernel_arrays(k);
     delete k;
@@ -485,6 +566,7 @@ extern "C" int vs_make_kernel(const vs_stack* stack, const vs_grid* grid,
   VS_BUILD_TRY(cudaMalloc(&d_T, sizeof(double) * (n + 1) * n));
   VS_BUILD_TRY(cudaMalloc(&d_K1, sizeof(double) * nn));
   VS_BUILD_TRY(cudaMalloc(&d_cos, sizeof(double) * 2 * n));
+  if (wide) VS_BUILD_TRY(cudaMalloc(&d_spr, sizeof(double) * (2 * kSprBlocks + 1)));
   VS_BUILD_TRY(cudaMemsetAsync(k->radial, 0, ((size_t)m_max + 1) * sizeof(double), s));
   VS_BUILD_TRY(cudaMemcpyAsync(d_mlist, mlist.data(), sizeof(int) * nu, cudaMemcpyHostToDevice, s));
 
@@ -508,8 +590,15 @@ extern "C" int vs_make_kernel(const vs_stack* stack, const vs_grid* grid,
   k_cos_rows<<<gr, 128, 0, s>>>(d_kper, n + 1, n, dmax, d_cos, d_T);
   dim3 gc((n + 127) / 128, n);
   k_cos_cols<<<gc, 128, 0, s>>>(d_T, n, dmax, d_cos, d_K1);
-  // 4: spectral part, FP32 copy, transient tables
-  k_spectral<<<gc, 128, 0, s>>>(d_K1, n, L, S, k->st, a, dt, k->Kt64, k->Kt32, k->trA, k->trRho);
+  // 4: the wider spreader's uniform mode, spectral part, FP32 copy, transient tables
+  const double* g0w = nullptr;
+  if (wide) {
+    k_spreader_partial<<<kSprBlocks, kSprThreads, 0, s>>>(k->st, L, d_spr + 1);
+    k_spreader_g0<<<1, 1, 0, s>>>(k->st, d_spr + 1, d_spr);
+    g0w = d_spr;
+  }
+  k_spectral<<<gc, 128, 0, s>>>(d_K1, n, L, S, k->st, a, dt, k->Kt64, k->Kt32, k->trA, k->trRho,
+                                g0w);
   VS_BUILD_TRY(cudaGetLastError());
 
   std::vector<float> host(nn);
@@ -531,6 +620,7 @@ extern "C" int vs_make_kernel(const vs_stack* stack, const vs_grid* grid,
   cudaFree(d_T);
   cudaFree(d_K1);
   cudaFree(d_cos);
+  cudaFree(d_spr);
   free_quad_rule(&q, s);
   cudaError_t e = cudaStreamSynchronize(s);
   if (e != cudaSuccess) {
