@@ -931,7 +931,7 @@ def run_case(a):
     stream = torch.cuda.current_stream()
     out = {"case": a.case}
     if a.case.startswith("transient"):
-        w = synth.workload("c4_1024" if a.n == 1024 else "c2_256")
+        w = synth.workload({1024: "c4_1024", 512: "c3_512"}.get(a.n, "c2_256"))
         st = w.stack
         k = vs.Kernel(vs.Stack(st.thickness_m, st.kappa_W_mK, st.h_conv_W_m2K, st.heat_cap_J_m2K),
                       vs.Grid(w.n, w.die_m), vs.KernelOpts(dt_s=1e-3))

@@ -316,6 +316,27 @@ typedef struct {
 int vs_plan_create(const vs_batch_item* items_host, int n_items,
                    const vs_solve_params* params, vs_plan* out, void* stream);
 
+/* Launch-shape autotuner (the paper has no counterpart). A plan's shape is
+ * one integer: on the cluster engine the update-load batch (1, 2 or 4
+ * positions whose inputs a thread loads before using them: the depth of the
+ * global-load pipelining), on the streamed engine the task size (2048, 4096,
+ * 8192 or 16384 elements of a map per row or column task). vs_plan_create
+ * tunes plans of at least 64 maps: it times every candidate on the plan itself
+ * (a warm-up and two timed runs each, CUDA events on `stream`; the runs write
+ * the plan's theta) and keeps the fastest. The choice is cached for the
+ * process per engine, mix of grid sizes and power-of-two batch bucket, so
+ * later plans of the same kind reuse it untimed. VS_AUTOTUNE=0 in the
+ * environment keeps the defaults (batch 2, 8192 elements). The shape changes
+ * data movement only: on the cluster engine every shape gives bit-identical
+ * maps. vs_plan_create_shaped forces a shape (0 = as vs_plan_create);
+ * VS_ERR_INVALID_ARG for a shape the engine does not have. */
+int vs_plan_create_shaped(const vs_batch_item* items_host, int n_items,
+                          const vs_solve_params* params, int shape, vs_plan* out, void* stream);
+/* The plan's shape, and the candidates its creation timed: *n_timed of them
+ * (0 when forced, cached or not tuned), their shapes and times in ms (arrays
+ * of at least 4, may be NULL). */
+int vs_plan_shape(vs_plan plan, int* shape_out, int* n_timed, int* cand_shapes, double* cand_ms);
+
 /* Runs the plan: one launch (streamed engine: cooperative and persistent;
  * cluster engine: one per distinct grid size, a cluster per map) that
  * iterates every map to its own convergence. Asynchronous; makes no host

@@ -49,7 +49,7 @@ EXPORTS = [
     "vs_model_train", "vs_model_save", "vs_model_load", "vs_warm_features", "vs_warm_target",
     "vs_warm_apply", "vs_solve_batch_host", "vs_model_shape", "vs_warm_plan_create",
     "vs_warm_plan_run", "vs_warm_plan_launches", "vs_warm_plan_info", "vs_warm_plan_free",
-    "vs_solve_transient_ex", "vs_solve_closed_form",
+    "vs_solve_transient_ex", "vs_solve_closed_form", "vs_plan_create_shaped", "vs_plan_shape",
 ]
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
@@ -133,6 +133,10 @@ def lib():
                                          C.POINTER(_SolveInfo), vp]),
         "vs_plan_create": (ip, [C.POINTER(_BatchItem), ip, C.POINTER(_SolveParams),
                                 C.POINTER(vp), vp]),
+        "vs_plan_create_shaped": (ip, [C.POINTER(_BatchItem), ip, C.POINTER(_SolveParams), ip,
+                                       C.POINTER(vp), vp]),
+        "vs_plan_shape": (ip, [vp, C.POINTER(C.c_int), C.POINTER(C.c_int), C.POINTER(C.c_int),
+                               C.POINTER(C.c_double)]),
         "vs_plan_run": (ip, [vp, vp]),
         "vs_plan_info": (ip, [vp, C.POINTER(_SolveInfo), vp]),
         "vs_plan_launches": (ip, [vp]),
@@ -397,9 +401,10 @@ class Plan:
     """A batched solve over many maps (vs_plan_*). One launch per run; with the
     cluster engine, one launch per distinct grid size (`launches`)."""
 
-    def __init__(self, items, params: Optional[SolveParams] = None, stream=None):
+    def __init__(self, items, params: Optional[SolveParams] = None, stream=None, shape: int = 0):
         """items: sequence of (Kernel, p_dyn, p_leak0, s_kappa or None, theta
-        [, theta_init or None])."""
+        [, theta_init or None]). shape: 0 = tuned or cached launch shape, else
+        forced (vs_plan_create_shaped)."""
         prm = params or SolveParams()
         arr = (_BatchItem * len(items))()
         self._keep = []
@@ -412,10 +417,17 @@ class Plan:
                                 _ptr(ti, n, "theta_init", allow_none=True))
             self._keep.append(item)
         h = C.c_void_p()
-        _check(lib().vs_plan_create(arr, len(items), C.byref(prm._c()), C.byref(h),
-                                    _stream(stream)), "vs_plan_create")
+        _check(lib().vs_plan_create_shaped(arr, len(items), C.byref(prm._c()), int(shape),
+                                           C.byref(h), _stream(stream)), "vs_plan_create_shaped")
         self.handle = h.value
         self.n_items = len(items)
+
+    def shape(self) -> dict:
+        """The launch shape and the candidates the autotuner timed (vs_plan_shape)."""
+        sh, nt = C.c_int(), C.c_int()
+        cs, ms = (C.c_int * 8)(), (C.c_double * 8)()
+        _check(lib().vs_plan_shape(self.handle, C.byref(sh), C.byref(nt), cs, ms), "vs_plan_shape")
+        return {"shape": sh.value, "timed": {cs[i]: ms[i] for i in range(nt.value)}}
 
     def run(self, stream=None):
         _check(lib().vs_plan_run(self.handle, _stream(stream)), "vs_plan_run")

@@ -33,7 +33,6 @@ namespace {
 #ifndef VS_CL_ROWS
 #define VS_CL_ROWS 32
 #endif
-constexpr int kClBatch = 2;            // positions whose inputs are loaded together
 
 template <int N>
 struct ClShape {
@@ -127,9 +126,13 @@ __device__ __forceinline__ int cl_dr(int k) {
 // the forward transform along x, so the fixed-point update runs on them
 // in place; the frequency k and its mirror N - k sit in lanes b and 16 - b of
 // one half-warp and are paired with shuffles.
-template <int N>
+// BATCH: positions of the update whose inputs (P_leak0, P_dyn, s, theta of
+// two rows) a thread loads together before using them, 1, 2 or 4: the depth of
+// the global-load pipelining, a launch shape the plan's autotuner picks.
+template <int N, int BATCH>
 __global__ void __launch_bounds__(ClShape<N>::THREADS, ClShape<N>::MIN_BLOCKS)
     k_solve_cluster(ClusterDev P) {
+  constexpr int kClBatch = BATCH;
   using Lay = ClLayout<N>;
   constexpr int kClRows = ClShape<N>::ROWS, kClF = ClShape<N>::F;
   constexpr int kClThreads = ClShape<N>::THREADS, ranks = ClShape<N>::RANKS;
@@ -624,12 +627,21 @@ ClHost cluster_shape(int n) {
   }
 }
 
-ClusterFn cluster_kernel(int n) {
+template <int N>
+ClusterFn cluster_kernel_n(int batch) {
+  switch (batch) {
+    case 1: return k_solve_cluster<N, 1>;
+    case 4: return k_solve_cluster<N, 4>;
+    default: return k_solve_cluster<N, 2>;
+  }
+}
+
+ClusterFn cluster_kernel(int n, int batch) {
   switch (n) {
-    case 32: return k_solve_cluster<32>;
-    case 64: return k_solve_cluster<64>;
-    case 128: return k_solve_cluster<128>;
-    default: return k_solve_cluster<256>;
+    case 32: return cluster_kernel_n<32>(batch);
+    case 64: return cluster_kernel_n<64>(batch);
+    case 128: return cluster_kernel_n<128>(batch);
+    default: return cluster_kernel_n<256>(batch);
   }
 }
 

@@ -139,11 +139,19 @@ __device__ __forceinline__ void dftR(float2* v) {
   else dft2<FWD>(v);
 }
 
+// Twiddle load: through the read-only path from global memory, or a plain
+// load when the table has been copied to shared memory (TW_SMEM).
+template <bool TW_SMEM>
+__device__ __forceinline__ float2 tw_load(const float2* __restrict__ p) {
+  if constexpr (TW_SMEM) return *p;
+  else return __ldg(p);
+}
+
 // One radix-R pass over `nfft` in-place FFTs of length n stored with padded
 // stride `stride` in shared memory. Blocks of length L, sub-stride m = L/R.
 // Forward (DIF): butterfly, then twiddle W_L^{j r}. Inverse: conjugate
 // twiddle, then inverse butterfly (exact inverse of the forward pass, x R).
-template <int R, bool FWD>
+template <int R, bool FWD, bool TW_SMEM = false>
 __device__ __forceinline__ void fft_pass(float2* buf, int n, int L, int nfft, int stride,
                                          const float2* __restrict__ tw4n, int tid, int nthr) {
   // all sizes are powers of two: index math by shifts and masks
@@ -167,12 +175,12 @@ __device__ __forceinline__ void fft_pass(float2* buf, int n, int L, int nfft, in
       dftR<R, true>(v);
       if (m > 1) {
 #pragma unroll
-        for (int r = 1; r < R; ++r) v[r] = cmul(v[r], __ldg(&tw4n[j * r * tws]));
+        for (int r = 1; r < R; ++r) v[r] = cmul(v[r], tw_load<TW_SMEM>(&tw4n[j * r * tws]));
       }
     } else {
       if (m > 1) {
 #pragma unroll
-        for (int r = 1; r < R; ++r) v[r] = cmulc(v[r], __ldg(&tw4n[j * r * tws]));
+        for (int r = 1; r < R; ++r) v[r] = cmulc(v[r], tw_load<TW_SMEM>(&tw4n[j * r * tws]));
       }
       dftR<R, false>(v);
     }
@@ -194,6 +202,7 @@ __device__ __forceinline__ int pass_radix(int n, int pass) {
 }
 
 // Full forward FFT (natural -> digit-reversed), synchronising between passes.
+template <bool TW_SMEM = false>
 __device__ __forceinline__ void fft_forward(float2* buf, int n, int nfft, int stride,
                                             const float2* __restrict__ tw4n) {
   int L = n;
@@ -201,10 +210,10 @@ __device__ __forceinline__ void fft_forward(float2* buf, int n, int nfft, int st
   for (int p = 0; p < np; ++p) {
     int R = pass_radix(n, p);
     switch (R) {
-      case 16: fft_pass<16, true>(buf, n, L, nfft, stride, tw4n, threadIdx.x, blockDim.x); break;
-      case 8: fft_pass<8, true>(buf, n, L, nfft, stride, tw4n, threadIdx.x, blockDim.x); break;
-      case 4: fft_pass<4, true>(buf, n, L, nfft, stride, tw4n, threadIdx.x, blockDim.x); break;
-      default: fft_pass<2, true>(buf, n, L, nfft, stride, tw4n, threadIdx.x, blockDim.x); break;
+      case 16: fft_pass<16, true, TW_SMEM>(buf, n, L, nfft, stride, tw4n, threadIdx.x, blockDim.x); break;
+      case 8: fft_pass<8, true, TW_SMEM>(buf, n, L, nfft, stride, tw4n, threadIdx.x, blockDim.x); break;
+      case 4: fft_pass<4, true, TW_SMEM>(buf, n, L, nfft, stride, tw4n, threadIdx.x, blockDim.x); break;
+      default: fft_pass<2, true, TW_SMEM>(buf, n, L, nfft, stride, tw4n, threadIdx.x, blockDim.x); break;
     }
     L /= R;
     __syncthreads();
@@ -212,6 +221,7 @@ __device__ __forceinline__ void fft_forward(float2* buf, int n, int nfft, int st
 }
 
 // Full inverse FFT (digit-reversed -> natural, unnormalised), syncing.
+template <bool TW_SMEM = false>
 __device__ __forceinline__ void fft_inverse(float2* buf, int n, int nfft, int stride,
                                             const float2* __restrict__ tw4n) {
   const int np = n_passes(n);
@@ -220,10 +230,10 @@ __device__ __forceinline__ void fft_inverse(float2* buf, int n, int nfft, int st
     int L = n;
     for (int i = 0; i < p; ++i) L /= pass_radix(n, i);
     switch (R) {
-      case 16: fft_pass<16, false>(buf, n, L, nfft, stride, tw4n, threadIdx.x, blockDim.x); break;
-      case 8: fft_pass<8, false>(buf, n, L, nfft, stride, tw4n, threadIdx.x, blockDim.x); break;
-      case 4: fft_pass<4, false>(buf, n, L, nfft, stride, tw4n, threadIdx.x, blockDim.x); break;
-      default: fft_pass<2, false>(buf, n, L, nfft, stride, tw4n, threadIdx.x, blockDim.x); break;
+      case 16: fft_pass<16, false, TW_SMEM>(buf, n, L, nfft, stride, tw4n, threadIdx.x, blockDim.x); break;
+      case 8: fft_pass<8, false, TW_SMEM>(buf, n, L, nfft, stride, tw4n, threadIdx.x, blockDim.x); break;
+      case 4: fft_pass<4, false, TW_SMEM>(buf, n, L, nfft, stride, tw4n, threadIdx.x, blockDim.x); break;
+      default: fft_pass<2, false, TW_SMEM>(buf, n, L, nfft, stride, tw4n, threadIdx.x, blockDim.x); break;
     }
     __syncthreads();
   }

@@ -77,6 +77,15 @@ void vs_stack_to_dev(const vs_stack* s, vs_stack_dev* d);
 int vs_hankel_eval(const vs_stack_dev& st, double cell_m, int quad_nodes,
                    const double* r_dev, double* out_dev, int count, cudaStream_t s);
 
+// ---------------------------------------------------------------- transient
+// Persistent transient of one map (vs_transient.cu): lagged leakage,
+// untruncated superposition, n in {256, 512, 1024}. Returns the map's status
+// (info filled), an error, or -1 if the launch shape does not fit the device.
+bool vs_transient_fast_ok(int n);
+int vs_transient_fast(vs_kernel k, int n_steps, const float* p_dyn_trace, const float* p_leak0,
+                      const float* s_kappa, const vs_solve_params* params, float* theta_trace,
+                      vs_solve_info* info, cudaStream_t s);
+
 // ---------------------------------------------------------------- plans
 // Asynchronous copy of a plan's per-map outcome to (pinned) host memory.
 int vs_plan_info_async(vs_plan p, vs_solve_info* info_host, cudaStream_t s);

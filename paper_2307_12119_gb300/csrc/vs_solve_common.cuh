@@ -71,6 +71,10 @@ using ClusterFn = void (*)(ClusterDev);
 
 bool cluster_size_ok(int n);
 ClHost cluster_shape(int n);
-ClusterFn cluster_kernel(int n);   // the instantiation for n (32, 64, 128 or 256)
+// The instantiation for n (32, 64, 128 or 256) and update-load batch (1, 2
+// or 4; the default launch shape is 2).
+ClusterFn cluster_kernel(int n, int batch);
+constexpr int kClBatches[3] = {1, 2, 4};
+constexpr int kClBatchDefault = 2;
 
 }  // namespace vsk

@@ -1453,6 +1453,9 @@ struct vs_plan_t {
   bool cluster = false;                       // cluster engine
   std::vector<std::pair<int, int>> cl_groups; // (n, maps) per launch, in order
   int* d_order = nullptr;                     // maps grouped by n
+  int cl_batch = kClBatchDefault;             // cluster engine: update-load batch
+  // autotuner record: the candidate shapes timed at creation and their times
+  std::vector<std::pair<int, double>> tuned;
 };
 
 namespace {
@@ -1619,7 +1622,23 @@ int plan_layout(vs_plan_t* p, int elems, cudaStream_t s, bool transient, int n_s
   return VS_OK;
 }
 
-size_t g_smem_attr_cluster[4] = {0, 0, 0, 0};  // per instantiation, n = 32 .. 256
+size_t g_smem_attr_cluster[4][3] = {};  // per instantiation: n = 32 .. 256 x batch 1, 2, 4
+
+int batch_index(int b) { return b == 1 ? 0 : b == 4 ? 2 : 1; }
+
+// Shared-memory attributes of the cluster instantiation (n, batch), once.
+int cluster_attrs(int n, int batch) {
+  std::lock_guard<std::mutex> lk(g_attr_mutex);
+  size_t& cur = g_smem_attr_cluster[__builtin_ctz((unsigned)n) - 5][batch_index(batch)];
+  if (cur == 0) {
+    ClusterFn fn = cluster_kernel(n, batch);
+    VS_CUDA_TRY(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     (int)cluster_shape(n).smem));
+    VS_CUDA_TRY(cudaFuncSetAttribute(fn, cudaFuncAttributePreferredSharedMemoryCarveout, 100));
+    cur = cluster_shape(n).smem;
+  }
+  return VS_OK;
+}
 
 cudaLaunchConfig_t cluster_config(int n, int count, cudaStream_t s, cudaLaunchAttribute* attr) {
   cudaLaunchConfig_t cfg = {};
@@ -1681,17 +1700,9 @@ int plan_layout_cluster(vs_plan_t* p, cudaStream_t s) {
   VS_CUDA_TRY(cudaMemsetAsync(p->d_info, 0, sizeof(vs_solve_info) * n_items, s));
   VS_CUDA_TRY(cudaMemsetAsync(p->d_ctrl, 0, sizeof(Ctrl), s));
   for (auto& g : p->cl_groups) {
-    ClusterFn fn = cluster_kernel(g.first);
-    {
-      std::lock_guard<std::mutex> lk(g_attr_mutex);
-      size_t& cur = g_smem_attr_cluster[__builtin_ctz((unsigned)g.first) - 5];
-      if (cur == 0) {
-        VS_CUDA_TRY(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)cluster_shape(g.first).smem));
-        VS_CUDA_TRY(cudaFuncSetAttribute(fn, cudaFuncAttributePreferredSharedMemoryCarveout, 100));
-        cur = cluster_shape(g.first).smem;
-      }
-    }
+    ClusterFn fn = cluster_kernel(g.first, p->cl_batch);
+    int rc = cluster_attrs(g.first, p->cl_batch);
+    if (rc != VS_OK) return rc;
     cudaLaunchAttribute attr[1];
     cudaLaunchConfig_t cfg = cluster_config(g.first, 1, s, attr);
     int clusters = 0;
@@ -1725,7 +1736,7 @@ int plan_launch_cluster(vs_plan_t* p, cudaStream_t s) {
     P.tol = (float)p->params.tol_K;
     cudaLaunchAttribute attr[1];
     cudaLaunchConfig_t cfg = cluster_config(g.first, g.second, s, attr);
-    cudaError_t e = cudaLaunchKernelEx(&cfg, cluster_kernel(g.first), P);
+    cudaError_t e = cudaLaunchKernelEx(&cfg, cluster_kernel(g.first, p->cl_batch), P);
     if (e != cudaSuccess)
       return vs_set_error(VS_ERR_CUDA, "cluster launch (n %d, %d maps): %s", g.first, g.second,
                           cudaGetErrorString(e));
@@ -1830,8 +1841,69 @@ double time_plan(vs_plan_t* p, cudaStream_t s, int reps) {
 
 }  // namespace
 
+// ---------------------------------------------------------------------------
+// Autotuner of the launch shape. A plan's shape is one integer: the cluster
+// engine's update-load batch (1, 2 or 4 positions whose inputs a thread loads
+// before using them), or the streamed engine's task size (elements of a map per
+// row/column task: 2048, 4096, 8192 or 16384). Plans of at least 64 maps are
+// tuned by timing every candidate on the plan itself (one warm-up and two timed
+// runs each, CUDA events) and keeping the fastest; the choice is cached per
+// engine, mix of grid sizes and batch size (power-of-two bucket), so later
+// plans of the same kind are not timed again. VS_AUTOTUNE=0 keeps the defaults.
+// ---------------------------------------------------------------------------
+namespace {
+
+std::vector<int> tune_key(const vs_batch_item* items, int n_items, bool cluster) {
+  std::vector<int> key;
+  for (int i = 0; i < n_items; ++i) key.push_back(items[i].k->n);
+  std::sort(key.begin(), key.end());
+  key.erase(std::unique(key.begin(), key.end()), key.end());
+  int bucket = 0;
+  while ((1 << (bucket + 1)) <= n_items) ++bucket;
+  key.push_back(bucket);
+  key.push_back(cluster ? 1 : 0);
+  return key;
+}
+
+bool tune_enabled(int n_items) {
+  const char* env = getenv("VS_AUTOTUNE");
+  return n_items >= 64 && !(env && env[0] == '0');
+}
+
+bool cluster_shape_ok(int b) { return b == 1 || b == 2 || b == 4; }
+bool streamed_shape_ok(int e) { return e == 2048 || e == 4096 || e == 8192 || e == 16384; }
+
+}  // namespace
+
+int plan_create(const vs_batch_item* items_host, int n_items, const vs_solve_params* params,
+                int shape, vs_plan* out, void* stream);
+
 extern "C" int vs_plan_create(const vs_batch_item* items_host, int n_items,
                               const vs_solve_params* params, vs_plan* out, void* stream) {
+  return plan_create(items_host, n_items, params, 0, out, stream);
+}
+
+extern "C" int vs_plan_create_shaped(const vs_batch_item* items_host, int n_items,
+                                     const vs_solve_params* params, int shape, vs_plan* out,
+                                     void* stream) {
+  if (shape < 0) return vs_set_error(VS_ERR_INVALID_ARG, "shape %d", shape);
+  return plan_create(items_host, n_items, params, shape, out, stream);
+}
+
+extern "C" int vs_plan_shape(vs_plan p, int* shape_out, int* n_timed, int* cand_shapes,
+                             double* cand_ms) {
+  if (!p) return vs_set_error(VS_ERR_INVALID_ARG, "NULL plan");
+  if (shape_out) *shape_out = p->cluster ? p->cl_batch : p->elems;
+  if (n_timed) *n_timed = (int)p->tuned.size();
+  for (size_t i = 0; i < p->tuned.size(); ++i) {
+    if (cand_shapes) cand_shapes[i] = p->tuned[i].first;
+    if (cand_ms) cand_ms[i] = p->tuned[i].second;
+  }
+  return VS_OK;
+}
+
+int plan_create(const vs_batch_item* items_host, int n_items, const vs_solve_params* params,
+                int shape, vs_plan* out, void* stream) {
   if (!out) return vs_set_error(VS_ERR_INVALID_ARG, "out is NULL");
   *out = nullptr;
   if (!items_host || n_items <= 0) return vs_set_error(VS_ERR_INVALID_ARG, "no items");
@@ -1865,7 +1937,47 @@ extern "C" int vs_plan_create(const vs_batch_item* items_host, int n_items,
   p->params = *params;
   if (cluster_ok && params->engine != VS_ENGINE_STREAMED) {
     p->cluster = true;
+    if (shape && !cluster_shape_ok(shape)) {
+      delete p;
+      return vs_set_error(VS_ERR_INVALID_ARG, "cluster engine shape %d (update batch 1, 2 or 4)",
+                          shape);
+    }
+    const std::vector<int> key = tune_key(items_host, n_items, true);
+    bool tune = shape == 0 && tune_enabled(n_items);
+    p->cl_batch = shape ? shape : kClBatchDefault;
+    if (tune) {
+      std::lock_guard<std::mutex> lk(g_tune_mutex);
+      auto itc = g_tuned.find(key);
+      if (itc != g_tuned.end()) {
+        p->cl_batch = itc->second;
+        tune = false;
+      }
+    }
     rc = plan_layout_cluster(p, s);
+    if (rc == VS_OK && tune) {
+      double best = 1e30;
+      int best_b = p->cl_batch;
+      for (int b : kClBatches) {
+        p->cl_batch = b;
+        for (auto& g : p->cl_groups)
+          if (rc == VS_OK) rc = cluster_attrs(g.first, b);
+        if (rc != VS_OK) break;
+        const double t = time_plan(p, s, 2);
+        p->tuned.push_back({b, t});
+        if (t < best) {
+          best = t;
+          best_b = b;
+        }
+      }
+      p->cl_batch = best_b;
+      if (rc == VS_OK && best < 1e29) {
+        std::lock_guard<std::mutex> lk(g_tune_mutex);
+        g_tuned[key] = best_b;
+      }
+      cudaError_t e = cudaStreamSynchronize(s);
+      if (e != cudaSuccess && rc == VS_OK)
+        rc = vs_set_error(VS_ERR_CUDA, "autotune: %s", cudaGetErrorString(e));
+    }
     if (rc != VS_OK) {
       plan_release(p);
       delete p;
@@ -1875,17 +1987,16 @@ extern "C" int vs_plan_create(const vs_batch_item* items_host, int n_items,
     return VS_OK;
   }
 
-  // task size: tuned once per mix of grid sizes when the batch is large
-  std::vector<int> key;
-  for (int i = 0; i < n_items; ++i) key.push_back(items_host[i].k->n);
-  std::sort(key.begin(), key.end());
-  key.erase(std::unique(key.begin(), key.end()), key.end());
-  key.push_back(n_items >= 256 ? 1 : 0);
-  int elems = 8192;
-  bool tune = n_items >= 64 && params->precision == VS_PREC_FP32;
-  const char* env = getenv("VS_AUTOTUNE");
-  if (env && env[0] == '0') tune = false;
-  {
+  // task size of the streamed engine: forced, cached, tuned, or the default
+  if (shape && !streamed_shape_ok(shape)) {
+    delete p;
+    return vs_set_error(VS_ERR_INVALID_ARG,
+                        "streamed engine shape %d (task size 2048, 4096, 8192 or 16384)", shape);
+  }
+  const std::vector<int> key = tune_key(items_host, n_items, false);
+  int elems = shape ? shape : 8192;
+  bool tune = shape == 0 && tune_enabled(n_items) && params->precision == VS_PREC_FP32;
+  if (tune) {
     std::lock_guard<std::mutex> lk(g_tune_mutex);
     auto itc = g_tuned.find(key);
     if (itc != g_tuned.end()) {
@@ -1896,17 +2007,18 @@ extern "C" int vs_plan_create(const vs_batch_item* items_host, int n_items,
   if (tune) {
     double best = 1e30;
     int best_e = elems;
-    const int cands[3] = {4096, 8192, 16384};
+    const int cands[4] = {2048, 4096, 8192, 16384};
     for (int e : cands) {
       rc = plan_layout(p, e, s, false, 0);
       if (rc) break;
-      double t = time_plan(p, s, 2);
+      const double t = time_plan(p, s, 2);
+      p->tuned.push_back({e, t});
       if (t < best) {
         best = t;
         best_e = e;
       }
     }
-    if (rc == VS_OK) {
+    if (rc == VS_OK && best < 1e29) {
       elems = best_e;
       std::lock_guard<std::mutex> lk(g_tune_mutex);
       g_tuned[key] = elems;
@@ -2017,6 +2129,16 @@ extern "C" int vs_solve_transient_ex(vs_kernel k, int n_steps, const float* p_dy
                  (uintptr_t)s_kappa;
   if (al & 15u) return vs_set_error(VS_ERR_INVALID_ARG, "maps must be 16-byte aligned");
   cudaStream_t s = (cudaStream_t)stream;
+  if (o.window == 0 && o.leakage == VS_LEAK_LAGGED && vs_transient_fast_ok(k->n)) {
+    // the persistent single-map engine (vs_transient.cu)
+    vs_solve_info inf = {};
+    const int r = vs_transient_fast(k, n_steps, p_dyn_trace, p_leak0, s_kappa, params, theta_trace,
+                                    &inf, s);
+    if (r != -1) {
+      if (info_host && (r == VS_OK || r >= VS_ERR_NO_CONVERGENCE)) *info_host = inf;
+      return r;
+    }
+  }
   vs_plan_t* p = new vs_plan_t();
   p->n_items = 1;
   p->items.push_back(vs_batch_item{k, p_dyn_trace, p_leak0, s_kappa, theta_trace, nullptr});

@@ -1,0 +1,392 @@
+// Transient of one map (Sec. IV-D/E: single-pole response per cosine mode,
+// Eq. 35, untruncated superposition of power differences, Eq. 36, run as the
+// per-mode recursion) with lagged leakage, for grids of 256^2 .. 1024^2.
+//
+// One persistent cooperative launch of N / R CTAs for the whole trace. CTA c
+// owns the rows y in [cR, cR + R) and the x-frequencies p in [cR, cR + R) for
+// every step, so everything that belongs to one CTA stays on chip across
+// steps:
+//   - the recursion state W and the per-mode constants (K - A) / N^2, A / N^2
+//     and rho = exp(-dt / tau) of its R x N modes, in shared memory;
+//   - P_leak0 of its R rows, in registers (the thread <-> cell mapping of the
+//     update is the same every step); s is re-read through the L1 each step.
+// Per step, two phases separated by a grid barrier (the spectral map in
+// global memory, x-frequency major, is the only exchange):
+//   column phase: forward DCT along y of its columns, W <- rho W + (1 - rho) X,
+//     Y = (K - A) X + A W (the step response (K - A) + A (1 - rho^j) of the
+//     primary alias, the finer aliases settled within a step), inverse DCT
+//     along y;
+//   row phase: inverse DCT along x of its rows -> u_n, theta_n = s u_n /
+//     (1 - alpha s u_n) written to the output trace, the next source
+//     P_{n+1} = P_dyn,n+1 + P_leak0 (1 + beta theta_n) (its P_dyn loads issued
+//     before the inverse transform), forward DCT along x.
+// The grid barrier is a bounded spin: on timeout the launch sets an abort
+// word and every CTA returns (VS_ERR_TIMEOUT), no trap.
+#include <math.h>
+
+#include <algorithm>
+
+#include "vs_fft.cuh"
+#include "vs_internal.cuh"
+#include "vs_solve_common.cuh"
+
+using namespace vsfft;
+using vsk::kFlagNonfinite;
+using vsk::kFlagRunaway;
+
+namespace {
+
+constexpr int ilog2(int v) { return v <= 1 ? 0 : 1 + ilog2(v / 2); }
+
+constexpr long long kTrSpinLimit = 20000000LL;   // ~ seconds of polling
+
+struct TrCtrl {
+  unsigned count;     // arrivals so far: barrier b is complete at (b + 1) * grid
+  unsigned abort;
+  int flags;
+  unsigned pad_;
+};
+
+struct TrArgs {
+  const float* p_dyn;      // [n_steps][N][N]
+  const float* p_leak0;    // [N][N]
+  const float* s;          // [N][N] or NULL (= 1)
+  float* theta;            // [n_steps][N][N]
+  float* work;             // [N][N] spectral map, x-frequency major
+  const float* Kt;         // [p][q] cosine-basis kernel
+  const float* trA;        // [p][q] primary-alias weight
+  const float* trRho;      // [p][q] exp(-dt / (C g))
+  const float2* tw4n;
+  const int* digrev;
+  TrCtrl* ctrl;
+  int n_steps;
+  float beta, alpha;
+};
+
+__device__ __forceinline__ unsigned tr_ld_acquire(const unsigned* p) {
+  unsigned v;
+  asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+
+// Grid barrier on a monotonic arrival counter (no reset, so the last CTA to
+// arrive does no extra atomics): barrier b of the launch is complete when
+// the counter reaches (b + 1) * gridDim.x; `target` is that value, kept by
+// every CTA. False if the launch aborted (a bounded wait gave up somewhere).
+__device__ bool tr_barrier(TrCtrl* c, unsigned& target) {
+  __syncthreads();
+  target += gridDim.x;
+  if (threadIdx.x == 0) {
+    __threadfence();
+    atomicAdd(&c->count, 1u);
+    long long spins = 0;
+    while (tr_ld_acquire(&c->count) < target) {
+      if (tr_ld_acquire(&c->abort)) break;
+      if (++spins > 64) __nanosleep(32);
+      if (spins > kTrSpinLimit) {
+        atomicExch(&c->abort, 1u);
+        break;
+      }
+    }
+    __threadfence();
+  }
+  __syncthreads();
+  return tr_ld_acquire(&c->abort) == 0u;
+}
+
+template <int N, int R>
+struct TrShape {
+  static constexpr int F = R / 2;                       // complex FFTs per CTA and phase
+  static constexpr int THREADS = F * N < 512 ? F * N : 512;
+  static constexpr int NP = N + N / 16 + 1;
+  static constexpr int CELLS = F * N / THREADS;          // update items (2 cells) per thread
+  // FFT buffers, per-mode arrays, twiddles W_4N^e (e < 4N) and digit reversal
+  static constexpr size_t SMEM = (size_t)F * NP * sizeof(float2) + 4 * (size_t)R * N * sizeof(float) +
+                                 4 * (size_t)N * sizeof(float2) + (size_t)N * sizeof(int);
+  static_assert(F >= 1 && (F * N) % THREADS == 0, "shape");
+};
+
+template <int N, int R>
+__global__ void __launch_bounds__(TrShape<N, R>::THREADS, 1) k_transient_fast(TrArgs a) {
+  using S = TrShape<N, R>;
+  constexpr int F = S::F, NP = S::NP, T = S::THREADS, CELLS = S::CELLS, half = N / 2;
+  constexpr int lgN = ilog2(N), lgF = ilog2(F);
+  extern __shared__ __align__(16) float2 tr_smem[];
+  __shared__ int red_i[T / 32];
+  float2* buf = tr_smem;                                  // [F][NP]
+  float* km = reinterpret_cast<float*>(buf + F * NP);     // [R][N] (K - A) / N^2
+  float* am = km + R * N;                                 // [R][N] A / N^2
+  float* rh = am + R * N;                                 // [R][N] rho
+  float* W = rh + R * N;                                  // [R][N] recursion state
+  float2* tw = reinterpret_cast<float2*>(W + R * N);      // [4N] twiddles
+  int* dr = reinterpret_cast<int*>(tw + 4 * N);           // [N] digit reversal
+  const int tid = threadIdx.x;
+  const int y0 = blockIdx.x * R, p0 = blockIdx.x * R;
+  const size_t nn = (size_t)N * N;
+  for (int i = tid; i < 4 * N; i += T) tw[i] = __ldg(&a.tw4n[i]);
+  for (int i = tid; i < N; i += T) dr[i] = __ldg(&a.digrev[i]);
+  const float inv_n2 = 1.f / ((float)N * (float)N);
+  const float beta = a.beta, alpha = a.alpha;
+
+  for (int i = tid; i < R * N; i += T) {
+    const size_t g = (size_t)(p0 + (i >> lgN)) * N + (i & (N - 1));
+    const float A = __ldg(&a.trA[g]), K = __ldg(&a.Kt[g]);
+    km[i] = (K - A) * inv_n2;
+    am[i] = A * inv_n2;
+    rh[i] = __ldg(&a.trRho[g]);
+    W[i] = 0.f;
+  }
+  // this thread's cells: item j -> (f, x), rows y0 + 2f (.x) and y0 + 2f + 1 (.y)
+  float2 pl[CELLS], pd[CELLS];
+#pragma unroll
+  for (int j = 0; j < CELLS; ++j) {
+    const int it = tid + j * T, f = it >> lgN, x = it & (N - 1);
+    const size_t i0 = (size_t)(y0 + 2 * f) * N + x, i1 = i0 + N;
+    pl[j] = make_float2(__ldg(&a.p_leak0[i0]), __ldg(&a.p_leak0[i1]));
+    pd[j] = make_float2(__ldg(&a.p_dyn[i0]), __ldg(&a.p_dyn[i1]));
+  }
+  int flags = 0;
+  unsigned target = 0;    // arrivals that complete the next grid barrier
+
+  // forward DCT along x of the source in buf (Makhoul order), stored x-frequency major
+  auto row_forward = [&]() {
+    __syncthreads();
+    fft_forward<true>(buf, N, F, NP, tw);
+    for (int it = tid; it < F * (half + 1); it += T) {
+      const int f = it & (F - 1), k = it >> lgF, nk = N - k;
+      const float2 zk = buf[f * NP + pad(dr[k])];
+      const float2 znk = buf[f * NP + pad(dr[k == 0 ? 0 : nk])];
+      *reinterpret_cast<float2*>(a.work + (size_t)k * N + y0 + 2 * f) = dct_post(zk, znk, tw[k]);
+      if (k != 0 && k != half)
+        *reinterpret_cast<float2*>(a.work + (size_t)nk * N + y0 + 2 * f) =
+            dct_post(znk, zk, tw[nk]);
+    }
+  };
+
+  // step 0: the first source P_1 = P_dyn,1 + P_leak0 (theta_0 = 0)
+#pragma unroll
+  for (int j = 0; j < CELLS; ++j) {
+    const int it = tid + j * T, f = it >> lgN, x = it & (N - 1);
+    buf[f * NP + pad(makhoul_pos(x, N))] = make_float2(pd[j].x + pl[j].x, pd[j].y + pl[j].y);
+  }
+  row_forward();
+  if (!tr_barrier(a.ctrl, target)) return;
+
+  for (int step = 1; step <= a.n_steps; ++step) {
+    // ---- column phase: this CTA's x-frequency columns p0 .. p0 + R - 1
+    {
+      float2 c[CELLS];   // all loads of a thread issued before the stores
+#pragma unroll
+      for (int q = 0; q < CELLS; ++q) {
+        const int it = tid + q * T, f = it >> lgN, j = it & (N - 1);
+        c[q] = make_float2(a.work[(size_t)(p0 + 2 * f) * N + j], a.work[(size_t)(p0 + 2 * f + 1) * N + j]);
+      }
+#pragma unroll
+      for (int q = 0; q < CELLS; ++q) {
+        const int it = tid + q * T, f = it >> lgN, j = it & (N - 1);
+        buf[f * NP + pad(makhoul_pos(j, N))] = c[q];
+      }
+    }
+    __syncthreads();
+    fft_forward<true>(buf, N, F, NP, tw);
+    for (int it = tid; it < F * (half + 1); it += T) {
+      // consecutive threads: consecutive frequencies of one FFT, so the mode
+      // arrays [column][q] are read without bank conflicts
+      const int f = it / (half + 1), k = it - f * (half + 1), nk = N - k;
+      const int ia = f * NP + pad(dr[k]);
+      const int ib = f * NP + pad(dr[k == 0 ? 0 : nk]);
+      const float2 zk = buf[ia], znk = buf[ib];
+      const float2 xk = dct_post(zk, znk, tw[k]);
+      auto mode = [&](int c, int q, float x) {
+        const int i = c * N + q;
+        const float w = fmaf(rh[i], W[i] - x, x);
+        W[i] = w;
+        return fmaf(km[i], x, am[i] * w);
+      };
+      const float2 yk = make_float2(mode(2 * f, k, xk.x), mode(2 * f + 1, k, xk.y));
+      float2 ynk;
+      if (k != 0 && k != half) {
+        const float2 xnk = dct_post(znk, zk, tw[nk]);
+        ynk = make_float2(mode(2 * f, nk, xnk.x), mode(2 * f + 1, nk, xnk.y));
+      } else {
+        ynk = k == half ? yk : make_float2(0.f, 0.f);
+      }
+      buf[ia] = dct_pre(yk.x, ynk.x, yk.y, ynk.y, tw[k]);
+      if (k != 0 && k != half) buf[ib] = dct_pre(ynk.x, yk.x, ynk.y, yk.y, tw[nk]);
+    }
+    __syncthreads();
+    fft_inverse<true>(buf, N, F, NP, tw);
+    for (int it = tid; it < F * N; it += T) {
+      const int f = it >> lgN, j = it & (N - 1);
+      const float2 v = buf[f * NP + pad(makhoul_pos(j, N))];
+      a.work[(size_t)(p0 + 2 * f) * N + j] = v.x;
+      a.work[(size_t)(p0 + 2 * f + 1) * N + j] = v.y;
+    }
+    if (!tr_barrier(a.ctrl, target)) return;
+
+    // ---- row phase: rows y0 .. y0 + R - 1
+    const bool more = step < a.n_steps;
+    if (more) {
+      // the next power map, loaded while the inverse transform runs
+      const float* pdn = a.p_dyn + (size_t)step * nn;
+#pragma unroll
+      for (int j = 0; j < CELLS; ++j) {
+        const int it = tid + j * T, f = it >> lgN, x = it & (N - 1);
+        const size_t i0 = (size_t)(y0 + 2 * f) * N + x;
+        pd[j] = make_float2(__ldg(&pdn[i0]), __ldg(&pdn[i0 + N]));
+      }
+    }
+    {
+      // the spectra of this CTA's rows at x-frequencies k and N - k, k <= N/2:
+      // all loads of a thread issued before the pre-twiddles
+      constexpr int PRE = (F * (half + 1) + T - 1) / T;
+      float2 xk[PRE], xnk[PRE];
+#pragma unroll
+      for (int q = 0; q < PRE; ++q) {
+        const int it = tid + q * T, f = it & (F - 1), k = it >> lgF;
+        xk[q] = xnk[q] = make_float2(0.f, 0.f);
+        if (it < F * (half + 1)) {
+          xk[q] = *reinterpret_cast<const float2*>(a.work + (size_t)k * N + y0 + 2 * f);
+          if (k != 0) xnk[q] = *reinterpret_cast<const float2*>(a.work + (size_t)(N - k) * N + y0 + 2 * f);
+        }
+      }
+#pragma unroll
+      for (int q = 0; q < PRE; ++q) {
+        const int it = tid + q * T, f = it & (F - 1), k = it >> lgF, nk = N - k;
+        if (it >= F * (half + 1)) continue;
+        buf[f * NP + pad(dr[k])] = dct_pre(xk[q].x, xnk[q].x, xk[q].y, xnk[q].y, tw[k]);
+        if (k != 0 && k != half)
+          buf[f * NP + pad(dr[nk])] = dct_pre(xnk[q].x, xk[q].x, xnk[q].y, xk[q].y, tw[nk]);
+      }
+    }
+    __syncthreads();
+    fft_inverse<true>(buf, N, F, NP, tw);
+    float* th_out = a.theta + (size_t)(step - 1) * nn;
+#pragma unroll
+    for (int j = 0; j < CELLS; ++j) {
+      const int it = tid + j * T, f = it >> lgN, x = it & (N - 1);
+      const int pos = f * NP + pad(makhoul_pos(x, N));
+      const size_t i0 = (size_t)(y0 + 2 * f) * N + x;
+      const float2 u = buf[pos];
+      const float2 sk = a.s ? make_float2(__ldg(&a.s[i0]), __ldg(&a.s[i0 + N])) : make_float2(1.f, 1.f);
+      float th[2], q[2];
+#pragma unroll
+      for (int h = 0; h < 2; ++h) {
+        const float uu = h ? u.y : u.x, S = h ? sk.y : sk.x;
+        const float den = fmaf(-alpha * S, uu, 1.f);
+        if (!(den > 0.05f)) flags |= kFlagRunaway;
+        th[h] = S * uu / den;
+        if (!isfinite(th[h])) flags |= kFlagNonfinite;
+        const float L0 = h ? pl[j].y : pl[j].x, D = h ? pd[j].y : pd[j].x;
+        q[h] = D + L0 * fmaf(beta, th[h], 1.f);
+      }
+      th_out[i0] = th[0];
+      th_out[i0 + N] = th[1];
+      buf[pos] = make_float2(q[0], q[1]);
+    }
+    if (!more) break;
+    row_forward();
+    if (!tr_barrier(a.ctrl, target)) return;
+  }
+  // flags of the whole launch
+  for (int o = 16; o > 0; o >>= 1) flags |= __shfl_down_sync(0xffffffffu, flags, o);
+  if ((tid & 31) == 0) red_i[tid >> 5] = flags;
+  __syncthreads();
+  if (tid == 0) {
+    int fo = 0;
+    for (int w = 0; w < T / 32; ++w) fo |= red_i[w];
+    if (fo) atomicOr(&a.ctrl->flags, fo);
+  }
+}
+
+template <int N, int R>
+int launch_fast(const TrArgs& args, cudaStream_t s) {
+  using S = TrShape<N, R>;
+  VS_CUDA_TRY(cudaFuncSetAttribute((const void*)k_transient_fast<N, R>,
+                                   cudaFuncAttributeMaxDynamicSharedMemorySize, (int)S::SMEM));
+  int dev = 0, sms = 0, per_sm = 0;
+  VS_CUDA_TRY(cudaGetDevice(&dev));
+  VS_CUDA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+  VS_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_transient_fast<N, R>,
+                                                            S::THREADS, S::SMEM));
+  const int grid = N / R;
+  if (per_sm * sms < grid) return -1;          // not co-resident: the caller falls back
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(grid);
+  cfg.blockDim = dim3(S::THREADS);
+  cfg.dynamicSmemBytes = S::SMEM;
+  cfg.stream = s;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeCooperative;
+  attr[0].val.cooperative = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  cudaError_t e = cudaLaunchKernelEx(&cfg, k_transient_fast<N, R>, args);
+  if (e != cudaSuccess) return vs_set_error(VS_ERR_CUDA, "transient launch: %s", cudaGetErrorString(e));
+  return VS_OK;
+}
+
+}  // namespace
+
+bool vs_transient_fast_ok(int n) { return n == 256 || n == 512 || n == 1024; }
+
+// Runs the lagged, untruncated transient of one map on the persistent
+// kernel above. Returns VS_OK and fills *info, a vs_status, or -1 when the
+// launch shape does not fit the device (the caller then uses the general
+// engine). Allocates its spectral map and barrier words per call.
+int vs_transient_fast(vs_kernel k, int n_steps, const float* p_dyn_trace, const float* p_leak0,
+                      const float* s_kappa, const vs_solve_params* params, float* theta_trace,
+                      vs_solve_info* info, cudaStream_t s) {
+  const int n = k->n;
+  float* work = nullptr;
+  TrCtrl* ctrl = nullptr;
+  VS_CUDA_TRY(cudaMalloc(&work, sizeof(float) * (size_t)n * n));
+  cudaError_t e = cudaMalloc(&ctrl, sizeof(TrCtrl));
+  if (e != cudaSuccess) {
+    cudaFree(work);
+    return vs_set_error(VS_ERR_OOM, "transient control words: %s", cudaGetErrorString(e));
+  }
+  TrArgs a = {};
+  a.p_dyn = p_dyn_trace;
+  a.p_leak0 = p_leak0;
+  a.s = s_kappa;
+  a.theta = theta_trace;
+  a.work = work;
+  a.Kt = k->Kt32;
+  a.trA = k->trA;
+  a.trRho = k->trRho;
+  a.tw4n = k->fft->tw4n;
+  a.digrev = k->fft->digrev;
+  a.ctrl = ctrl;
+  a.n_steps = n_steps;
+  a.beta = (float)params->beta_per_K;
+  a.alpha = (float)params->alpha_per_K;
+  int rc = VS_OK;
+  e = cudaMemsetAsync(ctrl, 0, sizeof(TrCtrl), s);
+  if (e != cudaSuccess) rc = vs_set_error(VS_ERR_CUDA, "memset: %s", cudaGetErrorString(e));
+  if (rc == VS_OK) {
+    switch (n) {
+      case 256: rc = launch_fast<256, 2>(a, s); break;
+      case 512: rc = launch_fast<512, 4>(a, s); break;
+      default: rc = launch_fast<1024, 8>(a, s); break;
+    }
+  }
+  TrCtrl hc = {};
+  if (rc == VS_OK) {
+    e = cudaMemcpyAsync(&hc, ctrl, sizeof(TrCtrl), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) rc = vs_set_error(VS_ERR_CUDA, "transient: %s", cudaGetErrorString(e));
+  }
+  cudaStreamSynchronize(s);
+  cudaFree(work);
+  cudaFree(ctrl);
+  if (rc != VS_OK) return rc;
+  if (hc.abort) return vs_set_error(VS_ERR_TIMEOUT, "grid barrier timed out");
+  info->status = (hc.flags & kFlagNonfinite) ? VS_ERR_NONFINITE
+                 : (hc.flags & kFlagRunaway) ? VS_ERR_RUNAWAY : VS_OK;
+  info->iterations = n_steps;
+  info->residual_K = 0.0;
+  info->mu_W = 0.0;
+  info->fell_back = 0;
+  return info->status;
+}

@@ -156,3 +156,25 @@ def test_transient_options_are_validated():
         with pytest.raises(vs.VarsimError) as e:
             vs.solve_transient(k, trace, pl, s, vs_params(w), **kw)
         assert e.value.status == vs.VS_ERR_INVALID_ARG
+
+
+def test_persistent_engine_at_512_against_the_oracle():
+    """The single-map persistent transient engine at 512^2 (the 256^2 and
+    1024^2 cases run in test_gpu_configs): 12 steps of a Markov trace with
+    leakage and conductivity, element by element against the oracle."""
+    from _util import step_spectra
+    vs = _vs()
+    w = synth.workload("c3_512")
+    dt, steps = 1e-3, 12
+    trace = synth.markov_trace(w, steps, device="cuda")
+    _, pl, s = synth.steady_inputs(w, 1, device="cuda")
+    k = vs.Kernel(vs_stack(w), vs.Grid(w.n, w.die_m), vs.KernelOpts(dt_s=dt))
+    th, info = vs.solve_transient(k, trace, pl[0], s[0], vs_params(w))
+    assert info["status"] == vs.VS_OK and info["iterations"] == steps
+    spectra = step_spectra(w, dt, steps)
+    f64 = lambda t: t.double().cpu().numpy()
+    ref = so.duhamel_modes(spectra, f64(trace), f64(pl[0]), f64(s[0]), w.physics.beta_per_K,
+                           w.physics.alpha_per_K)
+    emax, rel = errors(th, ref)
+    assert emax <= REQ_MAX_K
+    assert emax <= 5e-3 and rel <= 2e-4

@@ -78,13 +78,33 @@ def _dataset(vs, k, w, count, first, prm_cold, prm_one, R):
     return pd, pl, s, ths, th1, x, t
 
 
-def test_warm_start_pipeline_on_the_bench_maps():
-    # The cold start of the FP32 engines begins at the uniform-mode temperature
-    # of each die, so their first iterate is already close to the fixed point
-    # and little correction is left for the network. This checks the pipeline:
-    # the network trains on (first iterate -> converged map) pairs, the warm
-    # plan reaches the same fixed point, and it costs at most about the one
-    # iteration its first-iterate plan adds.
+def _events_ms(fn, reps=5):
+    st = torch.cuda.current_stream()
+    fn()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(st)
+    for _ in range(reps):
+        fn()
+    e1.record(st)
+    torch.cuda.synchronize()
+    return e0.elapsed_time(e1) / reps
+
+
+def test_warm_start_gain_on_held_out_maps():
+    """What the learned warm start gains over the cold solve on held-out maps of
+    the bench workload (256^2), measured, at the 1e-2 K tolerance:
+
+    * both reach the fixed point within the metric's 0.05 K;
+    * the network's start is closer to the fixed point than the first iterate
+      it corrects (measured: 0.043 K against 0.050 K mean error);
+    * it saves no iteration: the cold FP32 engines start from the die's
+      uniform-mode temperature, so the first iterate is already within about
+      0.1 K and the remaining iterations are set by the contraction (measured
+      3.04 with the first-iterate plan against 3.00 cold);
+    * so end to end it is slower than the cold solve (measured about 8x: the
+      first-iterate plan and the network cost more than nothing saved).
+    This asserts that measured outcome; the design notes record the numbers."""
     import paper_2307_12119_gb300 as vs
     w = synth.batch_workload(256, 2048)
     k = vs.Kernel(vs_stack(w), vs.Grid(w.n, w.die_m))
@@ -100,24 +120,31 @@ def test_warm_start_pipeline_on_the_bench_maps():
     l1, _ = m.loss_grad(x[:256].contiguous(), t[:256].contiguous())
     assert np.isfinite(loss) and l1 < l0
     # held-out maps
-    pd, pl, s, ths, th1, xv, tv = _dataset(vs, k, w, 256, 100000, tight, one, R)
+    B = 256
+    pd, pl, s, ths, th1, xv, tv = _dataset(vs, k, w, B, 100000, tight, one, R)
     th_w = torch.empty_like(pd)
     wp = vs.WarmPlan(k, pd, pl, s, th_w, m, prm)
     wp.run()
     iw = wp.info()
     assert all(i["status"] == vs.VS_OK for i in iw)
     th_c = torch.empty_like(pd)
-    ic = vs.solve_batch([(k, pd[i], pl[i], s[i], th_c[i]) for i in range(256)], prm)
-    assert float((th_w - ths).abs().max()) <= 2 * tol
-    assert float((th_c - ths).abs().max()) <= 2 * tol
+    cold = vs.Plan([(k, pd[i], pl[i], s[i], th_c[i]) for i in range(B)], prm)
+    cold.run()
+    ic = cold.info()
+    assert all(i["status"] == vs.VS_OK for i in ic)
+    assert float((th_w - ths).abs().max()) <= 0.05 and float((th_c - ths).abs().max()) <= 0.05
     init_err = float((wp.theta_init - ths).abs().mean())
     first_err = float((th1 - ths).abs().mean())
     cold_it = np.mean([i["iterations"] for i in ic])
     warm_it = 1 + np.mean([i["iterations"] for i in iw])     # + the first-iterate plan
-    print("warm start: cold %.2f iterations, warm %.2f (incl. first iterate); "
-          "mean |theta_init - theta*| %.4f K vs |theta_1 - theta*| %.4f K"
-          % (cold_it, warm_it, init_err, first_err))
-    assert warm_it <= cold_it + 1.5
+    t_cold = _events_ms(cold.run)
+    t_warm = _events_ms(wp.run)
+    print("warm start: cold %.2f iterations %.3f ms, warm %.2f (incl. first iterate) %.3f ms "
+          "(%.1fx slower); mean |theta_init - theta*| %.4f K vs |theta_1 - theta*| %.4f K"
+          % (cold_it, t_cold, warm_it, t_warm, t_warm / t_cold, init_err, first_err))
+    assert init_err < first_err                  # the network improves the start
+    assert abs(warm_it - cold_it) <= 0.5         # but saves no iteration
+    assert t_warm > t_cold                       # and costs throughput
 
 
 def test_bad_warm_start_falls_back_to_cold_solve():
@@ -140,5 +167,6 @@ def test_bad_warm_start_falls_back_to_cold_solve():
     infos = wp.info(fallback=True)
     assert all(i["status"] == vs.VS_OK for i in infos)
     assert wp.fallbacks == 2
+    assert all(i["fell_back"] for i in infos)        # vs_solve_info.fell_back
     ref, _ = vs.solve_steady(k, pd[0], pl[0], s[0], vs_params(w))
     assert float((th[0] - ref).abs().max()) <= 1e-3
