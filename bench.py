@@ -128,6 +128,8 @@ KERNEL_SOURCES = {
     "k_cf_cols": [_CSRC + "vs_closed.cu"] + _COMMON,
     "k_cf_rows_inv": [_CSRC + "vs_closed.cu"] + _COMMON,
     "k_conv_fwd": [_CSRC + "vs_cnn.cu"] + _COMMON,
+    "k_solve_tcc": [_CSRC + "vs_tcc.cu", _CSRC + "vs_tc.cuh", _CSRC + "vs_internal.cuh"] + _COMMON,
+    "k_transient_fast": [_CSRC + "vs_transient.cu", _CSRC + "vs_internal.cuh"] + _COMMON,
 }
 TRAFFIC_JSON = os.path.join(ROOT, "profiles", "traffic.json")
 
@@ -529,9 +531,10 @@ def _train_warm_model(vs, synth, k, w, dev, n_train, epochs, seed_base, stream):
                "train_s": round(time.perf_counter() - t1, 2)}
 
 
-ALL_VARIANTS = ("fp32_cluster_cold", "fp32_streamed_cold", "bf16_split_cold", "fp32_learned_warm",
-                "bf16_split_learned_warm", "fp32_cluster_tol1e-4", "fp32_streamed_tol1e-4")
-BATCHED = ALL_VARIANTS[:5]          # candidates for the headline (tolerance 1e-2 K)
+ALL_VARIANTS = ("fp32_cluster_cold", "fp32_streamed_cold", "bf16_split_cold",
+                "bf16_split_streamed_cold", "fp32_learned_warm", "bf16_split_learned_warm",
+                "fp32_cluster_tol1e-4", "fp32_streamed_tol1e-4")
+BATCHED = ALL_VARIANTS[:6]          # candidates for the headline (tolerance 1e-2 K)
 
 
 def run_ours(a):
@@ -581,7 +584,10 @@ def run_ours(a):
         # BF16 hi/lo split precision on tcgen05, with and without the learned warm start
         "bf16_split_learned_warm":
             lambda th: vs.WarmPlan(k, pd, pl, s, th, model, mk(vs.VS_PREC_BF16_SPLIT)),
+        # the on-chip pair engine (n = 256, cold) and the streamed tensor-core engine
         "bf16_split_cold": lambda th: vs.Plan(items(th), mk(vs.VS_PREC_BF16_SPLIT)),
+        "bf16_split_streamed_cold":
+            lambda th: vs.Plan(items(th), mk(vs.VS_PREC_BF16_SPLIT, eng=vs.VS_ENGINE_STREAMED)),
         # FP32 with the learned warm start (its plans take the automatic engine)
         "fp32_learned_warm": lambda th: vs.WarmPlan(k, pd, pl, s, th, model, mk(vs.VS_PREC_FP32)),
         # FP32 cold starts on both engines, at the headline tolerance and at 1e-4 K
@@ -597,6 +603,7 @@ def run_ours(a):
     # parameters of the variants that vs_solve_batch_host can run (cold starts)
     host_params = {
         "bf16_split_cold": mk(vs.VS_PREC_BF16_SPLIT),
+        "bf16_split_streamed_cold": mk(vs.VS_PREC_BF16_SPLIT, eng=vs.VS_ENGINE_STREAMED),
         "fp32_streamed_cold": mk(vs.VS_PREC_FP32, eng=vs.VS_ENGINE_STREAMED),
         "fp32_cluster_cold": mk(vs.VS_PREC_FP32, eng=vs.VS_ENGINE_CLUSTER),
     }
@@ -842,18 +849,31 @@ def run_ours(a):
                             "start; bench.fp32_flops_per_map). hbm_view: 16 B/pixel of "
                             "algorithmic bytes against the %s HBM copy rate" % hbm_kind}
 
-        def tc_roof(name, extra_iteration):
-            # per map and iteration 4 transform passes of 2 n^3 flops, x 3 split products
+        def tc_roof(name, extra_iteration, pair_engine):
             r = results[name]
+            sec = r["ms_per_step"] * 1e-3
             it = r["iterations_mean"] + (1.0 if extra_iteration else 0.0)
-            ach = B * it * 4 * 2 * w.n ** 3 * 3 / (r["ms_per_step"] * 1e-3) / 1e12
-            tr = _traffic_record("k_solve_steady_tc")
+            # the dense GEMM-DCT count: 4 passes x 2 n^3 x 3 split products per iteration
+            dense = B * it * 4 * 2 * w.n ** 3 * 3 / sec / 1e12
+            if pair_engine:
+                # executed MMA work of the on-chip pair engine: every transform is two
+                # half-size GEMMs (even/odd symmetry), (1 + 4 iterations) GEMM stages
+                # per solve (the first source's forward transform along x, then 4 per
+                # iteration), each 2 (e/o) x 2 (CTAs) x 2 (n/2)^3 x 3 products
+                ach = B * (1 + 4 * r["iterations_mean"]) * 2 * 2 * 2 * (w.n // 2) ** 3 * 3 / sec / 1e12
+                kern = "k_solve_tcc"
+                note = ("achieved = executed MMA flops (even/odd half-size GEMMs) / step time; "
+                        "dense_equivalent = maps x iterations x 4 passes x 2n^3 x 3 / step time; "
+                        "peak = measured bf16 sustained")
+            else:
+                ach, kern = dense, "k_solve_steady_tc"
+                note = ("achieved = maps x iterations x 4 passes x 2n^3 x 3 split products / step "
+                        "time; peak = measured bf16 sustained")
+            tr = _traffic_record(kern)
             return {"bound": "tensor", "achieved": ach, "peak": tc_peak, "unit": "TFLOP/s",
-                    "frac": ach / tc_peak,
+                    "frac": ach / tc_peak, "dense_equivalent": dense,
                     "traffic": (tr["dram_bytes_per_unit"] * B) if tr else None,
-                    "kernel": "k_solve_steady_tc",
-                    "note": "achieved = maps x iterations x 4 passes x 2n^3 x 3 split products "
-                            "/ step time; peak = measured bf16 sustained"}
+                    "kernel": kern, "note": note}
 
         roofs = {}
         if "fp32_cluster_cold" in results:
@@ -863,9 +883,11 @@ def run_ours(a):
         if "fp32_learned_warm" in results:
             roofs["fp32_learned_warm"] = alu_roof("fp32_learned_warm", "k_solve_cluster")
         if "bf16_split_cold" in results:
-            roofs["bf16_split_cold"] = tc_roof("bf16_split_cold", False)
+            roofs["bf16_split_cold"] = tc_roof("bf16_split_cold", False, w.n == 256)
+        if "bf16_split_streamed_cold" in results:
+            roofs["bf16_split_streamed_cold"] = tc_roof("bf16_split_streamed_cold", False, False)
         if "bf16_split_learned_warm" in results:
-            roofs["bf16_split_learned_warm"] = tc_roof("bf16_split_learned_warm", True)
+            roofs["bf16_split_learned_warm"] = tc_roof("bf16_split_learned_warm", True, False)
         # the target's chosen form, batched + BF16 split + learned warm start,
         # against plain at the same tolerance (reported whether or not it is
         # the fastest variant)

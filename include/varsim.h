@@ -110,8 +110,20 @@ typedef struct {
 #define VS_PREC_BF16_SPLIT 1  /* cosine transforms as tcgen05 tensor-core GEMMs in
                                  BF16 hi/lo split precision with FP32 accumulation
                                  (x = hi + lo, products hi*hi + hi*lo + lo*hi);
-                                 n = 128 .. 1024 (power of two); outputs are
-                                 produced in chunks of 256 columns */
+                                 n = 128 .. 1024 (power of two). Two engines:
+                                 - n = 256 with cold starts, engine AUTO or
+                                   CLUSTER: one CTA pair per map keeps the map on
+                                   chip; every transform is two half-size GEMMs
+                                   (the even/odd symmetry of the DCT-II), the
+                                   start and preconditioner are those of the FP32
+                                   engines (the die's uniform mode);
+                                 - otherwise (engine STREAMED, other n, warm
+                                   starts): a persistent engine that streams the
+                                   map through global memory between GEMM passes,
+                                   outputs in chunks of 256 columns, b = beta mu,
+                                   theta_0 = 0 (or the warm start).
+                                 The rounding of the split (~1e-3 K at 30-130 K
+                                 rises) suits update tolerances of ~1e-2 K. */
 
 /* Execution engines of the FP32 steady solve (identical arithmetic, different
  * data movement). Both precondition the iteration
@@ -135,7 +147,8 @@ typedef struct {
  *   VS_ENGINE_AUTO: the cluster engine when precision is FP32 and every map
  *     has n in [32, 256], the streamed engine otherwise.
  * The transient solve and vs_solve_steady_noalloc always use the streamed
- * engine; VS_PREC_BF16_SPLIT has its own tensor-core engine (b = beta mu). */
+ * engine; VS_PREC_BF16_SPLIT has its own tensor-core engines (above), where
+ * engine CLUSTER asks for the on-chip pair engine. */
 #define VS_ENGINE_AUTO 0
 #define VS_ENGINE_STREAMED 1
 #define VS_ENGINE_CLUSTER 2

@@ -77,6 +77,15 @@ void vs_stack_to_dev(const vs_stack* s, vs_stack_dev* d);
 int vs_hankel_eval(const vs_stack_dev& st, double cell_m, int quad_nodes,
                    const double* r_dev, double* out_dev, int count, cudaStream_t s);
 
+// ---------------------------------------------------------------- tensor-core cluster engine
+// BF16 hi/lo split engine with the map on chip (vs_tcc.cu): n = 256, cold
+// starts, linear models. vs_tcc_launch runs `count` maps (cluster index ->
+// map through P.order).
+namespace vsk { struct ClusterDev; }
+bool vs_tcc_ok(int n);
+int vs_tcc_check(cudaStream_t s);
+int vs_tcc_launch(const vsk::ClusterDev& P, int count, cudaStream_t s);
+
 // ---------------------------------------------------------------- transient
 // Persistent transient of one map (vs_transient.cu): lagged leakage,
 // untruncated superposition, n in {256, 512, 1024}. Returns the map's status

@@ -1454,6 +1454,7 @@ struct vs_plan_t {
   std::vector<std::pair<int, int>> cl_groups; // (n, maps) per launch, in order
   int* d_order = nullptr;                     // maps grouped by n
   int cl_batch = kClBatchDefault;             // cluster engine: update-load batch
+  bool tcc = false;                           // split precision with the map on chip
   // autotuner record: the candidate shapes timed at creation and their times
   std::vector<std::pair<int, double>> tuned;
 };
@@ -1699,6 +1700,13 @@ int plan_layout_cluster(vs_plan_t* p, cudaStream_t s) {
                               cudaMemcpyHostToDevice, s));
   VS_CUDA_TRY(cudaMemsetAsync(p->d_info, 0, sizeof(vs_solve_info) * n_items, s));
   VS_CUDA_TRY(cudaMemsetAsync(p->d_ctrl, 0, sizeof(Ctrl), s));
+  if (p->tcc) {
+    int rc = vs_tcc_check(s);
+    if (rc != VS_OK) return rc;
+    p->grid = 0;
+    VS_CUDA_TRY(cudaStreamSynchronize(s));  // host vectors must outlive the copies
+    return VS_OK;
+  }
   for (auto& g : p->cl_groups) {
     ClusterFn fn = cluster_kernel(g.first, p->cl_batch);
     int rc = cluster_attrs(g.first, p->cl_batch);
@@ -1734,6 +1742,12 @@ int plan_launch_cluster(vs_plan_t* p, cudaStream_t s) {
     P.beta = (float)p->params.beta_per_K;
     P.alpha = (float)p->params.alpha_per_K;
     P.tol = (float)p->params.tol_K;
+    if (p->tcc) {
+      int rc = vs_tcc_launch(P, g.second, s);
+      if (rc != VS_OK) return rc;
+      off += g.second;
+      continue;
+    }
     cudaLaunchAttribute attr[1];
     cudaLaunchConfig_t cfg = cluster_config(g.first, g.second, s, attr);
     cudaError_t e = cudaLaunchKernelEx(&cfg, cluster_kernel(g.first, p->cl_batch), P);
@@ -1927,14 +1941,38 @@ int plan_create(const vs_batch_item* items_host, int n_items, const vs_solve_par
     return vs_set_error(VS_ERR_INVALID_ARG, "the physics variants run on the streamed engine");
   bool cluster_ok = params->precision == VS_PREC_FP32 && !vs_params_physics(params);
   for (int i = 0; i < n_items && cluster_ok; ++i) cluster_ok = cluster_size_ok(items_host[i].k->n);
-  if (params->engine == VS_ENGINE_CLUSTER && !cluster_ok)
+  if (params->engine == VS_ENGINE_CLUSTER && params->precision == VS_PREC_FP32 && !cluster_ok)
     return vs_set_error(VS_ERR_INVALID_ARG,
                         "the cluster engine needs FP32 precision and every n in [32, %d]", kClMaxN);
+  // split precision: the on-chip pair engine for n = 256 cold starts (engine
+  // AUTO or CLUSTER), the streamed tensor-core engine otherwise (STREAMED)
+  bool tcc_ok = params->precision == VS_PREC_BF16_SPLIT && !vs_params_physics(params);
+  for (int i = 0; i < n_items && tcc_ok; ++i)
+    tcc_ok = vs_tcc_ok(items_host[i].k->n) && !items_host[i].theta_init;
+  if (params->precision == VS_PREC_BF16_SPLIT && params->engine == VS_ENGINE_CLUSTER && !tcc_ok)
+    return vs_set_error(VS_ERR_INVALID_ARG,
+                        "the split-precision cluster engine needs n = 256 and cold starts");
   cudaStream_t s = (cudaStream_t)stream;
   vs_plan_t* p = new vs_plan_t();
   p->n_items = n_items;
   p->items.assign(items_host, items_host + n_items);
   p->params = *params;
+  if (tcc_ok && params->engine != VS_ENGINE_STREAMED) {
+    if (shape) {
+      delete p;
+      return vs_set_error(VS_ERR_INVALID_ARG, "the split-precision cluster engine has one shape (0)");
+    }
+    p->cluster = true;
+    p->tcc = true;
+    rc = plan_layout_cluster(p, s);
+    if (rc != VS_OK) {
+      plan_release(p);
+      delete p;
+      return rc;
+    }
+    *out = p;
+    return VS_OK;
+  }
   if (cluster_ok && params->engine != VS_ENGINE_STREAMED) {
     p->cluster = true;
     if (shape && !cluster_shape_ok(shape)) {
