@@ -177,11 +177,20 @@ def test_cluster_argument_checks():
         pd, pl, s = inputs(w)
         with pytest.raises(vs.VarsimError):
             vs.solve_steady(k, pd[0], pl[0], s[0], vs_params(w, engine=vs.VS_ENGINE_CLUSTER))
+    # split precision with the cluster engine means the on-chip pair engine:
+    # n = 256 only
+    w = synth.workload("c3_128")
+    k = _kernel(w)
+    pd, pl, s = inputs(w)
+    with pytest.raises(vs.VarsimError):
+        vs.solve_steady(k, pd[0], pl[0], s[0], vs_params(w, precision=vs.VS_PREC_BF16_SPLIT,
+                                                          engine=vs.VS_ENGINE_CLUSTER))
     w = synth.workload("c3_256")
     k = _kernel(w)
     pd, pl, s = inputs(w)
-    with pytest.raises(vs.VarsimError):             # the split path has its own engine
-        vs.solve_steady(k, pd[0], pl[0], s[0], vs_params(w, precision=vs.VS_PREC_BF16_SPLIT,
-                                                          engine=vs.VS_ENGINE_CLUSTER))
+    _, info = vs.solve_steady(k, pd[0], pl[0], s[0], vs_params(w, tol_K=1e-2,
+                                                               precision=vs.VS_PREC_BF16_SPLIT,
+                                                               engine=vs.VS_ENGINE_CLUSTER))
+    assert info["status"] == vs.VS_OK
     with pytest.raises(vs.VarsimError):
         vs.solve_steady(k, pd[0], pl[0], s[0], vs_params(w, engine=7))
