@@ -93,7 +93,7 @@ def _args():
                     help="comma-separated subset of the variants to time (default: all)")
     ap.add_argument("--unit", default="map", help="unit of --record-traffic's --batch count")
     ap.add_argument("--case", default="", choices=["", "transient", "transient_window5",
-                                                   "closed_form", "network"],
+                                                   "closed_form", "network", "network_tc"],
                     help="run one kernel's small case for a profiler capture (a warm-up "
                          "call, then one timed call) and print its timing instead of the bench")
     ap.add_argument("--tsteps", type=int, default=10, help="steps of --case transient*")
@@ -128,6 +128,7 @@ KERNEL_SOURCES = {
     "k_cf_cols": [_CSRC + "vs_closed.cu"] + _COMMON,
     "k_cf_rows_inv": [_CSRC + "vs_closed.cu"] + _COMMON,
     "k_conv_fwd": [_CSRC + "vs_cnn.cu"] + _COMMON,
+    "k_conv_tc": [_CSRC + "vs_conv_tc.cu", _CSRC + "vs_tc.cuh", _CSRC + "vs_internal.cuh"] + _COMMON,
     "k_solve_tcc": [_CSRC + "vs_tcc.cu", _CSRC + "vs_tc.cuh", _CSRC + "vs_internal.cuh"] + _COMMON,
     "k_transient_fast": [_CSRC + "vs_transient.cu", _CSRC + "vs_internal.cuh"] + _COMMON,
 }
@@ -292,6 +293,45 @@ def physics_variants(vs, k, w, pd, pl, s, th_lin, a, stream):
         del th
     return dict(out, how="streamed engine over the %d-map batch at 1e-2 K; deviation per map from "
                          "the headline path's linear-model maps" % B)
+
+
+def wide_spreader(vs, w, pd, pl, s, th_die, a, stream, mk):
+    """The heat spreader wider than the die (Sec. II-B's constant part of the
+    Green's function; layers 2.. a 30 mm square under the 20 mm die): the
+    cluster engine's throughput with that kernel and how far it moves the maps
+    from the die-sized stack (th_die)."""
+    import torch
+    st = w.stack
+    out = {}
+    for side in (25e-3, 30e-3, 40e-3):
+        stk = vs.Stack(st.thickness_m, st.kappa_W_mK, st.h_conv_W_m2K, st.heat_cap_J_m2K,
+                       spreader_layer=2, spreader_side_m=side)
+        kw = vs.Kernel(stk, vs.Grid(w.n, w.die_m))
+        th = torch.empty_like(pd)
+        B = pd.shape[0]
+        plan = vs.Plan([(kw, pd[i], pl[i], s[i], th[i]) for i in range(B)], mk(vs.VS_PREC_FP32))
+        for _ in range(max(3, a.warmup)):
+            plan.run(stream)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(a.steps):
+            plan.run(stream)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / a.steps
+        infos = plan.info(stream)
+        d = (th_die - th).double()
+        out["%g mm" % (side * 1e3)] = {
+            "value": whole_job_rate(1, B, ms * 1e-3), "unit": UNIT, "ms_per_step": ms,
+            "not_ok": sum(1 for i in infos if i["status"] != vs.VS_OK),
+            "iterations_mean": sum(i["iterations"] for i in infos) / B,
+            "mean_rise_drop_K": float(d.mean()), "max_rise_K_mean": float(th.amax(dim=(1, 2)).mean())}
+        plan.close()
+        del th
+    return dict(out, how="cluster engine over the %d-map batch at 1e-2 K, layers 2.. (the Cu "
+                         "spreader) wider than the 20 mm die, which changes only the uniform mode of "
+                         "the kernel (R34); drop of the mean rise against the die-sized stack" % pd.shape[0])
 
 
 class Clocks:
@@ -691,9 +731,9 @@ def run_ours(a):
             "how": "one vs_solve_transient call (plan set-up included), wall time",
             "roofline": {"bound": "hbm", "achieved": tbytes / dt_t / 1e9, "peak": _peaks()[0],
                          "unit": "GB/s", "frac": tbytes / dt_t / 1e9 / _peaks()[0],
-                         "traffic": (_traffic_record("k_solve_transient")["dram_bytes_per_unit"]
-                                     * steps_t) if _traffic_record("k_solve_transient") else None,
-                         "kernel": "k_solve_transient",
+                         "traffic": (_traffic_record("k_transient_fast")["dram_bytes_per_unit"]
+                                     * steps_t) if _traffic_record("k_transient_fast") else None,
+                         "kernel": "k_transient_fast",
                          "note": "8 B/pixel per step algorithmic (read P_dyn,n, write theta_n); "
                                  "traffic per launch from the committed per-step capture"}}
         # Sec. IV-E variants on the same trace: the paper's 5-step window, and the
@@ -766,6 +806,7 @@ def run_ours(a):
         extras["effect_ablation"] = effect_ablation(vs, k, w, pd[:ABLATION_MAPS], pl[:ABLATION_MAPS],
                                                     s[:ABLATION_MAPS], mk)
         extras["physics_variants"] = physics_variants(vs, k, w, pd, pl, s, th_best, a, stream)
+        extras["wide_spreader"] = wide_spreader(vs, w, pd, pl, s, th_best, a, stream, mk)
 
     # e2e: pinned host inputs -> device -> headline path -> host theta, every step
     e2e = None
@@ -981,8 +1022,10 @@ def run_case(a):
             R = 64
             m = vs.Model(16, R, seed=11)
             x = torch.rand(a.batch, 3, R, R, device=dev)
-            call = lambda: m.forward(x, stream)
-            out["workload"] = "warm-start network forward, %d inputs of 3x%dx%d" % (a.batch, R, R)
+            tc = a.case == "network_tc"
+            call = lambda: m.forward(x, stream, tensor_cores=tc)
+            out["workload"] = "warm-start network forward%s, %d inputs of 3x%dx%d" % (
+                " (tensor-core convolutions)" if tc else "", a.batch, R, R)
     call()
     torch.cuda.synchronize()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)

@@ -493,6 +493,12 @@ int vs_model_set_params(vs_model m, const float* host);
  * hold it) share its activation buffers: calls on one model must be ordered,
  * e.g. on one stream; different models are independent. */
 int vs_model_forward(vs_model m, const float* x, float* y, int batch, void* stream);
+/* The same forward with the convolutions as tcgen05 implicit GEMMs (BF16
+ * activations and weights, FP32 accumulation) wherever a layer's shape fits
+ * (its image a multiple of 128 pixels, padded weights <= 64 KB), the SIMT
+ * kernels elsewhere. Within BF16 rounding of vs_model_forward; the warm plan's
+ * prediction stage runs it. */
+int vs_model_forward_tc(vs_model m, const float* x, float* y, int batch, void* stream);
 /* Mean-squared-error loss against t[b][1][R][R] and its parameter gradient
  * (host arrays; grad_host may be NULL). No update. Blocking. */
 int vs_model_loss_grad(vs_model m, const float* x, const float* t, int batch,

@@ -50,6 +50,7 @@ EXPORTS = [
     "vs_warm_apply", "vs_solve_batch_host", "vs_model_shape", "vs_warm_plan_create",
     "vs_warm_plan_run", "vs_warm_plan_launches", "vs_warm_plan_info", "vs_warm_plan_free",
     "vs_solve_transient_ex", "vs_solve_closed_form", "vs_plan_create_shaped", "vs_plan_shape",
+    "vs_model_forward_tc",
 ]
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
@@ -158,6 +159,7 @@ def lib():
         "vs_model_get_params": (ip, [vp, vp]),
         "vs_model_set_params": (ip, [vp, vp]),
         "vs_model_forward": (ip, [vp, vp, vp, ip, vp]),
+        "vs_model_forward_tc": (ip, [vp, vp, vp, ip, vp]),
         "vs_model_loss_grad": (ip, [vp, vp, vp, ip, C.POINTER(C.c_double), vp, vp]),
         "vs_model_train": (ip, [vp, vp, vp, ip, ip, ip, C.c_float, C.c_ulonglong,
                                 C.POINTER(C.c_double), vp]),
@@ -589,11 +591,14 @@ class Model:
         assert a.size == self.nparams
         _check(lib().vs_model_set_params(self.handle, a.ctypes.data), "vs_model_set_params")
 
-    def forward(self, x, stream=None):
+    def forward(self, x, stream=None, tensor_cores: bool = False):
+        """y = net(x); tensor_cores: the convolutions as tcgen05 implicit GEMMs
+        (BF16 activations, vs_model_forward_tc), as the warm plan runs them."""
         import torch
         y = torch.empty(x.shape[0], 1, self.resolution, self.resolution, device=x.device)
-        _check(lib().vs_model_forward(self.handle, _ptr(x, None, "x"), y.data_ptr(), x.shape[0],
-                                      _stream(stream)), "vs_model_forward")
+        fn = lib().vs_model_forward_tc if tensor_cores else lib().vs_model_forward
+        _check(fn(self.handle, _ptr(x, None, "x"), y.data_ptr(), x.shape[0], _stream(stream)),
+               "vs_model_forward")
         return y
 
     def loss_grad(self, x, t, stream=None):

@@ -18,7 +18,7 @@ INCLUDE = os.path.join(ROOT, "include")
 BUILD = os.path.join(PKG, "_build")
 LIB = os.path.join(PKG, "libvarsim.so")
 SOURCES = ["vs_api.cu", "vs_kernel_build.cu", "vs_solver.cu", "vs_cluster.cu", "vs_host.cu", "vs_closed.cu",
-           "vs_cnn.cu", "vs_transient.cu", "vs_tcc.cu"]
+           "vs_cnn.cu", "vs_transient.cu", "vs_tcc.cu", "vs_conv_tc.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

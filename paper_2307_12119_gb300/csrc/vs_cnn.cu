@@ -15,8 +15,10 @@
 //   x[3,R] -> conv C -> conv C (=s1) -> pool -> conv 2C -> conv 2C (=s2) -> pool
 //   -> conv 2C -> up, concat s2 -> conv C -> up, concat s1 -> conv C -> conv 1
 // Weights are BF16 (FP32 master copy in the optimiser), activations and
-// accumulation FP32. All kernels are SIMT; every layer is a 3x3 convolution
-// with zero padding.
+// accumulation FP32; every layer is a 3x3 convolution with zero padding.
+// Training (forward and backward) runs these SIMT kernels; inference in the
+// warm plan runs the convolutions as tcgen05 implicit GEMMs (vs_conv_tc.cu,
+// BF16 activations) where a layer's shape fits.
 #include <math.h>
 #include <stdio.h>
 #include <stdlib.h>
@@ -411,8 +413,14 @@ int ensure_acts(vs_model_t* m, int B) {
   return VS_OK;
 }
 
-void conv_fwd(vs_model_t* m, int l, TView in, TView out, int B, cudaStream_t s) {
+void conv_fwd(vs_model_t* m, int l, TView in, TView out, int B, cudaStream_t s, bool tc = false) {
   int H = m->res[l];
+  if (tc) {
+    // tensor cores where the layer's shape fits (inference); else the SIMT kernel
+    const int rc = vs_conv_tc(in.p, in.ctot, m->cin[l], m->pb + m->woff[l], m->p + m->boff[l], out.p,
+                              out.ctot, m->cout[l], B, H, m->relu[l], s);
+    if (rc != -1) return;
+  }
   long long total = (long long)B * ((m->cout[l] + 3) / 4) * H * H;
   k_conv_fwd<<<blocks(total, 256), 256, 0, s>>>(in.p, in.ctot, m->cin[l], m->pb + m->woff[l],
                                                 m->p + m->boff[l], out.p, out.ctot, m->cout[l], B,
@@ -438,23 +446,24 @@ void relu_bwd(TView act, TView d, int c, int B, int H, cudaStream_t s) {
   k_relu_bwd<<<blocks(total, 256), 256, 0, s>>>(act.p, act.ctot, d.p, d.ctot, c, B, H * H);
 }
 
-// forward of a batch already in m->x
-void forward(vs_model_t* m, int B, cudaStream_t s) {
+// forward of a batch already in m->x; tc: the convolutions on the tensor
+// cores (BF16 activations, inference) where their shapes fit
+void forward(vs_model_t* m, int B, cudaStream_t s, bool tc = false) {
   const int C = m->C, R = m->R, h = R / 2, q = R / 4;
   const size_t R2 = (size_t)R * R, h2 = (size_t)h * h;
-  conv_fwd(m, 0, {m->x, 3}, {m->a1, C}, B, s);
-  conv_fwd(m, 1, {m->a1, C}, {m->c2 + C * R2, 2 * C}, B, s);                // s1 into c2[C:2C)
+  conv_fwd(m, 0, {m->x, 3}, {m->a1, C}, B, s, tc);
+  conv_fwd(m, 1, {m->a1, C}, {m->c2 + C * R2, 2 * C}, B, s, tc);            // s1 into c2[C:2C)
   k_pool_fwd<<<blocks((long long)B * C * h2, 256), 256, 0, s>>>(m->c2 + C * R2, 2 * C, m->p1, C, C, B, R);
-  conv_fwd(m, 2, {m->p1, C}, {m->a3, 2 * C}, B, s);
-  conv_fwd(m, 3, {m->a3, 2 * C}, {m->c1 + 2 * C * h2, 4 * C}, B, s);        // s2 into c1[2C:4C)
+  conv_fwd(m, 2, {m->p1, C}, {m->a3, 2 * C}, B, s, tc);
+  conv_fwd(m, 3, {m->a3, 2 * C}, {m->c1 + 2 * C * h2, 4 * C}, B, s, tc);    // s2 into c1[2C:4C)
   k_pool_fwd<<<blocks((long long)B * 2 * C * q * q, 256), 256, 0, s>>>(m->c1 + 2 * C * h2, 4 * C, m->p2,
                                                                      2 * C, 2 * C, B, h);
-  conv_fwd(m, 4, {m->p2, 2 * C}, {m->a5, 2 * C}, B, s);
+  conv_fwd(m, 4, {m->p2, 2 * C}, {m->a5, 2 * C}, B, s, tc);
   k_up_fwd<<<blocks((long long)B * 2 * C * h2, 256), 256, 0, s>>>(m->a5, 2 * C, m->c1, 4 * C, 2 * C, B, q);
-  conv_fwd(m, 5, {m->c1, 4 * C}, {m->a6, C}, B, s);
+  conv_fwd(m, 5, {m->c1, 4 * C}, {m->a6, C}, B, s, tc);
   k_up_fwd<<<blocks((long long)B * C * R2, 256), 256, 0, s>>>(m->a6, C, m->c2, 2 * C, C, B, h);
-  conv_fwd(m, 6, {m->c2, 2 * C}, {m->a7, C}, B, s);
-  conv_fwd(m, 7, {m->a7, C}, {m->y, 1}, B, s);
+  conv_fwd(m, 6, {m->c2, 2 * C}, {m->a7, C}, B, s, tc);
+  conv_fwd(m, 7, {m->a7, C}, {m->y, 1}, B, s, tc);
 }
 
 // backward from m->dy; fills m->g
@@ -599,7 +608,8 @@ extern "C" int vs_model_set_params(vs_model m, const float* host) {
   return VS_OK;
 }
 
-extern "C" int vs_model_forward(vs_model m, const float* x, float* y, int batch, void* stream) {
+namespace {
+int model_forward(vs_model m, const float* x, float* y, int batch, void* stream, bool tc) {
   if (!m || !x || !y || batch < 1) return vs_set_error(VS_ERR_INVALID_ARG, "bad model forward arguments");
   cudaStream_t s = (cudaStream_t)stream;
   const size_t R2 = (size_t)m->R * m->R;
@@ -610,12 +620,21 @@ extern "C" int vs_model_forward(vs_model m, const float* x, float* y, int batch,
     int B = std::min(chunk, batch - b0);
     VS_CUDA_TRY(cudaMemcpyAsync(m->x, x + (size_t)b0 * 3 * R2, sizeof(float) * 3 * R2 * B,
                                 cudaMemcpyDeviceToDevice, s));
-    forward(m, B, s);
+    forward(m, B, s, tc);
     VS_CUDA_TRY(cudaMemcpyAsync(y + (size_t)b0 * R2, m->y, sizeof(float) * R2 * B,
                                 cudaMemcpyDeviceToDevice, s));
   }
   VS_CUDA_TRY(cudaGetLastError());
   return VS_OK;
+}
+}  // namespace
+
+extern "C" int vs_model_forward(vs_model m, const float* x, float* y, int batch, void* stream) {
+  return model_forward(m, x, y, batch, stream, false);
+}
+
+extern "C" int vs_model_forward_tc(vs_model m, const float* x, float* y, int batch, void* stream) {
+  return model_forward(m, x, y, batch, stream, true);
 }
 
 extern "C" int vs_model_loss_grad(vs_model m, const float* x, const float* t, int batch,
@@ -895,7 +914,7 @@ extern "C" int vs_warm_plan_run(vs_warm_plan p, int stages, void* stream) {
   if (stages & VS_WARM_FIRST) rc = vs_plan_run(p->first, stream);
   if (rc == VS_OK && (stages & VS_WARM_PREDICT)) {
     rc = vs_warm_features(p->theta1, p->pl, p->sk, p->count, p->n, p->R, p->x, stream);
-    if (rc == VS_OK) rc = vs_model_forward(p->model, p->x, p->y, p->count, stream);
+    if (rc == VS_OK) rc = vs_model_forward_tc(p->model, p->x, p->y, p->count, stream);
     if (rc == VS_OK)
       rc = vs_warm_apply(p->theta1, p->y, p->count, p->n, p->R, p->theta_init, stream);
   }

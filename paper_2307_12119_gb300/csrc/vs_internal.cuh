@@ -86,6 +86,14 @@ bool vs_tcc_ok(int n);
 int vs_tcc_check(cudaStream_t s);
 int vs_tcc_launch(const vsk::ClusterDev& P, int count, cudaStream_t s);
 
+// ---------------------------------------------------------------- network
+// 3x3 convolution of the warm-start network as a tcgen05 implicit GEMM
+// (vs_conv_tc.cu; BF16 activations and weights, FP32 accumulation), for
+// inference. W: the layer's BF16 weights [cout][cin][3][3]. Returns VS_OK, an
+// error, or -1 if the layer's shape does not fit the kernel.
+int vs_conv_tc(const float* in, int in_ctot, int cin, const void* W, const float* bias,
+               float* out, int out_ctot, int cout, int B, int H, int relu, cudaStream_t s);
+
 // ---------------------------------------------------------------- transient
 // Persistent transient of one map (vs_transient.cu): lagged leakage,
 // untruncated superposition, n in {256, 512, 1024}. Returns the map's status

@@ -94,3 +94,51 @@ def test_split_engine_selection():
         vs.Plan([(k2, z[0], z[0], None, z[0].clone())],
                  vs_params(w2, precision=vs.VS_PREC_BF16_SPLIT, engine=vs.VS_ENGINE_CLUSTER))
     assert e.value.status == vs.VS_ERR_INVALID_ARG
+
+
+def test_pair_engine_statuses():
+    """Per-map outcomes on the pair engine: a map with a NaN reports
+    VS_ERR_NONFINITE, a huge leakage coefficient VS_ERR_RUNAWAY, one iteration
+    VS_ERR_NO_CONVERGENCE, and the other maps of the launch are unaffected."""
+    vs, w, k, pd, pl, s = _case(4)
+    B = pd.shape[0]
+    bad = pd.clone()
+    bad[1, 100, 37] = float("nan")
+    th = torch.empty_like(pd)
+    prm = vs_params(w, tol_K=SPLIT_TOL_K, precision=vs.VS_PREC_BF16_SPLIT)
+    infos = vs.solve_batch([(k, bad[i], pl[i], s[i], th[i]) for i in range(B)], prm)
+    assert infos[1]["status"] == vs.VS_ERR_NONFINITE
+    assert all(infos[i]["status"] == vs.VS_OK for i in (0, 2, 3))
+    th_ref = torch.empty_like(pd)
+    vs.solve_batch([(k, pd[i], pl[i], s[i], th_ref[i]) for i in range(B)], prm)
+    for i in (0, 2, 3):
+        assert torch.equal(th[i], th_ref[i])
+    one = vs_params(w, tol_K=SPLIT_TOL_K, max_iter=1, precision=vs.VS_PREC_BF16_SPLIT)
+    infos = vs.solve_batch([(k, pd[i], pl[i], s[i], th[i]) for i in range(B)], one)
+    assert all(i["status"] == vs.VS_ERR_NO_CONVERGENCE and i["iterations"] == 1 for i in infos)
+    hot = vs_params(w, tol_K=SPLIT_TOL_K, beta_per_K=50.0, precision=vs.VS_PREC_BF16_SPLIT)
+    infos = vs.solve_batch([(k, pd[i], pl[i], s[i], th[i]) for i in range(B)], hot)
+    assert all(i["status"] == vs.VS_ERR_RUNAWAY for i in infos)
+
+
+def test_pair_engine_without_variation_field_and_graph_capture():
+    """s = NULL (uniform conductivity) and a run captured in a CUDA graph give
+    the same maps as a direct run with s = 1."""
+    vs, w, k, pd, pl, s = _case(8)
+    B = pd.shape[0]
+    prm = vs_params(w, tol_K=SPLIT_TOL_K, precision=vs.VS_PREC_BF16_SPLIT)
+    ones = torch.ones_like(pd)
+    th_a, th_b = torch.empty_like(pd), torch.empty_like(pd)
+    vs.solve_batch([(k, pd[i], pl[i], None, th_a[i]) for i in range(B)], prm)
+    plan = vs.Plan([(k, pd[i], pl[i], ones[i], th_b[i]) for i in range(B)], prm)
+    stream = torch.cuda.Stream()
+    stream.wait_stream(torch.cuda.current_stream())
+    with torch.cuda.stream(stream):
+        g = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(g, stream=stream):
+            plan.run(stream)
+    torch.cuda.current_stream().wait_stream(stream)
+    g.replay()
+    torch.cuda.synchronize()
+    assert all(i["status"] == vs.VS_OK for i in plan.info())
+    assert torch.equal(th_a, th_b)

@@ -170,3 +170,37 @@ def test_bad_warm_start_falls_back_to_cold_solve():
     assert all(i["fell_back"] for i in infos)        # vs_solve_info.fell_back
     ref, _ = vs.solve_steady(k, pd[0], pl[0], s[0], vs_params(w))
     assert float((th[0] - ref).abs().max()) <= 1e-3
+
+
+@pytest.mark.parametrize("C,R", [(16, 64), (8, 32), (4, 8)])
+def test_tensor_core_forward_matches_simt_forward(C, R):
+    """The warm plan's inference (convolutions as tcgen05 implicit GEMMs with
+    BF16 activations) against the FP32-activation SIMT forward that training
+    uses: within BF16 rounding accumulated over the 8 layers (3 % of the
+    output's scale). At R = 8 the deeper layers (images under 128 pixels) run
+    on the SIMT kernels inside the same forward."""
+    import paper_2307_12119_gb300 as vs
+    m = vs.Model(C, R, seed=5)
+    g = torch.Generator(device="cuda").manual_seed(9)
+    x = torch.rand(300, 3, R, R, device="cuda", generator=g) * 2 - 1
+    y = m.forward(x)
+    yt = m.forward(x, tensor_cores=True)
+    scale = float(y.abs().max())
+    err = float((yt - y).abs().max())
+    print("forward C=%d R=%d: max |tc - simt| %.2e of scale %.2e" % (C, R, err, scale))
+    assert torch.isfinite(yt).all() and err <= 3e-2 * scale + 1e-6
+    if C == 16:
+        st = torch.cuda.current_stream()
+        ts = []
+        for tc in (False, True):
+            m.forward(x, tensor_cores=tc)
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(st)
+            for _ in range(3):
+                m.forward(x, tensor_cores=tc)
+            e1.record(st)
+            torch.cuda.synchronize()
+            ts.append(e0.elapsed_time(e1) / 3)
+        print("forward of 300 inputs: SIMT %.3f ms, tensor cores %.3f ms" % tuple(ts))
+        assert ts[1] < ts[0]
