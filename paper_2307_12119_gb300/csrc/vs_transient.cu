@@ -94,47 +94,168 @@ __device__ bool tr_barrier(TrCtrl* c, unsigned& target) {
   return tr_ld_acquire(&c->abort) == 0u;
 }
 
+// Radix schedule of a length-N FFT (16s first, then the remaining factor),
+// at compile time: radix and block length L of pass p, and the offset of its
+// twiddles in the per-pass table (entries W_L^{j r}, j < L / R, 1 <= r < R,
+// stored at (r - 1) L / R + j so that consecutive butterflies j read
+// consecutive entries: no bank conflicts, unlike strided reads of one W_4N
+// table).
+template <int N>
+struct TrSched {
+  __host__ __device__ static constexpr int radix(int p) {
+    int n = N;
+    for (int i = 0; i < p; ++i) n /= (n >= 16 ? 16 : n);
+    return n >= 16 ? 16 : n;
+  }
+  __host__ __device__ static constexpr int passes() {
+    int n = N, q = 0;
+    while (n > 1) { n /= (n >= 16 ? 16 : n); ++q; }
+    return q;
+  }
+  __host__ __device__ static constexpr int len(int p) {
+    int L = N;
+    for (int i = 0; i < p; ++i) L /= radix(i);
+    return L;
+  }
+  __host__ __device__ static constexpr int tw_off(int p) {
+    int o = 0;
+    for (int i = 0; i < p; ++i) o += (radix(i) - 1) * (len(i) / radix(i));
+    return o;
+  }
+  static constexpr int TW = tw_off(passes());            // entries of the table (< N)
+};
+
 template <int N, int R>
 struct TrShape {
   static constexpr int F = R / 2;                       // complex FFTs per CTA and phase
   static constexpr int THREADS = F * N < 512 ? F * N : 512;
   static constexpr int NP = N + N / 16 + 1;
+  // row stride of the per-mode arrays: 2 F MS = 32 (mod 32) words, so the
+  // F x 32/F (column pair, frequency) items of a warp fall in distinct banks
+  static constexpr int MS = N + 16 / F;
   static constexpr int CELLS = F * N / THREADS;          // update items (2 cells) per thread
-  // FFT buffers, per-mode arrays, twiddles W_4N^e (e < 4N) and digit reversal
-  static constexpr size_t SMEM = (size_t)F * NP * sizeof(float2) + 4 * (size_t)R * N * sizeof(float) +
-                                 4 * (size_t)N * sizeof(float2) + (size_t)N * sizeof(int);
-  static_assert(F >= 1 && (F * N) % THREADS == 0, "shape");
+  // FFT buffers, per-mode arrays, DCT twiddles W_4N^k (k < N), FFT pass
+  // twiddles and digit reversal
+  static constexpr size_t SMEM = (size_t)F * NP * sizeof(float2) + 4 * (size_t)R * MS * sizeof(float) +
+                                 (size_t)N * sizeof(float2) + (size_t)TrSched<N>::TW * sizeof(float2) +
+                                 (size_t)N * sizeof(int);
+  static_assert(F >= 1 && (F * N) % THREADS == 0 && 16 % F == 0, "shape");
 };
+
+// One radix-R pass (block length L) over the F in-place FFTs of length N in
+// buf (padded stride NP), twiddles from the pass's own table twp. Forward:
+// decimation in frequency (butterfly, then W_L^{j r}); inverse: conjugate
+// twiddle, then the inverse butterfly.
+template <int N, int L, int R, bool FWD>
+__device__ __forceinline__ void tr_pass(float2* buf, int nfft, int stride, const float2* twp) {
+  constexpr int m = L / R, per = N / R;
+  const int total = nfft * per;
+  for (int b = threadIdx.x; b < total; b += blockDim.x) {
+    const int f = b / per, rem = b % per, blk = rem / m, j = rem % m;
+    float2* base = buf + f * stride;
+    const int i0 = blk * L + j;
+    float2 v[R];
+#pragma unroll
+    for (int r = 0; r < R; ++r) v[r] = base[pad(i0 + r * m)];
+    if (FWD) {
+      dftR<R, true>(v);
+      if (m > 1) {
+#pragma unroll
+        for (int r = 1; r < R; ++r) v[r] = cmul(v[r], twp[(r - 1) * m + j]);
+      }
+    } else {
+      if (m > 1) {
+#pragma unroll
+        for (int r = 1; r < R; ++r) v[r] = cmulc(v[r], twp[(r - 1) * m + j]);
+      }
+      dftR<R, false>(v);
+    }
+#pragma unroll
+    for (int r = 0; r < R; ++r) base[pad(i0 + r * m)] = v[r];
+  }
+}
+
+template <int N, int P, bool FWD>
+__device__ __forceinline__ void tr_pass_p(float2* buf, int nfft, int stride, const float2* ptw) {
+  using Q = TrSched<N>;
+  tr_pass<N, Q::len(P), Q::radix(P), FWD>(buf, nfft, stride, ptw + Q::tw_off(P));
+}
+
+// Forward FFT (natural -> digit-reversed order), a block barrier after each pass.
+template <int N>
+__device__ __forceinline__ void tr_fft_forward(float2* buf, int nfft, int stride, const float2* ptw) {
+  constexpr int P = TrSched<N>::passes();
+  static_assert(P >= 2 && P <= 3, "schedule");
+  tr_pass_p<N, 0, true>(buf, nfft, stride, ptw);
+  __syncthreads();
+  tr_pass_p<N, 1, true>(buf, nfft, stride, ptw);
+  __syncthreads();
+  if constexpr (P == 3) {
+    tr_pass_p<N, 2, true>(buf, nfft, stride, ptw);
+    __syncthreads();
+  }
+}
+
+// Inverse FFT (digit-reversed -> natural, unnormalised), passes undone in reverse.
+template <int N>
+__device__ __forceinline__ void tr_fft_inverse(float2* buf, int nfft, int stride, const float2* ptw) {
+  constexpr int P = TrSched<N>::passes();
+  if constexpr (P == 3) {
+    tr_pass_p<N, 2, false>(buf, nfft, stride, ptw);
+    __syncthreads();
+  }
+  tr_pass_p<N, 1, false>(buf, nfft, stride, ptw);
+  __syncthreads();
+  tr_pass_p<N, 0, false>(buf, nfft, stride, ptw);
+  __syncthreads();
+}
 
 template <int N, int R>
 __global__ void __launch_bounds__(TrShape<N, R>::THREADS, 1) k_transient_fast(TrArgs a) {
   using S = TrShape<N, R>;
-  constexpr int F = S::F, NP = S::NP, T = S::THREADS, CELLS = S::CELLS, half = N / 2;
+  constexpr int F = S::F, NP = S::NP, MS = S::MS, T = S::THREADS, CELLS = S::CELLS, half = N / 2;
   constexpr int lgN = ilog2(N), lgF = ilog2(F);
   extern __shared__ __align__(16) float2 tr_smem[];
   __shared__ int red_i[T / 32];
   float2* buf = tr_smem;                                  // [F][NP]
-  float* km = reinterpret_cast<float*>(buf + F * NP);     // [R][N] (K - A) / N^2
-  float* am = km + R * N;                                 // [R][N] A / N^2
-  float* rh = am + R * N;                                 // [R][N] rho
-  float* W = rh + R * N;                                  // [R][N] recursion state
-  float2* tw = reinterpret_cast<float2*>(W + R * N);      // [4N] twiddles
-  int* dr = reinterpret_cast<int*>(tw + 4 * N);           // [N] digit reversal
+  float* km = reinterpret_cast<float*>(buf + F * NP);     // [R][MS] (K - A) / N^2
+  float* am = km + R * MS;                                // [R][MS] A / N^2
+  float* rh = am + R * MS;                                // [R][MS] rho
+  float* W = rh + R * MS;                                 // [R][MS] recursion state
+  float2* tw = reinterpret_cast<float2*>(W + R * MS);     // [N] DCT twiddles W_4N^k
+  float2* ptw = tw + N;                                   // [TW] FFT pass twiddles
+  int* dr = reinterpret_cast<int*>(ptw + TrSched<N>::TW); // [N] digit reversal
   const int tid = threadIdx.x;
   const int y0 = blockIdx.x * R, p0 = blockIdx.x * R;
   const size_t nn = (size_t)N * N;
-  for (int i = tid; i < 4 * N; i += T) tw[i] = __ldg(&a.tw4n[i]);
-  for (int i = tid; i < N; i += T) dr[i] = __ldg(&a.digrev[i]);
+  for (int i = tid; i < N; i += T) {
+    tw[i] = __ldg(&a.tw4n[i]);
+    dr[i] = __ldg(&a.digrev[i]);
+  }
+  {
+    // W_L^{j r} = W_4N^{j r 4N / L}, pass by pass
+    using Q = TrSched<N>;
+#pragma unroll
+    for (int p = 0; p < Q::passes(); ++p) {
+      const int L = Q::len(p), Rp = Q::radix(p), m = L / Rp, o = Q::tw_off(p);
+      if (m == 1) continue;
+      for (int e = tid; e < (Rp - 1) * m; e += T) {
+        const int r = e / m + 1, j = e % m;
+        ptw[o + e] = __ldg(&a.tw4n[j * r * (4 * N / L)]);
+      }
+    }
+  }
   const float inv_n2 = 1.f / ((float)N * (float)N);
   const float beta = a.beta, alpha = a.alpha;
 
   for (int i = tid; i < R * N; i += T) {
-    const size_t g = (size_t)(p0 + (i >> lgN)) * N + (i & (N - 1));
+    const int c = i >> lgN, q = i & (N - 1), o = c * MS + q;
+    const size_t g = (size_t)(p0 + c) * N + q;
     const float A = __ldg(&a.trA[g]), K = __ldg(&a.Kt[g]);
-    km[i] = (K - A) * inv_n2;
-    am[i] = A * inv_n2;
-    rh[i] = __ldg(&a.trRho[g]);
-    W[i] = 0.f;
+    km[o] = (K - A) * inv_n2;
+    am[o] = A * inv_n2;
+    rh[o] = __ldg(&a.trRho[g]);
+    W[o] = 0.f;
   }
   // this thread's cells: item j -> (f, x), rows y0 + 2f (.x) and y0 + 2f + 1 (.y)
   float2 pl[CELLS], pd[CELLS];
@@ -151,7 +272,7 @@ __global__ void __launch_bounds__(TrShape<N, R>::THREADS, 1) k_transient_fast(Tr
   // forward DCT along x of the source in buf (Makhoul order), stored x-frequency major
   auto row_forward = [&]() {
     __syncthreads();
-    fft_forward<true>(buf, N, F, NP, tw);
+    tr_fft_forward<N>(buf, F, NP, ptw);
     for (int it = tid; it < F * (half + 1); it += T) {
       const int f = it & (F - 1), k = it >> lgF, nk = N - k;
       const float2 zk = buf[f * NP + pad(dr[k])];
@@ -188,17 +309,18 @@ __global__ void __launch_bounds__(TrShape<N, R>::THREADS, 1) k_transient_fast(Tr
       }
     }
     __syncthreads();
-    fft_forward<true>(buf, N, F, NP, tw);
+    tr_fft_forward<N>(buf, F, NP, ptw);
     for (int it = tid; it < F * (half + 1); it += T) {
-      // consecutive threads: consecutive frequencies of one FFT, so the mode
-      // arrays [column][q] are read without bank conflicts
-      const int f = it / (half + 1), k = it - f * (half + 1), nk = N - k;
+      // a warp takes F column pairs x 32/F consecutive frequencies: the FFT
+      // outputs (blocks of odd padded stride) and the mode arrays (row stride
+      // MS) are then both read without bank conflicts
+      const int f = it & (F - 1), k = it >> lgF, nk = N - k;
       const int ia = f * NP + pad(dr[k]);
       const int ib = f * NP + pad(dr[k == 0 ? 0 : nk]);
       const float2 zk = buf[ia], znk = buf[ib];
       const float2 xk = dct_post(zk, znk, tw[k]);
       auto mode = [&](int c, int q, float x) {
-        const int i = c * N + q;
+        const int i = c * MS + q;
         const float w = fmaf(rh[i], W[i] - x, x);
         W[i] = w;
         return fmaf(km[i], x, am[i] * w);
@@ -215,7 +337,7 @@ __global__ void __launch_bounds__(TrShape<N, R>::THREADS, 1) k_transient_fast(Tr
       if (k != 0 && k != half) buf[ib] = dct_pre(ynk.x, yk.x, ynk.y, yk.y, tw[nk]);
     }
     __syncthreads();
-    fft_inverse<true>(buf, N, F, NP, tw);
+    tr_fft_inverse<N>(buf, F, NP, ptw);
     for (int it = tid; it < F * N; it += T) {
       const int f = it >> lgN, j = it & (N - 1);
       const float2 v = buf[f * NP + pad(makhoul_pos(j, N))];
@@ -260,7 +382,7 @@ __global__ void __launch_bounds__(TrShape<N, R>::THREADS, 1) k_transient_fast(Tr
       }
     }
     __syncthreads();
-    fft_inverse<true>(buf, N, F, NP, tw);
+    tr_fft_inverse<N>(buf, F, NP, ptw);
     float* th_out = a.theta + (size_t)(step - 1) * nn;
 #pragma unroll
     for (int j = 0; j < CELLS; ++j) {
