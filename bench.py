@@ -571,10 +571,13 @@ def _train_warm_model(vs, synth, k, w, dev, n_train, epochs, seed_base, stream):
                "train_s": round(time.perf_counter() - t1, 2)}
 
 
-ALL_VARIANTS = ("fp32_cluster_cold", "fp32_streamed_cold", "bf16_split_cold",
-                "bf16_split_streamed_cold", "fp32_learned_warm", "bf16_split_learned_warm",
+ALL_VARIANTS = ("fp32_cluster_cold", "fp32_cluster_cold_estimate", "fp32_streamed_cold",
+                "bf16_split_cold", "bf16_split_cold_estimate", "bf16_split_streamed_cold",
+                "fp32_learned_warm", "bf16_split_learned_warm",
                 "fp32_cluster_tol1e-4", "fp32_streamed_tol1e-4")
-BATCHED = ALL_VARIANTS[:6]          # candidates for the headline (tolerance 1e-2 K)
+BATCHED = ALL_VARIANTS[:8]          # candidates for the headline (tolerance 1e-2 K)
+# variants stopped by the error estimate (VS_STOP_ESTIMATE) instead of the update
+ESTIMATE_RULE = ("fp32_cluster_cold_estimate", "bf16_split_cold_estimate")
 
 
 def run_ours(a):
@@ -600,8 +603,9 @@ def run_ours(a):
     B = pd.shape[0]
     stream = torch.cuda.current_stream()
     tol = 1e-2
-    mk = lambda prec, t=tol, eng=vs.VS_ENGINE_AUTO: vs.SolveParams(phy.beta_per_K, phy.alpha_per_K,
-                                                                  t, 50, prec, eng)
+    mk = lambda prec, t=tol, eng=vs.VS_ENGINE_AUTO, stop=vs.VS_STOP_UPDATE: vs.SolveParams(
+        phy.beta_per_K, phy.alpha_per_K, t, 50, prec, eng, stop_rule=stop)
+    est = vs.VS_STOP_ESTIMATE
     model, train_info = None, None
     if any(v.endswith("learned_warm") for v in wanted):
         model, train_info = _train_warm_model(vs, synth, k, w, dev, a.train_maps, a.train_epochs,
@@ -626,6 +630,8 @@ def run_ours(a):
             lambda th: vs.WarmPlan(k, pd, pl, s, th, model, mk(vs.VS_PREC_BF16_SPLIT)),
         # the on-chip pair engine (n = 256, cold) and the streamed tensor-core engine
         "bf16_split_cold": lambda th: vs.Plan(items(th), mk(vs.VS_PREC_BF16_SPLIT)),
+        "bf16_split_cold_estimate":
+            lambda th: vs.Plan(items(th), mk(vs.VS_PREC_BF16_SPLIT, stop=est)),
         "bf16_split_streamed_cold":
             lambda th: vs.Plan(items(th), mk(vs.VS_PREC_BF16_SPLIT, eng=vs.VS_ENGINE_STREAMED)),
         # FP32 with the learned warm start (its plans take the automatic engine)
@@ -635,6 +641,9 @@ def run_ours(a):
             lambda th: vs.Plan(items(th), mk(vs.VS_PREC_FP32, eng=vs.VS_ENGINE_STREAMED)),
         "fp32_cluster_cold":
             lambda th: vs.Plan(items(th), mk(vs.VS_PREC_FP32, eng=vs.VS_ENGINE_CLUSTER)),
+        # the same, stopped where the a-posteriori error estimate reaches the tolerance
+        "fp32_cluster_cold_estimate":
+            lambda th: vs.Plan(items(th), mk(vs.VS_PREC_FP32, eng=vs.VS_ENGINE_CLUSTER, stop=est)),
         "fp32_streamed_tol1e-4":
             lambda th: vs.Plan(items(th), mk(vs.VS_PREC_FP32, 1e-4, vs.VS_ENGINE_STREAMED)),
         "fp32_cluster_tol1e-4":
@@ -646,6 +655,8 @@ def run_ours(a):
         "bf16_split_streamed_cold": mk(vs.VS_PREC_BF16_SPLIT, eng=vs.VS_ENGINE_STREAMED),
         "fp32_streamed_cold": mk(vs.VS_PREC_FP32, eng=vs.VS_ENGINE_STREAMED),
         "fp32_cluster_cold": mk(vs.VS_PREC_FP32, eng=vs.VS_ENGINE_CLUSTER),
+        "bf16_split_cold_estimate": mk(vs.VS_PREC_BF16_SPLIT, stop=est),
+        "fp32_cluster_cold_estimate": mk(vs.VS_PREC_FP32, eng=vs.VS_ENGINE_CLUSTER, stop=est),
     }
     for name in ALL_VARIANTS:
         if name not in wanted:
@@ -670,8 +681,8 @@ def run_ours(a):
     plain = {}
     plain_maps = min(64, B)
     plain_out = torch.empty_like(pd[:plain_maps])
-    for t_pl in (tol, 1e-4):
-        p32 = mk(vs.VS_PREC_FP32, t_pl)
+    for t_pl, rule in ((tol, vs.VS_STOP_UPDATE), (1e-4, vs.VS_STOP_UPDATE), (tol, est)):
+        p32 = mk(vs.VS_PREC_FP32, t_pl, stop=rule)
         plans1 = [vs.Plan([(k, pd[i], pl[i], s[i], plain_out[i])], p32) for i in range(plain_maps)]
         for pln in plans1[:4]:
             pln.run(stream)
@@ -682,7 +693,8 @@ def run_ours(a):
             pln.run(stream)
         e1.record(stream)
         torch.cuda.synchronize()
-        plain["tol_%g" % t_pl] = plain_maps / (e0.elapsed_time(e1) * 1e-3)
+        plain["tol_%g%s" % (t_pl, "_estimate" if rule == est else "")] = \
+            plain_maps / (e0.elapsed_time(e1) * 1e-3)
         for pln in plans1:
             pln.close()
     # the allocating convenience call, one map per vs_solve_steady (a plan
@@ -695,7 +707,8 @@ def run_ours(a):
         vs.solve_steady(k, pd[i], pl[i], s[i], p32, plain_out[i])
     torch.cuda.synchronize()
     plain_alloc = min(32, B) / (time.perf_counter() - t0)
-    plain_value = plain["tol_%g" % tol]
+    # plain takes the headline's stopping rule
+    plain_value = plain["tol_%g%s" % (tol, "_estimate" if best in ESTIMATE_RULE else "")]
     del plain_out
 
     # The transient (1024^2, 200 steps of 1 ms, Markov power trace) and the
@@ -917,14 +930,16 @@ def run_ours(a):
                     "kernel": kern, "note": note}
 
         roofs = {}
-        if "fp32_cluster_cold" in results:
-            roofs["fp32_cluster_cold"] = alu_roof("fp32_cluster_cold", "k_solve_cluster")
+        for name in ("fp32_cluster_cold", "fp32_cluster_cold_estimate"):
+            if name in results:
+                roofs[name] = alu_roof(name, "k_solve_cluster")
         if "fp32_streamed_cold" in results:
             roofs["fp32_streamed_cold"] = alu_roof("fp32_streamed_cold", "k_solve_steady")
         if "fp32_learned_warm" in results:
             roofs["fp32_learned_warm"] = alu_roof("fp32_learned_warm", "k_solve_cluster")
-        if "bf16_split_cold" in results:
-            roofs["bf16_split_cold"] = tc_roof("bf16_split_cold", False, w.n == 256)
+        for name in ("bf16_split_cold", "bf16_split_cold_estimate"):
+            if name in results:
+                roofs[name] = tc_roof(name, False, w.n == 256)
         if "bf16_split_streamed_cold" in results:
             roofs["bf16_split_streamed_cold"] = tc_roof("bf16_split_streamed_cold", False, False)
         if "bf16_split_learned_warm" in results:
@@ -960,12 +975,15 @@ def run_ours(a):
             "variants": results,
             "fastest_vs_plain": bv["value"] / plain_value,
             "plain": {"value": plain_value, "unit": UNIT, "tol_1e-4": plain["tol_0.0001"],
+                      "update_rule": plain["tol_%g" % tol],
+                      "estimate_rule": plain["tol_%g_estimate" % tol],
                       "per_call_alloc": plain_alloc,
                       "how": "FP32 (automatic engine), one map per launch: %d one-map plans made "
                              "before timing, run in sequence on one stream, CUDA events, cold "
                              "start, tol %g K (value) and 1e-4 K; per_call_alloc = one "
                              "vs_solve_steady call per map (plan created, run, read back and "
-                             "freed every call), wall time over 32 maps" % (plain_maps, tol)},
+                             "freed every call), wall time over 32 maps; value takes the "
+                             "headline's stopping rule" % (plain_maps, tol)},
             "chosen_form": chosen,
             "warm_start_model": train_info,
             **extras,

@@ -12,7 +12,9 @@ physics : layer-stack spectrum g^(k), the fast-decaying top-layer
           half-space closed form, and the spectral kernel K~ of the imaged die.
 solve   : the mirror-image convolution (direct summation and dense-cosine
           spectral form), the leakage/conductivity fixed point (plain Picard on
-          the unsplit equation, and the mean/variation split), the fixed point
+          the unsplit equation, the mean/variation split, and the engines'
+          preconditioned iteration from the uniform start with the update and
+          the error-estimate stopping rules), the fixed point
           with a piecewise-linear leakage and kappa(T) through the Kirchhoff
           transform, the paper's one-shot closed form, and the transient
           Duhamel superposition with its windowed and implicit-leakage variants.

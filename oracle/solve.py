@@ -144,6 +144,72 @@ def picard_split(Kt, p_dyn, p_leak0, s, beta, alpha, tol=1e-8, max_iter=400):
     raise SolveError("no convergence")
 
 
+def picard_uniform_start(Kt, p_dyn, p_leak0, s, beta, alpha, tol, stop="update",
+                         max_iter=100, guard=0.05):
+    """The preconditioned iteration of the GPU engines, in FP64, with both
+    stopping rules (a reading of this project: the paper iterates until the
+    temperatures settle, Sec. V-C, and states no rule).
+
+    Start: the die's uniform mode, the scalar fixed point
+      u_bar = K00 (mean P_dyn + mu (1 + beta theta_bar)), theta_bar = u_bar / (1 - alpha u_bar),
+    K00 the kernel's response to a uniform unit source; every cell starts at
+    theta_bar (u_0 = phi^-1(theta_bar) = theta_bar / (s (1 + alpha theta_bar))).
+    Preconditioner b = beta mu (1 + 2 alpha u_bar) (about the mean of
+    beta P_leak0 dtheta/du), the mean/variation split of Sec. IV-C with the
+    multiplier K~ / (1 - b K~) of Eq. 21:
+      u_{n+1} = L_b[P_dyn + P_leak0 (1 + beta theta_n) - b u_n],  theta = phi(u),
+    which has the fixed point of `picard` for every b.
+    Stopping, with r_n = max |theta_n - theta_{n-1}|:
+      "update":   r_n <= tol;
+      "estimate": from n = 2 on, the a-posteriori error estimate of a
+                  contraction, r_n q / (1 - q) <= tol with q = min(0.9,
+                  4 r_n / r_{n-1}) (the factor seen over the last two updates,
+                  times a safety factor 4); n = 1 uses the update rule.
+    Returns (theta, iterations, updates)."""
+    n = p_dyn.shape[0]
+    mu = float(np.mean(p_leak0))
+    k00 = float(spectral_convolve(Kt, np.ones_like(p_dyn))[0, 0])
+    ub = 0.0
+    for _ in range(200):
+        ub_new = k00 * (float(np.mean(p_dyn)) + mu * (1.0 + beta * ub / (1.0 - alpha * ub)))
+        if abs(ub_new - ub) <= 1e-14 * max(1.0, abs(ub_new)):
+            ub = ub_new
+            break
+        ub = ub_new
+    b = beta * mu * (1.0 + 2.0 * alpha * ub)
+    Kb = Kt / (1.0 - b * Kt)
+    th0 = ub / (1.0 - alpha * ub)
+    theta = np.full((n, n), th0)
+    u = th0 / (s * (1.0 + alpha * th0))        # phi(u) = theta_bar at every cell
+    rs = []
+    for it in range(1, max_iter + 1):
+        u = spectral_convolve(Kb, p_dyn + p_leak0 * (1.0 + beta * theta) - b * u)
+        den = 1.0 - alpha * s * u
+        if np.min(den) <= guard:
+            raise SolveError("conductivity runaway: 1 - alpha s u <= %g" % guard)
+        new = s * u / den
+        r = float(np.max(np.abs(new - theta)))
+        theta = new
+        rs.append(r)
+        if stop_test(rs, tol, stop):
+            return theta, it, rs
+    raise SolveError("no convergence in %d iterations" % max_iter)
+
+
+def stop_test(updates, tol, stop="update"):
+    """Stopping rule after the iterate whose update is updates[-1] (the
+    updates r_1 .. r_n so far, r = max |theta_n - theta_{n-1}|).
+    "update": r_n <= tol. "estimate": for n >= 2, the error of a contraction
+    with factor q after iterate n is at most r_n q / (1 - q) (the tail of the
+    geometric series of the following updates); q is estimated as
+    min(0.9, 4 r_n / r_{n-1}); stop when that estimate is <= tol."""
+    r = updates[-1]
+    if stop == "estimate" and len(updates) > 1:
+        q = min(0.9, 4.0 * r / updates[-2])
+        return r * q <= tol * (1.0 - q)
+    return r <= tol
+
+
 def shift_invariant(Kt, p_dyn, p_leak0, beta):
     """Closed form for a uniform leakage map (no variation, alpha = 0):
     u = IDCT(DCT(P_dyn + mu) K~ / (1 - beta mu K~)) (Eq. 21 with alpha = 0)."""

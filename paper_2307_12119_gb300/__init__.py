@@ -37,6 +37,7 @@ VS_WARM_FIRST, VS_WARM_PREDICT, VS_WARM_SOLVE, VS_WARM_ALL = 1, 2, 4, 7
 VS_LEAK_LAGGED, VS_LEAK_IMPLICIT, VS_MAX_WINDOW = 0, 1, 256
 VS_CF_CONV, VS_CF_IMPULSE = 0, 1
 VS_COND_LINEAR, VS_COND_KIRCHHOFF = 0, 1
+VS_STOP_UPDATE, VS_STOP_ESTIMATE = 0, 1
 VS_MAX_LAYERS = 8
 
 EXPORTS = [
@@ -89,7 +90,7 @@ class _SolveParams(C.Structure):
                 ("max_iter", C.c_int), ("precision", C.c_int), ("engine", C.c_int),
                 ("conductivity", C.c_int), ("eta", C.c_double), ("t_amb_K", C.c_double),
                 ("leak_points", C.c_int), ("leak_theta_K", C.c_double * VS_MAX_LEAK_POINTS),
-                ("leak_g", C.c_double * VS_MAX_LEAK_POINTS)]
+                ("leak_g", C.c_double * VS_MAX_LEAK_POINTS), ("stop_rule", C.c_int)]
 
 
 class _SolveInfo(C.Structure):
@@ -269,6 +270,7 @@ class SolveParams:
     eta: float = 0.0
     t_amb_K: float = 0.0
     leak_table: Optional[Sequence] = None  # [(theta_K, g), ...]: piecewise-linear leakage
+    stop_rule: int = 0                    # VS_STOP_UPDATE or VS_STOP_ESTIMATE
 
     def _c(self) -> _SolveParams:
         c = _SolveParams(self.beta_per_K, self.alpha_per_K, self.tol_K, self.max_iter,
@@ -279,6 +281,7 @@ class SolveParams:
                 break
             c.leak_theta_K[i] = x
             c.leak_g[i] = g
+        c.stop_rule = self.stop_rule
         return c
 
 

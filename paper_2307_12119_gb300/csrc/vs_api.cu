@@ -82,6 +82,8 @@ int vs_validate_params(const vs_solve_params* p) {
   if (p->engine != VS_ENGINE_AUTO && p->engine != VS_ENGINE_STREAMED &&
       p->engine != VS_ENGINE_CLUSTER)
     return vs_set_error(VS_ERR_INVALID_ARG, "unknown engine %d", p->engine);
+  if (p->stop_rule != VS_STOP_UPDATE && p->stop_rule != VS_STOP_ESTIMATE)
+    return vs_set_error(VS_ERR_INVALID_ARG, "unknown stopping rule %d", p->stop_rule);
   if (p->conductivity != VS_COND_LINEAR && p->conductivity != VS_COND_KIRCHHOFF)
     return vs_set_error(VS_ERR_INVALID_ARG, "unknown conductivity model %d", p->conductivity);
   if (p->conductivity == VS_COND_KIRCHHOFF &&

@@ -590,7 +590,7 @@ __global__ void __launch_bounds__(ClShape<N>::THREADS, ClShape<N>::MIN_BLOCKS)
       } else if (ff & kFlagRunaway) {
         status = VS_ERR_RUNAWAY;
         stop = true;
-      } else if (rr <= P.tol) {
+      } else if (converged(rr, prev, it, P.tol, P.stop_rule)) {
         status = VS_OK;
         stop = true;
       } else {

@@ -35,6 +35,19 @@ struct MapDesc {
   int row_off, col_off, part_off;
 };
 
+// Convergence test of iterate `it` with update r (max |theta_n - theta_{n-1}|)
+// and the previous update prev. VS_STOP_UPDATE: r <= tol. VS_STOP_ESTIMATE
+// (from the second iterate on): the a-posteriori error estimate r q / (1 - q)
+// <= tol, q = min(0.9, 4 r / prev) the contraction factor seen over the last
+// two updates with a safety factor of 4.
+__device__ __forceinline__ bool converged(float r, float prev, int it, float tol, int rule) {
+  if (rule == VS_STOP_ESTIMATE && it > 1) {
+    const float q = fminf(0.9f, 4.f * __fdividef(r, prev));
+    return r * q <= tol * (1.f - q);
+  }
+  return r <= tol;
+}
+
 // Sum of one double per thread over the block (valid in thread 0).
 __device__ __forceinline__ double block_sum(double v, double* red) {
   for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
@@ -58,6 +71,7 @@ struct ClusterDev {
   vs_solve_info* info;
   int max_iter;
   float beta, alpha, tol;
+  int stop_rule;         // VS_STOP_*
 };
 
 // Launch shape of the cluster kernel for grid side n: CTAs per cluster,

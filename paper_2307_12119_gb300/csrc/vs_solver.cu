@@ -77,6 +77,7 @@ struct PlanDev {
   int n_maps, row_tasks, col_tasks;
   int max_iter;
   float beta, alpha, tol;
+  int stop_rule;         // VS_STOP_* (steady solves)
   int n_steps;           // transient
   int warm;              // some map has a warm start
   int window;            // transient: 0 untruncated, K >= 1 step responses settled from age K on
@@ -635,7 +636,7 @@ __device__ void decide(const PlanDev& P, int it) {
       } else if (s.flags & kFlagRunaway) {
         s.active = 0;
         s.status = VS_ERR_RUNAWAY;
-      } else if (r <= P.tol) {
+      } else if (converged(r, s.prev_resid, it, P.tol, P.stop_rule)) {
         s.active = 0;
         s.status = VS_OK;
       } else {
@@ -1742,6 +1743,7 @@ int plan_launch_cluster(vs_plan_t* p, cudaStream_t s) {
     P.beta = (float)p->params.beta_per_K;
     P.alpha = (float)p->params.alpha_per_K;
     P.tol = (float)p->params.tol_K;
+    P.stop_rule = p->params.stop_rule;
     if (p->tcc) {
       int rc = vs_tcc_launch(P, g.second, s);
       if (rc != VS_OK) return rc;
@@ -1779,6 +1781,7 @@ int plan_launch(vs_plan_t* p, cudaStream_t s, bool transient) {
   P.beta = (float)p->params.beta_per_K;
   P.alpha = (float)p->params.alpha_per_K;
   P.tol = (float)p->params.tol_K;
+  P.stop_rule = p->params.stop_rule;
   P.n_steps = p->transient_steps;
   P.warm = p->warm;
   const vs_solve_params& pp = p->params;
@@ -2156,6 +2159,8 @@ extern "C" int vs_solve_transient_ex(vs_kernel k, int n_steps, const float* p_dy
   if (rc) return rc;
   if (vs_params_physics(params))
     return vs_set_error(VS_ERR_INVALID_ARG, "the transient runs the linear models only");
+  if (params->stop_rule != VS_STOP_UPDATE)
+    return vs_set_error(VS_ERR_INVALID_ARG, "the transient takes the update stopping rule only");
   const vs_transient_opts o = opts ? *opts : vs_transient_opts{0, VS_LEAK_LAGGED};
   if (o.window < 0 || o.window > VS_MAX_WINDOW)
     return vs_set_error(VS_ERR_INVALID_ARG, "window %d not in 0..%d", o.window, VS_MAX_WINDOW);
@@ -2363,6 +2368,7 @@ extern "C" int vs_solve_steady_noalloc(vs_kernel k, const float* p_dyn, const fl
   P.beta = (float)params->beta_per_K;
   P.alpha = (float)params->alpha_per_K;
   P.tol = (float)params->tol_K;
+  P.stop_rule = params->stop_rule;
   P.n_steps = 0;
   P.warm = 0;
   P.adaptive = 1;

@@ -55,6 +55,7 @@ using vsk::ClusterDev;
 using vsk::MapDesc;
 using vsk::kFlagNonfinite;
 using vsk::kFlagRunaway;
+using vsk::converged;
 
 namespace {
 
@@ -666,7 +667,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_solve_tcc(TccArgs a) {
     } else if (ff & kFlagRunaway) {
       status = VS_ERR_RUNAWAY;
       stop = true;
-    } else if (rr <= P.tol) {
+    } else if (converged(rr, prev, it, P.tol, P.stop_rule)) {
       status = VS_OK;
       stop = true;
     } else {

@@ -57,7 +57,6 @@ struct TrArgs {
   const float* trA;        // [p][q] primary-alias weight
   const float* trRho;      // [p][q] exp(-dt / (C g))
   const float2* tw4n;
-  const int* digrev;
   TrCtrl* ctrl;
   int n_steps;
   float beta, alpha;
@@ -94,22 +93,25 @@ __device__ bool tr_barrier(TrCtrl* c, unsigned& target) {
   return tr_ld_acquire(&c->abort) == 0u;
 }
 
-// Radix schedule of a length-N FFT (16s first, then the remaining factor),
-// at compile time: radix and block length L of pass p, and the offset of its
-// twiddles in the per-pass table (entries W_L^{j r}, j < L / R, 1 <= r < R,
-// stored at (r - 1) L / R + j so that consecutive butterflies j read
-// consecutive entries: no bank conflicts, unlike strided reads of one W_4N
-// table).
+// Radix schedule of a length-N FFT at compile time: radix and block length L
+// of pass p, and the offset of its twiddles in the per-pass table (entries
+// W_L^{j r}, j < L / R, 1 <= r < R, stored at (r - 1) L / R + j so that
+// consecutive butterflies j read consecutive entries: no bank conflicts,
+// unlike strided reads of one W_4N table). N = 1024 runs 8, 8, 16 (the two
+// radix-8 passes give all 512 threads of a CTA a butterfly, where 16, 16, 4
+// left half of them idle in two passes); other N run 16s first, then the
+// remaining factor.
 template <int N>
 struct TrSched {
   __host__ __device__ static constexpr int radix(int p) {
+    if (N == 1024) return p < 2 ? 8 : 16;
     int n = N;
     for (int i = 0; i < p; ++i) n /= (n >= 16 ? 16 : n);
     return n >= 16 ? 16 : n;
   }
   __host__ __device__ static constexpr int passes() {
     int n = N, q = 0;
-    while (n > 1) { n /= (n >= 16 ? 16 : n); ++q; }
+    while (n > 1) { n /= radix(q); ++q; }
     return q;
   }
   __host__ __device__ static constexpr int len(int p) {
@@ -123,6 +125,17 @@ struct TrSched {
     return o;
   }
   static constexpr int TW = tw_off(passes());            // entries of the table (< N)
+  // position of frequency k in the forward output (decimation in frequency):
+  // its mixed-radix digits, pass 0's least significant, each times the
+  // sub-stride L / R of its pass
+  __host__ __device__ static constexpr int digit_reversed(int k) {
+    int pos = 0;
+    for (int p = 0; p < passes(); ++p) {
+      pos += (k % radix(p)) * (len(p) / radix(p));
+      k /= radix(p);
+    }
+    return pos;
+  }
 };
 
 template <int N, int R>
@@ -230,7 +243,7 @@ __global__ void __launch_bounds__(TrShape<N, R>::THREADS, 1) k_transient_fast(Tr
   const size_t nn = (size_t)N * N;
   for (int i = tid; i < N; i += T) {
     tw[i] = __ldg(&a.tw4n[i]);
-    dr[i] = __ldg(&a.digrev[i]);
+    dr[i] = TrSched<N>::digit_reversed(i);
   }
   {
     // W_L^{j r} = W_4N^{j r 4N / L}, pass by pass
@@ -478,7 +491,6 @@ int vs_transient_fast(vs_kernel k, int n_steps, const float* p_dyn_trace, const 
   a.trA = k->trA;
   a.trRho = k->trRho;
   a.tw4n = k->fft->tw4n;
-  a.digrev = k->fft->digrev;
   a.ctrl = ctrl;
   a.n_steps = n_steps;
   a.beta = (float)params->beta_per_K;

@@ -88,6 +88,10 @@ def test_solve_params_marshal_the_physics_variants():
     # the default struct selects the linear models
     d = vs.SolveParams()._c()
     assert d.conductivity == vs.VS_COND_LINEAR and d.leak_points == 0
+    # ... and the update stopping rule; the last field of the C struct
+    assert d.stop_rule == vs.VS_STOP_UPDATE
+    assert vs.SolveParams(stop_rule=vs.VS_STOP_ESTIMATE)._c().stop_rule == 1
+    assert ctypes.sizeof(vs._SolveParams) == vs._SolveParams.stop_rule.offset + 8
 
 
 def test_invalid_physics_parameters_need_no_gpu(libpath):
@@ -99,7 +103,8 @@ def test_invalid_physics_parameters_need_no_gpu(libpath):
     cases = (({"conductivity": 3}, "conductivity model"),
              ({"conductivity": vs.VS_COND_KIRCHHOFF, "eta": 1.0, "t_amb_K": 300.0}, "Kirchhoff"),
              ({"leak_table": [(0.0, 1.0)]}, "leak_points"),
-             ({"leak_table": [(5.0, 1.0), (1.0, 2.0)]}, "must increase"))
+             ({"leak_table": [(5.0, 1.0), (1.0, 2.0)]}, "must increase"),
+             ({"stop_rule": 2}, "stopping rule"))
     for kw, msg in cases:
         prm = vs.SolveParams(**kw)._c()
         item = (vs._BatchItem * 1)()

@@ -68,3 +68,22 @@ def test_noalloc_rejects_other_engines_and_precisions():
         assert "streamed engine only" in vs.lib().vs_last_error().decode()
     rc, info = _call_noalloc(vs, k, pd[0], pl[0], s[0], vs_params(w, engine=vs.VS_ENGINE_STREAMED), out)
     assert rc == vs.VS_OK and info.status == vs.VS_OK
+
+
+def test_noalloc_takes_the_stopping_rule():
+    """The error-estimate rule reaches the streamed engine behind the entry
+    point: it stops as a one-map streamed plan with that rule does."""
+    import paper_2307_12119_gb300 as vs
+    w = synth.workload("c3_256")
+    k = vs.Kernel(vs_stack(w), vs.Grid(w.n, w.die_m))
+    pd, pl, s = inputs(w, count=1)
+    prm = vs_params(w, tol=1e-2, engine=vs.VS_ENGINE_STREAMED, stop_rule=vs.VS_STOP_ESTIMATE)
+    out, ref = torch.empty_like(pd[0]), torch.empty_like(pd[0])
+    rc, info = _call_noalloc(vs, k, pd[0], pl[0], s[0], prm, out)
+    assert rc == vs.VS_OK and info.status == vs.VS_OK
+    _, rinfo = vs.solve_steady(k, pd[0], pl[0], s[0], prm, ref)
+    assert abs(info.iterations - rinfo["iterations"]) <= 1
+    assert float((out - ref).abs().max()) <= ENG_TOL_K
+    upd = vs_params(w, tol=1e-2, engine=vs.VS_ENGINE_STREAMED)
+    rc, uinfo = _call_noalloc(vs, k, pd[0], pl[0], s[0], upd, out)
+    assert rc == vs.VS_OK and info.iterations <= uinfo.iterations
