@@ -212,10 +212,12 @@ def ablation_inputs(pl, s, s_var, l_var):
     return pl_x, (s if s_var else None)
 
 
-def effect_ablation(vs, k, w, pd, pl, s, mk):
+def effect_ablation(vs, k, w, pd, pl, s, mk, maps=None):
     """Max deviation of each scenario from the all-effects solve, per map, as
     K and as % of the all-effects maximum rise (the paper's percent deviation),
-    plus the one-shot closed form in the last row as the paper has its method."""
+    plus the one-shot closed form in the last row as the paper has its method.
+    `maps`, if a dict, receives every scenario's temperature maps by name
+    ("all effects" for the reference solve)."""
     import torch
     phy = w.physics
     B = pd.shape[0]
@@ -229,9 +231,13 @@ def effect_ablation(vs, k, w, pd, pl, s, mk):
 
     full, bad = solve(pl, s, phy.beta_per_K, phy.alpha_per_K)
     rise = full.amax(dim=(1, 2))
+    if maps is not None:
+        maps["all effects"] = full
     rows = []
 
     def row(name, th, nb):
+        if maps is not None:
+            maps[name] = th
         dev = (th - full).abs().amax(dim=(1, 2))
         rows.append({"effects": name, "max_rise_K_mean": float(th.amax(dim=(1, 2)).mean()),
                      "max_dev_K_mean": float(dev.mean()), "max_dev_K_max": float(dev.max()),
