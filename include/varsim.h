@@ -407,10 +407,29 @@ int vs_solve_batch(const vs_batch_item* items_host, int n_items,
  * map gets exactly the result vs_solve_batch gives it. Ordered after work
  * already queued on `stream`; returns when theta (and info_host, count entries,
  * if not NULL) are complete in host memory. Allocates its device buffers per
- * call. Returns the worst per-map status. */
+ * call (a vs_host_plan, below, keeps them). Returns the worst per-map status. */
 int vs_solve_batch_host(vs_kernel k, int count, const float* p_dyn, const float* p_leak0,
                         const float* s_kappa, float* theta, const vs_solve_params* params,
                         vs_solve_info* info_host, int chunk_maps, void* stream);
+
+/* The same as a reusable object: vs_host_plan_create allocates the internal
+ * streams, the two device buffer slots (4 arrays of chunk maps each, 3 without
+ * s), pinned staging for the per-map outcomes and the plans of the chunks, for
+ * `count` maps of grid k->n with (with_s = 1) or without (0) a conductivity
+ * field; chunk_maps as above. The chunk plans take the launch shape the
+ * autotuner cached for their kind, else the default, without timing runs
+ * (their buffers hold no maps yet). The kernel must outlive the host plan.
+ * vs_host_plan_run then solves one batch of host arrays exactly as
+ * vs_solve_batch_host does (same ordering on `stream`, same return), with no
+ * allocation; s_kappa must be non-NULL exactly when with_s = 1
+ * (VS_ERR_INVALID_ARG otherwise). Runs of one host plan must not overlap.
+ * vs_host_plan_free releases everything (NULL is a no-op). */
+typedef struct vs_host_plan_t* vs_host_plan;
+int vs_host_plan_create(vs_kernel k, int count, int with_s, const vs_solve_params* params,
+                        int chunk_maps, vs_host_plan* out);
+int vs_host_plan_run(vs_host_plan plan, const float* p_dyn, const float* p_leak0,
+                     const float* s_kappa, float* theta, vs_solve_info* info_host, void* stream);
+void vs_host_plan_free(vs_host_plan plan);
 
 /* ------------------------------------------------------------------------ */
 /* Transient (Sec. IV-D/E, Eqs. 27-37).                                     */

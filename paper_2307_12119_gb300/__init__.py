@@ -20,7 +20,7 @@ __all__ = [
     "VS_OK", "VS_ERR_INVALID_ARG", "VS_ERR_CUDA", "VS_ERR_OOM", "VS_ERR_NO_CONVERGENCE",
     "VS_ERR_RUNAWAY", "VS_ERR_NONFINITE", "VS_ERR_TIMEOUT", "VarsimError", "Stack", "Grid",
     "KernelOpts", "SolveParams", "Kernel", "Plan", "lib", "lib_path", "solve_steady",
-    "solve_batch", "solve_batch_host", "solve_transient", "hankel_radial", "EXPORTS",
+    "solve_batch", "solve_batch_host", "HostPlan", "solve_transient", "hankel_radial", "EXPORTS",
     "solve_steady_noalloc",
     "tc_transform", "VS_PREC_FP32", "VS_PREC_BF16_SPLIT", "VS_ENGINE_AUTO",
     "VS_ENGINE_STREAMED", "VS_ENGINE_CLUSTER", "Model", "WarmPlan",
@@ -48,7 +48,8 @@ EXPORTS = [
     "vs_tc_transform", "vs_model_create", "vs_free_model", "vs_model_nparams",
     "vs_model_get_params", "vs_model_set_params", "vs_model_forward", "vs_model_loss_grad",
     "vs_model_train", "vs_model_save", "vs_model_load", "vs_warm_features", "vs_warm_target",
-    "vs_warm_apply", "vs_solve_batch_host", "vs_model_shape", "vs_warm_plan_create",
+    "vs_warm_apply", "vs_solve_batch_host", "vs_host_plan_create", "vs_host_plan_run",
+    "vs_host_plan_free", "vs_model_shape", "vs_warm_plan_create",
     "vs_warm_plan_run", "vs_warm_plan_launches", "vs_warm_plan_info", "vs_warm_plan_free",
     "vs_solve_transient_ex", "vs_solve_closed_form", "vs_plan_create_shaped", "vs_plan_shape",
     "vs_model_forward_tc",
@@ -147,6 +148,9 @@ def lib():
                                 C.POINTER(_SolveInfo), vp]),
         "vs_solve_batch_host": (ip, [vp, ip, vp, vp, vp, vp, C.POINTER(_SolveParams),
                                      C.POINTER(_SolveInfo), ip, vp]),
+        "vs_host_plan_create": (ip, [vp, ip, ip, C.POINTER(_SolveParams), ip, C.POINTER(vp)]),
+        "vs_host_plan_run": (ip, [vp, vp, vp, vp, vp, C.POINTER(_SolveInfo), vp]),
+        "vs_host_plan_free": (None, [vp]),
         "vs_solve_transient": (ip, [vp, ip, vp, vp, vp, C.POINTER(_SolveParams), vp,
                                     C.POINTER(_SolveInfo), vp]),
         "vs_solve_transient_ex": (ip, [vp, ip, vp, vp, vp, C.POINTER(_SolveParams),
@@ -501,6 +505,45 @@ def solve_batch_host(kernel: Kernel, p_dyn, p_leak0, s_kappa=None, theta=None,
                                      int(chunk_maps), _stream(stream)),
            "vs_solve_batch_host", ok=_SOLVE_OK)
     return theta, [_info(i) for i in info]
+
+
+class HostPlan:
+    """vs_host_plan_*: the host-memory batch solve as a reusable object (streams,
+    device buffer slots and chunk plans made once); run() takes host (CPU)
+    tensors [count, n, n] and returns (theta, info list)."""
+
+    def __init__(self, kernel: Kernel, count: int, with_s: bool = True,
+                 params: Optional[SolveParams] = None, chunk_maps: int = 0):
+        self.kernel, self.count, self.with_s = kernel, count, bool(with_s)
+        prm = params or SolveParams()
+        h = C.c_void_p()
+        _check(lib().vs_host_plan_create(kernel.handle, count, int(self.with_s), C.byref(prm._c()),
+                                         int(chunk_maps), C.byref(h)), "vs_host_plan_create")
+        self.handle = h.value
+
+    def run(self, p_dyn, p_leak0, s_kappa=None, theta=None, stream=None):
+        import torch
+        n, count = self.kernel.n, self.count
+        if theta is None:
+            theta = torch.empty((count, n, n), dtype=torch.float32, pin_memory=p_dyn.is_pinned())
+        info = (_SolveInfo * count)()
+        _check(lib().vs_host_plan_run(self.handle, _host_ptr(p_dyn, n, count, "p_dyn"),
+                                      _host_ptr(p_leak0, n, count, "p_leak0"),
+                                      _host_ptr(s_kappa, n, count, "s_kappa", allow_none=True),
+                                      _host_ptr(theta, n, count, "theta"), info, _stream(stream)),
+               "vs_host_plan_run", ok=_SOLVE_OK)
+        return theta, [_info(i) for i in info]
+
+    def close(self):
+        if getattr(self, "handle", None):
+            lib().vs_host_plan_free(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 def solve_transient(kernel: Kernel, p_dyn_trace, p_leak0, s_kappa=None,

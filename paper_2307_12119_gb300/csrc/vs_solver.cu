@@ -1892,6 +1892,9 @@ bool streamed_shape_ok(int e) { return e == 2048 || e == 4096 || e == 8192 || e 
 
 }  // namespace
 
+// shape: > 0 forced; 0 the cached choice, else tuned on the plan; -1 the
+// cached choice, else the default, never timed (for plans whose buffers do
+// not hold their maps yet)
 int plan_create(const vs_batch_item* items_host, int n_items, const vs_solve_params* params,
                 int shape, vs_plan* out, void* stream);
 
@@ -1961,7 +1964,7 @@ int plan_create(const vs_batch_item* items_host, int n_items, const vs_solve_par
   p->items.assign(items_host, items_host + n_items);
   p->params = *params;
   if (tcc_ok && params->engine != VS_ENGINE_STREAMED) {
-    if (shape) {
+    if (shape > 0) {
       delete p;
       return vs_set_error(VS_ERR_INVALID_ARG, "the split-precision cluster engine has one shape (0)");
     }
@@ -1978,15 +1981,15 @@ int plan_create(const vs_batch_item* items_host, int n_items, const vs_solve_par
   }
   if (cluster_ok && params->engine != VS_ENGINE_STREAMED) {
     p->cluster = true;
-    if (shape && !cluster_shape_ok(shape)) {
+    if (shape > 0 && !cluster_shape_ok(shape)) {
       delete p;
       return vs_set_error(VS_ERR_INVALID_ARG, "cluster engine shape %d (update batch 1, 2 or 4)",
                           shape);
     }
     const std::vector<int> key = tune_key(items_host, n_items, true);
     bool tune = shape == 0 && tune_enabled(n_items);
-    p->cl_batch = shape ? shape : kClBatchDefault;
-    if (tune) {
+    p->cl_batch = shape > 0 ? shape : kClBatchDefault;
+    if (shape <= 0 && tune_enabled(n_items)) {
       std::lock_guard<std::mutex> lk(g_tune_mutex);
       auto itc = g_tuned.find(key);
       if (itc != g_tuned.end()) {
@@ -2029,15 +2032,15 @@ int plan_create(const vs_batch_item* items_host, int n_items, const vs_solve_par
   }
 
   // task size of the streamed engine: forced, cached, tuned, or the default
-  if (shape && !streamed_shape_ok(shape)) {
+  if (shape > 0 && !streamed_shape_ok(shape)) {
     delete p;
     return vs_set_error(VS_ERR_INVALID_ARG,
                         "streamed engine shape %d (task size 2048, 4096, 8192 or 16384)", shape);
   }
   const std::vector<int> key = tune_key(items_host, n_items, false);
-  int elems = shape ? shape : 8192;
+  int elems = shape > 0 ? shape : 8192;
   bool tune = shape == 0 && tune_enabled(n_items) && params->precision == VS_PREC_FP32;
-  if (tune) {
+  if (shape <= 0 && tune_enabled(n_items) && params->precision == VS_PREC_FP32) {
     std::lock_guard<std::mutex> lk(g_tune_mutex);
     auto itc = g_tuned.find(key);
     if (itc != g_tuned.end()) {

@@ -89,3 +89,32 @@ def test_host_batch_statuses_and_argument_checks():
         vs.solve_batch_host(k, pd.cpu()[:, :32], pl.cpu(), s.cpu(), params=vs_params(w))
     with pytest.raises(vs.VarsimError):
         vs.solve_batch_host(k, pd.cpu(), pl.cpu(), s.cpu(), params=vs_params(w, tol_K=0.0))
+
+
+def test_host_plan_runs_repeatedly_and_checks_its_arguments():
+    """vs_host_plan_*: one host plan, two batches in a row, each map equal to
+    the device-resident batch solve; the conductivity field must match the
+    plan's with_s."""
+    vs = _vs()
+    w = synth.workload("c3_256")
+    k = _kernel(w)
+    prm = vs_params(w, engine=2, tol=1e-2, stop_rule=vs.VS_STOP_ESTIMATE)
+    hp = vs.HostPlan(k, 9, True, prm, chunk_maps=4)
+    for seed in (synth.SEED + 71, synth.SEED + 72):
+        pd, pl, s = synth.steady_inputs(w, 9, seed=seed, device="cuda")
+        ref, iref = _device_reference(k, pd, pl, s, prm)
+        th, infos = hp.run(pd.cpu().pin_memory(), pl.cpu().pin_memory(), s.cpu().pin_memory())
+        assert torch.equal(th, ref.cpu())
+        assert [i["iterations"] for i in infos] == [i["iterations"] for i in iref]
+        assert all(i["status"] == vs.VS_OK for i in infos)
+    with pytest.raises(vs.VarsimError) as e:
+        hp.run(pd.cpu(), pl.cpu(), None)
+    assert e.value.status == vs.VS_ERR_INVALID_ARG
+    hp.close()
+    hp2 = vs.HostPlan(k, 3, False, prm)
+    th, infos = hp2.run(pd[:3].cpu(), pl[:3].cpu())
+    ref, _ = _device_reference(k, pd[:3], pl[:3], None, prm)
+    assert torch.equal(th, ref.cpu())
+    with pytest.raises(vs.VarsimError):
+        hp2.run(pd[:3].cpu(), pl[:3].cpu(), s[:3].cpu())
+    hp2.close()
