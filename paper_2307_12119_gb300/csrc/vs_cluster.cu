@@ -80,6 +80,9 @@ __device__ __forceinline__ unsigned cl_index() {
 __device__ __forceinline__ void cl_arrive_relaxed() {
   asm volatile("barrier.cluster.arrive.relaxed.aligned;" ::: "memory");
 }
+__device__ __forceinline__ void cl_arrive_release() {
+  asm volatile("barrier.cluster.arrive.release.aligned;" ::: "memory");
+}
 __device__ __forceinline__ void cl_wait() {
   asm volatile("barrier.cluster.wait.acquire.aligned;" ::: "memory");
 }
@@ -208,12 +211,65 @@ __global__ void __launch_bounds__(ClShape<N>::THREADS, ClShape<N>::MIN_BLOCKS)
     return make_float2(__shfl_sync(0xffffffffu, v.x, src), __shfl_sync(0xffffffffu, v.y, src));
   };
 
+  int status = VS_OK, iters = 0, growth = 0;
+  float prev = INFINITY;
+  double mu = 0.0;
+  bool stop = false;
+  // the residual and flags of an iterate to every CTA of the cluster
+  auto put_slots = [&]() {
+    if (t == 0) {
+      float rm = 0.f;
+      int fo = 0;
+      for (int w = 0; w < kClThreads / 32; ++w) {
+        rm = fmaxf(rm, red_f[w]);
+        fo |= red_i[w];
+      }
+      for (int r = 0; r < ranks; ++r) {
+        cl_put(cl_map(&slots->resid[rank], (unsigned)r), rm);
+        cl_put(cl_map(&slots->flags[rank], (unsigned)r), fo);
+      }
+    }
+  };
+  // the convergence decision of iterate `it` from the residuals and flags in
+  // the slots, the same in every thread of every CTA of the cluster
+  auto decide = [&](int it) {
+    float rr = 0.f;
+    int ff = 0;
+    for (int r = 0; r < ranks; ++r) {
+      rr = fmaxf(rr, slots->resid[r]);
+      ff |= slots->flags[r];
+    }
+    iters = it;
+    if (ff & kFlagNonfinite) {
+      status = VS_ERR_NONFINITE;
+      stop = true;
+    } else if (ff & kFlagRunaway) {
+      status = VS_ERR_RUNAWAY;
+      stop = true;
+    } else if (converged(rr, prev, it, P.tol, P.stop_rule)) {
+      status = VS_OK;
+      stop = true;
+    } else {
+      growth = (it > 2 && rr > prev) ? growth + 1 : 0;
+      if (it >= P.max_iter || growth >= 5) {
+        status = VS_ERR_NO_CONVERGENCE;
+        stop = true;
+      }
+    }
+    prev = rr;
+  };
+
   // Row phase. mode 1: initial source from theta_0, the warm start's map or
   // the uniform th0 (not stored); 2: iteration (brow holds the spectra of the
   // column phase, pre-twiddled, at digit-reversed places); 3: the first
   // iteration after a uniform theta_0 = th0 (not read). mu is the mean leakage
-  // of the preconditioner (source term - beta mu u).
-  auto row_phase = [&](int mode, float mu, float th0, float& resid, int& flags) {
+  // of the preconditioner (source term - beta mu u). early > 0: iterate
+  // `early` decides before the forward transform along x (the residuals are
+  // exchanged on a cluster barrier whose wait overlaps the radix-16 pass in
+  // registers), so a stopping map skips the transform's shared-memory pass
+  // and the stores into the column owners; a map that goes on then needs a
+  // cluster barrier before the next column phase, as with early = 0.
+  auto row_phase = [&](int mode, float mu, float th0, float& resid, int& flags, int early) {
     const bool iter = mode >= 2;
     if (iter) {
       // brow holds the spectra in natural frequency order: the radix-R2 pass
@@ -299,8 +355,10 @@ __global__ void __launch_bounds__(ClShape<N>::THREADS, ClShape<N>::MIN_BLOCKS)
           v[15 - r] = shfl2(make_float2(qo[0], qo[1]), partner16);
         }
       }
-      fwd16(v, j16);
-      store16(brow, v, f16, j16);
+      if (!early) {
+        fwd16(v, j16);
+        store16(brow, v, f16, j16);
+      }
     }
     // per-warp partials of the residual and flags of an iterate
     if (iter) {
@@ -315,6 +373,16 @@ __global__ void __launch_bounds__(ClShape<N>::THREADS, ClShape<N>::MIN_BLOCKS)
       red_i[warp] = flags;
     }
     __syncthreads();
+    if (early) {
+      put_slots();
+      cl_arrive_release();
+      if (p16) fwd16(v, j16);
+      cl_wait();
+      decide(early);
+      if (stop) return;
+      if (p16) store16(brow, v, f16, j16);
+      __syncthreads();
+    }
     // radix-R2 pass: Z[k], k = 16 r + blk; pair with N - k from the partner
     // lane, DCT-II post-twiddle, store into the column owner
     float2 z[R2];
@@ -426,31 +494,12 @@ __global__ void __launch_bounds__(ClShape<N>::THREADS, ClShape<N>::MIN_BLOCKS)
     }
   };
 
-  // the residual and flags of an iterate to every CTA of the cluster
-  auto put_slots = [&]() {
-    if (t == 0) {
-      float rm = 0.f;
-      int fo = 0;
-      for (int w = 0; w < kClThreads / 32; ++w) {
-        rm = fmaxf(rm, red_f[w]);
-        fo |= red_i[w];
-      }
-      for (int r = 0; r < ranks; ++r) {
-        cl_put(cl_map(&slots->resid[rank], (unsigned)r), rm);
-        cl_put(cl_map(&slots->flags[rank], (unsigned)r), fo);
-      }
-    }
-  };
   auto cluster_mu = [&]() {
     double sum = 0.0;
     for (int r = 0; r < ranks; ++r) sum += slots->part[r];
     return sum / ((double)N * N);
   };
 
-  int status = VS_OK, iters = 0, growth = 0;
-  float prev = INFINITY;
-  double mu = 0.0;
-  bool stop = false;
   // this CTA's kernel values for the multiplier table (pairs a / b of frequency
   // column j, N / 16 per thread), loaded while the cluster exchanges the
   // leakage partial sums
@@ -548,7 +597,7 @@ __global__ void __launch_bounds__(ClShape<N>::THREADS, ClShape<N>::MIN_BLOCKS)
     float r0 = 0.f;
     int f0 = 0;
     // the peers' start is already established by the barrier above
-    row_phase(1, mu_p, th0, r0, f0);
+    row_phase(1, mu_p, th0, r0, f0, 0);
     cl_sync();
   }
 
@@ -573,34 +622,17 @@ __global__ void __launch_bounds__(ClShape<N>::THREADS, ClShape<N>::MIN_BLOCKS)
       cl_sync();
       float resid = 0.f;
       int flags = 0;
-      row_phase(it == 1 && cold ? 3 : 2, mu_p, th0, resid, flags);
-      put_slots();
-      cl_sync();
-      // the same decision in every thread of every CTA of the cluster
-      float rr = 0.f;
-      int ff = 0;
-      for (int r = 0; r < ranks; ++r) {
-        rr = fmaxf(rr, slots->resid[r]);
-        ff |= slots->flags[r];
+      // from the second iterate on the decision comes before the forward
+      // transform (the first rarely stops: its update is the jump from the start)
+      const int early = it >= 2 ? it : 0;
+      row_phase(it == 1 && cold ? 3 : 2, mu_p, th0, resid, flags, early);
+      if (!early) {
+        put_slots();
+        cl_sync();
+        decide(it);
+      } else if (!stop) {
+        cl_sync();
       }
-      iters = it;
-      if (ff & kFlagNonfinite) {
-        status = VS_ERR_NONFINITE;
-        stop = true;
-      } else if (ff & kFlagRunaway) {
-        status = VS_ERR_RUNAWAY;
-        stop = true;
-      } else if (converged(rr, prev, it, P.tol, P.stop_rule)) {
-        status = VS_OK;
-        stop = true;
-      } else {
-        growth = (it > 2 && rr > prev) ? growth + 1 : 0;
-        if (it >= P.max_iter || growth >= 5) {
-          status = VS_ERR_NO_CONVERGENCE;
-          stop = true;
-        }
-      }
-      prev = rr;
       if (stop) break;
     }
   }
