@@ -141,10 +141,13 @@ struct TrSched {
   }
 };
 
-template <int N, int R>
+// N x N map, R rows (and R x-frequencies) per CTA, T threads per CTA; a CTA
+// of 256 threads is launched two to an SM.
+template <int N, int R, int NT>
 struct TrShape {
   static constexpr int F = R / 2;                       // complex FFTs per CTA and phase
-  static constexpr int THREADS = F * N < 512 ? F * N : 512;
+  static constexpr int THREADS = NT;
+  static constexpr int PER_SM = 512 / NT;
   static constexpr int NP = N + N / 16 + 1;
   // row stride of the per-mode arrays: 2 F MS = 32 (mod 32) words, so the
   // F x 32/F (column pair, frequency) items of a warp fall in distinct banks
@@ -155,7 +158,8 @@ struct TrShape {
   static constexpr size_t SMEM = (size_t)F * NP * sizeof(float2) + 4 * (size_t)R * MS * sizeof(float) +
                                  (size_t)N * sizeof(float2) + (size_t)TrSched<N>::TW * sizeof(float2) +
                                  (size_t)N * sizeof(int);
-  static_assert(F >= 1 && (F * N) % THREADS == 0 && 16 % F == 0, "shape");
+  static_assert(F >= 1 && (F * N) % THREADS == 0 && 16 % F == 0 && THREADS <= F * N &&
+                    SMEM * PER_SM <= 225 * 1024, "shape");
 };
 
 // One radix-R pass (block length L) over the F in-place FFTs of length N in
@@ -226,9 +230,9 @@ __device__ __forceinline__ void tr_fft_inverse(float2* buf, int nfft, int stride
   __syncthreads();
 }
 
-template <int N, int R>
-__global__ void __launch_bounds__(TrShape<N, R>::THREADS, 1) k_transient_fast(TrArgs a) {
-  using S = TrShape<N, R>;
+template <int N, int R, int NT>
+__global__ void __launch_bounds__(NT, 512 / NT) k_transient_fast(TrArgs a) {
+  using S = TrShape<N, R, NT>;
   constexpr int F = S::F, NP = S::NP, MS = S::MS, T = S::THREADS, CELLS = S::CELLS, half = N / 2;
   constexpr int lgN = ilog2(N), lgF = ilog2(F);
   extern __shared__ __align__(16) float2 tr_smem[];
@@ -438,15 +442,15 @@ __global__ void __launch_bounds__(TrShape<N, R>::THREADS, 1) k_transient_fast(Tr
   }
 }
 
-template <int N, int R>
+template <int N, int R, int NT>
 int launch_fast(const TrArgs& args, cudaStream_t s) {
-  using S = TrShape<N, R>;
-  VS_CUDA_TRY(cudaFuncSetAttribute((const void*)k_transient_fast<N, R>,
+  using S = TrShape<N, R, NT>;
+  VS_CUDA_TRY(cudaFuncSetAttribute((const void*)k_transient_fast<N, R, NT>,
                                    cudaFuncAttributeMaxDynamicSharedMemorySize, (int)S::SMEM));
   int dev = 0, sms = 0, per_sm = 0;
   VS_CUDA_TRY(cudaGetDevice(&dev));
   VS_CUDA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
-  VS_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_transient_fast<N, R>,
+  VS_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_transient_fast<N, R, NT>,
                                                             S::THREADS, S::SMEM));
   const int grid = N / R;
   if (per_sm * sms < grid) return -1;          // not co-resident: the caller falls back
@@ -460,7 +464,7 @@ int launch_fast(const TrArgs& args, cudaStream_t s) {
   attr[0].val.cooperative = 1;
   cfg.attrs = attr;
   cfg.numAttrs = 1;
-  cudaError_t e = cudaLaunchKernelEx(&cfg, k_transient_fast<N, R>, args);
+  cudaError_t e = cudaLaunchKernelEx(&cfg, k_transient_fast<N, R, NT>, args);
   if (e != cudaSuccess) return vs_set_error(VS_ERR_CUDA, "transient launch: %s", cudaGetErrorString(e));
   return VS_OK;
 }
@@ -504,9 +508,9 @@ int vs_transient_fast(vs_kernel k, int n_steps, const float* p_dyn_trace, const 
   if (e != cudaSuccess) rc = vs_set_error(VS_ERR_CUDA, "memset: %s", cudaGetErrorString(e));
   if (rc == VS_OK) {
     switch (n) {
-      case 256: rc = launch_fast<256, 2>(a, s); break;
-      case 512: rc = launch_fast<512, 4>(a, s); break;
-      default: rc = launch_fast<1024, 8>(a, s); break;
+      case 256: rc = launch_fast<256, 2, 256>(a, s); break;
+      case 512: rc = launch_fast<512, 4, 512>(a, s); break;
+      default: rc = launch_fast<1024, 8, 512>(a, s); break;
     }
   }
   TrCtrl hc = {};
