@@ -580,7 +580,7 @@ def _train_warm_model(vs, synth, k, w, dev, n_train, epochs, seed_base, stream):
 ALL_VARIANTS = ("fp32_cluster_cold", "fp32_cluster_cold_estimate", "fp32_streamed_cold",
                 "bf16_split_cold", "bf16_split_cold_estimate", "bf16_split_streamed_cold",
                 "fp32_learned_warm", "bf16_split_learned_warm",
-                "fp32_cluster_tol1e-4", "fp32_streamed_tol1e-4")
+                "fp32_cluster_tol1e-4", "fp32_cluster_tol1e-4_estimate", "fp32_streamed_tol1e-4")
 BATCHED = ALL_VARIANTS[:8]          # candidates for the headline (tolerance 1e-2 K)
 # variants stopped by the error estimate (VS_STOP_ESTIMATE) instead of the update
 ESTIMATE_RULE = ("fp32_cluster_cold_estimate", "bf16_split_cold_estimate")
@@ -654,6 +654,8 @@ def run_ours(a):
             lambda th: vs.Plan(items(th), mk(vs.VS_PREC_FP32, 1e-4, vs.VS_ENGINE_STREAMED)),
         "fp32_cluster_tol1e-4":
             lambda th: vs.Plan(items(th), mk(vs.VS_PREC_FP32, 1e-4, vs.VS_ENGINE_CLUSTER)),
+        "fp32_cluster_tol1e-4_estimate":
+            lambda th: vs.Plan(items(th), mk(vs.VS_PREC_FP32, 1e-4, vs.VS_ENGINE_CLUSTER, est)),
     }
     # parameters of the variants that vs_solve_batch_host can run (cold starts)
     host_params = {
