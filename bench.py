@@ -127,6 +127,7 @@ KERNEL_SOURCES = {
     "k_cf_rows_fwd": [_CSRC + "vs_closed.cu"] + _COMMON,
     "k_cf_cols": [_CSRC + "vs_closed.cu"] + _COMMON,
     "k_cf_rows_inv": [_CSRC + "vs_closed.cu"] + _COMMON,
+    "k_cf_cluster": [_CSRC + "vs_cluster.cu", _CSRC + "vs_closed.cu"] + _COMMON,
     "k_conv_fwd": [_CSRC + "vs_cnn.cu"] + _COMMON,
     "k_conv_tc": [_CSRC + "vs_conv_tc.cu", _CSRC + "vs_tc.cuh", _CSRC + "vs_internal.cuh"] + _COMMON,
     "k_solve_tcc": [_CSRC + "vs_tcc.cu", _CSRC + "vs_tc.cuh", _CSRC + "vs_internal.cuh"] + _COMMON,
@@ -807,6 +808,8 @@ def run_ours(a):
             rise_b = th_best.amax(dim=(1, 2))
             rel_err = ((th_cf - th_best).abs().amax(dim=(1, 2)) / rise_b)
             algo = B * w.n * w.n * 16                 # read P_dyn, P_leak0, s; write theta
+            on_cluster = 32 <= w.n <= 256
+            cf_kernels = ("k_cf_cluster",) if on_cluster else ("k_cf_rows_fwd", "k_cf_cols")
             cf[name] = {"value": whole_job_rate(1, B, ms_cf * 1e-3), "unit": UNIT, "ms_per_step": ms_cf,
                         "not_ok": sum(1 for i in infos_cf if i["status"] != vs.VS_OK),
                         "err_pct_of_max_rise": {"max": 100 * float(rel_err.max()),
@@ -816,13 +819,18 @@ def run_ours(a):
                                      "frac": algo / (ms_cf * 1e-3) / 1e9 / _peaks()[0],
                                      "traffic": {kn: (_traffic_record(kn)["dram_bytes_per_unit"]
                                                       * B) if _traffic_record(kn) else None
-                                                 for kn in ("k_cf_rows_fwd", "k_cf_cols")},
-                                     "kernel": "k_cf_rows_fwd + k_cf_cols + k_cf_rows_inv",
-                                     "note": "16 B/pixel algorithmic (3 maps in, theta out); the "
-                                             "three passes also move 24 B/pixel of spectra"}}
+                                                 for kn in cf_kernels},
+                                     "kernel": ("k_solve_cluster<n, 2, true> (closed-form "
+                                                "instantiation, one cluster per map)" if on_cluster
+                                                else "k_cf_rows_fwd + k_cf_cols + k_cf_rows_inv"),
+                                     "note": "16 B/pixel algorithmic (3 maps in, theta out); %s"
+                                             % ("the cluster instantiation stages u_det in theta "
+                                                "(L2) between its two inverse passes" if on_cluster
+                                                else "the three passes also move 24 B/pixel of "
+                                                     "spectra")}}
         del th_cf
-        extras["closed_form"] = dict(cf, how="vs_solve_closed_form over the %d-map batch (4 launches, "
-                                     "CUDA events, inputs > L2); error against the headline path's "
+        extras["closed_form"] = dict(cf, how="vs_solve_closed_form over the %d-map batch (CUDA "
+                                     "events, inputs > L2); error against the headline path's "
                                      "converged maps (tolerance %.0e K)" % (B, tol))
         extras["effect_ablation"] = effect_ablation(vs, k, w, pd[:ABLATION_MAPS], pl[:ABLATION_MAPS],
                                                     s[:ABLATION_MAPS], mk)

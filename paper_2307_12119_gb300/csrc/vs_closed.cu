@@ -14,6 +14,9 @@
 //          along y;
 //   rows : two inverse DCTs along x, Hadamard combination, phi;
 // and a fourth, one thread per map, that writes the per-map outcome.
+// Grids of 32^2 .. 256^2 take the cluster engine's closed-form instantiation
+// instead (vs_cluster.cu): one thread-block cluster per map, the map and its
+// spectra in shared memory, no spectral scratch in global memory.
 #include <math.h>
 #include <stdint.h>
 
@@ -22,6 +25,7 @@
 
 #include "vs_fft.cuh"
 #include "vs_internal.cuh"
+#include "vs_solve_common.cuh"
 
 using namespace vsfft;
 
@@ -254,6 +258,27 @@ __global__ void k_cf_info(CfArgs a) {
   a.info[b] = inf;
 }
 
+// Per-map descriptors of a contiguous batch for the cluster instantiation.
+__global__ void k_cf_descs(vsk::MapDesc* maps, int* order, const float* p_dyn, const float* p_leak0,
+                           const float* s, float* theta, const float* Kt, const float2* tw4n,
+                           const int* digrev, float kmax, int n, int count) {
+  const int b = blockIdx.x * blockDim.x + threadIdx.x;
+  if (b >= count) return;
+  const size_t off = (size_t)b * n * n;
+  vsk::MapDesc m = {};
+  m.p_dyn = p_dyn + off;
+  m.p_leak0 = p_leak0 + off;
+  m.s = s ? s + off : nullptr;
+  m.theta = theta + off;
+  m.Kt = Kt;
+  m.tw4n = tw4n;
+  m.digrev = digrev;
+  m.kmax = kmax;
+  m.n = n;
+  maps[b] = m;
+  order[b] = b;
+}
+
 size_t g_cf_smem_attr = 0;
 
 }  // namespace
@@ -275,6 +300,47 @@ extern "C" int vs_solve_closed_form(vs_kernel k, int count, const float* p_dyn,
   if (al & 15u) return vs_set_error(VS_ERR_INVALID_ARG, "maps must be 16-byte aligned");
   const int n = k->n;
   cudaStream_t s = (cudaStream_t)stream;
+  if (vsk::cluster_size_ok(n)) {
+    // the cluster instantiation: descriptors, order and outcomes only
+    void* scratch = nullptr;
+    const size_t b_maps = sizeof(vsk::MapDesc) * (size_t)count;
+    const size_t b_order = sizeof(int) * (size_t)count;
+    const size_t b_info = sizeof(vs_solve_info) * (size_t)count;
+    const size_t total = b_maps + b_order + b_info + 512;
+    cudaError_t e = cudaMallocAsync(&scratch, total, s);
+    if (e != cudaSuccess)
+      return vs_set_error(e == cudaErrorMemoryAllocation ? VS_ERR_OOM : VS_ERR_CUDA,
+                          "closed-form descriptors (%zu bytes): %s", total, cudaGetErrorString(e));
+    char* p = (char*)scratch;
+    vsk::MapDesc* maps = (vsk::MapDesc*)p;
+    int* order = (int*)(p + ((b_maps + 255) & ~(size_t)255));
+    vs_solve_info* info = (vs_solve_info*)((char*)order + ((b_order + 255) & ~(size_t)255) - 0);
+    k_cf_descs<<<(count + 127) / 128, 128, 0, s>>>(maps, order, p_dyn, p_leak0, s_kappa, theta,
+                                                   k->Kt32, k->fft->tw4n, k->fft->digrev, k->kmax,
+                                                   n, count);
+    e = cudaGetLastError();
+    vsk::ClusterDev P = {};
+    P.maps = maps;
+    P.order = order;
+    P.info = info;
+    P.max_iter = 1;
+    P.beta = (float)params->beta_per_K;
+    P.alpha = (float)params->alpha_per_K;
+    P.tol = (float)params->tol_K;
+    P.cf_mode = mode;
+    if (e == cudaSuccess) e = vsk::cluster_cf_launch(n, P, count, s);
+    if (e == cudaSuccess && info_host)
+      e = cudaMemcpyAsync(info_host, info, b_info, cudaMemcpyDeviceToHost, s);
+    cudaError_t ef = cudaFreeAsync(scratch, s);
+    if (e == cudaSuccess) e = ef;
+    if (e != cudaSuccess) return vs_set_error(VS_ERR_CUDA, "closed form: %s", cudaGetErrorString(e));
+    rc = VS_OK;
+    if (info_host) {
+      VS_CUDA_TRY(cudaStreamSynchronize(s));
+      for (int i = 0; i < count; ++i) rc = std::max(rc, info_host[i].status);
+    }
+    return rc;
+  }
   CfArgs a = {};
   a.p_dyn = p_dyn;
   a.p_leak0 = p_leak0;

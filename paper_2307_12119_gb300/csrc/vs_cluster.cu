@@ -132,7 +132,9 @@ __device__ __forceinline__ int cl_dr(int k) {
 // BATCH: positions of the update whose inputs (P_leak0, P_dyn, s, theta of
 // two rows) a thread loads together before using them, 1, 2 or 4: the depth of
 // the global-load pipelining, a launch shape the plan's autotuner picks.
-template <int N, int BATCH>
+// CF: the one-shot closed form (Sec. IV-C, Eqs. 21, 25, 26) instead of the
+// fixed point, on the same cluster layout (see the closed-form block below).
+template <int N, int BATCH, bool CF = false>
 __global__ void __launch_bounds__(ClShape<N>::THREADS, ClShape<N>::MIN_BLOCKS)
     k_solve_cluster(ClusterDev P) {
   constexpr int kClBatch = BATCH;
@@ -559,6 +561,229 @@ __global__ void __launch_bounds__(ClShape<N>::THREADS, ClShape<N>::MIN_BLOCKS)
   load_k();
   cl_sync();
   mu = cluster_mu();
+  if constexpr (CF) {
+    // One-shot closed form of the map (the three-pass kernels of vs_closed.cu
+    // compute the same):
+    //   u = L_det * q + (P_leak0 - mu) . r,  q = P_dyn + P_leak0,  theta = phi(u)
+    //   L_det = K / (1 - beta mu K) (Eq. 21), r = beta L_det^2 * q (Eq. 25 to
+    //   first order) or beta L_det^2 * delta_centre sum(q) (Eq. 26).
+    // Forward DCT of q along x (the first-source pass with theta_0 = 0), along
+    // y, both multipliers; the random part's spectra wait in the multiplier
+    // table's place while the L_det part goes back through the inverse
+    // transforms into theta (as a staging copy of u_det); then the random
+    // part follows and the last row pass combines the two.
+    const bool impulse = P.cf_mode == VS_CF_IMPULSE;
+    double tot_q = 0.0;
+    for (int r = 0; r < ranks; ++r) tot_q += slots->part[r] + slots->part2[r];
+    const float mu_f = (float)mu, nn = (float)N * (float)N;
+    int cf_flags = ((double)beta * mu * (double)d.kmax >= 0.999) ? kFlagRunaway : 0;
+    {
+      const float bm = beta * mu_f;
+      const float inv_n2 = 1.f / nn;
+#pragma unroll
+      for (int i = 0; i < kKv; ++i) {
+        const int it = t + i * kClThreads;
+        const int q = it % N, jj = it / N;
+        const float ka = kv[i].x, kb = kv[i].y;
+        Ls[q * kClF + (jj ^ (q & (kClF - 1)))] =
+            make_float2(ka / (1.f - bm * ka) * inv_n2, kb / (1.f - bm * kb) * inv_n2);
+      }
+      __syncthreads();
+    }
+    float r0 = 0.f;
+    int f0 = 0;
+    row_phase(1, mu_f, 0.f, r0, f0, 0);           // q = P_dyn + P_leak0, forward along x
+    cl_sync();
+    // the radix-16 inverse along y of bcol and the stores into the row owners
+    auto col_push = [&]() {
+      __syncthreads();
+      if (c16) {
+        float2 v[16];
+        load16(bcol, v, jc, j16c);
+        inv16(v, j16c);
+        const int j = j0 + jc;
+        const int pa = j, pb = j == 0 ? half : N - j;
+        const float2 twa = tw[pa], twb = tw[pb];
+        const unsigned ra = (unsigned)pad(pa) * 8u, rb = (unsigned)pad(pb) * 8u;
+#pragma unroll
+        for (int r = 0; r < 8; ++r) {
+          const float2 vb = shfl2(v[15 - r], lane ^ 16);
+          const float2 va = v[r];
+          float2 ea, eb;
+          if (j == 0) {
+            ea = dct_pre(va.x, 0.f, vb.x, 0.f, twa);
+            eb = dct_pre(va.y, va.y, vb.y, vb.y, twb);
+          } else {
+            ea = dct_pre(va.x, va.y, vb.x, vb.y, twa);
+            eb = dct_pre(va.y, va.x, vb.y, vb.x, twb);
+          }
+          const int ya = 2 * (j16c + r * M1);
+          const unsigned dst = cl_map(brow, (unsigned)(ya / kClRows)) +
+                               (unsigned)(((ya % kClRows) >> 1) * NP) * 8u;
+          cl_put(dst + ra, ea);
+          cl_put(dst + rb, eb);
+        }
+      }
+    };
+    // forward along y and both multipliers; the random part's pre-twiddled
+    // spectra go to the multiplier table's place ([r][thread]), the L_det
+    // part back to bcol
+    {
+      if (c16) {
+        float2 v[16];
+        load16(bcol, v, jc, j16c);
+        fwd16(v, j16c);
+        store16(bcol, v, jc, j16c);
+      }
+      __syncthreads();
+      float2* p = base2(bcol);
+      float2 z[R2], e1[R2], e2[R2];
+#pragma unroll
+      for (int r = 0; r < R2; ++r) z[r] = p[r];
+      dftR<R2, true>(z);
+      const int jj = f2, j = j0 + jj;
+      const int pa = j == 0 ? 0 : j, pb = j == 0 ? half : N - j;
+      // 2-D DCT-II of a unit impulse at the centre cell c = N/2:
+      // cos(pi p (2c + 1) / 2N) cos(pi k (2c + 1) / 2N)
+      auto dimp = [&](int f) { return cospif((float)((f * (N + 1)) % (4 * N)) / (float)(2 * N)); };
+      const float da = dimp(pa), db = dimp(pb);
+#pragma unroll
+      for (int r = 0; r < R2; ++r) {
+        const float2 give = blk == 0 ? z[(R2 - r) % R2] : z[R2 - 1 - r];
+        const float2 zn = shfl2(give, partner2);   // Z[N - q]
+        const int q = 16 * r + blk, qn = N - q;
+        const float2 L = Ls[q * kClF + (jj ^ (q & (kClF - 1)))];
+        const float2 y = dct_post(z[r], zn, tw[q]);
+        // random-part multiplier beta L_det^2 / N^2 = beta L^2 N^2 (L holds L_det / N^2)
+        auto rnd = [&](float2 x, float2 l, int qq) {
+          const float dq = impulse ? dimp(qq) : 0.f;
+          return make_float2((impulse ? da * dq : x.x) * beta * l.x * l.x * nn,
+                             (impulse ? db * dq : x.y) * beta * l.y * l.y * nn);
+        };
+        float2 y1 = make_float2(y.x * L.x, y.y * L.y), y2 = rnd(y, L, q);
+        float2 y1n, y2n;
+        if (q == 0) {
+          y1n = y2n = make_float2(0.f, 0.f);
+        } else if (q == half) {
+          y1n = y1;
+          y2n = y2;
+        } else {
+          const float2 Ln = Ls[qn * kClF + (jj ^ (qn & (kClF - 1)))];
+          const float2 yn = dct_post(zn, z[r], tw[qn]);
+          y1n = make_float2(yn.x * Ln.x, yn.y * Ln.y);
+          y2n = rnd(yn, Ln, qn);
+        }
+        e1[r] = dct_pre(y1.x, y1n.x, y1.y, y1n.y, tw[q]);
+        e2[r] = dct_pre(y2.x, y2n.x, y2.y, y2n.y, tw[q]);
+      }
+      dftR<R2, false>(e1);
+      dftR<R2, false>(e2);
+      __syncthreads();                              // every thread is done with Ls
+#pragma unroll
+      for (int r = 0; r < R2; ++r) {
+        p[r] = e1[r];
+        Ls[r * kClThreads + t] = e2[r];
+      }
+    }
+    col_push();                                     // L_det part -> the row owners
+    cl_sync();
+    // inverse along x of brow: v[r] = u at Makhoul position j16 + M1 r of rows
+    // ya, ya + 1 (the radix-R2 pass first, as in the row phase)
+    auto row_inverse = [&](float2* v) {
+      {
+        float2* p = brow + f2 * NP;
+        float2 w[R2];
+#pragma unroll
+        for (int r = 0; r < R2; ++r) w[r] = p[pad(blk + 16 * r)];
+        dftR<R2, false>(w);
+#pragma unroll
+        for (int r = 0; r < R2; ++r) p[pad(blk + 16 * r)] = w[r];
+      }
+      __syncthreads();
+      if (p16) {
+#pragma unroll
+        for (int r = 0; r < 16; ++r) v[r] = brow[f16 * NP + pad(16 * j16 + r)];
+      }
+      __syncthreads();
+      if (p16) inv16(v, j16);
+    };
+    const size_t row_a = (size_t)(y0 + 2 * f16) * N;
+    {
+      float2 v[16];
+      row_inverse(v);
+      if (p16) {
+        // u_det of the cells (x, x + 1) of rows ya, ya + 1, staged in theta
+#pragma unroll
+        for (int r = 0; r < 8; ++r) {
+          const float2 um = shfl2(v[15 - r], partner16);   // at x + 1 (mirror lane)
+          const int x = 2 * (j16 + r * M1);
+          *reinterpret_cast<float2*>(d.theta + row_a + x) = make_float2(v[r].x, um.x);
+          *reinterpret_cast<float2*>(d.theta + row_a + N + x) = make_float2(v[r].y, um.y);
+        }
+      }
+    }
+    cl_sync();                                      // every CTA has read its brow
+    {
+      float2* p = base2(bcol);
+#pragma unroll
+      for (int r = 0; r < R2; ++r) p[r] = Ls[r * kClThreads + t];
+    }
+    col_push();                                     // random part -> the row owners
+    cl_sync();
+    {
+      const float scale = impulse ? (float)tot_q : 1.f;
+      float2 v[16];
+      row_inverse(v);
+      if (p16) {
+#pragma unroll
+        for (int r = 0; r < 8; ++r) {
+          const float2 um = shfl2(v[15 - r], partner16);
+          const int x = 2 * (j16 + r * M1);
+#pragma unroll
+          for (int h = 0; h < 2; ++h) {
+            const size_t idx = row_a + (size_t)h * N + x;
+            float2* th = reinterpret_cast<float2*>(d.theta + idx);
+            const float2 ud = *th;
+            const float2 pl = __ldg(reinterpret_cast<const float2*>(d.p_leak0 + idx));
+            const float2 sk = d.s ? __ldg(reinterpret_cast<const float2*>(d.s + idx))
+                                  : make_float2(1.f, 1.f);
+            const float rr[2] = {h ? v[r].y : v[r].x, h ? um.y : um.x};
+            const float uu[2] = {ud.x, ud.y}, pp[2] = {pl.x, pl.y}, ss[2] = {sk.x, sk.y};
+            float o[2];
+#pragma unroll
+            for (int e = 0; e < 2; ++e) {
+              const float u = fmaf((pp[e] - mu_f) * scale, rr[e], uu[e]);
+              const float den = fmaf(-alpha * ss[e], u, 1.f);
+              if (!(den > 0.05f)) cf_flags |= kFlagRunaway;
+              o[e] = ss[e] * u / den;
+              if (!isfinite(o[e])) cf_flags |= kFlagNonfinite;
+            }
+            *th = make_float2(o[0], o[1]);
+          }
+        }
+      }
+    }
+    // the flags of the map, from every CTA
+    for (int o = 16; o > 0; o >>= 1) cf_flags |= __shfl_down_sync(0xffffffffu, cf_flags, o);
+    if (lane == 0) {
+      red_f[warp] = 0.f;
+      red_i[warp] = cf_flags;
+    }
+    __syncthreads();
+    put_slots();
+    cl_sync();
+    if (rank == 0 && t == 0) {
+      int ff = 0;
+      for (int r = 0; r < ranks; ++r) ff |= slots->flags[r];
+      vs_solve_info* inf = P.info + b;
+      inf->status = (ff & kFlagRunaway) ? VS_ERR_RUNAWAY : (ff & kFlagNonfinite) ? VS_ERR_NONFINITE : VS_OK;
+      inf->iterations = 0;
+      inf->residual_K = 0.0;
+      inf->mu_W = mu;
+      inf->fell_back = 0;
+    }
+    return;
+  }
   // Preconditioner and start. The source term - beta mu_p u and the
   // multiplier K / (1 - beta mu_p K) have the same fixed point for every mu_p.
   // A cold start solves the uniform mode of the die first (a scalar fixed
@@ -675,6 +900,38 @@ ClusterFn cluster_kernel(int n, int batch) {
     case 128: return cluster_kernel_n<128>(batch);
     default: return cluster_kernel_n<256>(batch);
   }
+}
+
+// The closed-form instantiation for grid side n (32 .. 256): one cluster per
+// map over `count` maps; shared-memory attributes set once per n.
+cudaError_t cluster_cf_launch(int n, const ClusterDev& P, int count, cudaStream_t s) {
+  static bool attr_set[4] = {};
+  ClusterFn fn = n == 32 ? k_solve_cluster<32, 2, true>
+                 : n == 64 ? k_solve_cluster<64, 2, true>
+                 : n == 128 ? k_solve_cluster<128, 2, true>
+                            : k_solve_cluster<256, 2, true>;
+  const ClHost h = cluster_shape(n);
+  const int ni = __builtin_ctz((unsigned)n) - 5;
+  if (!attr_set[ni]) {
+    cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)h.smem);
+    if (e == cudaSuccess)
+      e = cudaFuncSetAttribute(fn, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
+    if (e != cudaSuccess) return e;
+    attr_set[ni] = true;
+  }
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3((unsigned)h.ranks * (unsigned)count);
+  cfg.blockDim = dim3((unsigned)h.threads);
+  cfg.dynamicSmemBytes = h.smem;
+  cfg.stream = s;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeClusterDimension;
+  attr[0].val.clusterDim.x = (unsigned)h.ranks;
+  attr[0].val.clusterDim.y = 1;
+  attr[0].val.clusterDim.z = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, fn, P);
 }
 
 

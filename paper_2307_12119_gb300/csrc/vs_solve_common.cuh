@@ -72,6 +72,7 @@ struct ClusterDev {
   int max_iter;
   float beta, alpha, tol;
   int stop_rule;         // VS_STOP_*
+  int cf_mode;           // closed-form instantiation: VS_CF_CONV or VS_CF_IMPULSE
 };
 
 // Launch shape of the cluster kernel for grid side n: CTAs per cluster,
@@ -88,6 +89,9 @@ ClHost cluster_shape(int n);
 // The instantiation for n (32, 64, 128 or 256) and update-load batch (1, 2
 // or 4; the default launch shape is 2).
 ClusterFn cluster_kernel(int n, int batch);
+// The one-shot closed form on the cluster layout (n in [32, 256]), one
+// cluster per map of P.maps / P.order, P.cf_mode the closed-form mode.
+cudaError_t cluster_cf_launch(int n, const ClusterDev& P, int count, cudaStream_t s);
 constexpr int kClBatches[3] = {1, 2, 4};
 constexpr int kClBatchDefault = 2;
 

@@ -169,6 +169,27 @@ def test_cluster_statuses_and_isolation():
     assert float((th1 - th2).abs().max()) <= 2e-4
 
 
+@pytest.mark.parametrize("max_iter", [2, 3])
+def test_cluster_stops_at_max_iter_in_the_early_decision(max_iter):
+    """From the second iterate the cluster engine decides before the forward
+    transform along x; a map stopped there by max_iter reports
+    VS_ERR_NO_CONVERGENCE after exactly max_iter iterates, and its map is the
+    same iterate the streamed engine (which decides after the transform)
+    stops at."""
+    vs = _vs()
+    w = synth.workload("c2_256")
+    k = _kernel(w)
+    pd, pl, s = inputs(w, count=3)
+    prm = lambda eng: vs_params(w, tol=1e-9, max_iter=max_iter, engine=eng)
+    th_c, inf_c, _ = _solve(k, pd, pl, s, prm(vs.VS_ENGINE_CLUSTER))
+    th_s, inf_s, _ = _solve(k, pd, pl, s, prm(vs.VS_ENGINE_STREAMED))
+    for a, b in zip(inf_c, inf_s):
+        assert a["status"] == b["status"] == vs.VS_ERR_NO_CONVERGENCE
+        assert a["iterations"] == b["iterations"] == max_iter
+        assert abs(a["residual_K"] - b["residual_K"]) <= 1e-3 * max(1.0, b["residual_K"])
+    assert float((th_c - th_s).abs().max()) <= ENG_TOL_K
+
+
 def test_cluster_argument_checks():
     vs = _vs()
     for name in ("tiny_16", "c3_512"):               # outside [32, 256]
