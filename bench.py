@@ -89,6 +89,8 @@ def _args():
                          "of a capture over --batch maps (no GPU needed) and exit")
     ap.add_argument("--kernel", default="k_solve_cluster")
     ap.add_argument("--how", default="")
+    ap.add_argument("--match", default="",
+                    help="text of the captured kernel's name for --record-traffic (default: --kernel)")
     ap.add_argument("--variants", default="",
                     help="comma-separated subset of the variants to time (default: all)")
     ap.add_argument("--unit", default="map", help="unit of --record-traffic's --batch count")
@@ -163,18 +165,19 @@ def _traffic_record(kernel: str):
     return d
 
 
-def record_traffic(csv_path: str, kernel: str, maps: int, how: str, unit: str = "map"):
+def record_traffic(csv_path: str, kernel: str, maps: int, how: str, unit: str = "map",
+                   match: str = ""):
     """Writes the traffic record of `kernel` from `ncu -i <report> --page raw
     --csv` output: dram__bytes_read.sum + dram__bytes_write.sum of the first
-    captured launch of that kernel, divided by the units (maps, or transient
-    steps) the launch processed."""
+    captured launch whose name contains `match` (default: the record's name),
+    divided by the units (maps, or transient steps) the launch processed."""
     import csv
     rows = list(csv.reader(open(csv_path)))
     head, units = rows[0], rows[1]
     col = {name: i for i, name in enumerate(head)}
     scale = {"byte": 1.0, "Kbyte": 1e3, "Mbyte": 1e6, "Gbyte": 1e9, "KB": 1e3, "MB": 1e6, "GB": 1e9}
     for r in rows[2:]:
-        if kernel not in r[col["Kernel Name"]]:
+        if (match or kernel) not in r[col["Kernel Name"]]:
             continue
         get = lambda m: float(r[col[m]].replace(",", "")) * scale.get(units[col[m]], 1.0)
         rd, wr = get("dram__bytes_read.sum"), get("dram__bytes_write.sum")
@@ -1088,7 +1091,7 @@ def run_case(a):
 if __name__ == "__main__":
     args = _args()
     if args.record_traffic:
-        record_traffic(args.record_traffic, args.kernel, args.batch, args.how, args.unit)
+        record_traffic(args.record_traffic, args.kernel, args.batch, args.how, args.unit, args.match)
     elif args.case:
         run_case(args)
     elif args.impl == "reference":

@@ -782,8 +782,8 @@ __global__ void __launch_bounds__(ClShape<N>::THREADS, ClShape<N>::MIN_BLOCKS)
       inf->mu_W = mu;
       inf->fell_back = 0;
     }
-    return;
-  }
+    // (the fixed-point path below is not compiled into this instantiation)
+  } else {
   // Preconditioner and start. The source term - beta mu_p u and the
   // multiplier K / (1 - beta mu_p K) have the same fixed point for every mu_p.
   // A cold start solves the uniform mode of the die first (a scalar fixed
@@ -868,6 +868,7 @@ __global__ void __launch_bounds__(ClShape<N>::THREADS, ClShape<N>::MIN_BLOCKS)
     inf->residual_K = (double)prev;
     inf->mu_W = mu;
   }
+  }   // fixed-point path
 }
 
 
