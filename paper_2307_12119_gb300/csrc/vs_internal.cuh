@@ -100,8 +100,8 @@ int vs_conv_tc(const float* in, int in_ctot, int cin, const void* W, const float
 // (info filled), an error, or -1 if the launch shape does not fit the device.
 bool vs_transient_fast_ok(int n);
 int vs_transient_fast(vs_kernel k, int n_steps, const float* p_dyn_trace, const float* p_leak0,
-                      const float* s_kappa, const vs_solve_params* params, float* theta_trace,
-                      vs_solve_info* info, cudaStream_t s);
+                      const float* s_kappa, const vs_solve_params* params, int implicit,
+                      int window, float* theta_trace, vs_solve_info* info, cudaStream_t s);
 
 // ---------------------------------------------------------------- plans
 // Asynchronous copy of a plan's per-map outcome to (pinned) host memory.

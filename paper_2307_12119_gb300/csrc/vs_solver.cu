@@ -2175,11 +2175,12 @@ extern "C" int vs_solve_transient_ex(vs_kernel k, int n_steps, const float* p_dy
                  (uintptr_t)s_kappa;
   if (al & 15u) return vs_set_error(VS_ERR_INVALID_ARG, "maps must be 16-byte aligned");
   cudaStream_t s = (cudaStream_t)stream;
-  if (o.window == 0 && o.leakage == VS_LEAK_LAGGED && vs_transient_fast_ok(k->n)) {
-    // the persistent single-map engine (vs_transient.cu)
+  if ((o.window == 0 || o.leakage == VS_LEAK_LAGGED) && vs_transient_fast_ok(k->n)) {
+    // the persistent single-map engine (vs_transient.cu): lagged leakage with or
+    // without a window, or implicit leakage without one
     vs_solve_info inf = {};
-    const int r = vs_transient_fast(k, n_steps, p_dyn_trace, p_leak0, s_kappa, params, theta_trace,
-                                    &inf, s);
+    const int r = vs_transient_fast(k, n_steps, p_dyn_trace, p_leak0, s_kappa, params,
+                                    o.leakage == VS_LEAK_IMPLICIT, o.window, theta_trace, &inf, s);
     if (r != -1) {
       if (info_host && (r == VS_OK || r >= VS_ERR_NO_CONVERGENCE)) *info_host = inf;
       return r;

@@ -46,6 +46,13 @@ struct TrCtrl {
   unsigned count[2][32];
   unsigned abort;
   int flags;
+  // implicit leakage: the iterates' largest change (float bits, two words
+  // used alternately), iterations over all steps, the largest final change,
+  // and whether a step ended unconverged
+  unsigned resid[2];
+  int iters;
+  float max_resid;
+  int growth;
 };
 
 struct TrArgs {
@@ -61,6 +68,10 @@ struct TrArgs {
   TrCtrl* ctrl;
   int n_steps;
   float beta, alpha;
+  float tol;               // implicit leakage: per-step fixed point
+  int max_iter;
+  int window;              // WIN: step responses settled from age `window` on (>= 1)
+  float* ring;             // WIN, window >= 2: [window - 1][N][N] the last sources per mode
 };
 
 __device__ __forceinline__ unsigned tr_ld_acquire(const unsigned* p) {
@@ -230,7 +241,18 @@ __device__ __forceinline__ void tr_fft_inverse(float2* buf, int nfft, int stride
   __syncthreads();
 }
 
-template <int N, int R, int NT>
+// IMPL: implicit leakage (the leakage of step n at theta_n): each step
+// iterates the column and row phases from theta_{n-1} until the largest
+// change is <= tol (or max_iter), the recursion state W committed with the
+// source of the step's last iterate; the decision of an iterate is read by
+// every CTA from the same word after a grid barrier.
+// WIN: the window of Sec. IV-E with lagged leakage: step responses older than
+// `window` steps are taken as settled, S_j = K for j >= window, so a mode's
+// response is Y_n = K X_n - A sum_{j < window} rho^j (X_{n-j+1} - X_{n-j})
+// from a ring of its last window - 1 sources (X_m in slot m mod (window - 1),
+// in global memory: the CTA's own modes, L2-resident); window 1 is the
+// settled response K X_n.
+template <int N, int R, int NT, bool IMPL, bool WIN = false>
 __global__ void __launch_bounds__(NT, 512 / NT) k_transient_fast(TrArgs a) {
   using S = TrShape<N, R, NT>;
   constexpr int F = S::F, NP = S::NP, MS = S::MS, T = S::THREADS, CELLS = S::CELLS, half = N / 2;
@@ -246,6 +268,7 @@ __global__ void __launch_bounds__(NT, 512 / NT) k_transient_fast(TrArgs a) {
   float2* tw = reinterpret_cast<float2*>(W + R * MS);     // [N] DCT twiddles W_4N^k
   float2* ptw = tw + N;                                   // [TW] FFT pass twiddles
   int* dr = reinterpret_cast<int*>(ptw + TrSched<N>::TW); // [N] digit reversal
+  float* Xs = reinterpret_cast<float*>(dr + N);           // [R][MS] IMPL: the last source
   const int tid = threadIdx.x;
   const int y0 = blockIdx.x * R, p0 = blockIdx.x * R;
   const size_t nn = (size_t)N * N;
@@ -314,7 +337,18 @@ __global__ void __launch_bounds__(NT, 512 / NT) k_transient_fast(TrArgs a) {
   row_forward();
   if (!tr_barrier(a.ctrl, target, abort_sm)) return;
 
-  for (int step = 1; step <= a.n_steps; ++step) {
+  // IMPL: the iterate of the current step, whether the previous step is still
+  // to be committed into W, the previous iterate of this thread's cells
+  // (theta_{n-1} at the first iterate) and the iterate count of the launch
+  int iter = 1, g = 0;
+  bool commit = false;
+  float2 thp[IMPL ? CELLS : 1];
+#pragma unroll
+  for (int j = 0; j < (IMPL ? CELLS : 1); ++j) thp[j] = make_float2(0.f, 0.f);
+  __shared__ float dec_r;
+  __shared__ int dec_f;
+
+  for (int step = 1; step <= a.n_steps;) {
     // ---- column phase: this CTA's x-frequency columns p0 .. p0 + R - 1
     {
       float2 c[CELLS];   // all loads of a thread issued before the stores
@@ -342,9 +376,38 @@ __global__ void __launch_bounds__(NT, 512 / NT) k_transient_fast(TrArgs a) {
       const float2 xk = dct_post(zk, znk, tw[k]);
       auto mode = [&](int c, int q, float x) {
         const int i = c * MS + q;
-        const float w = fmaf(rh[i], W[i] - x, x);
-        W[i] = w;
-        return fmaf(km[i], x, am[i] * w);
+        if constexpr (WIN) {
+          const float Ks = km[i] + am[i];         // K / N^2
+          const int Rw = a.window - 1;
+          if (Rw == 0) return Ks * x;
+          const size_t gi = (size_t)(p0 + c) * N + q;
+          auto slot = [&](int m) { return (size_t)(((m % Rw) + Rw) % Rw) * nn + gi; };
+          const float rho = rh[i];
+          float acc = 0.f, r = rho, prev = x;
+          for (int j = 1; j <= Rw; ++j) {
+            const float older = a.ring[slot(step - j)];
+            acc = fmaf(r, prev - older, acc);
+            prev = older;
+            r *= rho;
+          }
+          a.ring[slot(step)] = x;
+          return fmaf(Ks, x, -am[i] * acc);
+        } else if constexpr (IMPL) {
+          // W stays at the last committed step; the step before this one is
+          // committed (with its last source) at its first column phase
+          float Wc = W[i];
+          if (commit) {
+            Wc = fmaf(rh[i], Wc - Xs[i], Xs[i]);
+            W[i] = Wc;
+          }
+          Xs[i] = x;
+          const float w = fmaf(rh[i], Wc - x, x);
+          return fmaf(km[i], x, am[i] * w);
+        } else {
+          const float w = fmaf(rh[i], W[i] - x, x);
+          W[i] = w;
+          return fmaf(km[i], x, am[i] * w);
+        }
       };
       const float2 yk = make_float2(mode(2 * f, k, xk.x), mode(2 * f + 1, k, xk.y));
       float2 ynk;
@@ -365,11 +428,12 @@ __global__ void __launch_bounds__(NT, 512 / NT) k_transient_fast(TrArgs a) {
       a.work[(size_t)(p0 + 2 * f) * N + j] = v.x;
       a.work[(size_t)(p0 + 2 * f + 1) * N + j] = v.y;
     }
+    commit = false;
     if (!tr_barrier(a.ctrl, target, abort_sm)) return;
 
     // ---- row phase: rows y0 .. y0 + R - 1
     const bool more = step < a.n_steps;
-    if (more) {
+    if (!IMPL && more) {
       // the next power map, loaded while the inverse transform runs
       const float* pdn = a.p_dyn + (size_t)step * nn;
 #pragma unroll
@@ -405,6 +469,7 @@ __global__ void __launch_bounds__(NT, 512 / NT) k_transient_fast(TrArgs a) {
     __syncthreads();
     tr_fft_inverse<N>(buf, F, NP, ptw);
     float* th_out = a.theta + (size_t)(step - 1) * nn;
+    float resid = 0.f;
 #pragma unroll
     for (int j = 0; j < CELLS; ++j) {
       const int it = tid + j * T, f = it >> lgN, x = it & (N - 1);
@@ -425,11 +490,84 @@ __global__ void __launch_bounds__(NT, 512 / NT) k_transient_fast(TrArgs a) {
       }
       th_out[i0] = th[0];
       th_out[i0 + N] = th[1];
-      buf[pos] = make_float2(q[0], q[1]);
+      if constexpr (IMPL) {
+        const float2 o = thp[IMPL ? j : 0];
+        if (isfinite(th[0])) resid = fmaxf(resid, fabsf(th[0] - o.x));
+        if (isfinite(th[1])) resid = fmaxf(resid, fabsf(th[1] - o.y));
+        thp[IMPL ? j : 0] = make_float2(th[0], th[1]);
+      } else {
+        buf[pos] = make_float2(q[0], q[1]);
+      }
     }
-    if (!more) break;
-    row_forward();
-    if (!tr_barrier(a.ctrl, target, abort_sm)) return;
+    if constexpr (!IMPL) {
+      if (!more) break;
+      row_forward();
+      if (!tr_barrier(a.ctrl, target, abort_sm)) return;
+      ++step;
+    } else {
+      // the decision of this iterate: its largest change over the map and the
+      // flags, gathered on the control words and read back after a barrier
+      const int cur = g & 1;
+      ++g;
+      float rb = resid;
+      int fb = flags;
+      for (int o = 16; o > 0; o >>= 1) {
+        rb = fmaxf(rb, __shfl_down_sync(0xffffffffu, rb, o));
+        fb |= __shfl_down_sync(0xffffffffu, fb, o);
+      }
+      if ((tid & 31) == 0) red_i[tid >> 5] = fb;
+      if ((tid & 31) == 0) atomicMax(&a.ctrl->resid[cur], __float_as_uint(rb));
+      __syncthreads();
+      if (tid == 0) {
+        int fo = 0;
+        for (int w = 0; w < T / 32; ++w) fo |= red_i[w];
+        if (fo) atomicOr(&a.ctrl->flags, fo);
+      }
+      if (!tr_barrier(a.ctrl, target, abort_sm)) return;
+      if (tid == 0) {
+        dec_r = __uint_as_float(tr_ld_acquire(&a.ctrl->resid[cur]));
+        dec_f = (int)tr_ld_acquire(reinterpret_cast<const unsigned*>(&a.ctrl->flags));
+      }
+      __syncthreads();
+      const float r = dec_r;
+      const bool done = r <= a.tol || iter >= a.max_iter || (dec_f & kFlagNonfinite);
+      if (blockIdx.x == 0 && tid == 0) {
+        // every CTA read the other word one iterate ago, before this iterate's barriers
+        a.ctrl->resid[cur ^ 1] = 0u;
+        if (done) {
+          a.ctrl->iters += iter;
+          a.ctrl->max_resid = fmaxf(a.ctrl->max_resid, r);
+          if (r > a.tol) a.ctrl->growth = 1;
+        }
+      }
+      if (done && step == a.n_steps) break;
+      if (done) {
+        // the next step's power, its source at this step's temperature
+        const float* pdn = a.p_dyn + (size_t)step * nn;
+#pragma unroll
+        for (int j = 0; j < CELLS; ++j) {
+          const int it = tid + j * T, f = it >> lgN, x = it & (N - 1);
+          const size_t i0 = (size_t)(y0 + 2 * f) * N + x;
+          pd[j] = make_float2(__ldg(&pdn[i0]), __ldg(&pdn[i0 + N]));
+        }
+      }
+#pragma unroll
+      for (int j = 0; j < CELLS; ++j) {
+        const int it = tid + j * T, f = it >> lgN, x = it & (N - 1);
+        const float2 th = thp[IMPL ? j : 0];
+        buf[f * NP + pad(makhoul_pos(x, N))] =
+            make_float2(pd[j].x + pl[j].x * fmaf(beta, th.x, 1.f), pd[j].y + pl[j].y * fmaf(beta, th.y, 1.f));
+      }
+      row_forward();
+      if (!tr_barrier(a.ctrl, target, abort_sm)) return;
+      if (done) {
+        ++step;
+        iter = 1;
+        commit = true;
+      } else {
+        ++iter;
+      }
+    }
   }
   // flags of the whole launch
   for (int o = 16; o > 0; o >>= 1) flags |= __shfl_down_sync(0xffffffffu, flags, o);
@@ -442,29 +580,32 @@ __global__ void __launch_bounds__(NT, 512 / NT) k_transient_fast(TrArgs a) {
   }
 }
 
-template <int N, int R, int NT>
+template <int N, int R, int NT, bool IMPL, bool WIN = false>
 int launch_fast(const TrArgs& args, cudaStream_t s) {
   using S = TrShape<N, R, NT>;
-  VS_CUDA_TRY(cudaFuncSetAttribute((const void*)k_transient_fast<N, R, NT>,
-                                   cudaFuncAttributeMaxDynamicSharedMemorySize, (int)S::SMEM));
+  // implicit leakage: one more [R][MS] array (the step's last source)
+  constexpr size_t smem = S::SMEM + (IMPL ? 4 * (size_t)R * S::MS : 0);
+  static_assert(smem <= 227 * 1024, "shared memory");
+  VS_CUDA_TRY(cudaFuncSetAttribute((const void*)k_transient_fast<N, R, NT, IMPL, WIN>,
+                                   cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   int dev = 0, sms = 0, per_sm = 0;
   VS_CUDA_TRY(cudaGetDevice(&dev));
   VS_CUDA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
-  VS_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_transient_fast<N, R, NT>,
-                                                            S::THREADS, S::SMEM));
+  VS_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_transient_fast<N, R, NT, IMPL, WIN>,
+                                                            S::THREADS, smem));
   const int grid = N / R;
   if (per_sm * sms < grid) return -1;          // not co-resident: the caller falls back
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3(grid);
   cfg.blockDim = dim3(S::THREADS);
-  cfg.dynamicSmemBytes = S::SMEM;
+  cfg.dynamicSmemBytes = smem;
   cfg.stream = s;
   cudaLaunchAttribute attr[1];
   attr[0].id = cudaLaunchAttributeCooperative;
   attr[0].val.cooperative = 1;
   cfg.attrs = attr;
   cfg.numAttrs = 1;
-  cudaError_t e = cudaLaunchKernelEx(&cfg, k_transient_fast<N, R, NT>, args);
+  cudaError_t e = cudaLaunchKernelEx(&cfg, k_transient_fast<N, R, NT, IMPL, WIN>, args);
   if (e != cudaSuccess) return vs_set_error(VS_ERR_CUDA, "transient launch: %s", cudaGetErrorString(e));
   return VS_OK;
 }
@@ -473,17 +614,20 @@ int launch_fast(const TrArgs& args, cudaStream_t s) {
 
 bool vs_transient_fast_ok(int n) { return n == 256 || n == 512 || n == 1024; }
 
-// Runs the lagged, untruncated transient of one map on the persistent
-// kernel above. Returns VS_OK and fills *info, a vs_status, or -1 when the
+// Runs the untruncated transient of one map on the persistent kernel above,
+// with lagged leakage or (implicit) the leakage of each step at its own
+// temperature. Returns VS_OK and fills *info, a vs_status, or -1 when the
 // launch shape does not fit the device (the caller then uses the general
 // engine). Allocates its spectral map and barrier words per call.
 int vs_transient_fast(vs_kernel k, int n_steps, const float* p_dyn_trace, const float* p_leak0,
-                      const float* s_kappa, const vs_solve_params* params, float* theta_trace,
-                      vs_solve_info* info, cudaStream_t s) {
+                      const float* s_kappa, const vs_solve_params* params, int implicit,
+                      int window, float* theta_trace, vs_solve_info* info, cudaStream_t s) {
   const int n = k->n;
   float* work = nullptr;
   TrCtrl* ctrl = nullptr;
-  VS_CUDA_TRY(cudaMalloc(&work, sizeof(float) * (size_t)n * n));
+  // the spectral map, and for a window of 2 or more the ring of past sources
+  const size_t ring_maps = window >= 2 ? (size_t)(window - 1) : 0;
+  VS_CUDA_TRY(cudaMalloc(&work, sizeof(float) * (size_t)n * n * (1 + ring_maps)));
   cudaError_t e = cudaMalloc(&ctrl, sizeof(TrCtrl));
   if (e != cudaSuccess) {
     cudaFree(work);
@@ -503,14 +647,30 @@ int vs_transient_fast(vs_kernel k, int n_steps, const float* p_dyn_trace, const 
   a.n_steps = n_steps;
   a.beta = (float)params->beta_per_K;
   a.alpha = (float)params->alpha_per_K;
+  a.tol = (float)params->tol_K;
+  a.max_iter = params->max_iter;
+  a.window = window;
+  a.ring = ring_maps ? work + (size_t)n * n : nullptr;
   int rc = VS_OK;
   e = cudaMemsetAsync(ctrl, 0, sizeof(TrCtrl), s);
+  if (e == cudaSuccess && ring_maps)
+    e = cudaMemsetAsync(a.ring, 0, sizeof(float) * (size_t)n * n * ring_maps, s);
   if (e != cudaSuccess) rc = vs_set_error(VS_ERR_CUDA, "memset: %s", cudaGetErrorString(e));
   if (rc == VS_OK) {
+    // lagged (untruncated or windowed) or implicit (untruncated)
     switch (n) {
-      case 256: rc = launch_fast<256, 2, 256>(a, s); break;
-      case 512: rc = launch_fast<512, 4, 512>(a, s); break;
-      default: rc = launch_fast<1024, 8, 512>(a, s); break;
+      case 256:
+        rc = implicit ? launch_fast<256, 2, 256, true>(a, s)
+             : window ? launch_fast<256, 2, 256, false, true>(a, s) : launch_fast<256, 2, 256, false>(a, s);
+        break;
+      case 512:
+        rc = implicit ? launch_fast<512, 4, 512, true>(a, s)
+             : window ? launch_fast<512, 4, 512, false, true>(a, s) : launch_fast<512, 4, 512, false>(a, s);
+        break;
+      default:
+        rc = implicit ? launch_fast<1024, 8, 512, true>(a, s)
+             : window ? launch_fast<1024, 8, 512, false, true>(a, s) : launch_fast<1024, 8, 512, false>(a, s);
+        break;
     }
   }
   TrCtrl hc = {};
@@ -525,9 +685,10 @@ int vs_transient_fast(vs_kernel k, int n_steps, const float* p_dyn_trace, const 
   if (rc != VS_OK) return rc;
   if (hc.abort) return vs_set_error(VS_ERR_TIMEOUT, "grid barrier timed out");
   info->status = (hc.flags & kFlagNonfinite) ? VS_ERR_NONFINITE
-                 : (hc.flags & kFlagRunaway) ? VS_ERR_RUNAWAY : VS_OK;
-  info->iterations = n_steps;
-  info->residual_K = 0.0;
+                 : (hc.flags & kFlagRunaway) ? VS_ERR_RUNAWAY
+                 : (implicit && hc.growth) ? VS_ERR_NO_CONVERGENCE : VS_OK;
+  info->iterations = implicit ? hc.iters : n_steps;
+  info->residual_K = implicit ? (double)hc.max_resid : 0.0;
   info->mu_W = 0.0;
   info->fell_back = 0;
   return info->status;

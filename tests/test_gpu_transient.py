@@ -122,8 +122,10 @@ def test_implicit_leakage_matches_oracle(window):
     assert float((th - lag).abs().max()) > 1e-3
 
 
-def test_implicit_reports_unconverged_steps():
-    vs, w, k, trace, pl, s = _tr_case(6)
+@pytest.mark.parametrize("config", ["c1_64", "c2_256"])
+def test_implicit_reports_unconverged_steps(config):
+    # 64^2 runs on the general engine, 256^2 on the persistent one
+    vs, w, k, trace, pl, s = _tr_case(6, config=config)
     th, info = vs.solve_transient(k, trace, pl, s, vs_params(w, tol_K=1e-9, max_iter=2),
                                   leakage=vs.VS_LEAK_IMPLICIT)
     assert info["status"] == vs.VS_ERR_NO_CONVERGENCE
@@ -177,4 +179,49 @@ def test_persistent_engine_at_512_against_the_oracle():
                            w.physics.alpha_per_K)
     emax, rel = errors(th, ref)
     assert emax <= REQ_MAX_K
+    assert emax <= 5e-3 and rel <= 2e-4
+
+
+def test_persistent_engine_implicit_leakage_at_256_against_the_oracle():
+    """Implicit leakage on the persistent engine (256^2, 10 steps): every step
+    iterated to 1e-4 K against the oracle's implicit superposition (iterated
+    to 1e-10 K), element by element; fewer iterations than the oracle, at
+    least one per step, and a result that differs from the lagged solve."""
+    from _util import step_spectra
+    vs = _vs()
+    w = synth.workload("c2_256")
+    dt, steps = 1e-3, 10
+    trace = synth.markov_trace(w, steps, device="cuda")
+    _, pl, s = synth.steady_inputs(w, 1, device="cuda")
+    k = vs.Kernel(vs_stack(w), vs.Grid(w.n, w.die_m), vs.KernelOpts(dt_s=dt))
+    th, info = vs.solve_transient(k, trace, pl[0], s[0], vs_params(w, tol_K=1e-4),
+                                  leakage=vs.VS_LEAK_IMPLICIT)
+    assert info["status"] == vs.VS_OK and info["residual_K"] <= 1e-4
+    spectra = step_spectra(w, dt, steps)
+    st = w.stack
+    Kt = ph.spectrum(w.n, w.die_m, st.thickness_m, st.kappa_W_mK, st.h_conv_W_m2K)
+    f64 = lambda t: t.double().cpu().numpy()
+    ref, its = so.transient_variants(spectra, Kt, f64(trace), f64(pl[0]), f64(s[0]),
+                                     w.physics.beta_per_K, w.physics.alpha_per_K, implicit=True,
+                                     tol=1e-10)
+    emax, rel = errors(th, ref)
+    print("implicit 256^2: %d iterations over %d steps (oracle %d), max |dT| %.2e K"
+          % (info["iterations"], steps, int(its.sum()), emax))
+    assert emax <= 5e-3 and rel <= 2e-4
+    assert steps <= info["iterations"] <= int(its.sum())
+    lag, _ = vs.solve_transient(k, trace, pl[0], s[0], vs_params(w))
+    assert float((th - lag).abs().max()) > 1e-3
+
+
+@pytest.mark.parametrize("window", [1, 2, 5])
+def test_persistent_engine_window_at_256_against_the_oracle(window):
+    """The windowed superposition (lagged leakage) on the persistent engine at
+    256^2: 12 steps against the oracle's windowed sum, element by element."""
+    vs = _vs()
+    dt, steps = 1e-3, 12
+    vs_, w, k, trace, pl, s = _tr_case(steps, dt, "c2_256")
+    th, info = vs.solve_transient(k, trace, pl, s, vs_params(w), window=window)
+    assert info["status"] == vs.VS_OK and info["iterations"] == steps
+    ref, _ = _oracle_variant(w, trace, pl, s, dt, window, False)
+    emax, rel = errors(th, ref)
     assert emax <= 5e-3 and rel <= 2e-4
