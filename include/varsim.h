@@ -469,7 +469,10 @@ typedef struct {
 } vs_transient_opts;
 
 /* vs_solve_transient with options (opts NULL => window 0, lagged leakage).
- * Device state: (max(1, window - 1) + implicit) * n * n floats. info_host:
+ * n = 256, 512, 1024 without the combination of a window with implicit
+ * leakage run on one persistent launch (a CTA per 2-8 rows, grid barriers);
+ * the rest on the general streamed engine. Device state: (max(1, window - 1)
+ * + implicit) * n * n floats at most. info_host:
  * lagged, iterations = steps; implicit, iterations = fixed-point iterations
  * summed over the steps, residual_K = the largest final change of a step, and
  * status VS_ERR_NO_CONVERGENCE if a step ended above tol_K. */
@@ -495,8 +498,11 @@ int vs_solve_transient_ex(vs_kernel k, int n_steps, const float* p_dyn_trace,
  *       total-power scaling of the impulse response, literally),
  * with * the mirror-image convolution and . the Hadamard product. No
  * iteration: the result differs from the fixed point of vs_solve_steady by
- * the approximation. Four kernel launches; scratch 8 bytes per cell from the
- * stream-ordered allocator. info_host (may be NULL => no synchronisation)
+ * the approximation. n = 32 .. 256: one launch, a thread-block cluster per
+ * map (the cluster engine's layout), plus a small descriptor table from the
+ * stream-ordered allocator; other n: four kernel launches and scratch of
+ * 8 bytes per cell from the stream-ordered allocator. The two forms compute
+ * the same (to rounding). info_host (may be NULL => no synchronisation)
  * gets status VS_OK, VS_ERR_RUNAWAY or VS_ERR_NONFINITE per map,
  * iterations 0, residual_K 0 and mu_W. */
 #define VS_CF_CONV 0
