@@ -260,9 +260,9 @@ def effect_ablation(vs, k, w, pd, pl, s, mk, maps=None):
 
 
 def physics_variants(vs, k, w, pd, pl, s, th_lin, a, stream):
-    """The streamed engine with kappa(T) through the Kirchhoff transform (Eq. 10,
-    eta and T_amb of the workload) and with a convex leakage as a
-    piecewise-linear table: throughput on the batch and the deviation of the
+    """kappa(T) through the Kirchhoff transform (Eq. 10, eta and T_amb of the
+    workload) and a convex leakage as a piecewise-linear table, on the streamed
+    and on the cluster engine: throughput on the batch and the deviation of the
     result from the linear models (th_lin)."""
     import torch
     phy = w.physics
@@ -272,12 +272,15 @@ def physics_variants(vs, k, w, pd, pl, s, th_lin, a, stream):
     table = [(x, 1.0 + phy.beta_per_K * x * (1.0 + x / 400.0))
              for x in (0.0, 25.0, 50.0, 75.0, 100.0, 150.0, 200.0, 300.0)]
     out = {}
-    for name, kw in (("linear (streamed)", {}),
-                     ("kirchhoff", {"conductivity": vs.VS_COND_KIRCHHOFF, "eta": phy.eta,
-                                    "t_amb_K": phy.t_amb_K}),
-                     ("pwl convex leakage", {"leak_table": table})):
+    kir = {"conductivity": vs.VS_COND_KIRCHHOFF, "eta": phy.eta, "t_amb_K": phy.t_amb_K}
+    for name, eng, kw in (("linear (streamed)", vs.VS_ENGINE_STREAMED, {}),
+                          ("kirchhoff", vs.VS_ENGINE_STREAMED, kir),
+                          ("pwl convex leakage", vs.VS_ENGINE_STREAMED, {"leak_table": table}),
+                          ("kirchhoff (cluster)", vs.VS_ENGINE_CLUSTER, kir),
+                          ("pwl convex leakage (cluster)", vs.VS_ENGINE_CLUSTER,
+                           {"leak_table": table})):
         prm = vs.SolveParams(phy.beta_per_K, phy.alpha_per_K, 1e-2, 200, vs.VS_PREC_FP32,
-                             vs.VS_ENGINE_STREAMED, **kw)
+                             eng, **kw)
         th = torch.empty_like(pd)
         plan = vs.Plan([(k, pd[i], pl[i], s[i], th[i]) for i in range(B)], prm, stream)
         for _ in range(max(3, a.warmup)):
@@ -301,8 +304,8 @@ def physics_variants(vs, k, w, pd, pl, s, th_lin, a, stream):
                      "dev_from_linear_K_mean": float(dev.mean()),
                      "dev_from_linear_pct_of_rise_max": 100 * float((dev / rise).max())}
         del th
-    return dict(out, how="streamed engine over the %d-map batch at 1e-2 K; deviation per map from "
-                         "the headline path's linear-model maps" % B)
+    return dict(out, how="streamed or cluster engine (named) over the %d-map batch at 1e-2 K; "
+                         "deviation per map from the headline path's linear-model maps" % B)
 
 
 def wide_spreader(vs, w, pd, pl, s, th_die, a, stream, mk):

@@ -194,9 +194,11 @@ typedef struct {
  *                 iteration then preconditions with the table's slope at
  *                 theta = 0 instead of beta_per_K (the fixed point is the
  *                 same); that slope also enters the runaway check.
- * A variant needs the streamed FP32 engine (VS_ENGINE_AUTO selects it) and a
- * steady solve; the cluster and tensor-core engines, the transient and
- * vs_solve_steady_noalloc return VS_ERR_INVALID_ARG for it.
+ * A variant needs FP32 and a steady solve: the cluster engine (one launch
+ * shape, update-load batch 2; a cold map starts from theta_0 = 0) or the
+ * streamed engine, VS_ENGINE_AUTO choosing as for the linear models; the
+ * tensor-core engines, the transient and vs_solve_steady_noalloc return
+ * VS_ERR_INVALID_ARG for it.
  *   stop_rule  : VS_STOP_UPDATE (0, what a zero-initialised struct selects) or
  *                VS_STOP_ESTIMATE, on every steady engine; the transient
  *                solves return VS_ERR_INVALID_ARG for VS_STOP_ESTIMATE. */

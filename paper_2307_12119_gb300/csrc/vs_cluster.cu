@@ -132,9 +132,41 @@ __device__ __forceinline__ int cl_dr(int k) {
 // BATCH: positions of the update whose inputs (P_leak0, P_dyn, s, theta of
 // two rows) a thread loads together before using them, 1, 2 or 4: the depth of
 // the global-load pipelining, a launch shape the plan's autotuner picks.
+// The physics variants (PHYS): the leakage factor g(theta) of a piecewise-linear
+// table (Sec. II-E) and the field-point map of kappa(T) through the Kirchhoff
+// transform (Eq. 10), as in the streamed engine's variant update.
+__device__ __forceinline__ float cl_leak(const ClusterDev& P, float th) {
+  if (P.leak_n == 0) return fmaf(P.beta, th, 1.f);
+  int i = 0;
+  while (i < P.leak_n - 2 && th >= P.leak_x[i + 1]) ++i;
+  const float x0 = P.leak_x[i], y0 = P.leak_y[i];
+  return fmaf((P.leak_y[i + 1] - y0) / (P.leak_x[i + 1] - x0), th - x0, y0);
+}
+__device__ __forceinline__ float cl_field_theta(const ClusterDev& P, float sk, float uu, int& flags) {
+  if (P.cond == VS_COND_KIRCHHOFF) {
+    float x = P.one_me * sk * uu / P.t_amb;
+    if (!(x > -0.95f)) {
+      flags |= kFlagRunaway;
+      x = -0.95f;                         // keep theta finite; the map stops on the flag
+    }
+    return P.t_amb * expm1f(log1pf(x) / P.one_me);
+  }
+  const float den = fmaf(-P.alpha * sk, uu, 1.f);
+  if (!(den > 0.05f)) flags |= kFlagRunaway;
+  return sk * uu / den;
+}
+__device__ __forceinline__ float cl_field_u(const ClusterDev& P, float sk, float t0) {
+  if (P.cond == VS_COND_KIRCHHOFF)
+    return P.t_amb * expm1f(P.one_me * log1pf(t0 / P.t_amb)) / (P.one_me * sk);
+  return t0 / (sk * fmaf(P.alpha, t0, 1.f));
+}
+
 // CF: the one-shot closed form (Sec. IV-C, Eqs. 21, 25, 26) instead of the
 // fixed point, on the same cluster layout (see the closed-form block below).
-template <int N, int BATCH, bool CF = false>
+// PHYS: the physics variants in the update (P.beta is then the preconditioner
+// slope, the table's at theta = 0); a cold map starts from theta_0 = 0 instead
+// of the die's uniform mode, as on the streamed engine.
+template <int N, int BATCH, bool CF = false, bool PHYS = false>
 __global__ void __launch_bounds__(ClShape<N>::THREADS, ClShape<N>::MIN_BLOCKS)
     k_solve_cluster(ClusterDev P) {
   constexpr int kClBatch = BATCH;
@@ -333,7 +365,20 @@ __global__ void __launch_bounds__(ClShape<N>::THREADS, ClShape<N>::MIN_BLOCKS)
               const float PL = e ? pl[u][h].y : pl[u][h].x, PD = e ? pd[u][h].y : pd[u][h].x;
               const float S = e ? sk[u][h].y : sk[u][h].x, O = e ? old[u][h].y : old[u][h].x;
               float q;
-              if (mode == 1) {
+              if constexpr (PHYS) {
+                // P_dyn + P_leak0 g(theta) - b u, b = slope mu (Sec. IV-C)
+                if (mode == 1) {
+                  const float u0 = O == 0.f ? 0.f : cl_field_u(P, S, O);
+                  th[e] = O;
+                  q = fmaf(PL, cl_leak(P, O), PD) - beta * mu * u0;
+                } else {
+                  const float uu = e ? (h ? um.y : um.x) : (h ? v[r].y : v[r].x);
+                  th[e] = cl_field_theta(P, S, uu, flags);
+                  if (!isfinite(th[e])) flags |= kFlagNonfinite;
+                  else resid = fmaxf(resid, fabsf(th[e] - O));
+                  q = fmaf(PL, cl_leak(P, th[e]), PD) - beta * mu * uu;
+                }
+              } else if (mode == 1) {
                 // u_0 = theta_0 / (s (1 + alpha theta_0))
                 const float u0 = __fdividef(O, S * fmaf(alpha, O, 1.f));
                 th[e] = O;
@@ -800,7 +845,7 @@ __global__ void __launch_bounds__(ClShape<N>::THREADS, ClShape<N>::MIN_BLOCKS)
       for (int i = t; i < kClRows * N / 4; i += kClThreads)
         *reinterpret_cast<float4*>(d.theta + (size_t)y0 * N + 4 * i) = make_float4(0.f, 0.f, 0.f, 0.f);
   } else {
-    if (cold) {
+    if (!PHYS && cold) {
       double pd_sum = 0.0;
       for (int r = 0; r < ranks; ++r) pd_sum += slots->part2[r];
       const float pdm = (float)(pd_sum / ((double)N * N)), muf = (float)mu;
@@ -900,6 +945,16 @@ ClusterFn cluster_kernel(int n, int batch) {
     case 64: return cluster_kernel_n<64>(batch);
     case 128: return cluster_kernel_n<128>(batch);
     default: return cluster_kernel_n<256>(batch);
+  }
+}
+
+// The physics-variant instantiation for grid side n (update-load batch 2).
+ClusterFn cluster_kernel_phys(int n) {
+  switch (n) {
+    case 32: return k_solve_cluster<32, 2, false, true>;
+    case 64: return k_solve_cluster<64, 2, false, true>;
+    case 128: return k_solve_cluster<128, 2, false, true>;
+    default: return k_solve_cluster<256, 2, false, true>;
   }
 }
 

@@ -73,6 +73,11 @@ struct ClusterDev {
   float beta, alpha, tol;
   int stop_rule;         // VS_STOP_*
   int cf_mode;           // closed-form instantiation: VS_CF_CONV or VS_CF_IMPULSE
+  // physics-variant instantiation (beta above is then the preconditioner slope)
+  int cond;              // VS_COND_*
+  float one_me, t_amb;   // Kirchhoff: 1 - eta, T_amb
+  int leak_n;            // 0 or the points of a piecewise-linear leakage factor
+  float leak_x[VS_MAX_LEAK_POINTS], leak_y[VS_MAX_LEAK_POINTS];
 };
 
 // Launch shape of the cluster kernel for grid side n: CTAs per cluster,
@@ -89,6 +94,8 @@ ClHost cluster_shape(int n);
 // The instantiation for n (32, 64, 128 or 256) and update-load batch (1, 2
 // or 4; the default launch shape is 2).
 ClusterFn cluster_kernel(int n, int batch);
+// The instantiation with the physics variants in the update (batch 2).
+ClusterFn cluster_kernel_phys(int n);
 // The one-shot closed form on the cluster layout (n in [32, 256]), one
 // cluster per map of P.maps / P.order, P.cf_mode the closed-form mode.
 cudaError_t cluster_cf_launch(int n, const ClusterDev& P, int count, cudaStream_t s);

@@ -1642,6 +1642,21 @@ int cluster_attrs(int n, int batch) {
   return VS_OK;
 }
 
+// Shared-memory attributes of the physics-variant instantiation for n, once.
+int cluster_attrs_phys(int n) {
+  static size_t done[4] = {};
+  std::lock_guard<std::mutex> lk(g_attr_mutex);
+  size_t& cur = done[__builtin_ctz((unsigned)n) - 5];
+  if (cur == 0) {
+    ClusterFn fn = cluster_kernel_phys(n);
+    VS_CUDA_TRY(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     (int)cluster_shape(n).smem));
+    VS_CUDA_TRY(cudaFuncSetAttribute(fn, cudaFuncAttributePreferredSharedMemoryCarveout, 100));
+    cur = cluster_shape(n).smem;
+  }
+  return VS_OK;
+}
+
 cudaLaunchConfig_t cluster_config(int n, int count, cudaStream_t s, cudaLaunchAttribute* attr) {
   cudaLaunchConfig_t cfg = {};
   const ClHost h = cluster_shape(n);
@@ -1750,9 +1765,31 @@ int plan_launch_cluster(vs_plan_t* p, cudaStream_t s) {
       off += g.second;
       continue;
     }
+    const vs_solve_params& pp = p->params;
+    const bool phys = vs_params_physics(&pp) != 0;
+    if (phys) {
+      P.cond = pp.conductivity;
+      P.one_me = (float)(1.0 - pp.eta);
+      P.t_amb = (float)pp.t_amb_K;
+      P.leak_n = pp.leak_points;
+      for (int i = 0; i < VS_MAX_LEAK_POINTS; ++i) {
+        P.leak_x[i] = i < pp.leak_points ? (float)pp.leak_theta_K[i] : 0.f;
+        P.leak_y[i] = i < pp.leak_points ? (float)pp.leak_g[i] : 0.f;
+      }
+      if (pp.leak_points >= 2) {
+        // precondition with the slope of the table at theta = 0, as the streamed engine
+        int i = 0;
+        while (i < pp.leak_points - 2 && pp.leak_theta_K[i + 1] <= 0.0) ++i;
+        P.beta = (float)std::max(0.0, (pp.leak_g[i + 1] - pp.leak_g[i]) /
+                                          (pp.leak_theta_K[i + 1] - pp.leak_theta_K[i]));
+      }
+      int rc = cluster_attrs_phys(g.first);
+      if (rc != VS_OK) return rc;
+    }
     cudaLaunchAttribute attr[1];
     cudaLaunchConfig_t cfg = cluster_config(g.first, g.second, s, attr);
-    cudaError_t e = cudaLaunchKernelEx(&cfg, cluster_kernel(g.first, p->cl_batch), P);
+    cudaError_t e = cudaLaunchKernelEx(
+        &cfg, phys ? cluster_kernel_phys(g.first) : cluster_kernel(g.first, p->cl_batch), P);
     if (e != cudaSuccess)
       return vs_set_error(VS_ERR_CUDA, "cluster launch (n %d, %d maps): %s", g.first, g.second,
                           cudaGetErrorString(e));
@@ -1943,9 +1980,7 @@ int plan_create(const vs_batch_item* items_host, int n_items, const vs_solve_par
   }
   if (vs_params_physics(params) && params->precision != VS_PREC_FP32)
     return vs_set_error(VS_ERR_INVALID_ARG, "the physics variants need FP32 precision");
-  if (vs_params_physics(params) && params->engine == VS_ENGINE_CLUSTER)
-    return vs_set_error(VS_ERR_INVALID_ARG, "the physics variants run on the streamed engine");
-  bool cluster_ok = params->precision == VS_PREC_FP32 && !vs_params_physics(params);
+  bool cluster_ok = params->precision == VS_PREC_FP32;
   for (int i = 0; i < n_items && cluster_ok; ++i) cluster_ok = cluster_size_ok(items_host[i].k->n);
   if (params->engine == VS_ENGINE_CLUSTER && params->precision == VS_PREC_FP32 && !cluster_ok)
     return vs_set_error(VS_ERR_INVALID_ARG,
@@ -1987,9 +2022,17 @@ int plan_create(const vs_batch_item* items_host, int n_items, const vs_solve_par
                           shape);
     }
     const std::vector<int> key = tune_key(items_host, n_items, true);
-    bool tune = shape == 0 && tune_enabled(n_items);
+    // the physics variants have one instantiation (update-load batch 2)
+    const bool phys = vs_params_physics(params) != 0;
+    if (phys && shape > 0 && shape != kClBatchDefault) {
+      delete p;
+      return vs_set_error(VS_ERR_INVALID_ARG,
+                          "the physics variants on the cluster engine have one shape (%d)",
+                          kClBatchDefault);
+    }
+    bool tune = shape == 0 && tune_enabled(n_items) && !phys;
     p->cl_batch = shape > 0 ? shape : kClBatchDefault;
-    if (shape <= 0 && tune_enabled(n_items)) {
+    if (shape <= 0 && tune_enabled(n_items) && !phys) {
       std::lock_guard<std::mutex> lk(g_tune_mutex);
       auto itc = g_tuned.find(key);
       if (itc != g_tuned.end()) {

@@ -59,10 +59,11 @@ def _oracle(w, pd, pl, s, kirchhoff, table):
     return th
 
 
+@pytest.mark.parametrize("engine", [1, 2])          # streamed, cluster
 @pytest.mark.parametrize("kirchhoff,table", [(True, None), (False, EXP_TABLE), (True, EXP_TABLE),
                                              (False, CONVEX_TABLE), (True, CONVEX_TABLE)])
 @pytest.mark.parametrize("config,n", [("c1_64", None), ("c2_256", None), ("c1_64", 128)])
-def test_physics_variants_match_oracle(config, n, kirchhoff, table):
+def test_physics_variants_match_oracle(config, n, kirchhoff, table, engine):
     if config == "c2_256" and table is EXP_TABLE:
         pytest.skip("thermal runaway of the exponential leakage on these maps (oracle too)")
     vs, w, k, pd, pl, s = _case(config, 2, n)
@@ -70,7 +71,7 @@ def test_physics_variants_match_oracle(config, n, kirchhoff, table):
     # the stronger couplings contract slowly (an update of 1e-3 K can leave
     # 1e-2 K of error): stop at 2e-4 K and allow more iterations
     infos = vs.solve_batch([(k, pd[b], pl[b], s[b], th[b]) for b in range(2)],
-                           _params(vs, w, kirchhoff, table, tol=2e-4, max_iter=400))
+                           _params(vs, w, kirchhoff, table, tol=2e-4, max_iter=400, engine=engine))
     for b in range(2):
         assert infos[b]["status"] == vs.VS_OK, infos[b]
         emax, rel = errors(th[b], _oracle(w, pd[b], pl[b], s[b], kirchhoff, table))
@@ -112,13 +113,37 @@ def test_physics_variant_full_batch_and_warm_start():
     assert float((th2 - th[:4]).abs().max()) <= 1e-2
 
 
+def test_physics_variants_on_both_engines_agree():
+    """The cluster engine (the automatic choice for n <= 256) and the streamed
+    engine give the same maps for the physics variants, warm starts included;
+    the cluster engine's physics instantiation has one launch shape."""
+    vs, w, k, pd, pl, s = _case("c2_256", 3)
+    out = {}
+    for eng in (vs.VS_ENGINE_STREAMED, vs.VS_ENGINE_CLUSTER):
+        th = torch.empty_like(pd)
+        # as in the oracle parity test: these couplings contract slowly, so stop
+        # at 2e-4 K with room for iterations
+        prm = _params(vs, w, True, CONVEX_TABLE, tol=2e-4, max_iter=400, engine=eng)
+        infos = vs.solve_batch([(k, pd[b], pl[b], s[b], th[b]) for b in range(3)], prm)
+        assert all(i["status"] == vs.VS_OK for i in infos), [(i["status"], i["iterations"]) for i in infos]
+        init = (th * 0.95).contiguous()
+        th2 = torch.empty_like(pd)
+        infos = vs.solve_batch([(k, pd[b], pl[b], s[b], th2[b], init[b]) for b in range(3)], prm)
+        assert all(i["status"] == vs.VS_OK for i in infos), [(i["status"], i["iterations"]) for i in infos]
+        out[eng] = (th, th2)
+    a, b = out[vs.VS_ENGINE_STREAMED], out[vs.VS_ENGINE_CLUSTER]
+    assert float((a[0] - b[0]).abs().max()) <= 5e-3
+    assert float((a[1] - b[1]).abs().max()) <= 5e-3
+    z = torch.empty_like(pd[0])
+    with pytest.raises(vs.VarsimError) as e:
+        vs.Plan([(k, pd[0], pl[0], s[0], z)], _params(vs, w, True, None, engine=vs.VS_ENGINE_CLUSTER),
+                shape=4)
+    assert e.value.status == vs.VS_ERR_INVALID_ARG
+
+
 def test_physics_variants_are_rejected_where_not_supported():
     vs, w, k, pd, pl, s = _case("c1_64", 1)
     prm = _params(vs, w, True, None)
-    with pytest.raises(vs.VarsimError) as e:
-        vs.solve_batch([(k, pd[0], pl[0], s[0], torch.empty_like(pd[0]))],
-                       _params(vs, w, True, None, engine=vs.VS_ENGINE_CLUSTER))
-    assert e.value.status == vs.VS_ERR_INVALID_ARG
     with pytest.raises(vs.VarsimError):
         vs.solve_steady_noalloc(k, pd[0], pl[0], s[0], prm)
     with pytest.raises(vs.VarsimError):
