@@ -155,6 +155,20 @@ __device__ __forceinline__ float cl_field_theta(const ClusterDev& P, float sk, f
   if (!(den > 0.05f)) flags |= kFlagRunaway;
   return sk * uu / den;
 }
+// dg/dtheta of the leakage factor at theta, and dtheta/du of the field map at u
+// (s = 1): the uniform start's preconditioner for the variants.
+__device__ __forceinline__ float cl_leak_slope(const ClusterDev& P, float th) {
+  if (P.leak_n == 0) return P.beta;
+  int i = 0;
+  while (i < P.leak_n - 2 && th >= P.leak_x[i + 1]) ++i;
+  return (P.leak_y[i + 1] - P.leak_y[i]) / (P.leak_x[i + 1] - P.leak_x[i]);
+}
+__device__ __forceinline__ float cl_field_dtheta(const ClusterDev& P, float u) {
+  if (P.cond == VS_COND_KIRCHHOFF)
+    return expf(log1pf(P.one_me * u / P.t_amb) * (1.f / P.one_me - 1.f));
+  const float den = fmaf(-P.alpha, u, 1.f);
+  return 1.f / (den * den);
+}
 __device__ __forceinline__ float cl_field_u(const ClusterDev& P, float sk, float t0) {
   if (P.cond == VS_COND_KIRCHHOFF)
     return P.t_amb * expm1f(P.one_me * log1pf(t0 / P.t_amb)) / (P.one_me * sk);
@@ -164,8 +178,8 @@ __device__ __forceinline__ float cl_field_u(const ClusterDev& P, float sk, float
 // CF: the one-shot closed form (Sec. IV-C, Eqs. 21, 25, 26) instead of the
 // fixed point, on the same cluster layout (see the closed-form block below).
 // PHYS: the physics variants in the update (P.beta is then the preconditioner
-// slope, the table's at theta = 0); a cold map starts from theta_0 = 0 instead
-// of the die's uniform mode, as on the streamed engine.
+// slope, the table's at theta = 0); a cold map starts from the die's uniform
+// mode of the variant (below).
 template <int N, int BATCH, bool CF = false, bool PHYS = false>
 __global__ void __launch_bounds__(ClShape<N>::THREADS, ClShape<N>::MIN_BLOCKS)
     k_solve_cluster(ClusterDev P) {
@@ -845,23 +859,41 @@ __global__ void __launch_bounds__(ClShape<N>::THREADS, ClShape<N>::MIN_BLOCKS)
       for (int i = t; i < kClRows * N / 4; i += kClThreads)
         *reinterpret_cast<float4*>(d.theta + (size_t)y0 * N + 4 * i) = make_float4(0.f, 0.f, 0.f, 0.f);
   } else {
-    if (!PHYS && cold) {
+    if (cold) {
       double pd_sum = 0.0;
       for (int r = 0; r < ranks; ++r) pd_sum += slots->part2[r];
       const float pdm = (float)(pd_sum / ((double)N * N)), muf = (float)mu;
       const float k00 = __ldg(d.Kt);
-      float ub = 0.f;
-      bool ok = true;
-      for (int k = 0; k < 16 && ok; ++k) {   // contracts by ~beta mu K00 per step
+      if constexpr (!PHYS) {
+        float ub = 0.f;
+        bool ok = true;
+        for (int k = 0; k < 16 && ok; ++k) {   // contracts by ~beta mu K00 per step
+          const float den = fmaf(-alpha, ub, 1.f);
+          ok = den > 0.05f;
+          ub = k00 * fmaf(muf, fmaf(beta, __fdividef(ub, den), 1.f), pdm);
+        }
         const float den = fmaf(-alpha, ub, 1.f);
-        ok = den > 0.05f;
-        ub = k00 * fmaf(muf, fmaf(beta, __fdividef(ub, den), 1.f), pdm);
-      }
-      const float den = fmaf(-alpha, ub, 1.f);
-      const float mp = muf * fmaf(2.f * alpha, ub, 1.f);
-      if (ok && den > 0.05f && isfinite(ub) && beta * mp * d.kmax < 0.95f) {
-        th0 = __fdividef(ub, den);
-        mu_p = mp;
+        const float mp = muf * fmaf(2.f * alpha, ub, 1.f);
+        if (ok && den > 0.05f && isfinite(ub) && beta * mp * d.kmax < 0.95f) {
+          th0 = __fdividef(ub, den);
+          mu_p = mp;
+        }
+      } else {
+        // the same for a variant: u = K00 (mean P_dyn + mu g(theta(u))) at s = 1,
+        // preconditioner b = mu g'(theta) dtheta/du there, i.e. mu_p = b / beta
+        // (beta the slope the source term and the multiplier scale by)
+        float ub = 0.f, tb = 0.f;
+        int fl = 0;
+        for (int k = 0; k < 16 && !fl; ++k) {
+          tb = cl_field_theta(P, 1.f, ub, fl);
+          ub = k00 * fmaf(muf, cl_leak(P, tb), pdm);
+        }
+        tb = cl_field_theta(P, 1.f, ub, fl);
+        const float b = muf * cl_leak_slope(P, tb) * cl_field_dtheta(P, ub);
+        if (!fl && isfinite(tb) && isfinite(b) && beta > 0.f && b > 0.f && b * d.kmax < 0.95f) {
+          th0 = tb;
+          mu_p = b / beta;
+        }
       }
     }
     float r0 = 0.f;
