@@ -132,6 +132,13 @@ __device__ __forceinline__ int cl_dr(int k) {
 // BATCH: positions of the update whose inputs (P_leak0, P_dyn, s, theta of
 // two rows) a thread loads together before using them, 1, 2 or 4: the depth of
 // the global-load pipelining, a launch shape the plan's autotuner picks.
+// Compensated FP32 accumulation (Knuth's two-sum): hi + lo carries the sum.
+__device__ __forceinline__ void two_sum_add(float& hi, float& lo, float x) {
+  const float tsum = hi + x, bp = tsum - hi;
+  lo += (hi - (tsum - bp)) + (x - bp);
+  hi = tsum;
+}
+
 // The physics variants (PHYS): the leakage factor g(theta) of a piecewise-linear
 // table (Sec. II-E) and the field-point map of kappa(T) through the Kirchhoff
 // transform (Eq. 10), as in the streamed engine's variant update.
@@ -307,6 +314,10 @@ __global__ void __launch_bounds__(ClShape<N>::THREADS, ClShape<N>::MIN_BLOCKS)
     prev = rr;
   };
 
+  // closed form: the sums of P_leak0 and P_dyn over this CTA's cells, taken in
+  // the first-source row pass (the closed form has no separate means pass)
+  float cf_lh = 0.f, cf_ll = 0.f, cf_dh = 0.f, cf_dl = 0.f;
+
   // Row phase. mode 1: initial source from theta_0, the warm start's map or
   // the uniform th0 (not stored); 2: iteration (brow holds the spectra of the
   // column phase, pre-twiddled, at digit-reversed places); 3: the first
@@ -358,6 +369,12 @@ __global__ void __launch_bounds__(ClShape<N>::THREADS, ClShape<N>::MIN_BLOCKS)
             const size_t idx = row_a + (size_t)h * N + x;
             pl[u][h] = ld2(d.p_leak0, idx);
             pd[u][h] = ld2(d.p_dyn, idx);
+            if constexpr (CF) {
+              two_sum_add(cf_lh, cf_ll, pl[u][h].x);
+              two_sum_add(cf_lh, cf_ll, pl[u][h].y);
+              two_sum_add(cf_dh, cf_dl, pd[u][h].x);
+              two_sum_add(cf_dh, cf_dl, pd[u][h].y);
+            }
             sk[u][h] = d.s ? ld2(d.s, idx) : make_float2(1.f, 1.f);
             old[u][h] = mode == 2 ? *reinterpret_cast<const float2*>(d.theta + idx)
                         : (mode == 1 && d.theta_init) ? ld2(d.theta_init, idx)
@@ -580,7 +597,7 @@ __global__ void __launch_bounds__(ClShape<N>::THREADS, ClShape<N>::MIN_BLOCKS)
   // The means of the inputs over the die: mu = mean(P_leak0) (Sec. IV-C) and,
   // for a cold start, mean(P_dyn), as compensated FP32 sums.
   const bool cold = !d.theta_init;
-  {
+  if constexpr (!CF) {
     float lh = 0.f, ll = 0.f, dh = 0.f, dl = 0.f;
     auto add2 = [](float& hi, float& lo, float x) {
       const float tsum = hi + x, bp = tsum - hi;
@@ -616,10 +633,10 @@ __global__ void __launch_bounds__(ClShape<N>::THREADS, ClShape<N>::MIN_BLOCKS)
         cl_put(cl_map(&slots->part[rank], (unsigned)r), tot_l);
         cl_put(cl_map(&slots->part2[rank], (unsigned)r), tot_d);
       }
+    load_k();
+    cl_sync();
+    mu = cluster_mu();
   }
-  load_k();
-  cl_sync();
-  mu = cluster_mu();
   if constexpr (CF) {
     // One-shot closed form of the map (the three-pass kernels of vs_closed.cu
     // compute the same):
@@ -630,8 +647,27 @@ __global__ void __launch_bounds__(ClShape<N>::THREADS, ClShape<N>::MIN_BLOCKS)
     // y, both multipliers; the random part's spectra wait in the multiplier
     // table's place while the L_det part goes back through the inverse
     // transforms into theta (as a staging copy of u_det); then the random
-    // part follows and the last row pass combines the two.
+    // part follows and the last row pass combines the two. The means come
+    // from the first row pass (q needs no mean), exchanged on its barrier.
     const bool impulse = P.cf_mode == VS_CF_IMPULSE;
+    cl_wait();                                      // every CTA has started
+    load_k();
+    {
+      float r0 = 0.f;
+      int f0 = 0;
+      row_phase(1, 0.f, 0.f, r0, f0, 0);          // q = P_dyn + P_leak0, forward along x
+    }
+    {
+      const double tot_l = block_sum((double)cf_lh + (double)cf_ll, red_d);
+      const double tot_d = block_sum((double)cf_dh + (double)cf_dl, red_d);
+      if (t == 0)
+        for (int r = 0; r < ranks; ++r) {
+          cl_put(cl_map(&slots->part[rank], (unsigned)r), tot_l);
+          cl_put(cl_map(&slots->part2[rank], (unsigned)r), tot_d);
+        }
+    }
+    cl_sync();
+    mu = cluster_mu();
     double tot_q = 0.0;
     for (int r = 0; r < ranks; ++r) tot_q += slots->part[r] + slots->part2[r];
     const float mu_f = (float)mu, nn = (float)N * (float)N;
@@ -649,10 +685,6 @@ __global__ void __launch_bounds__(ClShape<N>::THREADS, ClShape<N>::MIN_BLOCKS)
       }
       __syncthreads();
     }
-    float r0 = 0.f;
-    int f0 = 0;
-    row_phase(1, mu_f, 0.f, r0, f0, 0);           // q = P_dyn + P_leak0, forward along x
-    cl_sync();
     // the radix-16 inverse along y of bcol and the stores into the row owners
     auto col_push = [&]() {
       __syncthreads();
