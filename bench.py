@@ -344,7 +344,101 @@ def wide_spreader(vs, w, pd, pl, s, th_die, a, stream, mk):
         del th
     return dict(out, how="cluster engine over the %d-map batch at 1e-2 K, layers 2.. (the Cu "
                          "spreader) wider than the 20 mm die, which changes only the uniform mode of "
-                         "the kernel (R34); drop of the mean rise against the die-sized stack" % pd.shape[0])
+                         "the kernel; drop of the mean rise against the die-sized stack" % pd.shape[0])
+
+
+def _time_runs(runs, stream, steps, warmup):
+    """Milliseconds per step of calling every function in `runs` in order
+    (CUDA events on `stream`, after warm-up)."""
+    import torch
+    for _ in range(max(3, warmup)):
+        for r in runs:
+            r()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(steps):
+        for r in runs:
+            r()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    return e0.elapsed_time(e1) / steps
+
+
+def mixed_sizes(vs, synth, tol, a, stream):
+    """The Monte Carlo batch of mixed grid sizes: 4096 maps, a third each of
+    128^2, 256^2 and 512^2 (22 floorplans per size, every sample its own
+    variation field), FP32 at the headline tolerance. One plan over all of them
+    is one persistent launch of the streamed engine (a 512^2 map is beyond the
+    cluster engine); the split alternative runs the maps up to 256^2 on the
+    cluster engine (one launch per size) and the 512^2 maps on the streamed one."""
+    import torch
+    sizes, total = (128, 256, 512), 4096
+    ws = {n: synth.workload("c3_%d" % n) for n in sizes}
+    ks = {}
+    for n in sizes:
+        st = ws[n].stack
+        ks[n] = vs.Kernel(vs.Stack(st.thickness_m, st.kappa_W_mK, st.h_conv_W_m2K, st.heat_cap_J_m2K),
+                          vs.Grid(n, ws[n].die_m))
+    counts = {n: len(range(i0, total, 3)) for i0, n in enumerate(sizes)}
+    data = {n: synth.steady_inputs(ws[n], counts[n], n_floorplans=22, device="cuda") for n in sizes}
+    th = {n: torch.empty_like(data[n][0]) for n in sizes}
+    items = []
+    for i in range(total):
+        n, j = sizes[i % 3], i // 3
+        pd_, pl_, s_ = data[n]
+        items.append((ks[n], pd_[j], pl_[j], s_[j], th[n][j]))
+    phy = ws[256].physics
+    prm = lambda eng: vs.SolveParams(phy.beta_per_K, phy.alpha_per_K, tol, 50, vs.VS_PREC_FP32, eng)
+    one = vs.Plan(items, prm(vs.VS_ENGINE_AUTO), stream)
+    ms_one = _time_runs([lambda: one.run(stream)], stream, a.steps, a.warmup)
+    infos = one.info(stream)
+    out = {"one_launch": {"value": whole_job_rate(1, total, ms_one * 1e-3), "unit": UNIT,
+                          "ms_per_step": ms_one, "launches": one.launches,
+                          "iterations_mean": sum(i["iterations"] for i in infos) / total,
+                          "not_ok": sum(1 for i in infos if i["status"] != vs.VS_OK)}}
+    one.close()
+    small = [it for it in items if it[0].n <= 256]
+    big = [it for it in items if it[0].n > 256]
+    p_small = vs.Plan(small, prm(vs.VS_ENGINE_CLUSTER), stream)
+    p_big = vs.Plan(big, prm(vs.VS_ENGINE_STREAMED), stream)
+    ms_split = _time_runs([lambda: p_small.run(stream), lambda: p_big.run(stream)], stream,
+                          a.steps, a.warmup)
+    out["split_engines"] = {"value": whole_job_rate(1, total, ms_split * 1e-3), "unit": UNIT,
+                            "ms_per_step": ms_split, "launches": p_small.launches + p_big.launches}
+    p_small.close()
+    p_big.close()
+    return dict(out, how="4096 maps, a third each of 128^2, 256^2, 512^2 (c3 workloads), tol %g K; "
+                         "one_launch: one plan (the streamed engine, one persistent launch); "
+                         "split_engines: the maps up to 256^2 on the cluster engine and the "
+                         "512^2 maps on the streamed engine, in sequence on one stream" % tol)
+
+
+def split_1024(vs, synth, tol, a, stream):
+    """BF16 hi/lo split precision on tensor cores at 1024^2 (the streamed
+    tensor-core engine) against FP32 (streamed engine), 64 maps."""
+    import torch
+    w = synth.workload("c4_1024")
+    st, phy = w.stack, w.physics
+    k = vs.Kernel(vs.Stack(st.thickness_m, st.kappa_W_mK, st.h_conv_W_m2K, st.heat_cap_J_m2K),
+                  vs.Grid(w.n, w.die_m))
+    B = 64
+    pd_, pl_, s_ = synth.steady_inputs(w, B, device="cuda")
+    out, maps = {}, {}
+    for name, prec in (("fp32", vs.VS_PREC_FP32), ("bf16_split", vs.VS_PREC_BF16_SPLIT)):
+        th = torch.empty_like(pd_)
+        plan = vs.Plan([(k, pd_[i], pl_[i], s_[i], th[i]) for i in range(B)],
+                       vs.SolveParams(phy.beta_per_K, phy.alpha_per_K, tol, 50, prec,
+                                      vs.VS_ENGINE_STREAMED), stream)
+        ms = _time_runs([lambda: plan.run(stream)], stream, a.steps, a.warmup)
+        infos = plan.info(stream)
+        out[name] = {"value": whole_job_rate(1, B, ms * 1e-3), "unit": UNIT, "ms_per_step": ms,
+                     "iterations_mean": sum(i["iterations"] for i in infos) / B,
+                     "not_ok": sum(1 for i in infos if i["status"] != vs.VS_OK)}
+        maps[name] = th
+        plan.close()
+    out["bf16_split"]["max_abs_dev_from_fp32_K"] = float((maps["bf16_split"] - maps["fp32"]).abs().max())
+    return dict(out, how="64 maps of 1024^2 (c4 workload), tol %g K, streamed engines" % tol)
 
 
 class Clocks:
@@ -842,6 +936,8 @@ def run_ours(a):
                                                     s[:ABLATION_MAPS], mk)
         extras["physics_variants"] = physics_variants(vs, k, w, pd, pl, s, th_best, a, stream)
         extras["wide_spreader"] = wide_spreader(vs, w, pd, pl, s, th_best, a, stream, mk)
+        extras["mixed_sizes"] = mixed_sizes(vs, synth, tol, a, stream)
+        extras["split_1024"] = split_1024(vs, synth, tol, a, stream)
 
     # e2e: pinned host inputs -> device -> headline path -> host theta, every step
     e2e = None

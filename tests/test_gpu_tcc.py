@@ -12,7 +12,7 @@ from _util import REQ_MAX_K, REQ_REL_L2, errors, oracle_spectrum, oracle_steady,
 
 pytestmark = pytest.mark.gpu
 
-# Split-precision bound (R25): the hi/lo split drops the lo x lo product
+# Split-precision bound: the hi/lo split drops the lo x lo product
 # (~2^-16 relative per transform, ~1e-3 K of rounding at 30-130 K rises), so
 # the split engines iterate to a 1e-2 K update and are held to 1e-2 K.
 SPLIT_TOL_K = 1e-2
