@@ -50,7 +50,8 @@ typedef enum {
   VS_ERR_RUNAWAY = 5,        /* beta*mu*max(K) >= 1 (thermal runaway) or
                                 1 - alpha*s*u <= 0.05 (conductivity model breaks) */
   VS_ERR_NONFINITE = 6,      /* NaN/Inf met in a map */
-  VS_ERR_TIMEOUT = 7         /* an internal grid barrier gave up waiting */
+  VS_ERR_TIMEOUT = 7         /* an internal wait on other CTAs (a grid barrier or
+                                an exchange between phases) gave up */
 } vs_status;
 
 #define VS_MAX_LAYERS 8
@@ -472,9 +473,10 @@ typedef struct {
 
 /* vs_solve_transient with options (opts NULL => window 0, lagged leakage).
  * n = 256, 512, 1024 without the combination of a window with implicit
- * leakage run on one persistent launch (a CTA per 2-8 rows, grid barriers);
- * the rest on the general streamed engine. Device state: (max(1, window - 1)
- * + implicit) * n * n floats at most. info_host:
+ * leakage run on one persistent launch (a CTA per 2-8 rows; the phases
+ * exchange tagged words with lagged leakage and meet at grid barriers with
+ * implicit leakage); the rest on the general streamed engine. Device state on
+ * the persistent launch: (2 + max(0, window - 1)) * n * n floats. info_host:
  * lagged, iterations = steps; implicit, iterations = fixed-point iterations
  * summed over the steps, residual_K = the largest final change of a step, and
  * status VS_ERR_NO_CONVERGENCE if a step ended above tol_K. */

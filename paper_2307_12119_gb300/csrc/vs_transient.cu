@@ -10,8 +10,8 @@
 //     and rho = exp(-dt / tau) of its R x N modes, in shared memory;
 //   - P_leak0 of its R rows, in registers (the thread <-> cell mapping of the
 //     update is the same every step); s is re-read through the L1 each step.
-// Per step, two phases separated by a grid barrier (the spectral map in
-// global memory, x-frequency major, is the only exchange):
+// Per step, two phases, each ending in an exchange through the spectral map in
+// global memory (x-frequency major):
 //   column phase: forward DCT along y of its columns, W <- rho W + (1 - rho) X,
 //     Y = (K - A) X + A W (the step response (K - A) + A (1 - rho^j) of the
 //     primary alias, the finer aliases settled within a step), inverse DCT
@@ -20,8 +20,16 @@
 //     (1 - alpha s u_n) written to the output trace, the next source
 //     P_{n+1} = P_dyn,n+1 + P_leak0 (1 + beta theta_n) (its P_dyn loads issued
 //     before the inverse transform), forward DCT along x.
-// The grid barrier is a bounded spin: on timeout the launch sets an abort
-// word and every CTA returns (VS_ERR_TIMEOUT), no trap.
+// With lagged leakage the exchange needs no grid barrier: every word of the
+// map carries, in its upper half, the number of the phase that wrote it, and
+// a consumer polls its own words until they carry the phase it waits for (one
+// L2 round trip when the data is there, instead of a barrier's arrive, poll
+// and then load). One buffer suffices: a CTA overwrites a word only after it
+// has received data computed from every read of that word's previous value.
+// With implicit leakage every iterate ends in a grid barrier, which also
+// carries the iterate's decision. Both waits are bounded spins: on timeout
+// the launch sets an abort word and every CTA returns (VS_ERR_TIMEOUT), no
+// trap.
 #include <math.h>
 
 #include <algorithm>
@@ -39,6 +47,7 @@ namespace {
 constexpr int ilog2(int v) { return v <= 1 ? 0 : 1 + ilog2(v / 2); }
 
 constexpr long long kTrSpinLimit = 20000000LL;   // ~ seconds of polling
+constexpr long long kTrPollLimit = 4000000LL;    // tag polls (each an L2 round trip): ~ seconds
 
 struct TrCtrl {
   // arrivals so far of the even and of the odd CTAs, each on its own 128-byte
@@ -60,7 +69,8 @@ struct TrArgs {
   const float* p_leak0;    // [N][N]
   const float* s;          // [N][N] or NULL (= 1)
   float* theta;            // [n_steps][N][N]
-  float* work;             // [N][N] spectral map, x-frequency major
+  float* work;             // [N][N] spectral map, x-frequency major (implicit leakage)
+  unsigned long long* xw;  // [N][N] the same map as tagged words (lagged leakage; zeroed)
   const float* Kt;         // [p][q] cosine-basis kernel
   const float* trA;        // [p][q] primary-alias weight
   const float* trRho;      // [p][q] exp(-dt / (C g))
@@ -113,6 +123,46 @@ __device__ bool tr_barrier(TrCtrl* c, unsigned& target, unsigned* abort_sm) {
   }
   __syncthreads();
   return (abort_sm[0] | abort_sm[1]) == 0u;
+}
+
+// Tagged words of the lagged exchange: the value's bits in the lower half,
+// the number of the phase that wrote it in the upper half. Relaxed accesses at
+// GPU scope (served by the L2, never a stale L1 line); an aligned 64-bit access
+// is single-copy atomic, and a vector of them is a set of such accesses, so a
+// reader sees a value together with its own tag.
+__device__ __forceinline__ unsigned long long tr_tag(float v, unsigned tag) {
+  return ((unsigned long long)tag << 32) | __float_as_uint(v);
+}
+__device__ __forceinline__ unsigned tr_tag_of(unsigned long long w) { return (unsigned)(w >> 32); }
+__device__ __forceinline__ float tr_val(unsigned long long w) { return __uint_as_float((unsigned)w); }
+__device__ __forceinline__ unsigned long long tr_ld64(const unsigned long long* p) {
+  unsigned long long v;
+  asm volatile("ld.relaxed.gpu.global.b64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+  return v;
+}
+__device__ __forceinline__ ulonglong2 tr_ld128(const unsigned long long* p) {
+  ulonglong2 v;
+  asm volatile("ld.relaxed.gpu.global.v2.b64 {%0, %1}, [%2];" : "=l"(v.x), "=l"(v.y) : "l"(p) : "memory");
+  return v;
+}
+__device__ __forceinline__ void tr_st64(unsigned long long* p, unsigned long long v) {
+  asm volatile("st.relaxed.gpu.global.b64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
+}
+__device__ __forceinline__ void tr_st128(unsigned long long* p, unsigned long long v0, unsigned long long v1) {
+  asm volatile("st.relaxed.gpu.global.v2.b64 [%0], {%1, %2};" ::"l"(p), "l"(v0), "l"(v1) : "memory");
+}
+
+// One more round of a bounded tag poll: false once the launch aborted or this
+// thread gave up (it then sets the abort word).
+__device__ __forceinline__ bool tr_poll_round(TrCtrl* c, long long& spins) {
+  ++spins;
+  if ((spins & 15) == 0 && tr_ld_acquire(&c->abort) != 0u) return false;
+  if (spins > kTrPollLimit) {
+    atomicExch(&c->abort, 1u);
+    return false;
+  }
+  if (spins > 2) __nanosleep(64);
+  return true;
 }
 
 template <int N>
@@ -257,9 +307,11 @@ __global__ void __launch_bounds__(NT, 512 / NT) k_transient_fast(TrArgs a) {
   using S = TrShape<N, R, NT>;
   constexpr int F = S::F, NP = S::NP, MS = S::MS, T = S::THREADS, CELLS = S::CELLS, half = N / 2;
   constexpr int lgN = ilog2(N), lgF = ilog2(F);
+  constexpr bool TAG = !IMPL;   // exchange by tagged words instead of grid barriers
   extern __shared__ __align__(16) float2 tr_smem[];
   __shared__ int red_i[T / 32];
   __shared__ unsigned abort_sm[2];
+  __shared__ int tag_abort;
   float2* buf = tr_smem;                                  // [F][NP]
   float* km = reinterpret_cast<float*>(buf + F * NP);     // [R][MS] (K - A) / N^2
   float* am = km + R * MS;                                // [R][MS] A / N^2
@@ -272,6 +324,7 @@ __global__ void __launch_bounds__(NT, 512 / NT) k_transient_fast(TrArgs a) {
   const int tid = threadIdx.x;
   const int y0 = blockIdx.x * R, p0 = blockIdx.x * R;
   const size_t nn = (size_t)N * N;
+  if (tid == 0) tag_abort = 0;
   for (int i = tid; i < N; i += T) {
     tw[i] = __ldg(&a.tw4n[i]);
     dr[i] = TrSched<N>::digit_reversed(i);
@@ -312,6 +365,7 @@ __global__ void __launch_bounds__(NT, 512 / NT) k_transient_fast(TrArgs a) {
   }
   int flags = 0;
   unsigned target = 0;    // arrivals that complete the next grid barrier
+  unsigned ex = 0;        // TAG: phases completed so far (the tag of the data last written)
 
   // forward DCT along x of the source in buf (Makhoul order), stored x-frequency major
   auto row_forward = [&]() {
@@ -321,10 +375,30 @@ __global__ void __launch_bounds__(NT, 512 / NT) k_transient_fast(TrArgs a) {
       const int f = it & (F - 1), k = it >> lgF, nk = N - k;
       const float2 zk = buf[f * NP + pad(dr[k])];
       const float2 znk = buf[f * NP + pad(dr[k == 0 ? 0 : nk])];
-      *reinterpret_cast<float2*>(a.work + (size_t)k * N + y0 + 2 * f) = dct_post(zk, znk, tw[k]);
-      if (k != 0 && k != half)
-        *reinterpret_cast<float2*>(a.work + (size_t)nk * N + y0 + 2 * f) =
-            dct_post(znk, zk, tw[nk]);
+      const float2 vk = dct_post(zk, znk, tw[k]);
+      if constexpr (TAG) {
+        tr_st128(a.xw + (size_t)k * N + y0 + 2 * f, tr_tag(vk.x, ex + 1), tr_tag(vk.y, ex + 1));
+      } else {
+        *reinterpret_cast<float2*>(a.work + (size_t)k * N + y0 + 2 * f) = vk;
+      }
+      if (k != 0 && k != half) {
+        const float2 vn = dct_post(znk, zk, tw[nk]);
+        if constexpr (TAG) {
+          tr_st128(a.xw + (size_t)nk * N + y0 + 2 * f, tr_tag(vn.x, ex + 1), tr_tag(vn.y, ex + 1));
+        } else {
+          *reinterpret_cast<float2*>(a.work + (size_t)nk * N + y0 + 2 * f) = vn;
+        }
+      }
+    }
+  };
+  // the end of a phase: TAG, the next phase's data carries tag ex + 1;
+  // otherwise a grid barrier. False if the launch aborted.
+  auto exchange = [&]() -> bool {
+    if constexpr (TAG) {
+      ++ex;
+      return true;
+    } else {
+      return tr_barrier(a.ctrl, target, abort_sm);
     }
   };
 
@@ -335,7 +409,7 @@ __global__ void __launch_bounds__(NT, 512 / NT) k_transient_fast(TrArgs a) {
     buf[f * NP + pad(makhoul_pos(x, N))] = make_float2(pd[j].x + pl[j].x, pd[j].y + pl[j].y);
   }
   row_forward();
-  if (!tr_barrier(a.ctrl, target, abort_sm)) return;
+  if (!exchange()) return;
 
   // IMPL: the iterate of the current step, whether the previous step is still
   // to be committed into W, the previous iterate of this thread's cells
@@ -352,10 +426,45 @@ __global__ void __launch_bounds__(NT, 512 / NT) k_transient_fast(TrArgs a) {
     // ---- column phase: this CTA's x-frequency columns p0 .. p0 + R - 1
     {
       float2 c[CELLS];   // all loads of a thread issued before the stores
+      if constexpr (TAG) {
+        // poll this thread's words until they carry phase ex, then (block
+        // barrier: the previous phase's reads of buf are done) stage them
+        unsigned long long wa[CELLS], wb[CELLS];
+        auto col = [&](int q, int h) {
+          const int it = tid + q * T, f = it >> lgN, j = it & (N - 1);
+          return a.xw + (size_t)(p0 + 2 * f + h) * N + j;
+        };
 #pragma unroll
-      for (int q = 0; q < CELLS; ++q) {
-        const int it = tid + q * T, f = it >> lgN, j = it & (N - 1);
-        c[q] = make_float2(a.work[(size_t)(p0 + 2 * f) * N + j], a.work[(size_t)(p0 + 2 * f + 1) * N + j]);
+        for (int q = 0; q < CELLS; ++q) {
+          wa[q] = tr_ld64(col(q, 0));
+          wb[q] = tr_ld64(col(q, 1));
+        }
+        long long spins = 0;
+        for (;;) {
+          bool ready = true;
+#pragma unroll
+          for (int q = 0; q < CELLS; ++q) ready &= tr_tag_of(wa[q]) == ex && tr_tag_of(wb[q]) == ex;
+          if (ready) break;
+          if (!tr_poll_round(a.ctrl, spins)) {
+            tag_abort = 1;
+            break;
+          }
+#pragma unroll
+          for (int q = 0; q < CELLS; ++q) {
+            if (tr_tag_of(wa[q]) != ex) wa[q] = tr_ld64(col(q, 0));
+            if (tr_tag_of(wb[q]) != ex) wb[q] = tr_ld64(col(q, 1));
+          }
+        }
+#pragma unroll
+        for (int q = 0; q < CELLS; ++q) c[q] = make_float2(tr_val(wa[q]), tr_val(wb[q]));
+        __syncthreads();
+        if (tag_abort) return;
+      } else {
+#pragma unroll
+        for (int q = 0; q < CELLS; ++q) {
+          const int it = tid + q * T, f = it >> lgN, j = it & (N - 1);
+          c[q] = make_float2(a.work[(size_t)(p0 + 2 * f) * N + j], a.work[(size_t)(p0 + 2 * f + 1) * N + j]);
+        }
       }
 #pragma unroll
       for (int q = 0; q < CELLS; ++q) {
@@ -425,11 +534,16 @@ __global__ void __launch_bounds__(NT, 512 / NT) k_transient_fast(TrArgs a) {
     for (int it = tid; it < F * N; it += T) {
       const int f = it >> lgN, j = it & (N - 1);
       const float2 v = buf[f * NP + pad(makhoul_pos(j, N))];
-      a.work[(size_t)(p0 + 2 * f) * N + j] = v.x;
-      a.work[(size_t)(p0 + 2 * f + 1) * N + j] = v.y;
+      if constexpr (TAG) {
+        tr_st64(a.xw + (size_t)(p0 + 2 * f) * N + j, tr_tag(v.x, ex + 1));
+        tr_st64(a.xw + (size_t)(p0 + 2 * f + 1) * N + j, tr_tag(v.y, ex + 1));
+      } else {
+        a.work[(size_t)(p0 + 2 * f) * N + j] = v.x;
+        a.work[(size_t)(p0 + 2 * f + 1) * N + j] = v.y;
+      }
     }
     commit = false;
-    if (!tr_barrier(a.ctrl, target, abort_sm)) return;
+    if (!exchange()) return;
 
     // ---- row phase: rows y0 .. y0 + R - 1
     const bool more = step < a.n_steps;
@@ -448,13 +562,55 @@ __global__ void __launch_bounds__(NT, 512 / NT) k_transient_fast(TrArgs a) {
       // all loads of a thread issued before the pre-twiddles
       constexpr int PRE = (F * (half + 1) + T - 1) / T;
       float2 xk[PRE], xnk[PRE];
+      if constexpr (TAG) {
+        // the words of frequencies k and N - k (absent ones pre-tagged as ready)
+        ulonglong2 wk[PRE], wn[PRE];
+        const unsigned long long zero = tr_tag(0.f, ex);
+        auto row = [&](int q, bool other) {
+          const int it = tid + q * T, f = it & (F - 1), k = it >> lgF;
+          return a.xw + (size_t)(other ? N - k : k) * N + y0 + 2 * f;
+        };
+        auto has_k = [&](int q) { return tid + q * T < F * (half + 1); };
+        auto has_nk = [&](int q) { return has_k(q) && ((tid + q * T) >> lgF) != 0; };
 #pragma unroll
-      for (int q = 0; q < PRE; ++q) {
-        const int it = tid + q * T, f = it & (F - 1), k = it >> lgF;
-        xk[q] = xnk[q] = make_float2(0.f, 0.f);
-        if (it < F * (half + 1)) {
-          xk[q] = *reinterpret_cast<const float2*>(a.work + (size_t)k * N + y0 + 2 * f);
-          if (k != 0) xnk[q] = *reinterpret_cast<const float2*>(a.work + (size_t)(N - k) * N + y0 + 2 * f);
+        for (int q = 0; q < PRE; ++q) {
+          wk[q] = wn[q] = make_ulonglong2(zero, zero);
+          if (has_k(q)) wk[q] = tr_ld128(row(q, false));
+          if (has_nk(q)) wn[q] = tr_ld128(row(q, true));
+        }
+        auto ok = [&](const ulonglong2& w) { return tr_tag_of(w.x) == ex && tr_tag_of(w.y) == ex; };
+        long long spins = 0;
+        for (;;) {
+          bool ready = true;
+#pragma unroll
+          for (int q = 0; q < PRE; ++q) ready &= ok(wk[q]) && ok(wn[q]);
+          if (ready) break;
+          if (!tr_poll_round(a.ctrl, spins)) {
+            tag_abort = 1;
+            break;
+          }
+#pragma unroll
+          for (int q = 0; q < PRE; ++q) {
+            if (!ok(wk[q])) wk[q] = tr_ld128(row(q, false));
+            if (!ok(wn[q])) wn[q] = tr_ld128(row(q, true));
+          }
+        }
+#pragma unroll
+        for (int q = 0; q < PRE; ++q) {
+          xk[q] = make_float2(tr_val(wk[q].x), tr_val(wk[q].y));
+          xnk[q] = make_float2(tr_val(wn[q].x), tr_val(wn[q].y));
+        }
+        __syncthreads();
+        if (tag_abort) return;
+      } else {
+#pragma unroll
+        for (int q = 0; q < PRE; ++q) {
+          const int it = tid + q * T, f = it & (F - 1), k = it >> lgF;
+          xk[q] = xnk[q] = make_float2(0.f, 0.f);
+          if (it < F * (half + 1)) {
+            xk[q] = *reinterpret_cast<const float2*>(a.work + (size_t)k * N + y0 + 2 * f);
+            if (k != 0) xnk[q] = *reinterpret_cast<const float2*>(a.work + (size_t)(N - k) * N + y0 + 2 * f);
+          }
         }
       }
 #pragma unroll
@@ -502,7 +658,7 @@ __global__ void __launch_bounds__(NT, 512 / NT) k_transient_fast(TrArgs a) {
     if constexpr (!IMPL) {
       if (!more) break;
       row_forward();
-      if (!tr_barrier(a.ctrl, target, abort_sm)) return;
+      if (!exchange()) return;
       ++step;
     } else {
       // the decision of this iterate: its largest change over the map and the
@@ -618,16 +774,19 @@ bool vs_transient_fast_ok(int n) { return n == 256 || n == 512 || n == 1024; }
 // with lagged leakage or (implicit) the leakage of each step at its own
 // temperature. Returns VS_OK and fills *info, a vs_status, or -1 when the
 // launch shape does not fit the device (the caller then uses the general
-// engine). Allocates its spectral map and barrier words per call.
+// engine). Allocates its spectral map (tagged words for lagged leakage, zeroed
+// so that no word carries a phase number yet) and control words per call.
 int vs_transient_fast(vs_kernel k, int n_steps, const float* p_dyn_trace, const float* p_leak0,
                       const float* s_kappa, const vs_solve_params* params, int implicit,
                       int window, float* theta_trace, vs_solve_info* info, cudaStream_t s) {
   const int n = k->n;
+  const size_t nn = (size_t)n * n;
   float* work = nullptr;
   TrCtrl* ctrl = nullptr;
-  // the spectral map, and for a window of 2 or more the ring of past sources
+  // the spectral map (8 bytes a word), and for a window of 2 or more the ring
+  // of past sources
   const size_t ring_maps = window >= 2 ? (size_t)(window - 1) : 0;
-  VS_CUDA_TRY(cudaMalloc(&work, sizeof(float) * (size_t)n * n * (1 + ring_maps)));
+  VS_CUDA_TRY(cudaMalloc(&work, sizeof(unsigned long long) * nn + sizeof(float) * nn * ring_maps));
   cudaError_t e = cudaMalloc(&ctrl, sizeof(TrCtrl));
   if (e != cudaSuccess) {
     cudaFree(work);
@@ -639,6 +798,7 @@ int vs_transient_fast(vs_kernel k, int n_steps, const float* p_dyn_trace, const 
   a.s = s_kappa;
   a.theta = theta_trace;
   a.work = work;
+  a.xw = reinterpret_cast<unsigned long long*>(work);
   a.Kt = k->Kt32;
   a.trA = k->trA;
   a.trRho = k->trRho;
@@ -650,11 +810,12 @@ int vs_transient_fast(vs_kernel k, int n_steps, const float* p_dyn_trace, const 
   a.tol = (float)params->tol_K;
   a.max_iter = params->max_iter;
   a.window = window;
-  a.ring = ring_maps ? work + (size_t)n * n : nullptr;
+  a.ring = ring_maps ? work + 2 * nn : nullptr;
   int rc = VS_OK;
   e = cudaMemsetAsync(ctrl, 0, sizeof(TrCtrl), s);
+  if (e == cudaSuccess && !implicit) e = cudaMemsetAsync(a.xw, 0, sizeof(unsigned long long) * nn, s);
   if (e == cudaSuccess && ring_maps)
-    e = cudaMemsetAsync(a.ring, 0, sizeof(float) * (size_t)n * n * ring_maps, s);
+    e = cudaMemsetAsync(a.ring, 0, sizeof(float) * nn * ring_maps, s);
   if (e != cudaSuccess) rc = vs_set_error(VS_ERR_CUDA, "memset: %s", cudaGetErrorString(e));
   if (rc == VS_OK) {
     // lagged (untruncated or windowed) or implicit (untruncated)
@@ -683,7 +844,7 @@ int vs_transient_fast(vs_kernel k, int n_steps, const float* p_dyn_trace, const 
   cudaFree(work);
   cudaFree(ctrl);
   if (rc != VS_OK) return rc;
-  if (hc.abort) return vs_set_error(VS_ERR_TIMEOUT, "grid barrier timed out");
+  if (hc.abort) return vs_set_error(VS_ERR_TIMEOUT, "transient exchange timed out");
   info->status = (hc.flags & kFlagNonfinite) ? VS_ERR_NONFINITE
                  : (hc.flags & kFlagRunaway) ? VS_ERR_RUNAWAY
                  : (implicit && hc.growth) ? VS_ERR_NO_CONVERGENCE : VS_OK;
