@@ -81,7 +81,7 @@ struct TrArgs {
   float tol;               // implicit leakage: per-step fixed point
   int max_iter;
   int window;              // WIN: step responses settled from age `window` on (>= 1)
-  float* ring;             // WIN, window >= 2: [window - 1][N][N] the last sources per mode
+  float* ring;             // WIN, window >= 2: [window - 1][N][N] X - W of the last steps per mode
 };
 
 __device__ __forceinline__ unsigned tr_ld_acquire(const unsigned* p) {
@@ -298,16 +298,17 @@ __device__ __forceinline__ void tr_fft_inverse(float2* buf, int nfft, int stride
 // every CTA from the same word after a grid barrier.
 // WIN: the window of Sec. IV-E with lagged leakage: step responses older than
 // `window` steps are taken as settled, S_j = K for j >= window, so a mode's
-// response is Y_n = K X_n - A sum_{j < window} rho^j (X_{n-j+1} - X_{n-j})
-// from a ring of its last window - 1 sources (X_m in slot m mod (window - 1),
-// in global memory: the CTA's own modes, L2-resident); window 1 is the
-// settled response K X_n.
+// response is Y_n = K X_n - A sum_{0 < j < window} rho^j (X_{n-j+1} - X_{n-j}),
+// computed from the untruncated recursion and a ring of its last window - 1
+// differences X_m - W_m per mode (slot m mod (window - 1), in global memory:
+// the CTA's own modes, L2-resident); window 1 is the settled response K X_n.
 template <int N, int R, int NT, bool IMPL, bool WIN = false>
 __global__ void __launch_bounds__(NT, 512 / NT) k_transient_fast(TrArgs a) {
   using S = TrShape<N, R, NT>;
   constexpr int F = S::F, NP = S::NP, MS = S::MS, T = S::THREADS, CELLS = S::CELLS, half = N / 2;
   constexpr int lgN = ilog2(N), lgF = ilog2(F);
   constexpr bool TAG = !IMPL;   // exchange by tagged words instead of grid barriers
+  static_assert(!(IMPL && WIN) && (!WIN || (R * N) % T == 0), "variant");
   extern __shared__ __align__(16) float2 tr_smem[];
   __shared__ int red_i[T / 32];
   __shared__ unsigned abort_sm[2];
@@ -320,7 +321,8 @@ __global__ void __launch_bounds__(NT, 512 / NT) k_transient_fast(TrArgs a) {
   float2* tw = reinterpret_cast<float2*>(W + R * MS);     // [N] DCT twiddles W_4N^k
   float2* ptw = tw + N;                                   // [TW] FFT pass twiddles
   int* dr = reinterpret_cast<int*>(ptw + TrSched<N>::TW); // [N] digit reversal
-  float* Xs = reinterpret_cast<float*>(dr + N);           // [R][MS] IMPL: the last source
+  float* Xs = reinterpret_cast<float*>(dr + N);           // [R][MS] IMPL: the last source;
+                                                          // WIN: X - W of `window - 1` steps ago
   const int tid = threadIdx.x;
   const int y0 = blockIdx.x * R, p0 = blockIdx.x * R;
   const size_t nn = (size_t)N * N;
@@ -426,6 +428,17 @@ __global__ void __launch_bounds__(NT, 512 / NT) k_transient_fast(TrArgs a) {
     // ---- column phase: this CTA's x-frequency columns p0 .. p0 + R - 1
     {
       float2 c[CELLS];   // all loads of a thread issued before the stores
+      // WIN: X - W of this CTA's modes from `window - 1` steps ago (rows p0 ..
+      // of the ring slot this step overwrites), loaded while the phase polls
+      constexpr int RG = WIN ? R * N / T : 1;
+      float rg[RG];
+      if constexpr (WIN) {
+        if (a.window >= 2) {
+          const float* src = a.ring + (size_t)(step % (a.window - 1)) * nn + (size_t)p0 * N;
+#pragma unroll
+          for (int u = 0; u < RG; ++u) rg[u] = __ldcg(src + tid + u * T);
+        }
+      }
       if constexpr (TAG) {
         // poll this thread's words until they carry phase ex, then (block
         // barrier: the previous phase's reads of buf are done) stage them
@@ -459,6 +472,15 @@ __global__ void __launch_bounds__(NT, 512 / NT) k_transient_fast(TrArgs a) {
         for (int q = 0; q < CELLS; ++q) c[q] = make_float2(tr_val(wa[q]), tr_val(wb[q]));
         __syncthreads();
         if (tag_abort) return;
+        if constexpr (WIN) {
+          if (a.window >= 2) {
+#pragma unroll
+            for (int u = 0; u < RG; ++u) {
+              const int i = tid + u * T;
+              Xs[(i >> lgN) * MS + (i & (N - 1))] = rg[u];
+            }
+          }
+        }
       } else {
 #pragma unroll
         for (int q = 0; q < CELLS; ++q) {
@@ -489,17 +511,21 @@ __global__ void __launch_bounds__(NT, 512 / NT) k_transient_fast(TrArgs a) {
           const float Ks = km[i] + am[i];         // K / N^2
           const int Rw = a.window - 1;
           if (Rw == 0) return Ks * x;
-          const size_t gi = (size_t)(p0 + c) * N + q;
-          auto slot = [&](int m) { return (size_t)(((m % Rw) + Rw) % Rw) * nn + gi; };
+          // the truncated sum as the untruncated one minus its value Rw steps
+          // back: with S_m = X_m - W_m (W the recursion of the untruncated
+          // response), sum_{j=1..Rw} rho^j (X_{n-j+1} - X_{n-j}) =
+          // S_n - rho^Rw S_{n-Rw}; the ring holds S of the last Rw steps per
+          // mode (zero before the first step), S_{n-Rw} in the slot S_n takes
+          // (loaded into Xs at the start of the phase, so that no load of a
+          // ring word is pending when it is overwritten)
           const float rho = rh[i];
-          float acc = 0.f, r = rho, prev = x;
-          for (int j = 1; j <= Rw; ++j) {
-            const float older = a.ring[slot(step - j)];
-            acc = fmaf(r, prev - older, acc);
-            prev = older;
-            r *= rho;
-          }
-          a.ring[slot(step)] = x;
+          const float w = fmaf(rho, W[i] - x, x);
+          W[i] = w;
+          float rp = rho;
+          for (int j = 1; j < Rw; ++j) rp *= rho;
+          const float s_now = x - w;
+          const float acc = fmaf(-rp, Xs[i], s_now);
+          __stcg(a.ring + (size_t)(step % Rw) * nn + (size_t)(p0 + c) * N + q, s_now);
           return fmaf(Ks, x, -am[i] * acc);
         } else if constexpr (IMPL) {
           // W stays at the last committed step; the step before this one is
@@ -739,8 +765,9 @@ __global__ void __launch_bounds__(NT, 512 / NT) k_transient_fast(TrArgs a) {
 template <int N, int R, int NT, bool IMPL, bool WIN = false>
 int launch_fast(const TrArgs& args, cudaStream_t s) {
   using S = TrShape<N, R, NT>;
-  // implicit leakage: one more [R][MS] array (the step's last source)
-  constexpr size_t smem = S::SMEM + (IMPL ? 4 * (size_t)R * S::MS : 0);
+  // implicit leakage or a window: one more [R][MS] array (the step's last
+  // source, or the window's X - W from `window - 1` steps ago)
+  constexpr size_t smem = S::SMEM + ((IMPL || WIN) ? 4 * (size_t)R * S::MS : 0);
   static_assert(smem <= 227 * 1024, "shared memory");
   VS_CUDA_TRY(cudaFuncSetAttribute((const void*)k_transient_fast<N, R, NT, IMPL, WIN>,
                                    cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
