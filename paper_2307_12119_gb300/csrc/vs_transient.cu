@@ -9,7 +9,9 @@
 //   - the recursion state W and the per-mode constants (K - A) / N^2, A / N^2
 //     and rho = exp(-dt / tau) of its R x N modes, in shared memory;
 //   - P_leak0 of its R rows, in registers (the thread <-> cell mapping of the
-//     update is the same every step); s is re-read through the L1 each step.
+//     update is the same every step); s of its rows in shared memory (with
+//     implicit leakage or a window that space holds other per-mode state, and
+//     s is re-read through the L1 each step).
 // Per step, two phases, each ending in an exchange through the spectral map in
 // global memory (x-frequency major):
 //   column phase: forward DCT along y of its columns, W <- rho W + (1 - rho) X,
@@ -262,13 +264,16 @@ __device__ __forceinline__ void tr_pass_p(float2* buf, int nfft, int stride, con
   tr_pass<N, Q::len(P), Q::radix(P), FWD>(buf, nfft, stride, ptw + Q::tw_off(P));
 }
 
-// Forward FFT (natural -> digit-reversed order), a block barrier after each pass.
-template <int N>
+// Forward FFT (natural -> digit-reversed order), a block barrier after each
+// pass; FIRST = 1 starts after pass 0 (run by the caller in registers).
+template <int N, int FIRST = 0>
 __device__ __forceinline__ void tr_fft_forward(float2* buf, int nfft, int stride, const float2* ptw) {
   constexpr int P = TrSched<N>::passes();
   static_assert(P >= 2 && P <= 3, "schedule");
-  tr_pass_p<N, 0, true>(buf, nfft, stride, ptw);
-  __syncthreads();
+  if constexpr (FIRST == 0) {
+    tr_pass_p<N, 0, true>(buf, nfft, stride, ptw);
+    __syncthreads();
+  }
   tr_pass_p<N, 1, true>(buf, nfft, stride, ptw);
   __syncthreads();
   if constexpr (P == 3) {
@@ -277,8 +282,9 @@ __device__ __forceinline__ void tr_fft_forward(float2* buf, int nfft, int stride
   }
 }
 
-// Inverse FFT (digit-reversed -> natural, unnormalised), passes undone in reverse.
-template <int N>
+// Inverse FFT (digit-reversed -> natural, unnormalised), passes undone in
+// reverse; LAST = 1 stops before pass 0 (left to the caller).
+template <int N, int LAST = 0>
 __device__ __forceinline__ void tr_fft_inverse(float2* buf, int nfft, int stride, const float2* ptw) {
   constexpr int P = TrSched<N>::passes();
   if constexpr (P == 3) {
@@ -287,8 +293,10 @@ __device__ __forceinline__ void tr_fft_inverse(float2* buf, int nfft, int stride
   }
   tr_pass_p<N, 1, false>(buf, nfft, stride, ptw);
   __syncthreads();
-  tr_pass_p<N, 0, false>(buf, nfft, stride, ptw);
-  __syncthreads();
+  if constexpr (LAST == 0) {
+    tr_pass_p<N, 0, false>(buf, nfft, stride, ptw);
+    __syncthreads();
+  }
 }
 
 // IMPL: implicit leakage (the leakage of step n at theta_n): each step
@@ -322,7 +330,11 @@ __global__ void __launch_bounds__(NT, 512 / NT) k_transient_fast(TrArgs a) {
   float2* ptw = tw + N;                                   // [TW] FFT pass twiddles
   int* dr = reinterpret_cast<int*>(ptw + TrSched<N>::TW); // [N] digit reversal
   float* Xs = reinterpret_cast<float*>(dr + N);           // [R][MS] IMPL: the last source;
-                                                          // WIN: X - W of `window - 1` steps ago
+                                                          // WIN: X - W of `window - 1` steps ago;
+                                                          // otherwise s of the CTA's rows
+  constexpr bool S_SMEM = !IMPL && !WIN;                  // s read from shared memory
+  // s of rows y0 + 2f (.x) and y0 + 2f + 1 (.y) at x, for the update
+  const float2* s2 = reinterpret_cast<const float2*>(Xs);
   const int tid = threadIdx.x;
   const int y0 = blockIdx.x * R, p0 = blockIdx.x * R;
   const size_t nn = (size_t)N * N;
@@ -356,11 +368,44 @@ __global__ void __launch_bounds__(NT, 512 / NT) k_transient_fast(TrArgs a) {
     rh[o] = __ldg(&a.trRho[g]);
     W[o] = 0.f;
   }
-  // this thread's cells: item j -> (f, x), rows y0 + 2f (.x) and y0 + 2f + 1 (.y)
+  // This thread's cells: item j -> (f, x), rows y0 + 2f (.x) and y0 + 2f + 1
+  // (.y). FUSE (lagged leakage, pass 0 of the schedule one butterfly per
+  // thread): the cells of this thread's pass-0 butterfly, the Makhoul
+  // positions jj + j M0 of FFT f, so that the row phase runs the inverse
+  // pass 0, the update and the forward pass 0 in registers; otherwise
+  // consecutive cells of a row.
+  constexpr int R0 = TrSched<N>::radix(0), M0 = N / R0;
+  constexpr bool FUSE = !IMPL && F * M0 == T && R0 == CELLS;
+  auto cell = [&](int j, int& f, int& x) {
+    if constexpr (FUSE) {
+      f = tid / M0;
+      const int p = tid % M0 + j * M0;
+      x = p < half ? 2 * p : 2 * (N - 1 - p) + 1;
+    } else {
+      const int it = tid + j * T;
+      f = it >> lgN;
+      x = it & (N - 1);
+    }
+  };
+  if constexpr (S_SMEM) {
+    // s is the same every step: its cells stay in shared memory, item j of
+    // thread t at j T + t
+    if (a.s) {
+      float2* sw = reinterpret_cast<float2*>(Xs);
+#pragma unroll
+      for (int j = 0; j < CELLS; ++j) {
+        int f, x;
+        cell(j, f, x);
+        const size_t g = (size_t)(y0 + 2 * f) * N + x;
+        sw[j * T + tid] = make_float2(__ldg(&a.s[g]), __ldg(&a.s[g + N]));
+      }
+    }
+  }
   float2 pl[CELLS], pd[CELLS];
 #pragma unroll
   for (int j = 0; j < CELLS; ++j) {
-    const int it = tid + j * T, f = it >> lgN, x = it & (N - 1);
+    int f, x;
+    cell(j, f, x);
     const size_t i0 = (size_t)(y0 + 2 * f) * N + x, i1 = i0 + N;
     pl[j] = make_float2(__ldg(&a.p_leak0[i0]), __ldg(&a.p_leak0[i1]));
     pd[j] = make_float2(__ldg(&a.p_dyn[i0]), __ldg(&a.p_dyn[i1]));
@@ -369,10 +414,14 @@ __global__ void __launch_bounds__(NT, 512 / NT) k_transient_fast(TrArgs a) {
   unsigned target = 0;    // arrivals that complete the next grid barrier
   unsigned ex = 0;        // TAG: phases completed so far (the tag of the data last written)
 
-  // forward DCT along x of the source in buf (Makhoul order), stored x-frequency major
-  auto row_forward = [&]() {
+  // forward DCT along x of the source in buf (Makhoul order), stored
+  // x-frequency major; from1: pass 0 is done (FUSE)
+  auto row_forward = [&](bool from1) {
     __syncthreads();
-    tr_fft_forward<N>(buf, F, NP, ptw);
+    if (from1)
+      tr_fft_forward<N, 1>(buf, F, NP, ptw);
+    else
+      tr_fft_forward<N, 0>(buf, F, NP, ptw);
     for (int it = tid; it < F * (half + 1); it += T) {
       const int f = it & (F - 1), k = it >> lgF, nk = N - k;
       const float2 zk = buf[f * NP + pad(dr[k])];
@@ -407,10 +456,11 @@ __global__ void __launch_bounds__(NT, 512 / NT) k_transient_fast(TrArgs a) {
   // step 0: the first source P_1 = P_dyn,1 + P_leak0 (theta_0 = 0)
 #pragma unroll
   for (int j = 0; j < CELLS; ++j) {
-    const int it = tid + j * T, f = it >> lgN, x = it & (N - 1);
+    int f, x;
+    cell(j, f, x);
     buf[f * NP + pad(makhoul_pos(x, N))] = make_float2(pd[j].x + pl[j].x, pd[j].y + pl[j].y);
   }
-  row_forward();
+  row_forward(false);
   if (!exchange()) return;
 
   // IMPL: the iterate of the current step, whether the previous step is still
@@ -578,7 +628,8 @@ __global__ void __launch_bounds__(NT, 512 / NT) k_transient_fast(TrArgs a) {
       const float* pdn = a.p_dyn + (size_t)step * nn;
 #pragma unroll
       for (int j = 0; j < CELLS; ++j) {
-        const int it = tid + j * T, f = it >> lgN, x = it & (N - 1);
+        int f, x;
+        cell(j, f, x);
         const size_t i0 = (size_t)(y0 + 2 * f) * N + x;
         pd[j] = make_float2(__ldg(&pdn[i0]), __ldg(&pdn[i0 + N]));
       }
@@ -649,16 +700,67 @@ __global__ void __launch_bounds__(NT, 512 / NT) k_transient_fast(TrArgs a) {
       }
     }
     __syncthreads();
-    tr_fft_inverse<N>(buf, F, NP, ptw);
     float* th_out = a.theta + (size_t)(step - 1) * nn;
     float resid = 0.f;
+    if constexpr (FUSE) {
+      tr_fft_inverse<N, 1>(buf, F, NP, ptw);
+      // this thread's pass-0 butterfly: inverse, the update of its cells, and
+      // (unless this was the last step) the forward butterfly of the next
+      // source, in registers and in place
+      const int jj = tid % M0;
+      float2* base = buf + (tid / M0) * NP;
+      float2 v[R0];
+#pragma unroll
+      for (int r = 0; r < R0; ++r) v[r] = base[pad(jj + r * M0)];
+#pragma unroll
+      for (int r = 1; r < R0; ++r) v[r] = cmulc(v[r], ptw[(r - 1) * M0 + jj]);
+      dftR<R0, false>(v);
+#pragma unroll
+      for (int j = 0; j < CELLS; ++j) {
+        int f, x;
+        cell(j, f, x);
+        const size_t i0 = (size_t)(y0 + 2 * f) * N + x;
+        const float2 u = v[j];
+        const float2 sk = !a.s ? make_float2(1.f, 1.f)
+                          : S_SMEM ? s2[j * T + tid]
+                                   : make_float2(__ldg(&a.s[i0]), __ldg(&a.s[i0 + N]));
+        float th[2], q[2];
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+          const float uu = h ? u.y : u.x, S = h ? sk.y : sk.x;
+          const float den = fmaf(-alpha * S, uu, 1.f);
+          if (!(den > 0.05f)) flags |= kFlagRunaway;
+          th[h] = S * uu / den;
+          if (!isfinite(th[h])) flags |= kFlagNonfinite;
+          const float L0 = h ? pl[j].y : pl[j].x, D = h ? pd[j].y : pd[j].x;
+          q[h] = D + L0 * fmaf(beta, th[h], 1.f);
+        }
+        th_out[i0] = th[0];
+        th_out[i0 + N] = th[1];
+        v[j] = make_float2(q[0], q[1]);
+      }
+      if (!more) break;
+      dftR<R0, true>(v);
+#pragma unroll
+      for (int r = 1; r < R0; ++r) v[r] = cmul(v[r], ptw[(r - 1) * M0 + jj]);
+#pragma unroll
+      for (int r = 0; r < R0; ++r) base[pad(jj + r * M0)] = v[r];
+      row_forward(true);
+      if (!exchange()) return;
+      ++step;
+      continue;
+    }
+    tr_fft_inverse<N>(buf, F, NP, ptw);
 #pragma unroll
     for (int j = 0; j < CELLS; ++j) {
-      const int it = tid + j * T, f = it >> lgN, x = it & (N - 1);
+      int f, x;
+      cell(j, f, x);
       const int pos = f * NP + pad(makhoul_pos(x, N));
       const size_t i0 = (size_t)(y0 + 2 * f) * N + x;
       const float2 u = buf[pos];
-      const float2 sk = a.s ? make_float2(__ldg(&a.s[i0]), __ldg(&a.s[i0 + N])) : make_float2(1.f, 1.f);
+      const float2 sk = !a.s ? make_float2(1.f, 1.f)
+                        : S_SMEM ? s2[j * T + tid]
+                                 : make_float2(__ldg(&a.s[i0]), __ldg(&a.s[i0 + N]));
       float th[2], q[2];
 #pragma unroll
       for (int h = 0; h < 2; ++h) {
@@ -683,7 +785,7 @@ __global__ void __launch_bounds__(NT, 512 / NT) k_transient_fast(TrArgs a) {
     }
     if constexpr (!IMPL) {
       if (!more) break;
-      row_forward();
+      row_forward(false);
       if (!exchange()) return;
       ++step;
     } else {
@@ -728,19 +830,21 @@ __global__ void __launch_bounds__(NT, 512 / NT) k_transient_fast(TrArgs a) {
         const float* pdn = a.p_dyn + (size_t)step * nn;
 #pragma unroll
         for (int j = 0; j < CELLS; ++j) {
-          const int it = tid + j * T, f = it >> lgN, x = it & (N - 1);
+          int f, x;
+          cell(j, f, x);
           const size_t i0 = (size_t)(y0 + 2 * f) * N + x;
           pd[j] = make_float2(__ldg(&pdn[i0]), __ldg(&pdn[i0 + N]));
         }
       }
 #pragma unroll
       for (int j = 0; j < CELLS; ++j) {
-        const int it = tid + j * T, f = it >> lgN, x = it & (N - 1);
+        int f, x;
+        cell(j, f, x);
         const float2 th = thp[IMPL ? j : 0];
         buf[f * NP + pad(makhoul_pos(x, N))] =
             make_float2(pd[j].x + pl[j].x * fmaf(beta, th.x, 1.f), pd[j].y + pl[j].y * fmaf(beta, th.y, 1.f));
       }
-      row_forward();
+      row_forward(false);
       if (!tr_barrier(a.ctrl, target, abort_sm)) return;
       if (done) {
         ++step;
@@ -765,9 +869,9 @@ __global__ void __launch_bounds__(NT, 512 / NT) k_transient_fast(TrArgs a) {
 template <int N, int R, int NT, bool IMPL, bool WIN = false>
 int launch_fast(const TrArgs& args, cudaStream_t s) {
   using S = TrShape<N, R, NT>;
-  // implicit leakage or a window: one more [R][MS] array (the step's last
-  // source, or the window's X - W from `window - 1` steps ago)
-  constexpr size_t smem = S::SMEM + ((IMPL || WIN) ? 4 * (size_t)R * S::MS : 0);
+  // one more [R][MS] array: the step's last source (implicit leakage), the
+  // window's X - W from `window - 1` steps ago, or s of the CTA's rows
+  constexpr size_t smem = S::SMEM + 4 * (size_t)R * S::MS;
   static_assert(smem <= 227 * 1024, "shared memory");
   VS_CUDA_TRY(cudaFuncSetAttribute((const void*)k_transient_fast<N, R, NT, IMPL, WIN>,
                                    cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
