@@ -12,8 +12,9 @@ from oracle import solve as so
 def test_closed_form_error_on_the_64_configuration_is_within_the_papers_bound():
     # Sec. V: about 2 % mean and at most 4 % of the maximum rise against the
     # reference simulator. Against the exact fixed point on the 64^2 stand-in
-    # for the paper's test chips, the one-shot form (R28 reading) stays below
-    # 4 % of each map's rise, and dropping its random part is closer still.
+    # for the paper's test chips, the one-shot form (Eqs. 21, 25, 26, the
+    # random part to first order) stays below 4 % of each map's rise, and
+    # dropping its random part is closer still.
     w = synth.workload("c1_64")
     pd, pl, s = synth.steady_inputs(w, 3, dtype=torch.float64)
     st, phy = w.stack, w.physics
