@@ -225,3 +225,19 @@ def test_persistent_engine_window_at_256_against_the_oracle(window):
     ref, _ = _oracle_variant(w, trace, pl, s, dt, window, False)
     emax, rel = errors(th, ref)
     assert emax <= 5e-3 and rel <= 2e-4
+
+
+@pytest.mark.parametrize("config,steps", [("c3_512", 10), ("c4_1024", 8)])
+def test_persistent_engine_window_at_512_and_1024_against_the_oracle(config, steps):
+    """The paper's 5-step window on the persistent engine at 512^2 and at the
+    bench's 1024^2 (where the row phase runs pass 0 in registers): the ring of
+    the last four differences wraps at least once, element by element against
+    the oracle's windowed sum."""
+    vs = _vs()
+    dt = 1e-3
+    vs_, w, k, trace, pl, s = _tr_case(steps, dt, config)
+    th, info = vs.solve_transient(k, trace, pl, s, vs_params(w), window=5)
+    assert info["status"] == vs.VS_OK and info["iterations"] == steps
+    ref, _ = _oracle_variant(w, trace, pl, s, dt, 5, False)
+    emax, rel = errors(th, ref)
+    assert emax <= 5e-3 and rel <= 2e-4
