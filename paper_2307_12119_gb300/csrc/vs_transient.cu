@@ -750,6 +750,8 @@ __global__ void __launch_bounds__(NT, 512 / NT) k_transient_fast(TrArgs a) {
       ++step;
       continue;
     }
+    // not FUSE (the other grids, implicit leakage): the whole inverse
+    // transform through shared memory, then the update from there
     tr_fft_inverse<N>(buf, F, NP, ptw);
 #pragma unroll
     for (int j = 0; j < CELLS; ++j) {
