@@ -834,11 +834,12 @@ def run_ours(a):
         prm_t = vs.SolveParams(wt.physics.beta_per_K, wt.physics.alpha_per_K, 1e-4, 50)
         out_t = torch.empty_like(trace)
 
-        def run_transient(out, **opts):
-            vs.solve_transient(kt, trace[:4].contiguous(), pl_t[0], s_t[0], prm_t, **opts)  # warm-up
+        def run_transient(out, prm=None, **opts):
+            prm = prm or prm_t
+            vs.solve_transient(kt, trace[:4].contiguous(), pl_t[0], s_t[0], prm, **opts)  # warm-up
             torch.cuda.synchronize()
             t0 = time.perf_counter()
-            _, info = vs.solve_transient(kt, trace, pl_t[0], s_t[0], prm_t, out, **opts)
+            _, info = vs.solve_transient(kt, trace, pl_t[0], s_t[0], prm, out, **opts)
             torch.cuda.synchronize()
             return time.perf_counter() - t0, info
 
@@ -859,15 +860,20 @@ def run_ours(a):
                          "note": "8 B/pixel per step algorithmic (read P_dyn,n, write theta_n); "
                                  "traffic per launch from the committed per-step capture"}}
         # Sec. IV-E variants on the same trace: the paper's 5-step window, and the
-        # leakage of each step taken at its own temperature (per-step fixed point)
+        # leakage of each step taken at its own temperature (per-step fixed point,
+        # stopped on the update or on its error estimate)
         rise = float(out_t.abs().max())
         variants_t = {}
-        for name, opts, against in (
-                ("window5_lagged", {"window": 5}, "untruncated, lagged leakage"),
-                ("untruncated_implicit", {"leakage": vs.VS_LEAK_IMPLICIT},
+        prm_est = vs.SolveParams(wt.physics.beta_per_K, wt.physics.alpha_per_K, 1e-4, 50,
+                                 stop_rule=vs.VS_STOP_ESTIMATE)
+        for name, prm_v, opts, against in (
+                ("window5_lagged", None, {"window": 5}, "untruncated, lagged leakage"),
+                ("untruncated_implicit", None, {"leakage": vs.VS_LEAK_IMPLICIT},
+                 "untruncated, lagged leakage"),
+                ("untruncated_implicit_estimate", prm_est, {"leakage": vs.VS_LEAK_IMPLICIT},
                  "untruncated, lagged leakage")):
             out_v = torch.empty_like(trace)
-            dt_v, info_v = run_transient(out_v, **opts)
+            dt_v, info_v = run_transient(out_v, prm_v, **opts)
             dev_v = float((out_v - out_t).abs().max())
             dev_late = float((out_v[steps_t // 2:] - out_t[steps_t // 2:]).abs().max())
             variants_t[name] = {"ms_per_step": 1e3 * dt_v / steps_t, "status": info_v["status"],

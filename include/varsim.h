@@ -201,8 +201,9 @@ typedef struct {
  * tensor-core engines, the transient and vs_solve_steady_noalloc return
  * VS_ERR_INVALID_ARG for it.
  *   stop_rule  : VS_STOP_UPDATE (0, what a zero-initialised struct selects) or
- *                VS_STOP_ESTIMATE, on every steady engine; the transient
- *                solves return VS_ERR_INVALID_ARG for VS_STOP_ESTIMATE. */
+ *                VS_STOP_ESTIMATE, on every steady engine and for the per-step
+ *                fixed point of a transient with implicit leakage (a lagged
+ *                transient has no fixed point and ignores it). */
 typedef struct {
   double beta_per_K;
   double alpha_per_K;
@@ -479,7 +480,8 @@ typedef struct {
  * the persistent launch: (2 + max(0, window - 1)) * n * n floats. info_host:
  * lagged, iterations = steps; implicit, iterations = fixed-point iterations
  * summed over the steps, residual_K = the largest final change of a step, and
- * status VS_ERR_NO_CONVERGENCE if a step ended above tol_K. */
+ * status VS_ERR_NO_CONVERGENCE if a step reached max_iter without meeting the
+ * stopping rule (stop_rule of vs_solve_params). */
 int vs_solve_transient_ex(vs_kernel k, int n_steps, const float* p_dyn_trace,
                           const float* p_leak0, const float* s_kappa,
                           const vs_solve_params* params, const vs_transient_opts* opts,

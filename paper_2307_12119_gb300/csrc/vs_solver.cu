@@ -767,10 +767,11 @@ __device__ __forceinline__ bool transient_lagged(const PlanDev& P, float2* smem)
 }
 
 // Implicit leakage: P_n = P_dyn,n + P_leak0 (1 + beta theta_n); every step
-// iterates theta <- phi(u_n(P_n(theta))) from theta_{n-1} until the change is
-// <= tol or max_iter iterations. The history takes the source of the last
-// iteration. Every block reads the same residual word after the barrier, so
-// all take the same decision. The plan holds one map.
+// iterates theta <- phi(u_n(P_n(theta))) from theta_{n-1} until the stopping
+// rule holds (the change <= tol, or its error estimate from the step's last
+// two changes) or max_iter iterations. The history takes the source of the
+// last iteration. Every block reads the same residual word after the
+// barrier, so all take the same decision. The plan holds one map.
 __device__ __noinline__ bool transient_implicit(const PlanDev& P, float2* smem) {
   unsigned* slot = P.ctrl->active;          // two residual words, used alternately
   MapState* ms = P.st;
@@ -778,6 +779,7 @@ __device__ __noinline__ bool transient_implicit(const PlanDev& P, float2* smem) 
   if (!grid_barrier(P.ctrl)) return false;
   int g = 0;
   for (int s = 0; s < P.n_steps; ++s) {
+    float prev_r = INFINITY;   // the step's previous change (the same in every block)
     for (int it = 1; it <= P.max_iter; ++it) {
       const int cur = g & 1;
       ++g;
@@ -789,7 +791,9 @@ __device__ __noinline__ bool transient_implicit(const PlanDev& P, float2* smem) 
       if (!grid_barrier(P.ctrl)) return false;
       const float r = __uint_as_float(ld_acquire(slot + cur));
       const bool bad = ld_acquire(reinterpret_cast<const unsigned*>(&ms->flags)) & kFlagNonfinite;
-      const bool done = r <= P.tol || it == P.max_iter || bad;
+      const bool conv = converged(r, prev_r, it, P.tol, P.stop_rule);
+      const bool done = conv || it == P.max_iter || bad;
+      prev_r = r;
       if (blockIdx.x == 0 && threadIdx.x == 0) {
         // every block read the other word one iteration ago, before this
         // iteration's barriers
@@ -797,7 +801,7 @@ __device__ __noinline__ bool transient_implicit(const PlanDev& P, float2* smem) 
         if (done) {
           ms->iters += it;
           ms->prev_resid = fmaxf(ms->prev_resid, r);
-          if (r > P.tol) ms->growth = 1;     // a step ended unconverged
+          if (!conv) ms->growth = 1;         // a step ended unconverged
         }
       }
       if (done && s == P.n_steps - 1) break;
@@ -2205,8 +2209,6 @@ extern "C" int vs_solve_transient_ex(vs_kernel k, int n_steps, const float* p_dy
   if (rc) return rc;
   if (vs_params_physics(params))
     return vs_set_error(VS_ERR_INVALID_ARG, "the transient runs the linear models only");
-  if (params->stop_rule != VS_STOP_UPDATE)
-    return vs_set_error(VS_ERR_INVALID_ARG, "the transient takes the update stopping rule only");
   const vs_transient_opts o = opts ? *opts : vs_transient_opts{0, VS_LEAK_LAGGED};
   if (o.window < 0 || o.window > VS_MAX_WINDOW)
     return vs_set_error(VS_ERR_INVALID_ARG, "window %d not in 0..%d", o.window, VS_MAX_WINDOW);

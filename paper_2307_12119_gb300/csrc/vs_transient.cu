@@ -82,6 +82,7 @@ struct TrArgs {
   float beta, alpha;
   float tol;               // implicit leakage: per-step fixed point
   int max_iter;
+  int stop_rule;           // VS_STOP_* of that fixed point
   int window;              // WIN: step responses settled from age `window` on (>= 1)
   float* ring;             // WIN, window >= 2: [window - 1][N][N] X - W of the last steps per mode
 };
@@ -300,8 +301,9 @@ __device__ __forceinline__ void tr_fft_inverse(float2* buf, int nfft, int stride
 }
 
 // IMPL: implicit leakage (the leakage of step n at theta_n): each step
-// iterates the column and row phases from theta_{n-1} until the largest
-// change is <= tol (or max_iter), the recursion state W committed with the
+// iterates the column and row phases from theta_{n-1} until the stopping rule
+// holds on the largest change (<= tol, or its error estimate from the step's
+// last two changes) or max_iter, the recursion state W committed with the
 // source of the step's last iterate; the decision of an iterate is read by
 // every CTA from the same word after a grid barrier.
 // WIN: the window of Sec. IV-E with lagged leakage: step responses older than
@@ -468,6 +470,7 @@ __global__ void __launch_bounds__(NT, 512 / NT) k_transient_fast(TrArgs a) {
   // (theta_{n-1} at the first iterate) and the iterate count of the launch
   int iter = 1, g = 0;
   bool commit = false;
+  float prev_r = INFINITY;   // IMPL: the previous change of the current step
   float2 thp[IMPL ? CELLS : 1];
 #pragma unroll
   for (int j = 0; j < (IMPL ? CELLS : 1); ++j) thp[j] = make_float2(0.f, 0.f);
@@ -816,14 +819,16 @@ __global__ void __launch_bounds__(NT, 512 / NT) k_transient_fast(TrArgs a) {
       }
       __syncthreads();
       const float r = dec_r;
-      const bool done = r <= a.tol || iter >= a.max_iter || (dec_f & kFlagNonfinite);
+      const bool conv = vsk::converged(r, prev_r, iter, a.tol, a.stop_rule);
+      const bool done = conv || iter >= a.max_iter || (dec_f & kFlagNonfinite);
+      prev_r = done ? INFINITY : r;
       if (blockIdx.x == 0 && tid == 0) {
         // every CTA read the other word one iterate ago, before this iterate's barriers
         a.ctrl->resid[cur ^ 1] = 0u;
         if (done) {
           a.ctrl->iters += iter;
           a.ctrl->max_resid = fmaxf(a.ctrl->max_resid, r);
-          if (r > a.tol) a.ctrl->growth = 1;
+          if (!conv) a.ctrl->growth = 1;
         }
       }
       if (done && step == a.n_steps) break;
@@ -942,6 +947,7 @@ int vs_transient_fast(vs_kernel k, int n_steps, const float* p_dyn_trace, const 
   a.alpha = (float)params->alpha_per_K;
   a.tol = (float)params->tol_K;
   a.max_iter = params->max_iter;
+  a.stop_rule = params->stop_rule;
   a.window = window;
   a.ring = ring_maps ? work + 2 * nn : nullptr;
   int rc = VS_OK;

@@ -111,6 +111,11 @@ def test_stopping_rule_arguments():
     assert e.value.status == vs.VS_ERR_INVALID_ARG
     kt = vs.Kernel(vs_stack(w), vs.Grid(w.n, w.die_m), vs.KernelOpts(dt_s=1e-3))
     trace = torch.zeros(3, 64, 64, device="cuda")
+    # the transient takes either rule (it applies to the implicit per-step fixed point)
+    for leakage in (vs.VS_LEAK_LAGGED, vs.VS_LEAK_IMPLICIT):
+        th, info = vs.solve_transient(kt, trace, z[0], None,
+                                      vs_params(w, stop_rule=vs.VS_STOP_ESTIMATE), leakage=leakage)
+        assert info["status"] == vs.VS_OK and float(th.abs().max()) == 0.0
     with pytest.raises(vs.VarsimError) as e:
-        vs.solve_transient(kt, trace, z[0], None, vs_params(w, stop_rule=vs.VS_STOP_ESTIMATE))
+        vs.solve_transient(kt, trace, z[0], None, vs_params(w, stop_rule=7))
     assert e.value.status == vs.VS_ERR_INVALID_ARG

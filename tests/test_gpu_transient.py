@@ -241,3 +241,28 @@ def test_persistent_engine_window_at_512_and_1024_against_the_oracle(config, ste
     ref, _ = _oracle_variant(w, trace, pl, s, dt, 5, False)
     emax, rel = errors(th, ref)
     assert emax <= 5e-3 and rel <= 2e-4
+
+
+@pytest.mark.parametrize("config,steps", [("c1_64", 12), ("c2_256", 10)])
+def test_implicit_leakage_with_the_error_estimate_stop(config, steps):
+    """The per-step fixed point of implicit leakage stopped by the error
+    estimate (64^2 on the general engine, 256^2 on the persistent one): every
+    step within the bar of the oracle's implicit superposition iterated to
+    1e-10 K, element by element, in no more iterations than the update rule
+    takes at the same tolerance."""
+    vs = _vs()
+    dt = 1e-3
+    vs_, w, k, trace, pl, s = _tr_case(steps, dt, config)
+    est = vs_params(w, tol_K=1e-4, stop_rule=vs.VS_STOP_ESTIMATE)
+    th, info = vs.solve_transient(k, trace, pl, s, est, leakage=vs.VS_LEAK_IMPLICIT)
+    assert info["status"] == vs.VS_OK
+    upd, info_u = vs.solve_transient(k, trace, pl, s, vs_params(w, tol_K=1e-4),
+                                     leakage=vs.VS_LEAK_IMPLICIT)
+    assert info_u["status"] == vs.VS_OK
+    assert steps <= info["iterations"] <= info_u["iterations"]
+    ref, _ = _oracle_variant(w, trace, pl, s, dt, 0, True)
+    emax, rel = errors(th, ref)
+    print("%s implicit: %d iterations with the estimate, %d with the update rule, "
+          "max |dT| %.2e K" % (config, info["iterations"], info_u["iterations"], emax))
+    assert emax <= 5e-3 and rel <= 2e-4
+    assert float((th - upd).abs().max()) <= 1e-3
